@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Throughput of the SPGM hot path (A_B s, A_B^H r, gradient step, prox) on one GB300.
+
+Workload: mid-size synthetic scene, 16 TX + 16 RX boundary array on a 0.3 m
+aperture (256 pairs), 64 equally spaced frequencies 70-80 GHz (M = 16384),
+64 x 64 x 32 voxels (N = 131072), minibatches of 16 pairs x 64 frequencies.
+One step = one SPGM epoch = 16 minibatch iterations, each a forward A_B s with
+the residual, an adjoint A_B^H r fused with the gradient step and the prox.
+
+Metric: (measurement row, voxel) element pairs processed per second by the
+forward and the adjoint, in units of 1e9: each epoch touches
+2 * M * N = 4.29e9 pairs.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (its own scene) and rank
+0 prints one JSON line with the whole-job throughput.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G (meas,voxel) pairs/s for A_B s + A_B^H r; SPGM time to oracle NMSE"
+UNIT = "G pairs/s"
+FLOPS_PER_PAIR = 8.0            # one complex multiply-accumulate
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="bound on the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.samples = []
+        self.proc = None
+        self.marks = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), line.strip()))
+
+    def mark(self):
+        self.marks.append(time.perf_counter())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, line in self.samples:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((t, float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        t0, t1 = (self.marks[0], self.marks[-1]) if len(self.marks) >= 2 else (rows[0][0], rows[-1][0])
+        inside = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+# ---------------------------------------------------------------------------
+def build_problem(torch, ctx, w, seed_offset):
+    """Scene, noisy measurements y = A s + w (GPU forward), step 1/L and lambda (GPU)."""
+    import numpy as np
+    from paper_2509_00774_gb300 import inputs as I
+    geom = w.geom
+    ctx.set_geometry(geom)
+    dev = torch.device("cuda", ctx.device)
+    s_true = torch.from_numpy(w.scene_vector().astype(np.complex64)).to(dev)
+    all_pairs = torch.arange(geom.P, dtype=torch.int32, device=dev)
+    clean = ctx.forward(all_pairs, s_true)
+    g = torch.from_numpy(I.complex_gaussian(geom.M, w.seeds["noise"] + seed_offset).astype(np.complex64)).to(dev)
+    sigma = float(torch.sqrt(torch.mean(clean.abs() ** 2) / 10 ** (w.snr_db / 10)))
+    y = clean + sigma * g
+    v0 = torch.from_numpy(I.complex_gaussian(geom.N, w.seeds["power"]).astype(np.complex64)).to(dev)
+    L = ctx.power_iteration(v0, 50)
+    lam = 0.05 * ctx.lambda_max(y)
+    return y, 1.0 / L, lam
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("sources_sha256") != sources_digest():
+        return None
+    return d.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch_full")
+
+
+def sources_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2509_00774_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def cpu_baseline(w, y_np, eta, lam, seconds):
+    """Time the FP64 oracle on SPGM minibatch steps of the same workload (bounded sample)."""
+    import numpy as np
+    import oracle
+    from paper_2509_00774_gb300 import inputs as I
+    oracle.build()
+    o = oracle.Oracle(w.geom)
+    cores = oracle.get_threads()
+    perm = I.epoch_permutation(w.geom.P, w.seeds["perm"], 0)
+    bp = w.pairs_per_batch
+    s = np.zeros(w.geom.N, dtype=np.complex128)
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        c = done % (w.geom.P // bp)
+        s = o.spgm_step(y_np, s, perm[c * bp:(c + 1) * bp], eta, lam)
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    pairs = done * 2.0 * bp * w.geom.K * w.geom.N
+    return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} SPGM minibatch step(s) of the workload ({bp} pairs x {w.geom.K} freqs x "
+                      f"{w.geom.N} voxels, forward + adjoint + prox) in FP64 on {cores} host threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle on the same workload, one minibatch step per step."""
+    import numpy as np
+    import oracle
+    from paper_2509_00774_gb300 import inputs as I
+    from paper_2509_00774_gb300 import workloads as W
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = W.mid_T16R16_K64_64x64x32()
+    oracle.build()
+    o = oracle.Oracle(w.geom)
+    y = I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db)
+    eta, lam = 1.0 / 70.0, 0.05 * 1e-3
+    perm = I.epoch_permutation(o.P, w.seeds["perm"], 0)
+    bp = w.pairs_per_batch
+    s = np.zeros(o.N, dtype=np.complex128)
+    n_chunks = o.P // bp
+    for i in range(args.warmup):
+        s = o.spgm_step(y, s, perm[(i % n_chunks) * bp:(i % n_chunks + 1) * bp], eta, lam)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        c = (args.warmup + i) % n_chunks
+        s = o.spgm_step(y, s, perm[c * bp:(c + 1) * bp], eta, lam)
+    dt = time.perf_counter() - t0
+    per_step = 2.0 * bp * o.K * o.N
+    value = per_step * args.steps / dt / 1e9
+    cores = oracle.get_threads()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "pairs_per_batch": bp, "step": "one SPGM minibatch step (16 pairs x 64 freqs)"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} SPGM minibatch steps on {cores} host threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2509_00774_gb300 import build as nb
+    from paper_2509_00774_gb300 import inputs as I
+    from paper_2509_00774_gb300 import workloads as W
+    from paper_2509_00774_gb300.nfmimo import Context
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    nb.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    w = W.mid_T16R16_K64_64x64x32()
+    geom = w.geom
+    with torch.cuda.stream(stream):
+        ctx = Context(local, stream=stream)
+        y, eta, lam = build_problem(torch, ctx, w, seed_offset=rank)
+        E = args.warmup + args.steps
+        perms = np.stack([I.epoch_permutation(geom.P, w.seeds["perm"] + 1000 * rank, e) for e in range(E)])
+        perms_d = torch.from_numpy(perms.astype(np.int32)).to(dev)
+        s = torch.zeros(geom.N, dtype=torch.complex64, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        bp = w.pairs_per_batch
+        for e in range(args.warmup):
+            ctx.spgm_epoch(y, s, perms_d[e], bp, eta, lam)
+        torch.cuda.synchronize()
+        props = torch.cuda.get_device_properties(dev)
+        uuid = str(getattr(props, "uuid", "") or "")
+        sampler = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else uuid)
+        sampler.start()
+        time.sleep(0.3)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ctx.profile_enable(True)
+        ctx.profile_report()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler.mark()
+        for k in range(args.steps):
+            flush.fill_(float(k))                  # L2 flush, outside the timed events
+            starts[k].record(stream)
+            ctx.spgm_epoch(y, s, perms_d[args.warmup + k], bp, eta, lam)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        sampler.mark()
+        prof = ctx.profile_report()
+        ctx.profile_enable(False)
+        time.sleep(0.25)
+        sampler.stop()
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        total_ms = float(sum(step_ms))
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        pairs_per_step = 2.0 * geom.M * geom.N
+        value = pairs_per_step * args.steps * world / (total_ms * 1e-3) / 1e9
+
+        # end to end through the host-buffer entry point (copies inside the timed region)
+        y_host = torch.empty(geom.M, dtype=torch.complex64, pin_memory=True)
+        y_host.copy_(y)
+        s_host = torch.zeros(geom.N, dtype=torch.complex64, pin_memory=True)
+        perms_host = torch.from_numpy(perms.astype(np.int32)).pin_memory()
+        for e in range(min(args.warmup, 2)):
+            ctx.spgm_epochs_host(y_host, s_host, perms_host[e:e + 1], bp, eta, lam)
+        e2e_steps = max(1, min(args.steps, 50))
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            ctx.spgm_epochs_host(y_host, s_host, perms_host[k % E:k % E + 1], bp, eta, lam)
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e_value = pairs_per_step * e2e_steps * world / e2e_s / 1e9
+        h2d = geom.M * 8 + geom.N * 8 + geom.P * 4
+        d2h = geom.N * 8
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peaks, peak_src = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    kernels = {}
+    elems = bp * geom.K * geom.N        # (row, voxel) pairs per forward / adjoint launch
+    for kind, (ms, n) in prof.items():
+        if n == 0:
+            continue
+        avg_ms = ms / n
+        entry = {"launches": n, "total_ms": ms, "avg_us": avg_ms * 1e3}
+        if kind in ("forward_partial", "adjoint"):
+            tf = FLOPS_PER_PAIR * elems / (avg_ms * 1e-3) / 1e12
+            entry.update({"gpairs_per_s": elems / (avg_ms * 1e-3) / 1e9, "tflops_cmac": tf})
+        kernels[kind] = entry
+    dom = max(("forward_partial", "adjoint"), key=lambda k: kernels.get(k, {}).get("total_ms", 0.0))
+    dk = kernels[dom]
+    kname = {"forward_partial": "fwd_partial_kernel", "adjoint": "adj_kernel"}[dom]
+    roofline = {"bound": "alu", "kernel": kname, "achieved": dk["tflops_cmac"], "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": dk["tflops_cmac"] / fp32_peak_tflops,
+                "traffic": traffic_for(kname),
+                "peak_source": f"FP32 FMA lanes: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} x 2 flops x "
+                               f"{sm_mhz:.0f} MHz (sm_max_mhz, {peak_src})",
+                "work": f"{FLOPS_PER_PAIR:.0f} flops (one complex MAC) per (row, voxel) pair, {elems} pairs per launch"}
+    launches = sum(kernels.get(k, {}).get("launches", 0) for k in ("forward_partial", "forward_reduce", "adjoint"))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "T": geom.T, "R": geom.R, "K": geom.K, "N": geom.N, "M": geom.M,
+                   "pairs_per_batch": bp, "minibatches_per_step": geom.P // bp, "step": "one SPGM epoch",
+                   "operator": "fp32 cuda-core (phasor recurrence forward, Horner adjoint)",
+                   "l2": "256 MiB buffer written between timed steps, outside the timed events",
+                   "eta": eta, "lambda": lam, "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps, "api": "nfm_spgm_epochs_host (pinned host buffers)"},
+        "clocks": sampler.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, y.cpu().numpy().astype(np.complex128), eta, lam, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

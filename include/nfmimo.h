@@ -1,0 +1,155 @@
+/*
+ * nfmimo — GB300 (sm_103a) library for regularised 3D near-field MIMO imaging
+ * with the stochastic proximal gradient method (SPGM).
+ *
+ * Paper: O. Oral, "Fast Regularized 3D Near-Field MIMO Imaging Using
+ * Stochastic Proximal Gradient Method", arXiv 2509.00774.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex vectors are complex64, interleaved (re, im) float pairs.
+ *  - Measurement row m = pair * K + k with pair = t * R + r (TX t, RX r,
+ *    frequency k).  A minibatch is a list of pair indices; its rows are the
+ *    listed pairs in list order, each with all K frequencies.
+ *  - Voxel n = (iz * ny + iy) * nx + ix on the regular grid of nfm_grid.
+ *  - Unless an entry point says otherwise, vector pointers are DEVICE pointers
+ *    on the context's device, owned by the caller, and the call only enqueues
+ *    work on the context's stream (asynchronous).  Pointers must be 8-byte
+ *    aligned (complex) or 4-byte aligned (int).
+ *  - Return value: NFM_OK (0) or a negative nfm_status.  On error no work has
+ *    been enqueued, and nfm_last_error() describes the failure.
+ *  - Kernels that meet an out-of-range pair index skip it and raise a device
+ *    flag; the next synchronising call (nfm_synchronize, nfm_power_iteration,
+ *    nfm_objective, nfm_spgm_epoch_host) returns NFM_ERR_ARG and clears it.
+ *  - One context must not be used from two host threads at the same time.
+ */
+#ifndef NFMIMO_H
+#define NFMIMO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nfm_ctx nfm_ctx;
+
+typedef enum {
+    NFM_OK = 0,
+    NFM_ERR_ARG = -1,      /* invalid argument or geometry */
+    NFM_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    NFM_ERR_NOMEM = -3,    /* device allocation failed */
+    NFM_ERR_STATE = -4,    /* call order (e.g. no geometry set) */
+    NFM_ERR_TIMEOUT = -5,  /* a bounded device wait gave up */
+    NFM_ERR_NUMERIC = -6   /* non-finite result */
+} nfm_status;
+
+/* Regular voxel grid r_n = (x0 + ix dx, y0 + iy dy, z0 + iz dz) in metres. */
+typedef struct {
+    double x0, y0, z0;
+    double dx, dy, dz;
+    int nx, ny, nz;
+} nfm_grid;
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream stays owned
+ * by the caller.  *out receives the context (library-owned). */
+int nfm_create(nfm_ctx** out, int device, void* cuda_stream);
+
+/* Free the context and all device memory it owns.  NULL is ignored. */
+void nfm_destroy(nfm_ctx* ctx);
+
+/* Human-readable description of the last error on this context (or of the
+ * last failed nfm_create when ctx is NULL).  Library-owned string. */
+const char* nfm_last_error(const nfm_ctx* ctx);
+
+/* Replace the stream later calls enqueue on (caller-owned). */
+int nfm_set_stream(nfm_ctx* ctx, void* cuda_stream);
+
+/* Geometry of the observation model (Sec. II, Eq. 1-2).
+ *   tx_xyz [T][3], rx_xyz [R][3]: HOST FP64 antenna positions (the paper puts
+ *     them on z = 0; any z is accepted).
+ *   freq_hz [K]: HOST FP64 frequencies; they must be equally spaced (the
+ *     operator advances the phase by a fixed step per frequency).  1 <= K <= 128.
+ *   pulse_re_im [K][2]: HOST complex p(f_k), or NULL for p = 1.
+ *   grid: the voxel grid (HOST struct).  N = nx ny nz < 2^31.
+ *   c: propagation speed (m/s), > 0.
+ * Every antenna must lie outside the voxel grid's bounding box, at least
+ * 1e-6 m from it (the paper's antennas sit on z = 0 in front of the scene).
+ * Copies what it
+ * needs (the caller may free its arrays on return), builds the per-(antenna,
+ * voxel-tile) FP64 tables on the device and synchronises the stream.
+ * Errors: NFM_ERR_ARG (sizes, non-finite values, non-uniform frequencies,
+ * antenna on a voxel), NFM_ERR_NOMEM, NFM_ERR_CUDA. */
+int nfm_set_geometry(nfm_ctx* ctx,
+                     const double* tx_xyz, int T,
+                     const double* rx_xyz, int R,
+                     const double* freq_hz, int K,
+                     const double* pulse_re_im,
+                     const nfm_grid* grid,
+                     double c);
+
+/* Sizes of the current geometry (any pointer may be NULL). */
+int nfm_dims(const nfm_ctx* ctx, int* T, int* R, int* K, long long* N);
+
+/* Minibatch forward operator y = A_B s (Eq. 2 rows of the listed pairs).
+ *   pairs [n_pairs] int32 (device), s [N] complex64, y [n_pairs*K] complex64.
+ * y must not alias s.  Uses library-owned scratch (allocated on first need). */
+int nfm_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, float* y);
+
+/* Minibatch adjoint g = A_B^H r, the operator inside the gradient of Eq. 4/6.
+ *   pairs [n_pairs] int32 (device), r [n_pairs*K] complex64, g [N] complex64. */
+int nfm_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* r, float* g);
+
+/* One SPGM iteration (Sec. IV Eq. 5 with the minibatch gradient of Eq. 6):
+ *   s <- prox_{eta*lambda ||.||_1}( s - (eta/B) A_B^H (A_B s - y_B) ),
+ * B = n_pairs*K rows; y is the FULL measurement vector [P*K] (device),
+ * s [N] is updated in place.  prox(z) = z max(0, 1 - alpha/|z|). */
+int nfm_spgm_step(nfm_ctx* ctx, const float* y, float* s, const int* pairs, int n_pairs,
+                  float eta, float lambda);
+
+/* One SPGM epoch: the P pair indices in perm [P] (device) are taken in
+ * consecutive chunks of pairs_per_batch (the last chunk may be shorter and
+ * uses its own B) and nfm_spgm_step runs on each chunk in order. */
+int nfm_spgm_epoch(nfm_ctx* ctx, const float* y, float* s, const int* perm, int pairs_per_batch,
+                   float eta, float lambda);
+
+/* Same as nfm_spgm_epoch for n_epochs epochs, but y_host [P*K], s_host [N]
+ * (in/out) and perms_host [n_epochs][P] are HOST buffers: the call copies
+ * them to library-owned device buffers, runs, copies s back and synchronises.
+ * Pinned host memory makes the copies asynchronous-capable and faster. */
+int nfm_spgm_epochs_host(nfm_ctx* ctx, const float* y_host, float* s_host, const int* perms_host,
+                         int n_epochs, int pairs_per_batch, float eta, float lambda);
+
+/* Largest eigenvalue L of A^H A / M by `iters` power iterations from
+ * v0 [N] (device, complex64, not modified), with FP64 norms:
+ *   v <- A^H A v / ||A^H A v||, then L = ||A v||^2 / (M ||v||^2).
+ * Writes *L_out (host) and synchronises.  The SPGM step is eta = 1/L. */
+int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out);
+
+/* Objective of Eq. 3 with Eq. 4 and the l1 term, accumulated in FP64:
+ *   F(s) = ||y - A s||^2 / (2M) + lambda sum_n |s_n|.
+ * y [P*K], s [N] device.  Writes *F_out (host) and synchronises. */
+int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, double* F_out);
+
+/* lambda_max = max_n |(A^H y)_n| / M (FP64 result on the host; synchronises):
+ * for lambda >= lambda_max the l1 problem has s = 0 as a solution. */
+int nfm_lambda_max(nfm_ctx* ctx, const float* y, double* out);
+
+/* Wait for the context's stream and report device-side flags. */
+int nfm_synchronize(nfm_ctx* ctx);
+
+/* Kernel timing (tracing aid, not part of the paper's method).  While enabled,
+ * every kernel the operator entry points enqueue is bracketed by a pair of
+ * CUDA events on the context stream.  nfm_profile_report synchronises, adds up
+ * the elapsed times per kernel kind since the last report and resets them:
+ *   ms_out[i], launches_out[i] for i < n_kinds (host arrays), kinds:
+ *   0 = forward partial sums, 1 = forward chunk reduction (+ residual),
+ *   2 = adjoint (+ gradient step and prox), 3 = FP64 reductions. */
+#define NFM_PROFILE_KINDS 4
+int nfm_profile_enable(nfm_ctx* ctx, int enable);
+int nfm_profile_report(nfm_ctx* ctx, double* ms_out, long long* launches_out, int n_kinds);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NFMIMO_H */

@@ -1,0 +1,739 @@
+// C-ABI of the library (declared in include/nfmimo.h): context, geometry
+// validation and upload, launch planning, SPGM driver, power iteration and
+// FP64 objective.  Every step of the path runs in the kernels of this library;
+// the host only validates, plans and enqueues.
+#include "nfmimo.h"
+#include "nfm_kernels.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace nfm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct FwdPlan {
+    int Pc, VS, nt, n_groups, n_slots, n_chunks, base, rem;
+    size_t smem;
+    size_t partial_bytes;
+};
+
+}  // namespace
+
+struct nfm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+
+    bool has_geom = false;
+    int T = 0, R = 0, K = 0, K1 = 0, P = 0;
+    long long N = 0, M = 0;
+    nfm_grid grid{};
+    double c = 0, f0 = 0, df = 0;
+    GridDesc gd{};
+    PhaseConsts ph{};
+
+    AntTile* d_ant = nullptr;
+    double* d_ant_xyz = nullptr;
+    float2* d_pulse = nullptr;
+    int* d_pairs_all = nullptr;
+    int* d_err = nullptr;
+    double* d_red = nullptr;   // [RED_BLOCKS] partials + 8 scalars
+
+    void* d_partial = nullptr;
+    size_t partial_cap = 0;
+    void* d_resid = nullptr;
+    size_t resid_cap = 0;
+    void* d_v = nullptr;
+    size_t v_cap = 0;
+    void* d_g = nullptr;
+    size_t g_cap = 0;
+    void* d_y = nullptr;
+    size_t y_cap = 0;
+    void* d_hy = nullptr;
+    size_t hy_cap = 0;
+    void* d_hs = nullptr;
+    size_t hs_cap = 0;
+    void* d_hperm = nullptr;
+    size_t hperm_cap = 0;
+
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Pending { int kind, a, b; };
+    std::vector<Pending> pending;
+
+    int fwd_occ[MAX_K1 + 1][9] = {};
+    bool fwd_attr[MAX_K1 + 1] = {};
+    bool adj_attr[MAX_K1 + 1] = {};
+};
+
+namespace {
+
+int failv(nfm_ctx* ctx, int code, const char* fmt, va_list ap)
+{
+    char buf[512];
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+int fail(nfm_ctx* ctx, int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    int r = failv(ctx, code, fmt, ap);
+    va_end(ap);
+    return r;
+}
+
+#define NFM_CK(call)                                                                         \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(ctx, NFM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+#define NFM_TRY(expr)             \
+    do {                          \
+        int r_ = (expr);          \
+        if (r_ != NFM_OK) return r_; \
+    } while (0)
+
+int ensure(nfm_ctx* ctx, void** p, size_t* cap, size_t bytes)
+{
+    if (*cap >= bytes && *p) return NFM_OK;
+    if (*p) {
+        cudaError_t e = cudaFree(*p);   // synchronises the device before release
+        *p = nullptr;
+        *cap = 0;
+        if (e != cudaSuccess) return fail(ctx, NFM_ERR_CUDA, "cudaFree failed: %s", cudaGetErrorString(e));
+    }
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(p, want);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(ctx, NFM_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    *cap = want;
+    return NFM_OK;
+}
+
+void free_ptr(void* p)
+{
+    if (p) cudaFree(p);
+}
+
+OpDesc op_desc(const nfm_ctx* ctx)
+{
+    OpDesc op;
+    op.g = ctx->gd;
+    op.ph = ctx->ph;
+    op.ant = ctx->d_ant;
+    op.pulse = ctx->d_pulse;
+    op.T = ctx->T;
+    op.R = ctx->R;
+    op.K = ctx->K;
+    op.K1 = ctx->K1;
+    op.P = ctx->P;
+    op.err = ctx->d_err;
+    return op;
+}
+
+int require_geom(nfm_ctx* ctx)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    if (!ctx->has_geom) return fail(ctx, NFM_ERR_STATE, "no geometry: call nfm_set_geometry first");
+    return NFM_OK;
+}
+
+int check_ptr(nfm_ctx* ctx, const void* p, const char* name, size_t align)
+{
+    if (!p) return fail(ctx, NFM_ERR_ARG, "%s is NULL", name);
+    if (((uintptr_t)p) % align) return fail(ctx, NFM_ERR_ARG, "%s is not %zu-byte aligned", name, align);
+    return NFM_OK;
+}
+
+// Record a timing event on the context stream when profiling is on; returns
+// its pool index or -1.
+int prof_mark(nfm_ctx* ctx)
+{
+    if (!ctx->prof) return -1;
+    if (ctx->ev_used == ctx->ev_pool.size()) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) return -1;
+        ctx->ev_pool.push_back(ev);
+    }
+    int i = (int)ctx->ev_used++;
+    if (cudaEventRecord(ctx->ev_pool[i], ctx->stream) != cudaSuccess) return -1;
+    return i;
+}
+
+void prof_pair(nfm_ctx* ctx, int kind, int a, int b)
+{
+    if (ctx->prof && a >= 0 && b >= 0) ctx->pending.push_back({kind, a, b});
+}
+
+int plan_forward(nfm_ctx* ctx, int n_pairs, FwdPlan* pl)
+{
+    const int K1 = ctx->K1;
+    pl->Pc = n_pairs < 8 ? n_pairs : 8;
+    pl->VS = 256 / (pl->Pc * K1);
+    if (pl->VS < 1) pl->VS = 1;
+    pl->nt = pl->Pc * K1 * pl->VS;
+    pl->smem = fwd_smem_bytes(K1, pl->Pc, pl->nt);
+    const void* fn = fwd_kernel_ptr(K1);
+    if (!ctx->fwd_attr[K1]) {
+        NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin));
+        ctx->fwd_attr[K1] = true;
+    }
+    if (pl->smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "forward tile needs %zu B shared memory", pl->smem);
+    int& occ = ctx->fwd_occ[K1][pl->Pc];
+    if (occ == 0) {
+        NFM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, pl->nt, pl->smem));
+        if (occ < 1) occ = 1;
+    }
+    pl->n_groups = (n_pairs + pl->Pc - 1) / pl->Pc;
+    pl->n_slots = pl->n_groups * pl->Pc;
+    long long G = (long long)ctx->num_sms * occ;
+    long long nch = (G + pl->n_groups - 1) / pl->n_groups;
+    if (nch < 1) nch = 1;
+    if (nch > ctx->gd.n_tiles) nch = ctx->gd.n_tiles;
+    if (nch > 65535) nch = 65535;
+    pl->n_chunks = (int)nch;
+    pl->base = ctx->gd.n_tiles / pl->n_chunks;
+    pl->rem = ctx->gd.n_tiles % pl->n_chunks;
+    pl->partial_bytes = (size_t)pl->n_chunks * pl->n_slots * ctx->K * sizeof(float2);
+    return NFM_OK;
+}
+
+// out[b*K + k] = (A_B s)[b, k] (- y_obs[pair_b*K + k] if y_obs)
+int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
+                    float2* out)
+{
+    FwdPlan pl;
+    NFM_TRY(plan_forward(ctx, n_pairs, &pl));
+    NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, pl.partial_bytes));
+    OpDesc op = op_desc(ctx);
+    FwdArgs a;
+    a.pairs = pairs;
+    a.n_pairs = n_pairs;
+    a.s = s;
+    a.partial = (float2*)ctx->d_partial;
+    a.n_slots = pl.n_slots;
+    a.Pc = pl.Pc;
+    a.VS = pl.VS;
+    a.tiles_base = pl.base;
+    a.tiles_rem = pl.rem;
+    const int e0 = prof_mark(ctx);
+    NFM_CK(launch_fwd_partial(op, a, dim3(pl.n_groups, pl.n_chunks), pl.nt, pl.smem, ctx->stream));
+    const int e1 = prof_mark(ctx);
+    ReduceArgs ra;
+    ra.partial = (const float2*)ctx->d_partial;
+    ra.n_chunks = pl.n_chunks;
+    ra.n_slots = pl.n_slots;
+    ra.n_out = n_pairs * ctx->K;
+    ra.pairs = pairs;
+    ra.y_obs = y_obs;
+    ra.out = out;
+    NFM_CK(launch_fwd_reduce(op, ra, ctx->stream));
+    const int e2 = prof_mark(ctx);
+    prof_pair(ctx, 0, e0, e1);
+    prof_pair(ctx, 1, e1, e2);
+    return NFM_OK;
+}
+
+int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r, float2* g_out, float2* s,
+                    float step, float alpha)
+{
+    const int K1 = ctx->K1;
+    size_t smem = adj_smem_bytes(K1, ADJ_PCHUNK);
+    if (!ctx->adj_attr[K1]) {
+        NFM_CK(cudaFuncSetAttribute(adj_kernel_ptr(K1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ctx->smem_optin));
+        ctx->adj_attr[K1] = true;
+    }
+    AdjArgs a;
+    a.pairs = pairs;
+    a.n_pairs = n_pairs;
+    a.r = r;
+    a.g_out = g_out;
+    a.s = s;
+    a.step = step;
+    a.alpha = alpha;
+    a.pchunk = ADJ_PCHUNK;
+    const int e0 = prof_mark(ctx);
+    NFM_CK(launch_adjoint(op_desc(ctx), a, smem, ctx->stream));
+    prof_pair(ctx, 2, e0, prof_mark(ctx));
+    return NFM_OK;
+}
+
+int check_flags(nfm_ctx* ctx)
+{
+    int flags = 0;
+    NFM_CK(cudaMemcpy(&flags, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flags) {
+        NFM_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+        if (flags & ERRF_PAIR) return fail(ctx, NFM_ERR_ARG, "a pair index was outside [0, P)");
+        return fail(ctx, NFM_ERR_NUMERIC, "device flag 0x%x", flags);
+    }
+    return NFM_OK;
+}
+
+int spgm_step_impl(nfm_ctx* ctx, const float2* y, float2* s, const int* pairs, int n_pairs, float eta,
+                   float lambda)
+{
+    NFM_TRY(ensure(ctx, &ctx->d_resid, &ctx->resid_cap, (size_t)n_pairs * ctx->K * sizeof(float2)));
+    float2* r = (float2*)ctx->d_resid;
+    NFM_TRY(enqueue_forward(ctx, pairs, n_pairs, s, y, r));
+    const double B = (double)n_pairs * ctx->K;
+    NFM_TRY(enqueue_adjoint(ctx, pairs, n_pairs, r, nullptr, s, (float)(eta / B), (float)((double)eta * lambda)));
+    return NFM_OK;
+}
+
+int spgm_epoch_impl(nfm_ctx* ctx, const float2* y, float2* s, const int* perm, int bp, float eta, float lambda)
+{
+    NFM_TRY(ensure(ctx, &ctx->d_resid, &ctx->resid_cap, (size_t)bp * ctx->K * sizeof(float2)));
+    for (int c0 = 0; c0 < ctx->P; c0 += bp) {
+        int nb = ctx->P - c0 < bp ? ctx->P - c0 : bp;
+        NFM_TRY(spgm_step_impl(ctx, y, s, perm + c0, nb, eta, lambda));
+    }
+    return NFM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int nfm_create(nfm_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return fail(nullptr, NFM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(nullptr, NFM_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return fail(nullptr, NFM_ERR_ARG, "device %d out of range (%d)", device, ndev);
+    DevGuard guard(device);
+    nfm_ctx* ctx = new nfm_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    int v = 0;
+    if ((e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, NFM_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
+    }
+    ctx->smem_optin = (size_t)v;
+    if ((e = cudaMalloc((void**)&ctx->d_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_red, (RED_BLOCKS + 8) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemset(ctx->d_err, 0, sizeof(int))) != cudaSuccess) {
+        free_ptr(ctx->d_err);
+        free_ptr(ctx->d_red);
+        delete ctx;
+        return fail(nullptr, NFM_ERR_NOMEM, "context allocation: %s", cudaGetErrorString(e));
+    }
+    *out = ctx;
+    return NFM_OK;
+}
+
+void nfm_destroy(nfm_ctx* ctx)
+{
+    if (!ctx) return;
+    DevGuard guard(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    void* ps[] = {ctx->d_ant, ctx->d_ant_xyz, ctx->d_pulse, ctx->d_pairs_all, ctx->d_err, ctx->d_red,
+                  ctx->d_partial, ctx->d_resid, ctx->d_v, ctx->d_g, ctx->d_y, ctx->d_hy, ctx->d_hs, ctx->d_hperm};
+    for (void* p : ps) free_ptr(p);
+    for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
+    delete ctx;
+}
+
+const char* nfm_last_error(const nfm_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int nfm_set_stream(nfm_ctx* ctx, void* cuda_stream)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return NFM_OK;
+}
+
+int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx_xyz, int R,
+                     const double* freq_hz, int K, const double* pulse_re_im, const nfm_grid* grid, double c)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    DevGuard guard(ctx->device);
+    if (!tx_xyz || !rx_xyz || !freq_hz || !grid) return fail(ctx, NFM_ERR_ARG, "NULL geometry array");
+    if (T < 1 || R < 1) return fail(ctx, NFM_ERR_ARG, "need T >= 1 and R >= 1 (got %d, %d)", T, R);
+    if (K < 1 || K > K2 * MAX_K1) return fail(ctx, NFM_ERR_ARG, "K = %d outside [1, %d]", K, K2 * MAX_K1);
+    if ((long long)T * R > (1LL << 30)) return fail(ctx, NFM_ERR_ARG, "too many pairs");
+    const nfm_grid g = *grid;
+    if (g.nx < 1 || g.ny < 1 || g.nz < 1) return fail(ctx, NFM_ERR_ARG, "grid dimensions must be >= 1");
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    if (N >= (1LL << 31)) return fail(ctx, NFM_ERR_ARG, "N = %lld voxels exceeds 2^31 - 1", N);
+    const double gv[6] = {g.x0, g.y0, g.z0, g.dx, g.dy, g.dz};
+    for (double x : gv)
+        if (!std::isfinite(x)) return fail(ctx, NFM_ERR_ARG, "non-finite grid parameter");
+    if (!(g.dx > 0 && g.dy > 0 && g.dz > 0)) return fail(ctx, NFM_ERR_ARG, "grid steps must be > 0");
+    if (!(c > 0) || !std::isfinite(c)) return fail(ctx, NFM_ERR_ARG, "c must be finite and > 0");
+    for (int i = 0; i < 3 * T; ++i)
+        if (!std::isfinite(tx_xyz[i])) return fail(ctx, NFM_ERR_ARG, "non-finite TX coordinate");
+    for (int i = 0; i < 3 * R; ++i)
+        if (!std::isfinite(rx_xyz[i])) return fail(ctx, NFM_ERR_ARG, "non-finite RX coordinate");
+    for (int k = 0; k < K; ++k)
+        if (!std::isfinite(freq_hz[k]) || !(freq_hz[k] > 0)) return fail(ctx, NFM_ERR_ARG, "frequency %d invalid", k);
+    if (pulse_re_im)
+        for (int k = 0; k < 2 * K; ++k)
+            if (!std::isfinite(pulse_re_im[k])) return fail(ctx, NFM_ERR_ARG, "non-finite pulse spectrum");
+    const double f0 = freq_hz[0];
+    const double df = K > 1 ? (freq_hz[K - 1] - freq_hz[0]) / (K - 1) : 0.0;
+    for (int k = 0; k < K; ++k) {
+        double want = f0 + k * df;
+        if (std::fabs(freq_hz[k] - want) > 1e-9 * std::fabs(freq_hz[K - 1]))
+            return fail(ctx, NFM_ERR_ARG, "frequencies must be equally spaced (f[%d] off by %g Hz)", k,
+                        freq_hz[k] - want);
+    }
+    // smallest antenna-voxel distance (distance to the grid's bounding box)
+    const double lo[3] = {g.x0, g.y0, g.z0};
+    const double hi[3] = {g.x0 + (g.nx - 1) * g.dx, g.y0 + (g.ny - 1) * g.dy, g.z0 + (g.nz - 1) * g.dz};
+    for (int a = 0; a < T + R; ++a) {
+        const double* p = a < T ? tx_xyz + 3 * a : rx_xyz + 3 * (a - T);
+        bool inside = true;
+        double d2 = 0;
+        for (int j = 0; j < 3; ++j) {
+            double q = p[j] < lo[j] ? lo[j] : (p[j] > hi[j] ? hi[j] : p[j]);
+            d2 += (p[j] - q) * (p[j] - q);
+            if (p[j] < lo[j] || p[j] > hi[j]) inside = false;
+        }
+        if (inside || d2 < 1e-12)
+            return fail(ctx, NFM_ERR_ARG, "antenna %d lies within 1e-6 m of the voxel grid", a);
+    }
+
+    // release the previous geometry
+    free_ptr(ctx->d_ant);
+    free_ptr(ctx->d_ant_xyz);
+    free_ptr(ctx->d_pulse);
+    free_ptr(ctx->d_pairs_all);
+    ctx->d_ant = nullptr;
+    ctx->d_ant_xyz = nullptr;
+    ctx->d_pulse = nullptr;
+    ctx->d_pairs_all = nullptr;
+    ctx->has_geom = false;
+
+    GridDesc gd;
+    gd.nx = g.nx;
+    gd.ny = g.ny;
+    gd.nz = g.nz;
+    gd.tiles_x = (g.nx + TILE_X - 1) / TILE_X;
+    gd.tiles_y = (g.ny + TILE_Y - 1) / TILE_Y;
+    gd.tiles_z = (g.nz + TILE_Z - 1) / TILE_Z;
+    gd.n_tiles = gd.tiles_x * gd.tiles_y * gd.tiles_z;
+    auto split = [](double x, float& h, float& l) {
+        h = (float)x;
+        l = (float)(x - (double)h);
+    };
+    split(g.dx, gd.dx_hi, gd.dx_lo);
+    split(g.dy, gd.dy_hi, gd.dy_lo);
+    split(g.dz, gd.dz_hi, gd.dz_lo);
+    PhaseConsts ph;
+    split(f0 / c, ph.f0c_hi, ph.f0c_lo);
+    ph.dfc = (float)(df / c);
+    ph.dfc2 = (float)(K2 * df / c);
+
+    const int n_ant = T + R;
+    const int P = T * R;
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&ctx->d_ant, (size_t)n_ant * gd.n_tiles * sizeof(AntTile))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_ant_xyz, (size_t)n_ant * 3 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ctx->d_pairs_all, (size_t)P * sizeof(int))) != cudaSuccess)
+        return fail(ctx, NFM_ERR_NOMEM, "geometry allocation: %s", cudaGetErrorString(e));
+    double* hxyz = new double[3 * n_ant];
+    memcpy(hxyz, tx_xyz, 3 * T * sizeof(double));
+    memcpy(hxyz + 3 * T, rx_xyz, 3 * R * sizeof(double));
+    int* hp = new int[P];
+    for (int i = 0; i < P; ++i) hp[i] = i;
+    e = cudaMemcpy(ctx->d_ant_xyz, hxyz, 3 * n_ant * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_pairs_all, hp, P * sizeof(int), cudaMemcpyHostToDevice);
+    delete[] hxyz;
+    delete[] hp;
+    NFM_CK(e);
+    if (pulse_re_im) {
+        float* hpl = new float[2 * K];
+        for (int i = 0; i < 2 * K; ++i) hpl[i] = (float)pulse_re_im[i];
+        e = cudaMalloc((void**)&ctx->d_pulse, K * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->d_pulse, hpl, K * sizeof(float2), cudaMemcpyHostToDevice);
+        delete[] hpl;
+        NFM_CK(e);
+    }
+    AntSetup as;
+    as.ant_xyz = ctx->d_ant_xyz;
+    as.n_ant = n_ant;
+    as.x0 = g.x0;
+    as.y0 = g.y0;
+    as.z0 = g.z0;
+    as.dx = g.dx;
+    as.dy = g.dy;
+    as.dz = g.dz;
+    as.f0c = f0 / c;
+    as.dfc = df / c;
+    as.dfc2 = K2 * df / c;
+    as.out = ctx->d_ant;
+    NFM_CK(launch_ant_setup(gd, as, ctx->stream));
+    NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
+
+    ctx->T = T;
+    ctx->R = R;
+    ctx->K = K;
+    ctx->K1 = (K + K2 - 1) / K2;
+    ctx->P = P;
+    ctx->N = N;
+    ctx->M = (long long)P * K;
+    ctx->grid = g;
+    ctx->c = c;
+    ctx->f0 = f0;
+    ctx->df = df;
+    ctx->gd = gd;
+    ctx->ph = ph;
+    ctx->has_geom = true;
+    return NFM_OK;
+}
+
+int nfm_dims(const nfm_ctx* ctx, int* T, int* R, int* K, long long* N)
+{
+    if (!ctx || !ctx->has_geom) return NFM_ERR_STATE;
+    if (T) *T = ctx->T;
+    if (R) *R = ctx->R;
+    if (K) *K = ctx->K;
+    if (N) *N = ctx->N;
+    return NFM_OK;
+}
+
+int nfm_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, float* y)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
+    NFM_TRY(check_ptr(ctx, pairs, "pairs", 4));
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    return enqueue_forward(ctx, pairs, n_pairs, (const float2*)s, nullptr, (float2*)y);
+}
+
+int nfm_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* r, float* g)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
+    NFM_TRY(check_ptr(ctx, pairs, "pairs", 4));
+    NFM_TRY(check_ptr(ctx, r, "r", 8));
+    NFM_TRY(check_ptr(ctx, g, "g", 8));
+    return enqueue_adjoint(ctx, pairs, n_pairs, (const float2*)r, (float2*)g, nullptr, 0.f, 0.f);
+}
+
+int nfm_spgm_step(nfm_ctx* ctx, const float* y, float* s, const int* pairs, int n_pairs, float eta, float lambda)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
+    if (!(eta > 0) || !std::isfinite(eta)) return fail(ctx, NFM_ERR_ARG, "eta must be finite and > 0");
+    if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(ctx, NFM_ERR_ARG, "lambda must be finite and >= 0");
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, pairs, "pairs", 4));
+    return spgm_step_impl(ctx, (const float2*)y, (float2*)s, pairs, n_pairs, eta, lambda);
+}
+
+int nfm_spgm_epoch(nfm_ctx* ctx, const float* y, float* s, const int* perm, int pairs_per_batch, float eta,
+                   float lambda)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (pairs_per_batch < 1) return fail(ctx, NFM_ERR_ARG, "pairs_per_batch must be >= 1");
+    if (!(eta > 0) || !std::isfinite(eta)) return fail(ctx, NFM_ERR_ARG, "eta must be finite and > 0");
+    if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(ctx, NFM_ERR_ARG, "lambda must be finite and >= 0");
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, perm, "perm", 4));
+    return spgm_epoch_impl(ctx, (const float2*)y, (float2*)s, perm, pairs_per_batch, eta, lambda);
+}
+
+int nfm_spgm_epochs_host(nfm_ctx* ctx, const float* y_host, float* s_host, const int* perms_host, int n_epochs,
+                         int pairs_per_batch, float eta, float lambda)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (n_epochs < 1 || pairs_per_batch < 1) return fail(ctx, NFM_ERR_ARG, "n_epochs and pairs_per_batch must be >= 1");
+    if (!(eta > 0) || !std::isfinite(eta)) return fail(ctx, NFM_ERR_ARG, "eta must be finite and > 0");
+    if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(ctx, NFM_ERR_ARG, "lambda must be finite and >= 0");
+    if (!y_host || !s_host || !perms_host) return fail(ctx, NFM_ERR_ARG, "NULL host buffer");
+    const size_t yb = (size_t)ctx->M * sizeof(float2), sb = (size_t)ctx->N * sizeof(float2);
+    const size_t pb = (size_t)n_epochs * ctx->P * sizeof(int);
+    NFM_TRY(ensure(ctx, &ctx->d_hy, &ctx->hy_cap, yb));
+    NFM_TRY(ensure(ctx, &ctx->d_hs, &ctx->hs_cap, sb));
+    NFM_TRY(ensure(ctx, &ctx->d_hperm, &ctx->hperm_cap, pb));
+    NFM_CK(cudaMemcpyAsync(ctx->d_hy, y_host, yb, cudaMemcpyHostToDevice, ctx->stream));
+    NFM_CK(cudaMemcpyAsync(ctx->d_hs, s_host, sb, cudaMemcpyHostToDevice, ctx->stream));
+    NFM_CK(cudaMemcpyAsync(ctx->d_hperm, perms_host, pb, cudaMemcpyHostToDevice, ctx->stream));
+    for (int e = 0; e < n_epochs; ++e)
+        NFM_TRY(spgm_epoch_impl(ctx, (const float2*)ctx->d_hy, (float2*)ctx->d_hs,
+                                (const int*)ctx->d_hperm + (size_t)e * ctx->P, pairs_per_batch, eta, lambda));
+    NFM_CK(cudaMemcpyAsync(s_host, ctx->d_hs, sb, cudaMemcpyDeviceToHost, ctx->stream));
+    NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
+    return check_flags(ctx);
+}
+
+int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (iters < 0) return fail(ctx, NFM_ERR_ARG, "iters must be >= 0");
+    NFM_TRY(check_ptr(ctx, v0, "v0", 8));
+    if (!L_out) return fail(ctx, NFM_ERR_ARG, "L_out is NULL");
+    const size_t nb = (size_t)ctx->N * sizeof(float2), mb = (size_t)ctx->M * sizeof(float2);
+    NFM_TRY(ensure(ctx, &ctx->d_v, &ctx->v_cap, nb));
+    NFM_TRY(ensure(ctx, &ctx->d_g, &ctx->g_cap, nb));
+    NFM_TRY(ensure(ctx, &ctx->d_y, &ctx->y_cap, mb));
+    float2* v = (float2*)ctx->d_v;
+    float2* g = (float2*)ctx->d_g;
+    float2* y = (float2*)ctx->d_y;
+    double* part = ctx->d_red;
+    double* sc = ctx->d_red + RED_BLOCKS;   // scalars
+    cudaStream_t st = ctx->stream;
+    NFM_CK(launch_norm2((const float2*)v0, ctx->N, part, sc + 0, st));
+    NFM_CK(launch_normalize((const float2*)v0, v, ctx->N, sc + 0, st));
+    for (int it = 0; it < iters; ++it) {
+        NFM_TRY(enqueue_forward(ctx, ctx->d_pairs_all, ctx->P, v, nullptr, y));
+        NFM_TRY(enqueue_adjoint(ctx, ctx->d_pairs_all, ctx->P, y, g, nullptr, 0.f, 0.f));
+        const int e0 = prof_mark(ctx);
+        NFM_CK(launch_norm2(g, ctx->N, part, sc + 0, st));
+        NFM_CK(launch_normalize(g, v, ctx->N, sc + 0, st));
+        prof_pair(ctx, 3, e0, prof_mark(ctx));
+    }
+    NFM_TRY(enqueue_forward(ctx, ctx->d_pairs_all, ctx->P, v, nullptr, y));
+    NFM_CK(launch_norm2(y, ctx->M, part, sc + 1, st));
+    NFM_CK(launch_norm2(v, ctx->N, part, sc + 2, st));
+    NFM_CK(launch_ratio(sc + 1, sc + 2, (double)ctx->M, sc + 3, st));
+    double L = 0;
+    NFM_CK(cudaMemcpyAsync(&L, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NFM_CK(st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize());
+    NFM_TRY(check_flags(ctx));
+    if (!std::isfinite(L)) return fail(ctx, NFM_ERR_NUMERIC, "power iteration gave a non-finite L");
+    *L_out = L;
+    return NFM_OK;
+}
+
+int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, double* F_out)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    if (!F_out) return fail(ctx, NFM_ERR_ARG, "F_out is NULL");
+    const size_t mb = (size_t)ctx->M * sizeof(float2);
+    NFM_TRY(ensure(ctx, &ctx->d_y, &ctx->y_cap, mb));
+    float2* res = (float2*)ctx->d_y;
+    double* part = ctx->d_red;
+    double* sc = ctx->d_red + RED_BLOCKS;
+    cudaStream_t st = ctx->stream;
+    NFM_TRY(enqueue_forward(ctx, ctx->d_pairs_all, ctx->P, (const float2*)s, (const float2*)y, res));
+    NFM_CK(launch_norm2(res, ctx->M, part, sc + 4, st));
+    NFM_CK(launch_abs_sum((const float2*)s, ctx->N, part, sc + 5, st));
+    NFM_CK(launch_axpby(sc + 4, 1.0 / (2.0 * (double)ctx->M), sc + 5, lambda, sc + 6, st));
+    double F = 0;
+    NFM_CK(cudaMemcpyAsync(&F, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NFM_CK(st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize());
+    NFM_TRY(check_flags(ctx));
+    *F_out = F;
+    return NFM_OK;
+}
+
+int nfm_lambda_max(nfm_ctx* ctx, const float* y, double* out)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    if (!out) return fail(ctx, NFM_ERR_ARG, "out is NULL");
+    const size_t nb = (size_t)ctx->N * sizeof(float2);
+    NFM_TRY(ensure(ctx, &ctx->d_g, &ctx->g_cap, nb));
+    double* part = ctx->d_red;
+    double* sc = ctx->d_red + RED_BLOCKS;
+    cudaStream_t st = ctx->stream;
+    NFM_TRY(enqueue_adjoint(ctx, ctx->d_pairs_all, ctx->P, (const float2*)y, (float2*)ctx->d_g, nullptr, 0.f, 0.f));
+    NFM_CK(launch_abs_max((const float2*)ctx->d_g, ctx->N, part, sc + 7, st));
+    double m = 0;
+    NFM_CK(cudaMemcpyAsync(&m, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NFM_CK(st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize());
+    NFM_TRY(check_flags(ctx));
+    *out = m / (double)ctx->M;
+    return NFM_OK;
+}
+
+int nfm_synchronize(nfm_ctx* ctx)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    DevGuard guard(ctx->device);
+    NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
+    return check_flags(ctx);
+}
+
+int nfm_profile_enable(nfm_ctx* ctx, int enable)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    ctx->prof = enable != 0;
+    return NFM_OK;
+}
+
+int nfm_profile_report(nfm_ctx* ctx, double* ms_out, long long* launches_out, int n_kinds)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    if (n_kinds < 0 || (n_kinds > 0 && (!ms_out || !launches_out)))
+        return fail(ctx, NFM_ERR_ARG, "bad output arrays");
+    DevGuard guard(ctx->device);
+    NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
+    for (int i = 0; i < n_kinds; ++i) {
+        ms_out[i] = 0.0;
+        launches_out[i] = 0;
+    }
+    for (const auto& p : ctx->pending) {
+        float ms = 0.f;
+        NFM_CK(cudaEventElapsedTime(&ms, ctx->ev_pool[p.a], ctx->ev_pool[p.b]));
+        if (p.kind < n_kinds) {
+            ms_out[p.kind] += ms;
+            launches_out[p.kind] += 1;
+        }
+    }
+    ctx->pending.clear();
+    ctx->ev_used = 0;
+    return NFM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Kernel argument blocks and host-side launch helpers shared by the
+// translation units of the library.
+#pragma once
+#include "nfm_device.cuh"
+
+namespace nfm {
+
+struct FwdArgs {
+    const int* pairs;        // [n_pairs] pair indices (device)
+    int n_pairs;
+    const float2* s;         // [N]
+    float2* partial;         // [n_chunks][n_slots][K]
+    int n_slots;             // n_groups * Pc
+    int Pc;                  // pairs per CTA
+    int VS;                  // voxel subsets per CTA
+    int tiles_base;          // chunk c owns tiles_base (+1 for c < tiles_rem) tiles
+    int tiles_rem;
+};
+
+struct ReduceArgs {
+    const float2* partial;   // [n_chunks][n_slots][K]
+    int n_chunks;
+    int n_slots;
+    int n_out;               // n_pairs * K
+    const int* pairs;        // [n_pairs] (only read when y_obs != nullptr)
+    const float2* y_obs;     // full measurement vector [P*K] or nullptr
+    float2* out;             // [n_pairs * K]
+};
+
+struct AdjArgs {
+    const int* pairs;        // [n_pairs]
+    int n_pairs;
+    const float2* r;         // [n_pairs * K]
+    float2* g_out;           // [N] plain adjoint output, or nullptr
+    float2* s;               // [N] SPGM iterate updated in place, or nullptr
+    float step;              // eta / B
+    float alpha;             // eta * lambda
+    int pchunk;              // pairs staged in shared memory per round
+};
+
+// per (antenna, tile) FP64 set-up
+struct AntSetup {
+    const double* ant_xyz;   // [(T+R)][3]
+    int n_ant;
+    double x0, y0, z0, dx, dy, dz;
+    double f0c, dfc, dfc2;   // f0/c, df/c, K2 df/c
+    AntTile* out;            // [n_ant * n_tiles]
+};
+
+constexpr int ADJ_THREADS = 64;   // one 8x4x4 tile, two voxels per thread
+constexpr int ADJ_PCHUNK = 16;
+
+size_t fwd_smem_bytes(int K1, int Pc, int nt);
+const void* fwd_kernel_ptr(int K1);
+const void* adj_kernel_ptr(int K1);
+size_t adj_smem_bytes(int K1, int pchunk);
+
+cudaError_t launch_fwd_partial(const OpDesc& op, const FwdArgs& a, dim3 grid, int nt, size_t smem,
+                               cudaStream_t st);
+cudaError_t launch_fwd_reduce(const OpDesc& op, const ReduceArgs& a, cudaStream_t st);
+cudaError_t launch_adjoint(const OpDesc& op, const AdjArgs& a, size_t smem, cudaStream_t st);
+cudaError_t launch_ant_setup(const GridDesc& g, const AntSetup& a, cudaStream_t st);
+
+// FP64 reductions (deterministic: fixed grid, fixed tree)
+constexpr int RED_BLOCKS = 256;
+cudaError_t launch_norm2(const float2* v, long long n, double* partial, double* out, cudaStream_t st);
+cudaError_t launch_abs_sum(const float2* v, long long n, double* partial, double* out, cudaStream_t st);
+cudaError_t launch_abs_max(const float2* v, long long n, double* partial, double* out, cudaStream_t st);
+// dst = src / sqrt(*nrm2)
+cudaError_t launch_normalize(const float2* src, float2* dst, long long n, const double* nrm2, cudaStream_t st);
+// out[0] = a[0] / (scale * b[0])
+cudaError_t launch_ratio(const double* a, const double* b, double scale, double* out, cudaStream_t st);
+// out[0] = a[0] * sa + b[0] * sb
+cudaError_t launch_axpby(const double* a, double sa, const double* b, double sb, double* out, cudaStream_t st);
+
+}  // namespace nfm

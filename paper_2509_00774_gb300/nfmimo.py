@@ -1,0 +1,251 @@
+"""Python binding of the nfmimo C-ABI (include/nfmimo.h): argument marshalling only.
+
+Every entry point of the C library has a method of the same name on
+`Context`.  Device vectors are torch tensors on the context's GPU
+(complex64 for complex vectors, int32 for pair lists); host vectors for the
+`*_host` call are numpy arrays or CPU tensors.  All compute runs in the CUDA
+library; there is no fallback: if the library is missing or no GPU is
+present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnfmimo.so")
+
+NFM_OK = 0
+_STATUS = {-1: "NFM_ERR_ARG", -2: "NFM_ERR_CUDA", -3: "NFM_ERR_NOMEM", -4: "NFM_ERR_STATE",
+           -5: "NFM_ERR_TIMEOUT", -6: "NFM_ERR_NUMERIC"}
+
+_lib = None
+
+
+class NfmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+def load_library(path: str | None = None):
+    """Load libnfmimo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2509_00774_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i, f, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
+    sig = {
+        "nfm_create": (i, [ctypes.POINTER(vp), i, vp]),
+        "nfm_destroy": (None, [vp]),
+        "nfm_last_error": (ctypes.c_char_p, [vp]),
+        "nfm_set_stream": (i, [vp, vp]),
+        "nfm_set_geometry": (i, [vp, vp, i, vp, i, vp, i, vp, ctypes.POINTER(_Grid), d]),
+        "nfm_dims": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                         ctypes.POINTER(ctypes.c_longlong)]),
+        "nfm_forward": (i, [vp, vp, i, vp, vp]),
+        "nfm_adjoint": (i, [vp, vp, i, vp, vp]),
+        "nfm_spgm_step": (i, [vp, vp, vp, vp, i, f, f]),
+        "nfm_spgm_epoch": (i, [vp, vp, vp, vp, i, f, f]),
+        "nfm_spgm_epochs_host": (i, [vp, vp, vp, vp, i, i, f, f]),
+        "nfm_power_iteration": (i, [vp, i, vp, ctypes.POINTER(d)]),
+        "nfm_objective": (i, [vp, vp, vp, d, ctypes.POINTER(d)]),
+        "nfm_lambda_max": (i, [vp, vp, ctypes.POINTER(d)]),
+        "nfm_synchronize": (i, [vp]),
+        "nfm_profile_enable": (i, [vp, i]),
+        "nfm_profile_report": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(t, dtype, name, device=None):
+    """Data pointer of a contiguous torch tensor of the given dtype (complex64 -> float pairs)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None:
+        if t.device.type != "cuda" or t.device.index != device:
+            raise ValueError(f"{name} must live on cuda:{device}, got {t.device}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One nfm_ctx: a geometry on one GPU and a stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self._lib = load_library()
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        rc = self._lib.nfm_create(ctypes.byref(h), self.device, ctypes.c_void_p(stream.cuda_stream))
+        if rc != NFM_OK:
+            raise NfmError(rc, self._lib.nfm_last_error(None).decode())
+        self._h = h
+        self.T = self.R = self.K = self.N = None
+
+    def _check(self, rc):
+        if rc != NFM_OK:
+            raise NfmError(rc, self._lib.nfm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nfm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ---------------------------------------------------------------------
+    def set_stream(self, stream):
+        self._stream = stream
+        self._check(self._lib.nfm_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def set_geometry(self, geom):
+        """geom: an `inputs.Geometry` (FP64 antennas, frequencies, grid, pulse, c)."""
+        tx = np.ascontiguousarray(geom.tx, dtype=np.float64)
+        rx = np.ascontiguousarray(geom.rx, dtype=np.float64)
+        fr = np.ascontiguousarray(geom.freq, dtype=np.float64)
+        pulse = None
+        if geom.pulse is not None:
+            p = np.asarray(geom.pulse, dtype=np.complex128)
+            pulse = np.ascontiguousarray(np.stack([p.real, p.imag], 1))
+        g = geom.grid
+        grid = _Grid(g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, g.nx, g.ny, g.nz)
+        self._check(self._lib.nfm_set_geometry(
+            self._h, tx.ctypes.data_as(ctypes.c_void_p), tx.shape[0],
+            rx.ctypes.data_as(ctypes.c_void_p), rx.shape[0],
+            fr.ctypes.data_as(ctypes.c_void_p), fr.shape[0],
+            None if pulse is None else pulse.ctypes.data_as(ctypes.c_void_p),
+            ctypes.byref(grid), float(geom.c)))
+        self.T, self.R, self.K, self.N = tx.shape[0], rx.shape[0], fr.shape[0], g.N
+        self.P = self.T * self.R
+        self.M = self.P * self.K
+
+    def dims(self):
+        T, R, K, N = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        self._check(self._lib.nfm_dims(self._h, ctypes.byref(T), ctypes.byref(R), ctypes.byref(K),
+                                       ctypes.byref(N)))
+        return T.value, R.value, K.value, N.value
+
+    # ---------------------------------------------------------------------
+    def _c(self, t, name):
+        import torch
+        return _ptr(t, torch.complex64, name, self.device)
+
+    def _i(self, t, name):
+        import torch
+        return _ptr(t, torch.int32, name, self.device)
+
+    def forward(self, pairs, s, y=None):
+        """y = A_B s for the pair list `pairs` (int32, device); returns y [n_pairs*K]."""
+        import torch
+        n = pairs.numel()
+        if y is None:
+            y = torch.empty(n * self.K, dtype=torch.complex64, device=s.device)
+        self._check(self._lib.nfm_forward(self._h, self._i(pairs, "pairs"), n, self._c(s, "s"), self._c(y, "y")))
+        return y
+
+    def adjoint(self, pairs, r, g=None):
+        """g = A_B^H r; returns g [N]."""
+        import torch
+        n = pairs.numel()
+        if g is None:
+            g = torch.empty(self.N, dtype=torch.complex64, device=r.device)
+        self._check(self._lib.nfm_adjoint(self._h, self._i(pairs, "pairs"), n, self._c(r, "r"), self._c(g, "g")))
+        return g
+
+    def spgm_step(self, y, s, pairs, eta, lam):
+        self._check(self._lib.nfm_spgm_step(self._h, self._c(y, "y"), self._c(s, "s"), self._i(pairs, "pairs"),
+                                            pairs.numel(), float(eta), float(lam)))
+        return s
+
+    def spgm_epoch(self, y, s, perm, pairs_per_batch, eta, lam):
+        self._check(self._lib.nfm_spgm_epoch(self._h, self._c(y, "y"), self._c(s, "s"), self._i(perm, "perm"),
+                                             int(pairs_per_batch), float(eta), float(lam)))
+        return s
+
+    def spgm_epochs_host(self, y_host, s_host, perms_host, pairs_per_batch, eta, lam):
+        """Host-buffer SPGM: y_host [P*K] complex64, s_host [N] complex64 (updated in place),
+        perms_host [n_epochs, P] int32 (numpy arrays or CPU tensors, ideally pinned)."""
+        def hp(a, dt, name):
+            if hasattr(a, "data_ptr"):
+                if a.device.type != "cpu" or not a.is_contiguous():
+                    raise ValueError(f"{name} must be a contiguous CPU tensor")
+                return ctypes.c_void_p(a.data_ptr())
+            a = np.asarray(a)
+            if a.dtype != dt or not a.flags.c_contiguous:
+                raise ValueError(f"{name} must be a contiguous {dt} array")
+            return a.ctypes.data_as(ctypes.c_void_p)
+        perms = perms_host
+        n_epochs = perms.shape[0] if perms.ndim == 2 else 1
+        self._check(self._lib.nfm_spgm_epochs_host(
+            self._h, hp(y_host, np.complex64, "y_host"), hp(s_host, np.complex64, "s_host"),
+            hp(perms, np.int32, "perms_host"), n_epochs, int(pairs_per_batch), float(eta), float(lam)))
+        return s_host
+
+    def power_iteration(self, v0, iters: int = 50) -> float:
+        L = ctypes.c_double()
+        self._check(self._lib.nfm_power_iteration(self._h, int(iters), self._c(v0, "v0"), ctypes.byref(L)))
+        return L.value
+
+    def objective(self, y, s, lam) -> float:
+        F = ctypes.c_double()
+        self._check(self._lib.nfm_objective(self._h, self._c(y, "y"), self._c(s, "s"), float(lam), ctypes.byref(F)))
+        return F.value
+
+    def lambda_max(self, y) -> float:
+        out = ctypes.c_double()
+        self._check(self._lib.nfm_lambda_max(self._h, self._c(y, "y"), ctypes.byref(out)))
+        return out.value
+
+    def synchronize(self):
+        self._check(self._lib.nfm_synchronize(self._h))
+
+    PROFILE_KINDS = ("forward_partial", "forward_reduce", "adjoint", "reductions")
+
+    def profile_enable(self, on: bool = True):
+        self._check(self._lib.nfm_profile_enable(self._h, 1 if on else 0))
+
+    def profile_report(self) -> dict:
+        """{kind: (total_ms, launches)} since the last report (synchronises)."""
+        n = len(self.PROFILE_KINDS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        self._check(self._lib.nfm_profile_report(self._h, ms, cnt, n))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.PROFILE_KINDS)}

@@ -1,0 +1,140 @@
+"""GPU SPGM (Eq. 5 with the Eq. 6 minibatch gradient), power iteration, objective and
+lambda_max against the FP64 oracle, with identical seeded permutations."""
+import numpy as np
+import pytest
+
+from oracle import Oracle, nmse
+from paper_2509_00774_gb300 import inputs as I
+from paper_2509_00774_gb300 import workloads as W
+from paper_2509_00774_gb300.nfmimo import NfmError
+from tests.gpu_helpers import NMSE_TOL, OBJ_TOL, make_ctx, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _c64(z):
+    return np.asarray(z, dtype=np.complex64).astype(np.complex128)
+
+
+def _small_problem():
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    y = _c64(I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db))
+    return w, o, y
+
+
+def test_power_iteration_and_lambda_small():
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    v0 = _c64(I.complex_gaussian(o.N, w.seeds["power"]))
+    L_gpu = ctx.power_iteration(to_dev(v0), 50)
+    L_orc = o.power_iteration(v0, 50)
+    assert abs(L_gpu - L_orc) <= 1e-4 * L_orc, (L_gpu, L_orc)
+    lm_gpu = ctx.lambda_max(to_dev(y))
+    lm_orc = o.lambda_max(y)
+    assert abs(lm_gpu - lm_orc) <= 1e-5 * lm_orc, (lm_gpu, lm_orc)
+
+
+def test_objective_small():
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    s = _c64(I.point_scene(w.geom.grid, 40, 9)) * 0.7
+    lam = 0.01
+    F_gpu = ctx.objective(to_dev(y), to_dev(s), lam)
+    F_orc = o.objective(y, s, lam)
+    assert abs(F_gpu - F_orc) <= 1e-5 * F_orc, (F_gpu, F_orc)
+
+
+@pytest.mark.parametrize("bp", [4, 5])
+def test_spgm_small_matches_oracle(bp):
+    """All 30 epochs of the small workload; bp = 5 leaves a 1-pair last chunk."""
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
+    eta = float(np.float32(1.0 / L))
+    lam = float(np.float32(0.05 * o.lambda_max(y)))
+    s_orc = np.zeros(o.N, dtype=np.complex128)
+    s_gpu = to_dev(np.zeros(o.N))
+    y_dev = to_dev(y)
+    worst = 0.0
+    for e in range(w.epochs):
+        perm = I.epoch_permutation(o.P, w.seeds["perm"], e)
+        s_orc = o.spgm_epoch(y, s_orc, perm, bp, eta, lam)
+        ctx.spgm_epoch(y_dev, s_gpu, to_dev(perm, "int32"), bp, eta, lam)
+        err = nmse(to_host(s_gpu), s_orc)
+        worst = max(worst, err)
+        assert err <= NMSE_TOL, f"epoch {e}: NMSE {err:.3e}"
+    F_gpu = o.objective(y, to_host(s_gpu), lam)
+    F_orc = o.objective(y, s_orc, lam)
+    assert abs(F_gpu - F_orc) <= OBJ_TOL * F_orc
+    assert np.count_nonzero(s_orc) < o.N     # the l1 prox made the iterate sparse
+
+
+def test_spgm_host_buffers_match_device():
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    eta, lam = 0.01, 1e-4
+    perms = np.stack([I.epoch_permutation(o.P, 2, e) for e in range(3)]).astype(np.int32)
+    s_dev = to_dev(np.zeros(o.N))
+    y_dev = to_dev(y)
+    for e in range(3):
+        ctx.spgm_epoch(y_dev, s_dev, to_dev(perms[e], "int32"), 4, eta, lam)
+    s_host = np.zeros(o.N, dtype=np.complex64)
+    ctx.spgm_epochs_host(y.astype(np.complex64), s_host, perms, 4, eta, lam)
+    assert np.array_equal(s_host, s_dev.cpu().numpy())
+
+
+def test_spgm_mid_first_steps():
+    """Mid workload (N = 131072, 16 pairs x 64 frequencies per minibatch): first 3 SPGM steps."""
+    w = W.mid_T16R16_K64_64x64x32()
+    o = Oracle(w.geom)
+    y = _c64(I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db))
+    ctx = make_ctx(w.geom)
+    # step size from the GPU power iteration (checked separately on the small workload)
+    L = ctx.power_iteration(to_dev(_c64(I.complex_gaussian(o.N, w.seeds["power"]))), 20)
+    eta = float(np.float32(1.0 / L))
+    lam = float(np.float32(0.05 * ctx.lambda_max(to_dev(y))))
+    perm = I.epoch_permutation(o.P, w.seeds["perm"], 0)
+    s_orc = np.zeros(o.N, dtype=np.complex128)
+    s_gpu = to_dev(np.zeros(o.N))
+    y_dev = to_dev(y)
+    for c in range(3):
+        pairs = perm[16 * c:16 * (c + 1)]
+        s_orc = o.spgm_step(y, s_orc, pairs, eta, lam)
+        ctx.spgm_step(y_dev, s_gpu, to_dev(pairs, "int32"), eta, lam)
+        err = nmse(to_host(s_gpu), s_orc)
+        assert err <= NMSE_TOL, f"step {c}: NMSE {err:.3e}"
+
+
+# ---------------------------------------------------------------------------
+# errors
+# ---------------------------------------------------------------------------
+def test_out_of_range_pair_is_reported():
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    s = to_dev(np.zeros(o.N))
+    ctx.forward(to_dev(np.array([0, 16]), "int32"), s)
+    with pytest.raises(NfmError) as ei:
+        ctx.synchronize()
+    assert ei.value.code == -1
+    ctx.synchronize()    # flag cleared
+
+
+def test_invalid_geometry_rejected():
+    from paper_2509_00774_gb300.nfmimo import Context
+    w = W.small_T4R4_K16_16x16x8()
+    g = w.geom
+    ctx = Context(0)
+    bad_freq = I.Geometry(g.tx, g.rx, np.array([72e9, 73e9, 75e9]), g.grid)
+    too_many = I.Geometry(g.tx, g.rx, I.uniform_freqs(70e9, 80e9, 129), g.grid)
+    inside = I.Geometry(np.array([[0.0, 0.0, 0.27]]), g.rx, g.freq, g.grid)
+    for bad in (bad_freq, too_many, inside):
+        with pytest.raises(NfmError) as ei:
+            ctx.set_geometry(bad)
+        assert ei.value.code == -1
+    with pytest.raises(NfmError) as ei:
+        ctx.forward(to_dev(np.array([0]), "int32"), to_dev(np.zeros(g.N)))
+    assert ei.value.code == -4          # no geometry yet
+    ctx.set_geometry(g)
+    with pytest.raises(NfmError):
+        ctx.spgm_step(to_dev(np.zeros(g.M)), to_dev(np.zeros(g.N)), to_dev(np.array([0]), "int32"), -1.0, 0.1)
