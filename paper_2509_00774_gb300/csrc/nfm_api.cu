@@ -33,7 +33,7 @@ struct DevGuard {
 };
 
 struct FwdPlan {
-    int Pc, VS, nt, n_groups, n_slots, n_chunks, base, rem;
+    int VS, nt, n_groups, n_slots, n_chunks, base, rem;
     size_t smem;
     size_t partial_bytes;
 };
@@ -85,7 +85,7 @@ struct nfm_ctx {
     struct Pending { int kind, a, b; };
     std::vector<Pending> pending;
 
-    int fwd_occ[MAX_K1 + 1][9] = {};
+    int fwd_occ[MAX_K1 + 1] = {};
     bool fwd_attr[MAX_K1 + 1] = {};
     bool adj_attr[MAX_K1 + 1] = {};
 };
@@ -202,24 +202,23 @@ void prof_pair(nfm_ctx* ctx, int kind, int a, int b)
 int plan_forward(nfm_ctx* ctx, int n_pairs, FwdPlan* pl)
 {
     const int K1 = ctx->K1;
-    pl->Pc = n_pairs < 8 ? n_pairs : 8;
-    pl->VS = 256 / (pl->Pc * K1);
+    pl->VS = 256 / (FWD_PC * K1);
     if (pl->VS < 1) pl->VS = 1;
-    pl->nt = pl->Pc * K1 * pl->VS;
-    pl->smem = fwd_smem_bytes(K1, pl->Pc, pl->nt);
+    pl->nt = FWD_PC * K1 * pl->VS;
+    pl->smem = fwd_smem_bytes(K1, pl->nt);
     const void* fn = fwd_kernel_ptr(K1);
     if (!ctx->fwd_attr[K1]) {
         NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin));
         ctx->fwd_attr[K1] = true;
     }
     if (pl->smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "forward tile needs %zu B shared memory", pl->smem);
-    int& occ = ctx->fwd_occ[K1][pl->Pc];
+    int& occ = ctx->fwd_occ[K1];
     if (occ == 0) {
         NFM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, pl->nt, pl->smem));
         if (occ < 1) occ = 1;
     }
-    pl->n_groups = (n_pairs + pl->Pc - 1) / pl->Pc;
-    pl->n_slots = pl->n_groups * pl->Pc;
+    pl->n_groups = (n_pairs + FWD_PC - 1) / FWD_PC;
+    pl->n_slots = pl->n_groups * FWD_PC;
     long long G = (long long)ctx->num_sms * occ;
     long long nch = (G + pl->n_groups - 1) / pl->n_groups;
     if (nch < 1) nch = 1;
@@ -246,7 +245,6 @@ int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s
     a.s = s;
     a.partial = (float2*)ctx->d_partial;
     a.n_slots = pl.n_slots;
-    a.Pc = pl.Pc;
     a.VS = pl.VS;
     a.tiles_base = pl.base;
     a.tiles_rem = pl.rem;

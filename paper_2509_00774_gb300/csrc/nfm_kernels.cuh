@@ -10,8 +10,7 @@ struct FwdArgs {
     int n_pairs;
     const float2* s;         // [N]
     float2* partial;         // [n_chunks][n_slots][K]
-    int n_slots;             // n_groups * Pc
-    int Pc;                  // pairs per CTA
+    int n_slots;             // n_groups * FWD_PC
     int VS;                  // voxel subsets per CTA
     int tiles_base;          // chunk c owns tiles_base (+1 for c < tiles_rem) tiles
     int tiles_rem;
@@ -47,10 +46,11 @@ struct AntSetup {
     AntTile* out;            // [n_ant * n_tiles]
 };
 
-constexpr int ADJ_THREADS = 64;   // one 8x4x4 tile, two voxels per thread
-constexpr int ADJ_PCHUNK = 16;
+constexpr int FWD_PC = 8;         // pairs per forward CTA
+constexpr int ADJ_THREADS = 128;  // one 8x4x4 tile: two voxels per thread, pairs split in two halves
+constexpr int ADJ_PCHUNK = 32;
 
-size_t fwd_smem_bytes(int K1, int Pc, int nt);
+size_t fwd_smem_bytes(int K1, int nt);
 const void* fwd_kernel_ptr(int K1);
 const void* adj_kernel_ptr(int K1);
 size_t adj_smem_bytes(int K1, int pchunk);

@@ -177,6 +177,8 @@ class Context:
         import torch
         n = pairs.numel()
         if y is None:
+            if self.K is None:
+                raise NfmError(-4, "no geometry: call set_geometry first")
             y = torch.empty(n * self.K, dtype=torch.complex64, device=s.device)
         self._check(self._lib.nfm_forward(self._h, self._i(pairs, "pairs"), n, self._c(s, "s"), self._c(y, "y")))
         return y
@@ -186,6 +188,8 @@ class Context:
         import torch
         n = pairs.numel()
         if g is None:
+            if self.N is None:
+                raise NfmError(-4, "no geometry: call set_geometry first")
             g = torch.empty(self.N, dtype=torch.complex64, device=r.device)
         self._check(self._lib.nfm_adjoint(self._h, self._i(pairs, "pairs"), n, self._c(r, "r"), self._c(g, "g")))
         return g
