@@ -137,6 +137,30 @@ int nfm_lambda_max(nfm_ctx* ctx, const float* y, double* out);
 /* Wait for the context's stream and report device-side flags. */
 int nfm_synchronize(nfm_ctx* ctx);
 
+/* Allocation-free variant of nfm_forward.  The paper has no counterpart; this
+ * entry point exists for callers that cannot call cudaMalloc once they are
+ * running: a reconstruction loop with a fixed device-memory budget that must
+ * not grow after start-up, a process whose device memory is handed out by
+ * another allocator, or a latency-bound caller that cannot accept the device
+ * synchronisation cudaMalloc/cudaFree can imply.  nfm_forward keeps its chunk
+ * partial sums in library-owned scratch that grows with cudaMalloc; this call
+ * keeps them instead in one statically sized device array that is part of the
+ * loaded library (4 MiB, held on every GPU that loads the library until the
+ * process exits), and it allocates nothing.
+ *   Arguments, layout and result are those of nfm_forward (y = A_B s).
+ *   Limit: n_pairs * K <= 524288 (the scratch holds 524288 complex64 partial
+ *   sums; fewer voxel chunks are used when the usual plan does not fit).  A
+ *   larger request returns NFM_ERR_ARG and enqueues nothing.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   All calls in the process share the one array per device and it keeps the
+ *   previous call's contents; every partial sum a call reads is written by the
+ *   same call, so nothing has to start at zero.  Calls whose work overlaps on
+ *   the GPU (different streams or contexts on one device) race on the array
+ *   and give wrong results: order them, e.g. on one stream. */
+int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, float* y);
+
 /* Kernel timing (tracing aid, not part of the paper's method).  While enabled,
  * every kernel the operator entry points enqueue is bracketed by a pair of
  * CUDA events on the context stream.  nfm_profile_report synchronises, adds up

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -735,3 +736,85 @@ int nfm_profile_report(nfm_ctx* ctx, double* ms_out, long long* launches_out, in
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free forward: the chunk partial sums live in a static device
+// array instead of library-owned cudaMalloc scratch.  Nothing here allocates.
+namespace {
+constexpr size_t NOALLOC_SCRATCH_ELEMS = (size_t)1 << 19;   // complex64 partial sums, 4 MiB
+constexpr int NOALLOC_MAX_DEVICES = 64;
+}  // namespace
+
+static __device__ __align__(256) float2 g_noalloc_scratch[NOALLOC_SCRATCH_ELEMS];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on ctx->device (looked up once per
+// device, with that device current; the caller holds a DevGuard).
+int noalloc_scratch(nfm_ctx* ctx, float2** out)
+{
+    if (ctx->device < 0 || ctx->device >= NOALLOC_MAX_DEVICES)
+        return fail(ctx, NFM_ERR_ARG, "device %d: the allocation-free path supports devices 0..%d", ctx->device,
+                    NOALLOC_MAX_DEVICES - 1);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[ctx->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ctx, NFM_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        g_noalloc_addr[ctx->device] = p;
+    }
+    *out = (float2*)g_noalloc_addr[ctx->device];
+    return NFM_OK;
+}
+}  // namespace
+
+extern "C" int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, float* y)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
+    NFM_TRY(check_ptr(ctx, pairs, "pairs", 4));
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    if ((size_t)n_pairs * ctx->K > NOALLOC_SCRATCH_ELEMS)
+        return fail(ctx, NFM_ERR_ARG, "n_pairs * K = %lld exceeds the allocation-free limit %zu",
+                    (long long)n_pairs * ctx->K, NOALLOC_SCRATCH_ELEMS);
+    FwdPlan pl;
+    NFM_TRY(plan_forward(ctx, n_pairs, &pl));
+    const size_t per_chunk = (size_t)pl.n_slots * ctx->K;
+    if (per_chunk > NOALLOC_SCRATCH_ELEMS)
+        return fail(ctx, NFM_ERR_ARG, "%zu partial sums per voxel chunk exceed the allocation-free limit %zu",
+                    per_chunk, NOALLOC_SCRATCH_ELEMS);
+    const size_t max_chunks = NOALLOC_SCRATCH_ELEMS / per_chunk;
+    if ((size_t)pl.n_chunks > max_chunks) {
+        pl.n_chunks = (int)max_chunks;
+        pl.base = ctx->gd.n_tiles / pl.n_chunks;
+        pl.rem = ctx->gd.n_tiles % pl.n_chunks;
+    }
+    float2* scratch = nullptr;
+    NFM_TRY(noalloc_scratch(ctx, &scratch));
+    OpDesc op = op_desc(ctx);
+    FwdArgs a;
+    a.pairs = pairs;
+    a.n_pairs = n_pairs;
+    a.s = (const float2*)s;
+    a.partial = scratch;
+    a.n_slots = pl.n_slots;
+    a.VS = pl.VS;
+    a.tiles_base = pl.base;
+    a.tiles_rem = pl.rem;
+    NFM_CK(launch_fwd_partial(op, a, dim3(pl.n_groups, pl.n_chunks), pl.nt, pl.smem, ctx->stream));
+    ReduceArgs ra;
+    ra.partial = scratch;
+    ra.n_chunks = pl.n_chunks;
+    ra.n_slots = pl.n_slots;
+    ra.n_out = n_pairs * ctx->K;
+    ra.pairs = pairs;
+    ra.y_obs = nullptr;
+    ra.out = (float2*)y;
+    NFM_CK(launch_fwd_reduce(op, ra, ctx->stream));
+    return NFM_OK;
+}

@@ -55,6 +55,7 @@ def load_library(path: str | None = None):
         "nfm_dims": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                          ctypes.POINTER(ctypes.c_longlong)]),
         "nfm_forward": (i, [vp, vp, i, vp, vp]),
+        "nfm_forward_noalloc": (i, [vp, vp, i, vp, vp]),
         "nfm_adjoint": (i, [vp, vp, i, vp, vp]),
         "nfm_spgm_step": (i, [vp, vp, vp, vp, i, f, f]),
         "nfm_spgm_epoch": (i, [vp, vp, vp, vp, i, f, f]),
@@ -181,6 +182,12 @@ class Context:
                 raise NfmError(-4, "no geometry: call set_geometry first")
             y = torch.empty(n * self.K, dtype=torch.complex64, device=s.device)
         self._check(self._lib.nfm_forward(self._h, self._i(pairs, "pairs"), n, self._c(s, "s"), self._c(y, "y")))
+        return y
+
+    def forward_noalloc(self, pairs, s, y):
+        """y = A_B s through the allocation-free entry point (y must be given; nothing is allocated)."""
+        self._check(self._lib.nfm_forward_noalloc(self._h, self._i(pairs, "pairs"), pairs.numel(),
+                                                  self._c(s, "s"), self._c(y, "y")))
         return y
 
     def adjoint(self, pairs, r, g=None):
