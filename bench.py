@@ -269,8 +269,6 @@ def run_ours(args):
         time.sleep(0.3)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ctx.profile_enable(True)
-        ctx.profile_report()
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -282,6 +280,14 @@ def run_ours(args):
             ends[k].record(stream)
         torch.cuda.synchronize()
         sampler.mark()
+        # kernel timing pass: the same epochs with every kernel bracketed by events
+        # (kept out of the timed region above because the events add gaps)
+        ctx.profile_enable(True)
+        ctx.profile_report()
+        prof_steps = max(1, min(args.steps, 20))
+        for k in range(prof_steps):
+            flush.fill_(float(k))
+            ctx.spgm_epoch(y, s, perms_d[args.warmup + k], bp, eta, lam)
         prof = ctx.profile_report()
         ctx.profile_enable(False)
         time.sleep(0.25)
@@ -344,8 +350,10 @@ def run_ours(args):
                 "traffic": traffic_for(kname),
                 "peak_source": f"FP32 FMA lanes: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} x 2 flops x "
                                f"{sm_mhz:.0f} MHz (sm_max_mhz, {peak_src})",
-                "work": f"{FLOPS_PER_PAIR:.0f} flops (one complex MAC) per (row, voxel) pair, {elems} pairs per launch"}
+                "work": f"{FLOPS_PER_PAIR:.0f} flops (one complex MAC) per (row, voxel) pair, {elems} pairs per launch",
+                "timing": f"CUDA events around every launch over {prof_steps} epochs run right after the timed region"}
     launches = sum(kernels.get(k, {}).get("launches", 0) for k in ("forward_partial", "forward_reduce", "adjoint"))
+    launches = launches * args.steps // prof_steps      # per timed region (same kernels every epoch)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -203,9 +203,8 @@ void prof_pair(nfm_ctx* ctx, int kind, int a, int b)
 int plan_forward(nfm_ctx* ctx, int n_pairs, FwdPlan* pl)
 {
     const int K1 = ctx->K1;
-    pl->VS = 256 / (FWD_PC * K1);
-    if (pl->VS < 1) pl->VS = 1;
-    pl->nt = FWD_PC * K1 * pl->VS;
+    pl->VS = 32 / K1;            // voxel subsets per warp; one warp per pair
+    pl->nt = 32 * FWD_PC;
     pl->smem = fwd_smem_bytes(K1, pl->nt);
     const void* fn = fwd_kernel_ptr(K1);
     if (!ctx->fwd_attr[K1]) {

@@ -39,12 +39,13 @@ struct __align__(16) AntTile {
 };
 
 // Per (pair, tile) constants: the TX and RX AntTile folded together.
-struct PairTile {
+struct __align__(16) PairTile {
     float vTx, vTy, vTz, dcT, dcT2;
     float vRx, vRy, vRz, dcR, dcR2;
     float B;               // frac(f0 D_c / c)
     float S_hi, S_lo;      // frac(df D_c / c)
     float S2_hi, S2_lo;    // frac(K2 df D_c / c)
+    float pad;
 };
 
 struct GridDesc {
@@ -102,6 +103,16 @@ __device__ __forceinline__ float2 cis_turns(float t)
     return make_float2(co, si);
 }
 
+// (cos 2 pi t, sin 2 pi t) for |t| <= 1/2 from the SFU sine/cosine
+// approximations (absolute error about 4e-7 on [-pi, pi]).  Used only where the
+// phasor starts a sequence and its error is not amplified by a recurrence.
+__device__ __forceinline__ float2 cis_turns_sfu(float t)
+{
+    float s, c;
+    __sincosf(6.28318530717958648f * t, &s, &c);
+    return make_float2(c, s);
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -124,6 +135,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 __device__ __forceinline__ PairTile fold_pair_tile(const AntTile& t, const AntTile& r)
 {
     PairTile p;
+    p.pad = 0.f;
     p.vTx = t.vx; p.vTy = t.vy; p.vTz = t.vz; p.dcT = t.dc; p.dcT2 = t.dc2;
     p.vRx = r.vx; p.vRy = r.vy; p.vRz = r.vz; p.dcR = r.dc; p.dcR2 = r.dc2;
     p.B = frac_turns(t.b + r.b);
@@ -138,7 +150,7 @@ __device__ __forceinline__ PairTile fold_pair_tile(const AntTile& t, const AntTi
 }
 
 // Position of a voxel relative to its tile centre, from its local index.
-struct VoxelOffset {
+struct __align__(16) VoxelOffset {
     float ux, uy, uz, uu;
 };
 
@@ -198,6 +210,41 @@ __device__ __forceinline__ void tile_coords(const GridDesc& g, int tile, int& tx
     int rest = tile / g.tiles_x;
     ty = rest % g.tiles_y;
     tz = rest / g.tiles_y;
+}
+
+// Programmatic dependent launch: wait until the preceding kernel in the stream
+// has completed and its writes are visible (no-op without the launch attribute),
+// and let the next kernel begin launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Asynchronous global -> shared copies (completion tracked per thread).
+__device__ __forceinline__ void cp_async_8(void* smem_dst, const void* gmem_src, bool valid)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    int n = valid ? 8 : 0;   // 0 source bytes: the destination is zero-filled
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem_src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Row of the AntTile table for (pair, tile): TX row and RX row.  An
+// out-of-range pair raises the flag and falls back to pair 0.
+__device__ __forceinline__ void pair_rows(const OpDesc& op, int pair, int tile, const AntTile*& at, const AntTile*& ar)
+{
+    if (pair < 0 || pair >= op.P) {
+        atomicOr(op.err, ERRF_PAIR);
+        pair = 0;
+    }
+    int t = pair / op.R;
+    int r = pair - t * op.R;
+    at = op.ant + (size_t)t * op.g.n_tiles + tile;
+    ar = op.ant + (size_t)(op.T + r) * op.g.n_tiles + tile;
 }
 
 // Load the (pair, tile) constants; an out-of-range pair raises the flag and

@@ -51,6 +51,24 @@ constexpr int ADJ_THREADS = 128;  // one 8x4x4 tile: two voxels per thread, pair
 constexpr int ADJ_PCHUNK = 32;
 
 size_t fwd_smem_bytes(int K1, int nt);
+
+// Launch with programmatic stream serialisation (the kernel may start while the
+// previous kernel in the stream finishes; it calls pdl_wait() before reading
+// that kernel's results).
+inline cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void** args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
 const void* fwd_kernel_ptr(int K1);
 const void* adj_kernel_ptr(int K1);
 size_t adj_smem_bytes(int K1, int pchunk);

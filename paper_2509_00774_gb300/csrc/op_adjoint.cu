@@ -30,10 +30,10 @@ __device__ __forceinline__ AdjPhasors adj_phasors(const PairTile& P, const Voxel
 {
     const PVGeom G = pair_voxel(P, o, ph);
     AdjPhasors f;
-    const float2 c = cis_turns(G.th0);
+    const float2 c = cis_turns_sfu(G.th0);
     f.a = make_float2(G.amp * c.x, G.amp * c.y);
     f.z = cis_turns(G.dth);
-    f.Z = K1 > 1 ? cis_turns(G.dth2) : make_float2(1.f, 0.f);
+    f.Z = K1 > 1 ? cis_turns_sfu(G.dth2) : make_float2(1.f, 0.f);
     return f;
 }
 
@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(OpDesc op, AdjArgs a)
     constexpr int KB = K1 * K2;
 
     float2 g0 = make_float2(0.f, 0.f), g1 = make_float2(0.f, 0.f);
+    pdl_wait();                              // r comes from the previous kernel
 
     for (int c0 = 0; c0 < a.n_pairs; c0 += a.pchunk) {
         const int nc = min(a.pchunk, a.n_pairs - c0);
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(OpDesc op, AdjArgs a)
     }
 
     // combine the two pair halves in a fixed order, then the epilogue
+    pdl_launch_dependents();
     __syncthreads();
     float2* comb = reinterpret_cast<float2*>(smem);   // [64][2]
     if (half == 1) {
@@ -198,19 +200,10 @@ const void* adj_kernel_ptr(int K1)
 
 cudaError_t launch_adjoint(const OpDesc& op, const AdjArgs& a, size_t smem, cudaStream_t st)
 {
-    dim3 grid(op.g.n_tiles);
-    switch (op.K1) {
-    case 1: adj_kernel<1><<<grid, ADJ_THREADS, smem, st>>>(op, a); break;
-    case 2: adj_kernel<2><<<grid, ADJ_THREADS, smem, st>>>(op, a); break;
-    case 3: adj_kernel<3><<<grid, ADJ_THREADS, smem, st>>>(op, a); break;
-    case 4: adj_kernel<4><<<grid, ADJ_THREADS, smem, st>>>(op, a); break;
-    case 5: adj_kernel<5><<<grid, ADJ_THREADS, smem, st>>>(op, a); break;
-    case 6: adj_kernel<6><<<grid, ADJ_THREADS, smem, st>>>(op, a); break;
-    case 7: adj_kernel<7><<<grid, ADJ_THREADS, smem, st>>>(op, a); break;
-    case 8: adj_kernel<8><<<grid, ADJ_THREADS, smem, st>>>(op, a); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    const void* fn = adj_kernel_ptr(op.K1);
+    if (!fn) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&op, (void*)&a};
+    return launch_pdl(fn, dim3(op.g.n_tiles), dim3(ADJ_THREADS), smem, st, args);
 }
 
 }  // namespace nfm

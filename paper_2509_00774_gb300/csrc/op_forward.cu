@@ -5,39 +5,99 @@
 // [FWD_PC][K] for its chunk; fwd_reduce_kernel sums the chunks in a fixed
 // order, so the result does not depend on scheduling.
 //
-// Per tile the CTA
-//  1. stages s for the tile's voxels and the Pc (pair, tile) constants,
-//  2. for every (voxel, pair) builds the block start values
+// The CTA walks its tiles in stages of half a tile (64 voxels).  For a stage
+// it loads s and the FWD_PC (pair, tile) constants, then builds for every
+// (voxel, pair) the block start values
 //        U[k1] = amp s exp(-j 2 pi (f0 + k1 K2 df) D / c)      (k1 < K1)
-//     and the fine step w = exp(-j 2 pi df D / c) in shared memory,
-//  3. thread (pair, k1, vs) walks its voxels two at a time and accumulates
-//     the K2 frequencies of block k1 with the recurrence t <- t w (6 FP32
-//     lane-instructions per (row, voxel) element).
+// and the fine step w = exp(-j 2 pi df D / c) in shared memory.  Warp p
+// (one pair) then walks the stage's voxels, lane (k1, vs) two voxels at a
+// time, and accumulates the K2 frequencies of block k1.  The terms u w^k come
+// from the real-coefficient recurrence t_{k+1} = 2 cos(theta) t_k - t_{k-1}
+// (4 FP32 lane-instructions per (row, voxel) element with the accumulation).
+// That recurrence amplifies rounding by 1/|sin theta|, so for (pair, tile)
+// whose step phase lies within 1/8 turn of 0 or 1/2 the sequence is generated
+// with w' = -j w (a quarter turn more per step) and the factor j^k is undone
+// exactly by permuting real and imaginary parts in the accumulation.  Stages
+// are software pipelined with one barrier each: iteration q loads stage q+2,
+// builds stage q+1 and consumes stage q, so every warp shares both kinds of work.
 #include "nfm_kernels.cuh"
 
 namespace nfm {
+
+constexpr int FWD_SV = TILE_V / 2;   // voxels per stage: half a tile (8 x 4 x 2)
+
+// Shared-memory layout of one stage buffer: U [SV][VSTR] with U[v][pair][k1]
+// at v*VSTR + pair*K1 + k1, then W [SV][PC+1].  VSTR = 9 K1 puts the K1-wide
+// groups a warp reads for consecutive voxels on distinct banks.
+template <int K1>
+struct FwdSmem {
+    static constexpr int VSTR = 9 * K1;
+    static constexpr int WSTR = FWD_PC + 1;
+    static constexpr int BUF = FWD_SV * VSTR + FWD_SV * WSTR;
+};
+
+// acc[k] += i^k t (rotated frame) or acc[k] += t, for k = j mod 4.
+template <bool ROT, int J>
+__device__ __forceinline__ void acc_add(float2& acc, float tx, float ty)
+{
+    if (!ROT || (J & 3) == 0) { acc.x += tx; acc.y += ty; }
+    else if ((J & 3) == 1) { acc.x -= ty; acc.y += tx; }
+    else if ((J & 3) == 2) { acc.x -= tx; acc.y -= ty; }
+    else { acc.x += ty; acc.y -= tx; }
+}
+
+// K2 terms of u w'^k for two voxels a, b by the real three-term recurrence
+// t_{k+1} = 2 cos(theta') t_k - t_{k-1} (w' = exp(-j theta'), |w'| = 1).
+template <bool ROT>
+__device__ __forceinline__ void run_block(float2 (&acc)[K2], float2 ta0, float2 wa, float2 tb0, float2 wb)
+{
+    const float ca = 2.0f * wa.x, cb = 2.0f * wb.x;
+    float2 ta1 = cmul(ta0, wa), tb1 = cmul(tb0, wb);
+    acc_add<ROT, 0>(acc[0], ta0.x + tb0.x, ta0.y + tb0.y);
+    acc_add<ROT, 1>(acc[1], ta1.x + tb1.x, ta1.y + tb1.y);
+#pragma unroll
+    for (int j = 2; j < K2; ++j) {
+        const float2 ta2 = make_float2(fmaf(ca, ta1.x, -ta0.x), fmaf(ca, ta1.y, -ta0.y));
+        const float2 tb2 = make_float2(fmaf(cb, tb1.x, -tb0.x), fmaf(cb, tb1.y, -tb0.y));
+        const float sx = ta2.x + tb2.x, sy = ta2.y + tb2.y;
+        switch (j & 3) {
+        case 0: acc_add<ROT, 0>(acc[j], sx, sy); break;
+        case 1: acc_add<ROT, 1>(acc[j], sx, sy); break;
+        case 2: acc_add<ROT, 2>(acc[j], sx, sy); break;
+        default: acc_add<ROT, 3>(acc[j], sx, sy); break;
+        }
+        ta0 = ta1; ta1 = ta2;
+        tb0 = tb1; tb1 = tb2;
+    }
+}
 
 template <int K1>
 __global__ void __launch_bounds__(256, 3) fwd_partial_kernel(OpDesc op, FwdArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int PC = FWD_PC;
-    const int VS = a.VS;
-    const int nt = blockDim.x;
+    constexpr int SV = FWD_SV;
+    constexpr int VSTR = FwdSmem<K1>::VSTR;
+    constexpr int WSTR = FwdSmem<K1>::WSTR;
+    constexpr int BUF = FwdSmem<K1>::BUF;
+    constexpr int VS = 32 / K1;             // voxel subsets per warp (lanes beyond VS*K1 idle)
+    const int nt = blockDim.x;              // 256: one warp per pair of the group
     const int tid = threadIdx.x;
     const int group = blockIdx.x;
     const int chunk = blockIdx.y;
 
-    float2* U = reinterpret_cast<float2*>(smem);          // [TILE_V][K1][PC]
-    float2* Wf = U + TILE_V * PC * K1;                    // [TILE_V][PC]
-    float2* s_t = Wf + TILE_V * PC;                       // [TILE_V]
-    PairTile* pt = reinterpret_cast<PairTile*>(s_t + TILE_V);   // [PC]
-    int* pair_s = reinterpret_cast<int*>(pt + PC);        // [PC]
+    float2* ubuf = reinterpret_cast<float2*>(smem);                     // [2][BUF]
+    VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(ubuf + 2 * BUF);  // [TILE_V]
+    AntTile* ant_st = reinterpret_cast<AntTile*>(voff + TILE_V);        // [3][PC][2] (TX, RX)
+    float2* s_st = reinterpret_cast<float2*>(ant_st + 3 * PC * 2);      // [3][SV]
+    int* pair_s = reinterpret_cast<int*>(s_st + 3 * SV);                // [PC]
+    int* rot_s = pair_s + PC;                                           // [2][PC]
 
-    // main-loop role: pair fastest so a warp reads 32 consecutive U entries
-    const int p = tid % PC;
-    const int k1 = (tid / PC) % K1;
-    const int vs = tid / (PC * K1);
+    // consume role: warp = pair, lane = (k1, voxel subset)
+    const int p = tid / 32;
+    const int lane = tid % 32;
+    const int k1 = lane % K1;
+    const int vs = lane / K1;
 
     float2 acc[K2];
 #pragma unroll
@@ -45,99 +105,138 @@ __global__ void __launch_bounds__(256, 3) fwd_partial_kernel(OpDesc op, FwdArgs 
 
     const int t_begin = chunk * a.tiles_base + min(chunk, a.tiles_rem);
     const int t_end = t_begin + a.tiles_base + (chunk < a.tiles_rem ? 1 : 0);
+    const int q0 = 2 * t_begin;             // stage = (tile, half)
+    const int nq = 2 * (t_end - t_begin);
 
+    for (int v = tid; v < TILE_V; v += nt)
+        voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
+    pdl_wait();                              // s and pairs may come from the previous kernel
     if (tid < PC) {
         int slot = group * PC + tid;
         pair_s[tid] = slot < a.n_pairs ? a.pairs[slot] : -1;
     }
+    __syncthreads();
 
-    for (int tile = t_begin; tile < t_end; ++tile) {
+    // asynchronous loads of a stage: its s values and the two AntTile rows per pair
+    auto load_small = [&](int q) {
+        const int sidx = q0 + q;
+        const int tile = sidx >> 1, half = sidx & 1;
         int tx, ty, tz;
         tile_coords(op.g, tile, tx, ty, tz);
-        __syncthreads();   // previous tile fully consumed; pair_s visible
-        for (int v = tid; v < TILE_V; v += nt) {
-            int lx = v % TILE_X, ly = (v / TILE_X) % TILE_Y, lz = v / (TILE_X * TILE_Y);
+        float2* sb = s_st + (q % 3) * SV;
+        for (int v = tid; v < SV; v += nt) {
+            int lx = v % TILE_X, ly = (v / TILE_X) % TILE_Y, lz = v / (TILE_X * TILE_Y) + 2 * half;
             int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
-            float2 sv = make_float2(0.f, 0.f);
-            if (ix < op.g.nx && iy < op.g.ny && iz < op.g.nz)
-                sv = a.s[((size_t)iz * op.g.ny + iy) * op.g.nx + ix];
-            s_t[v] = sv;
+            bool in = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
+            const float2* src = in ? a.s + ((size_t)iz * op.g.ny + iy) * op.g.nx + ix : a.s;
+            cp_async_8(sb + v, src, in);
         }
-        if (tid < PC) {
-            int pair = pair_s[tid];
-            pt[tid] = load_pair_tile(op, pair < 0 ? 0 : pair, tile);
+        if (tid < PC * 6) {                   // 2 rows x 48 B = 6 chunks of 16 B per pair
+            const int i = tid / 6, part = tid % 6;
+            const int pair = pair_s[i];
+            const AntTile *at, *ar;
+            pair_rows(op, pair < 0 ? 0 : pair, tile, at, ar);
+            const AntTile* src = part < 3 ? at : ar;
+            AntTile* dst = ant_st + ((q % 3) * PC + i) * 2 + (part < 3 ? 0 : 1);
+            cp_async_16(reinterpret_cast<float4*>(dst) + part % 3, reinterpret_cast<const float4*>(src) + part % 3);
         }
-        __syncthreads();
-        // staging: item = v * PC + i
+        cp_async_commit();
+    };
+
+    // block start values U[k1] and the step w' of every (voxel, pair) of a stage;
+    // w' is w turned by a quarter turn per step when the pair's step phase is
+    // near 0 or 1/2 turn, so the recurrence never divides by a small sine
+    auto stage = [&](int q) {
+        const int half = (q0 + q) & 1;
+        float2* U = ubuf + (q & 1) * BUF;
+        float2* Wf = U + SV * VSTR;
+        const float2* sb = s_st + (q % 3) * SV;
+        const int i = tid % PC;                      // every item of this thread has pair i
+        const bool live = pair_s[i] >= 0;
+        const AntTile* aq = ant_st + ((q % 3) * PC + i) * 2;
+        const PairTile P = fold_pair_tile(aq[0], aq[1]);
+        const float sa = fabsf(P.S_hi);
+        const bool rot = sa < 0.125f || sa > 0.375f;
+        if (tid < PC) rot_s[(q & 1) * PC + i] = rot;
 #pragma unroll 2
-        for (int item = tid; item < TILE_V * PC; item += nt) {
-            const int i = item % PC;
+        for (int item = tid; item < SV * PC; item += nt) {
             const int v = item / PC;
-            float2* Up = U + v * (K1 * PC) + i;
-            if (pair_s[i] < 0) {
+            float2* Up = U + v * VSTR + i * K1;
+            if (!live) {
 #pragma unroll
-                for (int j = 0; j < K1; ++j) Up[j * PC] = make_float2(0.f, 0.f);
-                Wf[item] = make_float2(1.f, 0.f);
+                for (int j = 0; j < K1; ++j) Up[j] = make_float2(0.f, 0.f);
+                Wf[v * WSTR + i] = make_float2(1.f, 0.f);
                 continue;
             }
-            const int lx = v % TILE_X, ly = (v / TILE_X) % TILE_Y, lz = v / (TILE_X * TILE_Y);
-            const float2 sv = s_t[v];
-            const VoxelOffset o = voxel_offset(op.g, lx, ly, lz);
-            const PVGeom gv = pair_voxel(pt[i], o, op.ph);
-            const float2 c0 = cis_turns(gv.th0);
+            const float2 sv = sb[v];
+            const VoxelOffset o = voff[v + SV * half];
+            const PVGeom gv = pair_voxel(P, o, op.ph);
+            const float2 c0 = cis_turns_sfu(gv.th0);
             const float2 cw = cis_turns(gv.dth);
             float2 u = cmul_conj(make_float2(gv.amp * sv.x, gv.amp * sv.y), c0);
             Up[0] = u;
             if (K1 > 1) {
-                const float2 cW = cis_turns(gv.dth2);
+                const float2 cW = cis_turns_sfu(gv.dth2);
                 const float2 Wc = make_float2(cW.x, -cW.y);
 #pragma unroll
                 for (int j = 1; j < K1; ++j) {
                     u = cmul(u, Wc);
-                    Up[j * PC] = u;
+                    Up[j] = u;
                 }
             }
-            Wf[item] = make_float2(cw.x, -cw.y);
+            // w = (c, -s); turned: -j w = (-s, -c)
+            Wf[v * WSTR + i] = rot ? make_float2(-cw.y, -cw.x) : make_float2(cw.x, -cw.y);
         }
+    };
+
+    // three-term recurrence over the K2 frequencies of block k1, two voxels at a time
+    auto consume = [&](int q) {
+        if (vs >= VS) return;
+        const float2* U = ubuf + (q & 1) * BUF;
+        const float2* Wf = U + SV * VSTR;
+        const bool rot = rot_s[(q & 1) * PC + p] != 0;   // warp-uniform
+        int v = vs;
+        for (; v + VS < SV; v += 2 * VS) {
+            const float2 ta = U[v * VSTR + p * K1 + k1];
+            const float2 wa = Wf[v * WSTR + p];
+            const float2 tb = U[(v + VS) * VSTR + p * K1 + k1];
+            const float2 wb = Wf[(v + VS) * WSTR + p];
+            if (rot) run_block<true>(acc, ta, wa, tb, wb);
+            else run_block<false>(acc, ta, wa, tb, wb);
+        }
+        if (v < SV) {
+            const float2 ta = U[v * VSTR + p * K1 + k1];
+            const float2 wa = Wf[v * WSTR + p];
+            const float2 zero = make_float2(0.f, 0.f), one = make_float2(1.f, 0.f);
+            if (rot) run_block<true>(acc, ta, wa, zero, one);
+            else run_block<false>(acc, ta, wa, zero, one);
+        }
+    };
+
+    // pipeline: iteration q loads stage q+2, builds stage q+1, consumes stage q
+    if (nq > 0) {
+        load_small(0);
+        if (nq > 1) load_small(1);
+        cp_async_wait_all();
         __syncthreads();
-        // main loop: two voxels per step for two independent recurrences
-        if (vs < VS) {
-            int v = vs;
-            for (; v + VS < TILE_V; v += 2 * VS) {
-                float2 t0 = U[v * (K1 * PC) + k1 * PC + p];
-                float2 w0 = Wf[v * PC + p];
-                float2 t1 = U[(v + VS) * (K1 * PC) + k1 * PC + p];
-                float2 w1 = Wf[(v + VS) * PC + p];
-#pragma unroll
-                for (int j = 0; j < K2; ++j) {
-                    acc[j].x += t0.x + t1.x;
-                    acc[j].y += t0.y + t1.y;
-                    if (j + 1 < K2) {
-                        t0 = cmul(t0, w0);
-                        t1 = cmul(t1, w1);
-                    }
-                }
-            }
-            if (v < TILE_V) {
-                float2 t0 = U[v * (K1 * PC) + k1 * PC + p];
-                float2 w0 = Wf[v * PC + p];
-#pragma unroll
-                for (int j = 0; j < K2; ++j) {
-                    acc[j].x += t0.x;
-                    acc[j].y += t0.y;
-                    if (j + 1 < K2) t0 = cmul(t0, w0);
-                }
-            }
+        stage(0);
+        __syncthreads();
+        for (int q = 0; q < nq; ++q) {
+            if (q + 2 < nq) load_small(q + 2);
+            if (q + 1 < nq) stage(q + 1);
+            consume(q);
+            cp_async_wait_all();
+            __syncthreads();
         }
     }
+    pdl_launch_dependents();
 
     // reduce the VS voxel subsets in a fixed order, then write the partial
-    __syncthreads();
-    float2* red = reinterpret_cast<float2*>(smem);        // [VS][PC][K1*K2]
+    float2* red = reinterpret_cast<float2*>(smem);        // [PC][VS][K1*K2]
     constexpr int KB = K1 * K2;
     if (vs < VS) {
 #pragma unroll
-        for (int j = 0; j < K2; ++j) red[((vs * PC + p) * K1 + k1) * K2 + j] = acc[j];
+        for (int j = 0; j < K2; ++j) red[((p * VS + vs) * K1 + k1) * K2 + j] = acc[j];
     }
     __syncthreads();
     for (int o = tid; o < PC * KB; o += nt) {
@@ -145,9 +244,9 @@ __global__ void __launch_bounds__(256, 3) fwd_partial_kernel(OpDesc op, FwdArgs 
         int kk = o - i * KB;
         int slot = group * PC + i;
         if (kk >= op.K || slot >= a.n_pairs) continue;
-        float2 sum = red[i * KB + kk];
+        float2 sum = red[(i * VS) * KB + kk];
         for (int u = 1; u < VS; ++u) {
-            float2 x = red[(u * PC + i) * KB + kk];
+            float2 x = red[(i * VS + u) * KB + kk];
             sum.x += x.x;
             sum.y += x.y;
         }
@@ -157,9 +256,9 @@ __global__ void __launch_bounds__(256, 3) fwd_partial_kernel(OpDesc op, FwdArgs 
 
 size_t fwd_smem_bytes(int K1, int nt)
 {
-    const int Pc = FWD_PC;
-    size_t stage = (size_t)TILE_V * Pc * (K1 + 1) * sizeof(float2) + TILE_V * sizeof(float2) +
-                   (size_t)Pc * sizeof(PairTile) + (size_t)Pc * sizeof(int);
+    const size_t buf = (size_t)FWD_SV * 9 * K1 + FWD_SV * (FWD_PC + 1);
+    size_t stage = 2 * buf * sizeof(float2) + TILE_V * sizeof(VoxelOffset) + 3 * FWD_PC * 2 * sizeof(AntTile) +
+                   3 * FWD_SV * sizeof(float2) + 3 * FWD_PC * sizeof(int);
     size_t red = (size_t)nt * K2 * sizeof(float2);
     return stage > red ? stage : red;
 }
@@ -182,18 +281,10 @@ const void* fwd_kernel_ptr(int K1)
 cudaError_t launch_fwd_partial(const OpDesc& op, const FwdArgs& a, dim3 grid, int nt, size_t smem,
                                cudaStream_t st)
 {
-    switch (op.K1) {
-    case 1: fwd_partial_kernel<1><<<grid, nt, smem, st>>>(op, a); break;
-    case 2: fwd_partial_kernel<2><<<grid, nt, smem, st>>>(op, a); break;
-    case 3: fwd_partial_kernel<3><<<grid, nt, smem, st>>>(op, a); break;
-    case 4: fwd_partial_kernel<4><<<grid, nt, smem, st>>>(op, a); break;
-    case 5: fwd_partial_kernel<5><<<grid, nt, smem, st>>>(op, a); break;
-    case 6: fwd_partial_kernel<6><<<grid, nt, smem, st>>>(op, a); break;
-    case 7: fwd_partial_kernel<7><<<grid, nt, smem, st>>>(op, a); break;
-    case 8: fwd_partial_kernel<8><<<grid, nt, smem, st>>>(op, a); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    const void* fn = fwd_kernel_ptr(op.K1);
+    if (!fn) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&op, (void*)&a};
+    return launch_pdl(fn, grid, dim3(nt), smem, st, args);
 }
 
 // Sum the chunk partials in chunk order (fixed), apply p(f_k), and optionally
@@ -203,6 +294,7 @@ __global__ void __launch_bounds__(1024) fwd_reduce_kernel(OpDesc op, ReduceArgs 
     __shared__ float2 red[32][33];
     const int o = blockIdx.x * 32 + threadIdx.x;
     const size_t stride = (size_t)a.n_slots * op.K;
+    pdl_wait();
     float2 s = make_float2(0.f, 0.f);
     if (o < a.n_out) {
         // chunk lane y sums chunks y, y+32, ... (four loads in flight, fixed order)
@@ -244,14 +336,15 @@ __global__ void __launch_bounds__(1024) fwd_reduce_kernel(OpDesc op, ReduceArgs 
         }
         a.out[o] = t;
     }
+    pdl_launch_dependents();
 }
 
 cudaError_t launch_fwd_reduce(const OpDesc& op, const ReduceArgs& a, cudaStream_t st)
 {
     dim3 block(32, 32);
     dim3 grid((a.n_out + 31) / 32);
-    fwd_reduce_kernel<<<grid, block, 0, st>>>(op, a);
-    return cudaGetLastError();
+    void* args[] = {(void*)&op, (void*)&a};
+    return launch_pdl((const void*)fwd_reduce_kernel, grid, block, 0, st, args);
 }
 
 }  // namespace nfm

@@ -52,6 +52,7 @@ def assert_close_operator(got, want, what="", scale=None):
     rel = np.linalg.norm(err) / np.linalg.norm(ref)
     rms = np.linalg.norm(ref) / np.sqrt(ref.size)
     worst = np.max(np.abs(err)) / rms
+    print(f"[parity] {what}: n={err.size} rel_l2={rel:.2e} worst/rms={worst:.2e}")
     assert rel <= REL_L2, f"{what}: relative l2 error {rel:.3e} > {REL_L2:.0e}"
     assert worst <= ELEM_FACTOR * REL_L2, f"{what}: worst element error {worst:.3e} rms > {ELEM_FACTOR * REL_L2:.0e}"
     return rel, worst
