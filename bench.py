@@ -30,7 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "G (meas,voxel) pairs/s for A_B s + A_B^H r; SPGM time to oracle NMSE"
 UNIT = "G pairs/s"
-FLOPS_PER_PAIR = 8.0            # one complex multiply-accumulate
+# Algorithmic work per (row, voxel) element: one complex multiply-accumulate plus
+# one complex phasor step of the frequency recurrence = 8 FP32 FMA-pipe
+# lane-instructions, counted as 16 flops (an FMA-pipe instruction = 2 flops).
+FLOPS_PER_PAIR = 16.0
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
@@ -142,22 +145,26 @@ def build_problem(torch, ctx, w, seed_offset):
     return y, 1.0 / L, lam
 
 
+KERNEL_SOURCES = {"fwd_partial_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_forward.cu"),
+                  "adj_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_adjoint.cu")}
+
+
 def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel sources are unchanged."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's sources are unchanged."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f)
-    if d.get("sources_sha256") != sources_digest():
+        d = json.load(f).get("kernels", {}).get(kernel, {})
+    if not d or d.get("sources_sha256") != sources_digest(kernel):
         return None
-    return d.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch_full")
+    return d.get("dram_bytes_per_launch")
 
 
-def sources_digest():
+def sources_digest(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2509_00774_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -340,17 +347,18 @@ def run_ours(args):
         entry = {"launches": n, "total_ms": ms, "avg_us": avg_ms * 1e3}
         if kind in ("forward_partial", "adjoint"):
             tf = FLOPS_PER_PAIR * elems / (avg_ms * 1e-3) / 1e12
-            entry.update({"gpairs_per_s": elems / (avg_ms * 1e-3) / 1e9, "tflops_cmac": tf})
+            entry.update({"gpairs_per_s": elems / (avg_ms * 1e-3) / 1e9, "tflops": tf})
         kernels[kind] = entry
     dom = max(("forward_partial", "adjoint"), key=lambda k: kernels.get(k, {}).get("total_ms", 0.0))
     dk = kernels[dom]
     kname = {"forward_partial": "fwd_partial_kernel", "adjoint": "adj_kernel"}[dom]
-    roofline = {"bound": "alu", "kernel": kname, "achieved": dk["tflops_cmac"], "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": dk["tflops_cmac"] / fp32_peak_tflops,
+    roofline = {"bound": "alu", "kernel": kname, "achieved": dk["tflops"], "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": dk["tflops"] / fp32_peak_tflops,
                 "traffic": traffic_for(kname),
                 "peak_source": f"FP32 FMA lanes: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} x 2 flops x "
                                f"{sm_mhz:.0f} MHz (sm_max_mhz, {peak_src})",
-                "work": f"{FLOPS_PER_PAIR:.0f} flops (one complex MAC) per (row, voxel) pair, {elems} pairs per launch",
+                "work": f"{FLOPS_PER_PAIR:.0f} flops = 8 FP32 FMA-pipe lane-instructions (complex MAC + phasor step) "
+                        f"per (row, voxel) pair, {elems} pairs per launch",
                 "timing": f"CUDA events around every launch over {prof_steps} epochs run right after the timed region"}
     launches = sum(kernels.get(k, {}).get("launches", 0) for k in ("forward_partial", "forward_reduce", "adjoint"))
     launches = launches * args.steps // prof_steps      # per timed region (same kernels every epoch)

@@ -119,6 +119,19 @@ int nfm_spgm_epoch(nfm_ctx* ctx, const float* y, float* s, const int* perm, int 
 int nfm_spgm_epochs_host(nfm_ctx* ctx, const float* y_host, float* s_host, const int* perms_host,
                          int n_epochs, int pairs_per_batch, float eta, float lambda);
 
+/* One full-batch PGM iteration (Sec. IV, Eq. 5): nfm_spgm_step with every
+ * pair in index order, B = M rows.  y [P*K], s [N] (in place), device. */
+int nfm_pgm_step(nfm_ctx* ctx, const float* y, float* s, float eta, float lambda);
+
+/* SPGM with the termination rule of Sec. V: run epochs e = 0, 1, ... with the
+ * permutation perms + e*P (device [max_epochs][P]) until the change in
+ * reflectivity magnitudes over one epoch, max_n | |s_n(after)| - |s_n(before)| |
+ * (FP64), drops below tol, or max_epochs epochs have run.  pairs_per_batch = P
+ * with identity permutations is PGM.  Synchronises once per epoch to read the
+ * statistic.  Writes *epochs_out (epochs run) and *change_out (last change). */
+int nfm_solve(nfm_ctx* ctx, const float* y, float* s, const int* perms, int max_epochs, int pairs_per_batch,
+              float eta, float lambda, double tol, int* epochs_out, double* change_out);
+
 /* Largest eigenvalue L of A^H A / M by `iters` power iterations from
  * v0 [N] (device, complex64, not modified), with FP64 norms:
  *   v <- A^H A v / ||A^H A v||, then L = ||A v||^2 / (M ||v||^2).

@@ -609,6 +609,54 @@ int nfm_spgm_epochs_host(nfm_ctx* ctx, const float* y_host, float* s_host, const
     return check_flags(ctx);
 }
 
+int nfm_pgm_step(nfm_ctx* ctx, const float* y, float* s, float eta, float lambda)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (!(eta > 0) || !std::isfinite(eta)) return fail(ctx, NFM_ERR_ARG, "eta must be finite and > 0");
+    if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(ctx, NFM_ERR_ARG, "lambda must be finite and >= 0");
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    return spgm_step_impl(ctx, (const float2*)y, (float2*)s, ctx->d_pairs_all, ctx->P, eta, lambda);
+}
+
+int nfm_solve(nfm_ctx* ctx, const float* y, float* s, const int* perms, int max_epochs, int pairs_per_batch,
+              float eta, float lambda, double tol, int* epochs_out, double* change_out)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (max_epochs < 1 || pairs_per_batch < 1) return fail(ctx, NFM_ERR_ARG, "max_epochs and pairs_per_batch must be >= 1");
+    if (!(eta > 0) || !std::isfinite(eta)) return fail(ctx, NFM_ERR_ARG, "eta must be finite and > 0");
+    if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(ctx, NFM_ERR_ARG, "lambda must be finite and >= 0");
+    if (!(tol >= 0)) return fail(ctx, NFM_ERR_ARG, "tol must be >= 0");
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, perms, "perms", 4));
+    if (!epochs_out || !change_out) return fail(ctx, NFM_ERR_ARG, "NULL output");
+    const size_t nb = (size_t)ctx->N * sizeof(float2);
+    NFM_TRY(ensure(ctx, &ctx->d_v, &ctx->v_cap, nb));
+    float2* prev = (float2*)ctx->d_v;
+    double* part = ctx->d_red;
+    double* sc = ctx->d_red + RED_BLOCKS;
+    cudaStream_t st = ctx->stream;
+    double change = 0.0;
+    int e = 0;
+    while (e < max_epochs) {
+        NFM_CK(cudaMemcpyAsync(prev, s, nb, cudaMemcpyDeviceToDevice, st));
+        NFM_TRY(spgm_epoch_impl(ctx, (const float2*)y, (float2*)s, perms + (size_t)e * ctx->P, pairs_per_batch,
+                                eta, lambda));
+        NFM_CK(launch_mag_change((const float2*)s, prev, ctx->N, part, sc + 0, st));
+        NFM_CK(cudaMemcpyAsync(&change, sc + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
+        NFM_CK(st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize());
+        ++e;
+        if (change < tol) break;
+    }
+    NFM_TRY(check_flags(ctx));
+    *epochs_out = e;
+    *change_out = change;
+    return NFM_OK;
+}
+
 int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out)
 {
     NFM_TRY(require_geom(ctx));

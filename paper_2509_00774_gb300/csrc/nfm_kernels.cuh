@@ -84,6 +84,9 @@ constexpr int RED_BLOCKS = 256;
 cudaError_t launch_norm2(const float2* v, long long n, double* partial, double* out, cudaStream_t st);
 cudaError_t launch_abs_sum(const float2* v, long long n, double* partial, double* out, cudaStream_t st);
 cudaError_t launch_abs_max(const float2* v, long long n, double* partial, double* out, cudaStream_t st);
+// out = max_n | |a_n| - |b_n| |  (FP64)
+cudaError_t launch_mag_change(const float2* a, const float2* b, long long n, double* partial, double* out,
+                              cudaStream_t st);
 // dst = src / sqrt(*nrm2)
 cudaError_t launch_normalize(const float2* src, float2* dst, long long n, const double* nrm2, cudaStream_t st);
 // out[0] = a[0] / (scale * b[0])

@@ -291,26 +291,26 @@ cudaError_t launch_fwd_partial(const OpDesc& op, const FwdArgs& a, dim3 grid, in
 // subtract the observed rows: out[slot*K + k] = p_k sum_c partial[c][slot][k] - y[pair*K + k].
 __global__ void __launch_bounds__(1024) fwd_reduce_kernel(OpDesc op, ReduceArgs a)
 {
+    constexpr int UN = 8;                 // loads in flight per thread
     __shared__ float2 red[32][33];
     const int o = blockIdx.x * 32 + threadIdx.x;
     const size_t stride = (size_t)a.n_slots * op.K;
     pdl_wait();
     float2 s = make_float2(0.f, 0.f);
     if (o < a.n_out) {
-        // chunk lane y sums chunks y, y+32, ... (four loads in flight, fixed order)
-        int c = threadIdx.y;
-        for (; c + 96 < a.n_chunks; c += 128) {
-            float2 x0 = a.partial[(size_t)c * stride + o];
-            float2 x1 = a.partial[(size_t)(c + 32) * stride + o];
-            float2 x2 = a.partial[(size_t)(c + 64) * stride + o];
-            float2 x3 = a.partial[(size_t)(c + 96) * stride + o];
-            s.x += ((x0.x + x1.x) + (x2.x + x3.x));
-            s.y += ((x0.y + x1.y) + (x2.y + x3.y));
-        }
-        for (; c < a.n_chunks; c += 32) {
-            float2 x = a.partial[(size_t)c * stride + o];
-            s.x += x.x;
-            s.y += x.y;
+        // chunk lane y sums chunks y, y+32, ... in that order
+        for (int c0 = threadIdx.y; c0 < a.n_chunks; c0 += 32 * UN) {
+            float2 x[UN];
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                const int c = c0 + 32 * u;
+                x[u] = c < a.n_chunks ? a.partial[(size_t)c * stride + o] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < UN; ++u) {
+                s.x += x[u].x;
+                s.y += x[u].y;
+            }
         }
     }
     red[threadIdx.y][threadIdx.x] = s;

@@ -129,6 +129,33 @@ cudaError_t launch_abs_max(const float2* v, long long n, double* partial, double
     return launch_reduce<RED_ABS_MAX>(v, n, partial, out, st);
 }
 
+__global__ void __launch_bounds__(256) mag_change_partial_kernel(const float2* a, const float2* b, long long n,
+                                                                 double* partial)
+{
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        const float2 x = a[i], y = b[i];
+        const double d = fabs(sqrt((double)x.x * x.x + (double)x.y * x.y) - sqrt((double)y.x * y.x + (double)y.y * y.y));
+        acc = d > acc ? d : acc;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+cudaError_t launch_mag_change(const float2* a, const float2* b, long long n, double* partial, double* out,
+                              cudaStream_t st)
+{
+    mag_change_partial_kernel<<<RED_BLOCKS, 256, 0, st>>>(a, b, n, partial);
+    reduce_final_kernel<RED_ABS_MAX><<<1, 256, 0, st>>>(partial, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+
 __global__ void normalize_kernel(const float2* src, float2* dst, long long n, const double* nrm2)
 {
     const double nv = nrm2[0];

@@ -60,6 +60,8 @@ def load_library(path: str | None = None):
         "nfm_spgm_step": (i, [vp, vp, vp, vp, i, f, f]),
         "nfm_spgm_epoch": (i, [vp, vp, vp, vp, i, f, f]),
         "nfm_spgm_epochs_host": (i, [vp, vp, vp, vp, i, i, f, f]),
+        "nfm_pgm_step": (i, [vp, vp, vp, f, f]),
+        "nfm_solve": (i, [vp, vp, vp, vp, i, i, f, f, d, ctypes.POINTER(i), ctypes.POINTER(d)]),
         "nfm_power_iteration": (i, [vp, i, vp, ctypes.POINTER(d)]),
         "nfm_objective": (i, [vp, vp, vp, d, ctypes.POINTER(d)]),
         "nfm_lambda_max": (i, [vp, vp, ctypes.POINTER(d)]),
@@ -229,6 +231,22 @@ class Context:
             self._h, hp(y_host, np.complex64, "y_host"), hp(s_host, np.complex64, "s_host"),
             hp(perms, np.int32, "perms_host"), n_epochs, int(pairs_per_batch), float(eta), float(lam)))
         return s_host
+
+    def pgm_step(self, y, s, eta, lam):
+        """One full-batch PGM iteration (every pair), s updated in place."""
+        self._check(self._lib.nfm_pgm_step(self._h, self._c(y, "y"), self._c(s, "s"), float(eta), float(lam)))
+        return s
+
+    def solve(self, y, s, perms, pairs_per_batch, eta, lam, tol, max_epochs=None):
+        """Epochs until the change in reflectivity magnitudes over an epoch < tol.
+        perms: int32 device tensor [max_epochs, P].  Returns (epochs_run, last_change)."""
+        n = perms.shape[0] if max_epochs is None else int(max_epochs)
+        ep = ctypes.c_int()
+        ch = ctypes.c_double()
+        self._check(self._lib.nfm_solve(self._h, self._c(y, "y"), self._c(s, "s"), self._i(perms, "perms"), n,
+                                        int(pairs_per_batch), float(eta), float(lam), float(tol),
+                                        ctypes.byref(ep), ctypes.byref(ch)))
+        return ep.value, ch.value
 
     def power_iteration(self, v0, iters: int = 50) -> float:
         L = ctypes.c_double()

@@ -69,6 +69,55 @@ def test_spgm_small_matches_oracle(bp):
     assert abs(F_gpu - F_orc) <= OBJ_TOL * F_orc
 
 
+def test_pgm_matches_oracle():
+    """Full-batch PGM (Eq. 5), 40 iterations on the small workload."""
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
+    eta = float(np.float32(1.0 / L))
+    lam = float(np.float32(0.05 * o.lambda_max(y)))
+    s_orc = np.zeros(o.N, dtype=np.complex128)
+    s_gpu = to_dev(np.zeros(o.N))
+    y_dev = to_dev(y)
+    for it in range(40):
+        s_orc = o.pgm_step(y, s_orc, eta, lam)
+        ctx.pgm_step(y_dev, s_gpu, eta, lam)
+    assert nmse(to_host(s_gpu), s_orc) <= NMSE_TOL
+    F_gpu = o.objective(y, to_host(s_gpu), lam)
+    F_orc = o.objective(y, s_orc, lam)
+    assert abs(F_gpu - F_orc) <= OBJ_TOL * F_orc
+
+
+def test_solve_termination_rule():
+    """Sec. V: epochs run until the change in reflectivity magnitudes drops below tol."""
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
+    eta = float(np.float32(1.0 / L))
+    lam = float(np.float32(0.05 * o.lambda_max(y)))
+    tol, E = 2e-3, 60
+    perms = np.stack([I.epoch_permutation(o.P, w.seeds["perm"], e) for e in range(E)]).astype(np.int32)
+    # oracle: the same rule in FP64
+    s = np.zeros(o.N, dtype=np.complex128)
+    changes = []
+    for e in range(E):
+        s_new = o.spgm_epoch(y, s, perms[e], 4, eta, lam)
+        changes.append(float(np.max(np.abs(np.abs(s_new) - np.abs(s)))))
+        s = s_new
+        if changes[-1] < tol:
+            break
+    s_gpu = to_dev(np.zeros(o.N))
+    n_run, last = ctx.solve(to_dev(y), s_gpu, to_dev(perms, "int32"), 4, eta, lam, tol)
+    assert last < tol or n_run == E
+    # FP32 vs FP64 may cross the threshold one epoch apart
+    assert abs(n_run - len(changes)) <= 1, (n_run, len(changes))
+    assert abs(last - changes[n_run - 1]) <= 1e-3 * max(changes[n_run - 1], 1e-3) + 2e-5
+    ref = o.spgm_epoch(y, np.zeros(o.N), perms[0], 4, eta, lam)
+    for e in range(1, n_run):
+        ref = o.spgm_epoch(y, ref, perms[e], 4, eta, lam)
+    assert nmse(to_host(s_gpu), ref) <= NMSE_TOL
+
+
 def test_spgm_host_buffers_match_device():
     w, o, y = _small_problem()
     ctx = make_ctx(w.geom)
