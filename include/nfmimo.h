@@ -132,6 +132,19 @@ int nfm_pgm_step(nfm_ctx* ctx, const float* y, float* s, float eta, float lambda
 int nfm_solve(nfm_ctx* ctx, const float* y, float* s, const int* perms, int max_epochs, int pairs_per_batch,
               float eta, float lambda, double tol, int* epochs_out, double* change_out);
 
+/* Gradient step and prox of Eq. 5 as a separate op (used by unrolled SPGM):
+ *   out = prox_alpha(s - step g),  prox(z) = z max(0, 1 - alpha/|z|).
+ * s, g, out: device complex64 [n] (out may alias s). */
+int nfm_prox_step(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n, float* out);
+
+/* Backward of nfm_prox_step for a real loss, with complex gradients as real
+ * pairs (d/dRe + j d/dIm, the PyTorch convention).  grad_out [n] is the
+ * gradient of the output; writes grad_s [n] and grad_g [n] (either may be
+ * NULL) and, to the device buffer grad_scalars [2] (FP64), dL/dstep and
+ * dL/dalpha.  All pointers device. */
+int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n,
+                           const float* grad_out, float* grad_s, float* grad_g, double* grad_scalars);
+
 /* Largest eigenvalue L of A^H A / M by `iters` power iterations from
  * v0 [N] (device, complex64, not modified), with FP64 norms:
  *   v <- A^H A v / ||A^H A v||, then L = ||A v||^2 / (M ||v||^2).

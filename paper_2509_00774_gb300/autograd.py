@@ -1,0 +1,127 @@
+"""Differentiable A_B, A_B^H and prox step, and SPGM unrolled with learnable steps.
+
+The forward of each op is a call into the CUDA library; its backward is the
+hand-written adjoint kernel (for A_B), the forward kernel (for A_B^H) or the
+prox-step backward kernel.  Complex gradients follow PyTorch's convention for
+a real loss L: grad = dL/dRe + j dL/dIm.  For a linear map y = A s this makes
+the vector-Jacobian product grad_s = A^H grad_y.
+
+UnrolledSPGM runs a fixed number of SPGM iterations (Sec. IV, Eq. 5 with the
+minibatch gradient of Eq. 6),
+
+    s_{i+1} = prox_{eta_i lambda_i}( s_i - (eta_i / B_i) A_{B_i}^H (A_{B_i} s_i - y_{B_i}) ),
+
+with a learnable step eta_i and weight lambda_i per iteration, and checkpoints
+each iteration's input so the backward pass recomputes the operator instead of
+storing residuals and gradients.
+"""
+from __future__ import annotations
+
+import torch
+from torch.utils.checkpoint import checkpoint as _checkpoint
+
+
+class _ForwardFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, s, op, pairs):
+        ctx.op = op
+        ctx.pairs = pairs
+        return op.forward(pairs, s.contiguous())
+
+    @staticmethod
+    def backward(ctx, gy):
+        return ctx.op.adjoint(ctx.pairs, gy.contiguous()), None, None
+
+
+class _AdjointFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, r, op, pairs):
+        ctx.op = op
+        ctx.pairs = pairs
+        return op.adjoint(pairs, r.contiguous())
+
+    @staticmethod
+    def backward(ctx, gg):
+        return ctx.op.forward(ctx.pairs, gg.contiguous()), None, None
+
+
+class _ProxStepFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, s, g, step, alpha, op):
+        s = s.contiguous()
+        g = g.contiguous()
+        st, al = float(step), float(alpha)
+        out = torch.empty_like(s)
+        op.prox_step(s, g, st, al, out)
+        ctx.save_for_backward(s, g)
+        ctx.op, ctx.st, ctx.al = op, st, al
+        ctx.scalar_meta = (step.dtype, step.device) if torch.is_tensor(step) else (torch.float64, torch.device("cpu"))
+        return out
+
+    @staticmethod
+    def backward(ctx, go):
+        s, g = ctx.saved_tensors
+        need_s, need_g, need_step, need_alpha = ctx.needs_input_grad[:4]
+        grad_s = torch.empty_like(s) if need_s else None
+        grad_g = torch.empty_like(g) if need_g else None
+        scalars = torch.empty(2, dtype=torch.float64, device=s.device)
+        ctx.op.prox_step_backward(s, g, ctx.st, ctx.al, go.contiguous(), grad_s, grad_g, scalars)
+        dt, dev = ctx.scalar_meta
+        sc = scalars.to(device=dev, dtype=dt)
+        return grad_s, grad_g, (sc[0] if need_step else None), (sc[1] if need_alpha else None), None
+
+
+def forward_op(op, pairs, s):
+    """y = A_B s, differentiable in s (op: nfmimo.Context, pairs: int32 device tensor)."""
+    return _ForwardFn.apply(s, op, pairs)
+
+
+def adjoint_op(op, pairs, r):
+    """g = A_B^H r, differentiable in r."""
+    return _AdjointFn.apply(r, op, pairs)
+
+
+def prox_step(op, s, g, step, alpha):
+    """prox_alpha(s - step g), differentiable in s, g, step and alpha (0-dim tensors or floats)."""
+    return _ProxStepFn.apply(s, g, step, alpha, op)
+
+
+class UnrolledSPGM(torch.nn.Module):
+    """n_iter SPGM iterations with learnable per-iteration eta_i and lambda_i (FP64 CPU parameters)."""
+
+    def __init__(self, op, n_iter: int, eta: float, lam: float, checkpoint: bool = True):
+        super().__init__()
+        self.op = op
+        self.n_iter = int(n_iter)
+        self.eta = torch.nn.Parameter(torch.full((self.n_iter,), float(eta), dtype=torch.float64))
+        self.lam = torch.nn.Parameter(torch.full((self.n_iter,), float(lam), dtype=torch.float64))
+        self.checkpoint = checkpoint
+
+    def _iteration(self, s, y_b, pairs, eta, lam):
+        B = pairs.numel() * self.op.K
+        r = forward_op(self.op, pairs, s) - y_b
+        g = adjoint_op(self.op, pairs, r)
+        return prox_step(self.op, s, g, eta / B, eta * lam)
+
+    def forward(self, y, batches, s0=None):
+        """y: [M] or [n_scenes, M] complex64 device; batches: n_iter int32 pair lists.
+        Returns the final iterate(s), [N] or [n_scenes, N]."""
+        single = y.dim() == 1
+        ys = y.unsqueeze(0) if single else y
+        K = self.op.K
+        outs = []
+        for j in range(ys.shape[0]):
+            yj = ys[j].view(-1, K)
+            if s0 is None:
+                s = torch.zeros(self.op.N, dtype=torch.complex64, device=y.device)
+            else:
+                s = (s0 if single else s0[j]).contiguous()
+            for i in range(self.n_iter):
+                pairs = batches[i % len(batches)]
+                y_b = yj[pairs.long()].reshape(-1).contiguous()
+                if self.checkpoint and torch.is_grad_enabled():
+                    s = _checkpoint(self._iteration, s, y_b, pairs, self.eta[i], self.lam[i], use_reentrant=False)
+                else:
+                    s = self._iteration(s, y_b, pairs, self.eta[i], self.lam[i])
+            outs.append(s)
+        return outs[0] if single else torch.stack(outs)

@@ -79,6 +79,8 @@ struct nfm_ctx {
     size_t hs_cap = 0;
     void* d_hperm = nullptr;
     size_t hperm_cap = 0;
+    void* d_prox_partial = nullptr;
+    size_t prox_partial_cap = 0;
 
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -367,7 +369,8 @@ void nfm_destroy(nfm_ctx* ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     void* ps[] = {ctx->d_ant, ctx->d_ant_xyz, ctx->d_pulse, ctx->d_pairs_all, ctx->d_err, ctx->d_red,
-                  ctx->d_partial, ctx->d_resid, ctx->d_v, ctx->d_g, ctx->d_y, ctx->d_hy, ctx->d_hs, ctx->d_hperm};
+                  ctx->d_partial, ctx->d_resid, ctx->d_v, ctx->d_g, ctx->d_y, ctx->d_hy, ctx->d_hs, ctx->d_hperm,
+                  ctx->d_prox_partial};
     for (void* p : ps) free_ptr(p);
     for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
     delete ctx;
@@ -654,6 +657,39 @@ int nfm_solve(nfm_ctx* ctx, const float* y, float* s, const int* perms, int max_
     NFM_TRY(check_flags(ctx));
     *epochs_out = e;
     *change_out = change;
+    return NFM_OK;
+}
+
+int nfm_prox_step(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n, float* out)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    DevGuard guard(ctx->device);
+    if (n < 1) return fail(ctx, NFM_ERR_ARG, "n must be >= 1");
+    if (!std::isfinite(step) || !(alpha >= 0) || !std::isfinite(alpha)) return fail(ctx, NFM_ERR_ARG, "bad step/alpha");
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, g, "g", 8));
+    NFM_TRY(check_ptr(ctx, out, "out", 8));
+    NFM_CK(launch_prox_step((const float2*)s, (const float2*)g, step, alpha, n, (float2*)out, ctx->stream));
+    return NFM_OK;
+}
+
+int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n,
+                           const float* grad_out, float* grad_s, float* grad_g, double* grad_scalars)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    DevGuard guard(ctx->device);
+    if (n < 1) return fail(ctx, NFM_ERR_ARG, "n must be >= 1");
+    if (!std::isfinite(step) || !(alpha >= 0) || !std::isfinite(alpha)) return fail(ctx, NFM_ERR_ARG, "bad step/alpha");
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, g, "g", 8));
+    NFM_TRY(check_ptr(ctx, grad_out, "grad_out", 8));
+    NFM_TRY(check_ptr(ctx, grad_scalars, "grad_scalars", 8));
+    if (grad_s) NFM_TRY(check_ptr(ctx, grad_s, "grad_s", 8));
+    if (grad_g) NFM_TRY(check_ptr(ctx, grad_g, "grad_g", 8));
+    NFM_TRY(ensure(ctx, &ctx->d_prox_partial, &ctx->prox_partial_cap, 2 * RED_BLOCKS * sizeof(double)));
+    NFM_CK(launch_prox_step_backward((const float2*)s, (const float2*)g, step, alpha, n, (const float2*)grad_out,
+                                     (float2*)grad_s, (float2*)grad_g, (double*)ctx->d_prox_partial, grad_scalars,
+                                     ctx->stream));
     return NFM_OK;
 }
 

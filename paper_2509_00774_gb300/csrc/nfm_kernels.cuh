@@ -87,6 +87,13 @@ cudaError_t launch_abs_max(const float2* v, long long n, double* partial, double
 // out = max_n | |a_n| - |b_n| |  (FP64)
 cudaError_t launch_mag_change(const float2* a, const float2* b, long long n, double* partial, double* out,
                               cudaStream_t st);
+// out = prox_alpha(s - step g)  and its backward (grad_s, grad_g may be null;
+// out2[0] = dL/dstep, out2[1] = dL/dalpha in FP64; partial holds 2*RED_BLOCKS doubles)
+cudaError_t launch_prox_step(const float2* s, const float2* g, float step, float alpha, long long n, float2* out,
+                             cudaStream_t st);
+cudaError_t launch_prox_step_backward(const float2* s, const float2* g, float step, float alpha, long long n,
+                                      const float2* go, float2* grad_s, float2* grad_g, double* partial,
+                                      double* out2, cudaStream_t st);
 // dst = src / sqrt(*nrm2)
 cudaError_t launch_normalize(const float2* src, float2* dst, long long n, const double* nrm2, cudaStream_t st);
 // out[0] = a[0] / (scale * b[0])

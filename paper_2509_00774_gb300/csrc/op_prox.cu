@@ -1,0 +1,102 @@
+// Gradient step + complex soft-threshold as a stand-alone differentiable op
+// (Eq. 5), for unrolled SPGM:
+//
+//     z = s - step * g,   out = prox_alpha(z) = z (1 - alpha/|z|) if |z| > alpha else 0.
+//
+// The backward kernel uses PyTorch's convention for complex gradients of a
+// real loss (grad = dL/dRe + j dL/dIm, i.e. real 2-vectors).  For |z| > alpha
+// the real Jacobian of prox is  J = s I + (alpha/r^3) z z^T  (r = |z|,
+// s = 1 - alpha/r), which is symmetric, so grad_z = s o + (alpha/r^3)(z.o) z
+// with o the incoming gradient; d out/d alpha = -z/r.  For |z| <= alpha the
+// output is 0 and every derivative is 0.
+#include "nfm_kernels.cuh"
+
+namespace nfm {
+
+__global__ void prox_step_kernel(const float2* s, const float2* g, float step, float alpha, long long n, float2* out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 sv = s[i], gv = g[i];
+        const float zr = fmaf(-step, gv.x, sv.x), zi = fmaf(-step, gv.y, sv.y);
+        const float mag = sqrtf(zr * zr + zi * zi);
+        float2 o = make_float2(0.f, 0.f);
+        if (mag > alpha) {
+            const float sc = 1.0f - alpha / mag;
+            o = make_float2(zr * sc, zi * sc);
+        }
+        out[i] = o;
+    }
+}
+
+// grad_s = grad_z, grad_g = -step grad_z, and FP64 block partials of
+// d/dstep = -sum grad_z . g and d/dalpha = -sum_{|z|>alpha} (z . o) / |z|.
+__global__ void __launch_bounds__(256) prox_step_backward_kernel(const float2* s, const float2* g, float step,
+                                                                 float alpha, long long n, const float2* go,
+                                                                 float2* grad_s, float2* grad_g, double* partial)
+{
+    __shared__ double sh0[256], sh1[256];
+    double a_step = 0.0, a_alpha = 0.0;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        const float2 sv = s[i], gv = g[i], o = go[i];
+        const float zr = fmaf(-step, gv.x, sv.x), zi = fmaf(-step, gv.y, sv.y);
+        const float mag = sqrtf(zr * zr + zi * zi);
+        float2 gz = make_float2(0.f, 0.f);
+        if (mag > alpha) {
+            const float sc = 1.0f - alpha / mag;
+            const float zo = zr * o.x + zi * o.y;
+            const float k = alpha / (mag * mag * mag) * zo;
+            gz = make_float2(fmaf(sc, o.x, k * zr), fmaf(sc, o.y, k * zi));
+            a_alpha -= (double)zo / (double)mag;
+        }
+        if (grad_s) grad_s[i] = gz;
+        if (grad_g) grad_g[i] = make_float2(-step * gz.x, -step * gz.y);
+        a_step -= (double)gz.x * gv.x + (double)gz.y * gv.y;
+    }
+    sh0[threadIdx.x] = a_step;
+    sh1[threadIdx.x] = a_alpha;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh0[threadIdx.x] += sh0[threadIdx.x + w];
+            sh1[threadIdx.x] += sh1[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sh0[0];
+        partial[2 * blockIdx.x + 1] = sh1[0];
+    }
+}
+
+__global__ void sum_pairs_kernel(const double* partial, int nb, double* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            a += partial[2 * i];
+            b += partial[2 * i + 1];
+        }
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+cudaError_t launch_prox_step(const float2* s, const float2* g, float step, float alpha, long long n, float2* out,
+                             cudaStream_t st)
+{
+    long long blocks = (n + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    prox_step_kernel<<<(int)blocks, 256, 0, st>>>(s, g, step, alpha, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prox_step_backward(const float2* s, const float2* g, float step, float alpha, long long n,
+                                      const float2* go, float2* grad_s, float2* grad_g, double* partial,
+                                      double* out2, cudaStream_t st)
+{
+    prox_step_backward_kernel<<<RED_BLOCKS, 256, 0, st>>>(s, g, step, alpha, n, go, grad_s, grad_g, partial);
+    sum_pairs_kernel<<<1, 32, 0, st>>>(partial, RED_BLOCKS, out2);
+    return cudaGetLastError();
+}
+
+}  // namespace nfm

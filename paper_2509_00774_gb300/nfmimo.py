@@ -62,6 +62,8 @@ def load_library(path: str | None = None):
         "nfm_spgm_epochs_host": (i, [vp, vp, vp, vp, i, i, f, f]),
         "nfm_pgm_step": (i, [vp, vp, vp, f, f]),
         "nfm_solve": (i, [vp, vp, vp, vp, i, i, f, f, d, ctypes.POINTER(i), ctypes.POINTER(d)]),
+        "nfm_prox_step": (i, [vp, vp, vp, f, f, ctypes.c_longlong, vp]),
+        "nfm_prox_step_backward": (i, [vp, vp, vp, f, f, ctypes.c_longlong, vp, vp, vp, vp]),
         "nfm_power_iteration": (i, [vp, i, vp, ctypes.POINTER(d)]),
         "nfm_objective": (i, [vp, vp, vp, d, ctypes.POINTER(d)]),
         "nfm_lambda_max": (i, [vp, vp, ctypes.POINTER(d)]),
@@ -247,6 +249,21 @@ class Context:
                                         int(pairs_per_batch), float(eta), float(lam), float(tol),
                                         ctypes.byref(ep), ctypes.byref(ch)))
         return ep.value, ch.value
+
+    def prox_step(self, s, g, step, alpha, out):
+        """out = prox_alpha(s - step g) (Eq. 5); out may be s."""
+        self._check(self._lib.nfm_prox_step(self._h, self._c(s, "s"), self._c(g, "g"), float(step), float(alpha),
+                                            s.numel(), self._c(out, "out")))
+        return out
+
+    def prox_step_backward(self, s, g, step, alpha, grad_out, grad_s, grad_g, scalars):
+        """Backward of prox_step; scalars: float64 device tensor [2] <- (dL/dstep, dL/dalpha)."""
+        import torch
+        ps = self._c(grad_s, "grad_s") if grad_s is not None else None
+        pg = self._c(grad_g, "grad_g") if grad_g is not None else None
+        self._check(self._lib.nfm_prox_step_backward(
+            self._h, self._c(s, "s"), self._c(g, "g"), float(step), float(alpha), s.numel(),
+            self._c(grad_out, "grad_out"), ps, pg, _ptr(scalars, torch.float64, "scalars", self.device)))
 
     def power_iteration(self, v0, iters: int = 50) -> float:
         L = ctypes.c_double()

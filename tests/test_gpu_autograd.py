@@ -1,0 +1,209 @@
+"""Differentiation through the CUDA operators (autograd.Function wrappers, unrolled SPGM),
+checked against the FP64 oracle: oracle gradients and FP64 central finite differences."""
+import numpy as np
+import pytest
+
+from oracle import Oracle, prox_l1
+from paper_2509_00774_gb300 import inputs as I
+from paper_2509_00774_gb300 import workloads as W
+from tests.gpu_helpers import make_ctx, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _c64(z):
+    return np.asarray(z, dtype=np.complex64).astype(np.complex128)
+
+
+def test_forward_op_gradient_matches_oracle_and_fd():
+    """L(s) = ||A_B s - y||^2: grad = 2 A_B^H (A_B s - y) (dL/dRe + j dL/dIm)."""
+    import torch
+    from paper_2509_00774_gb300.autograd import forward_op
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    ctx = make_ctx(w.geom)
+    pairs = np.array([3, 12, 0, 7])
+    rows = o.rows_of_pairs(pairs)
+    s = _c64(I.complex_gaussian(o.N, 40)) * 0.3
+    y = _c64(I.complex_gaussian(rows.size, 41))
+    s_d = to_dev(s).requires_grad_(True)
+    L = (forward_op(ctx, to_dev(pairs, "int32"), s_d) - to_dev(y)).abs().pow(2).sum()
+    L.backward()
+    got = to_host(s_d.grad)
+    want = 2.0 * o.adjoint(o.forward(s, rows=rows) - y, rows=rows)
+    assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+    # FP64 central differences on a few coordinates, through the oracle
+    h = 1e-6
+    loss = lambda v: float(np.sum(np.abs(o.forward(v, rows=rows) - y) ** 2))
+    for j in (0, 777, 2047):
+        e = np.zeros(o.N, dtype=np.complex128)
+        e[j] = h
+        d_re = (loss(s + e) - loss(s - e)) / (2 * h)
+        d_im = (loss(s + 1j * e) - loss(s - 1j * e)) / (2 * h)
+        assert abs(got[j] - (d_re + 1j * d_im)) <= 1e-4 * abs(d_re + 1j * d_im) + 1e-6
+
+
+def test_adjoint_op_gradient_matches_oracle():
+    """L(r) = ||A_B^H r - t||^2: grad = 2 A_B (A_B^H r - t)."""
+    from paper_2509_00774_gb300.autograd import adjoint_op
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    ctx = make_ctx(w.geom)
+    pairs = np.array([1, 9, 14])
+    rows = o.rows_of_pairs(pairs)
+    r = _c64(I.complex_gaussian(rows.size, 42))
+    t = _c64(I.complex_gaussian(o.N, 43)) * 0.01
+    r_d = to_dev(r).requires_grad_(True)
+    L = (adjoint_op(ctx, to_dev(pairs, "int32"), r_d) - to_dev(t)).abs().pow(2).sum()
+    L.backward()
+    got = to_host(r_d.grad)
+    want = 2.0 * o.forward(o.adjoint(r, rows=rows) - t, rows=rows)
+    assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+
+
+def test_prox_step_backward_matches_fd():
+    """out = prox_alpha(s - step g); L = sum Re(conj(c) out).  FP64 central differences of the
+    oracle prox for grad_s, grad_g, dL/dstep and dL/dalpha (entries near |z| = alpha excluded)."""
+    import torch
+    from paper_2509_00774_gb300.autograd import prox_step
+    w = W.small_T4R4_K16_16x16x8()
+    ctx = make_ctx(w.geom)
+    n = 4000
+    rng = np.random.default_rng(44)
+    s = _c64(I.complex_gaussian(n, 45))
+    g = _c64(I.complex_gaussian(n, 46))
+    c = _c64(I.complex_gaussian(n, 47))
+    step, alpha = 0.3, 0.6
+    z = s - step * g
+    keep = np.abs(np.abs(z) - alpha) > 1e-2           # away from the kink of the prox
+    s_d = to_dev(s).requires_grad_(True)
+    g_d = to_dev(g).requires_grad_(True)
+    st = torch.tensor(step, dtype=torch.float64, requires_grad=True)
+    al = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+    out = prox_step(ctx, s_d, g_d, st, al)
+    L = (torch.conj(to_dev(c)) * out).real.sum()
+    L.backward()
+    gs, gg = to_host(s_d.grad), to_host(g_d.grad)
+
+    def loss(s_, g_, st_, al_):
+        return float(np.sum((np.conj(c) * prox_l1(s_ - st_ * g_, al_)).real[keep]))
+
+    h = 1e-6
+    idx = np.flatnonzero(keep)[:: max(1, keep.sum() // 40)]
+    for j in idx:
+        e = np.zeros(n, dtype=np.complex128)
+        e[j] = h
+        fd_s = (loss(s + e, g, step, alpha) - loss(s - e, g, step, alpha)) / (2 * h) + \
+            1j * (loss(s + 1j * e, g, step, alpha) - loss(s - 1j * e, g, step, alpha)) / (2 * h)
+        assert abs(gs[j] - fd_s) <= 1e-4 * max(1.0, abs(fd_s)), (j, gs[j], fd_s)
+        assert abs(gg[j] + step * fd_s) <= 1e-4 * max(1.0, abs(fd_s))
+    # scalar derivatives use every entry away from the kink
+    mask = torch.from_numpy(keep).cuda()
+    s_d.grad = None
+    st2 = torch.tensor(step, dtype=torch.float64, requires_grad=True)
+    al2 = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+    out2 = prox_step(ctx, to_dev(s), to_dev(g), st2, al2)
+    L2 = ((torch.conj(to_dev(c)) * out2).real * mask).sum()
+    L2.backward()
+    fd_step = (loss(s, g, step + h, alpha) - loss(s, g, step - h, alpha)) / (2 * h)
+    fd_alpha = (loss(s, g, step, alpha + h) - loss(s, g, step, alpha - h)) / (2 * h)
+    assert abs(float(st2.grad) - fd_step) <= 1e-4 * abs(fd_step) + 1e-3
+    assert abs(float(al2.grad) - fd_alpha) <= 1e-4 * abs(fd_alpha) + 1e-3
+
+
+def _oracle_unrolled(o, y, batches, eta, lam, s_ref):
+    s = np.zeros(o.N, dtype=np.complex128)
+    for i, b in enumerate(batches):
+        s = o.spgm_step(y, s, b, eta[i], lam[i])
+    return float(np.sum(np.abs(s - s_ref) ** 2)), s
+
+
+def test_unrolled_spgm_gradients_match_fd():
+    """8 unrolled SPGM iterations, loss ||s_8 - s_true||^2: autograd d/deta_i, d/dlambda_i in FP32
+    kernels against FP64 central differences of the oracle's unrolled iterations."""
+    import torch
+    from paper_2509_00774_gb300.autograd import UnrolledSPGM
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    s_true = w.scene_vector()
+    y = _c64(I.add_noise(o.forward_sparse(s_true), I.complex_gaussian(o.M, 1), 30.0))
+    L = o.power_iteration(I.complex_gaussian(o.N, 3), 50)
+    eta0, lam0 = float(np.float32(0.8 / L)), float(np.float32(0.05 * o.lambda_max(y)))
+    perm = np.concatenate([I.epoch_permutation(o.P, 2, 0), I.epoch_permutation(o.P, 2, 1)])
+    batches = [perm[4 * i:4 * i + 4] for i in range(8)]
+    ctx = make_ctx(w.geom)
+    model = UnrolledSPGM(ctx, 8, eta0, lam0, checkpoint=True)
+    with torch.no_grad():
+        model.eta.copy_(torch.tensor(eta0 * (1 + 0.05 * np.arange(8)), dtype=torch.float64))
+        model.lam.copy_(torch.tensor(lam0 * (1 - 0.03 * np.arange(8)), dtype=torch.float64))
+    s8 = model(to_dev(y), [to_dev(b, "int32") for b in batches])
+    loss = (s8 - to_dev(s_true)).abs().pow(2).sum()
+    loss.backward()
+    g_eta = model.eta.grad.numpy().copy()
+    g_lam = model.lam.grad.numpy().copy()
+    eta = model.eta.detach().numpy().astype(np.float64)
+    lam = model.lam.detach().numpy().astype(np.float64)
+    L0, s_orc = _oracle_unrolled(o, y, batches, eta, lam, s_true)
+    assert abs(float(loss.detach()) - L0) <= 1e-4 * L0
+    fd_eta, fd_lam = np.zeros(8), np.zeros(8)
+    for i in range(8):
+        he, hl = 1e-5 * eta[i], 1e-5 * lam[i]
+        e1, e2 = eta.copy(), eta.copy()
+        e1[i] += he
+        e2[i] -= he
+        fd_eta[i] = (_oracle_unrolled(o, y, batches, e1, lam, s_true)[0] -
+                     _oracle_unrolled(o, y, batches, e2, lam, s_true)[0]) / (2 * he)
+        l1, l2 = lam.copy(), lam.copy()
+        l1[i] += hl
+        l2[i] -= hl
+        fd_lam[i] = (_oracle_unrolled(o, y, batches, eta, l1, s_true)[0] -
+                     _oracle_unrolled(o, y, batches, eta, l2, s_true)[0]) / (2 * hl)
+    err_eta = np.linalg.norm(g_eta - fd_eta) / np.linalg.norm(fd_eta)
+    err_lam = np.linalg.norm(g_lam - fd_lam) / np.linalg.norm(fd_lam)
+    print(f"[parity] unrolled grads: rel err eta {err_eta:.2e}, lambda {err_lam:.2e}")
+    assert err_eta <= 1e-3 and err_lam <= 1e-3
+
+
+def test_checkpointing_gives_identical_gradients():
+    import torch
+    from paper_2509_00774_gb300.autograd import UnrolledSPGM
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    y = _c64(I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, 1), 30.0))
+    ctx = make_ctx(w.geom)
+    batches = [to_dev(I.epoch_permutation(o.P, 2, 0)[4 * i:4 * i + 4], "int32") for i in range(4)]
+    grads = []
+    for ck in (True, False):
+        m = UnrolledSPGM(ctx, 8, 0.01, 0.05, checkpoint=ck)
+        out = m(to_dev(y), batches)
+        out.abs().pow(2).sum().backward()
+        grads.append((m.eta.grad.clone(), m.lam.grad.clone()))
+    assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
+
+
+def test_unrolled_batch_of_four_scenes_mid_geometry():
+    """Config-2 geometry (N = 131072), 4 scenes, 8 unrolled iterations of 16-pair minibatches."""
+    import time
+    import torch
+    from paper_2509_00774_gb300.autograd import UnrolledSPGM
+    w = W.mid_T16R16_K64_64x64x32()
+    ctx = make_ctx(w.geom)
+    P = w.geom.P
+    all_pairs = to_dev(np.arange(P), "int32")
+    ys = []
+    for sc in range(4):
+        s_true = to_dev(I.point_scene(w.geom.grid, 100, 200 + sc))
+        ys.append(ctx.forward(all_pairs, s_true))
+    y = torch.stack(ys)
+    batches = [to_dev(I.epoch_permutation(P, 7, 0)[16 * i:16 * i + 16], "int32") for i in range(8)]
+    model = UnrolledSPGM(ctx, 8, 0.02, 0.02, checkpoint=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = model(y, batches)
+    loss = out.abs().pow(2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(f"[timing] unrolled 8 iterations x 4 scenes, forward + backward with checkpointing: {dt * 1e3:.1f} ms")
+    assert out.shape == (4, w.geom.N)
+    assert torch.isfinite(model.eta.grad).all() and torch.isfinite(model.lam.grad).all()
