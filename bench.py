@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="bound on the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_bf16x3", "tc_fp16x3"],
+                    help="adjoint arithmetic: CUDA-core FP32 or tensor-core split precision")
+    ap.add_argument("--workload", default="mid", choices=["mid", "large"],
+                    help="mid = the headline workload; large = 32 TX x 32 RX, K = 128, N = 1048576")
     return ap.parse_args()
 
 
@@ -146,7 +150,8 @@ def build_problem(torch, ctx, w, seed_offset):
 
 
 KERNEL_SOURCES = {"fwd_partial_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_forward.cu"),
-                  "adj_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_adjoint.cu")}
+                  "adj_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_adjoint.cu"),
+                  "adj_tc_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_adjoint_tc.cu")}
 
 
 def traffic_for(kernel):
@@ -255,10 +260,11 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    w = W.mid_T16R16_K64_64x64x32()
+    w = W.mid_T16R16_K64_64x64x32() if args.workload == "mid" else W.large_T32R32_K128_128x128x64()
     geom = w.geom
     with torch.cuda.stream(stream):
         ctx = Context(local, stream=stream)
+        ctx.set_precision(args.precision)
         y, eta, lam = build_problem(torch, ctx, w, seed_offset=rank)
         E = args.warmup + args.steps
         perms = np.stack([I.epoch_permutation(geom.P, w.seeds["perm"] + 1000 * rank, e) for e in range(E)])
@@ -351,7 +357,8 @@ def run_ours(args):
         kernels[kind] = entry
     dom = max(("forward_partial", "adjoint"), key=lambda k: kernels.get(k, {}).get("total_ms", 0.0))
     dk = kernels[dom]
-    kname = {"forward_partial": "fwd_partial_kernel", "adjoint": "adj_kernel"}[dom]
+    kname = {"forward_partial": "fwd_partial_kernel",
+             "adjoint": "adj_kernel" if args.precision == "fp32" else "adj_tc_kernel"}[dom]
     roofline = {"bound": "alu", "kernel": kname, "achieved": dk["tflops"], "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": dk["tflops"] / fp32_peak_tflops,
                 "traffic": traffic_for(kname),
@@ -368,7 +375,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "T": geom.T, "R": geom.R, "K": geom.K, "N": geom.N, "M": geom.M,
                    "pairs_per_batch": bp, "minibatches_per_step": geom.P // bp, "step": "one SPGM epoch",
-                   "operator": "fp32 cuda-core (phasor recurrence forward, Horner adjoint)",
+                   "operator": "forward: fp32 cuda-core three-term phasor recurrence; adjoint: " +
+                               ("fp32 cuda-core Horner" if args.precision == "fp32" else
+                                f"tcgen05 {args.precision[3:]} split, FP32 accumulate in TMEM"),
                    "l2": "256 MiB buffer written between timed steps, outside the timed events",
                    "eta": eta, "lambda": lam, "parallelism": f"replicas x{world}"},
         "roofline": roofline,

@@ -90,6 +90,19 @@ int nfm_set_geometry(nfm_ctx* ctx,
 /* Sizes of the current geometry (any pointer may be NULL). */
 int nfm_dims(const nfm_ctx* ctx, int* T, int* R, int* K, long long* N);
 
+/* Arithmetic of the adjoint A_B^H r (and of every call that contains it:
+ * nfm_adjoint, SPGM/PGM steps and epochs, nfm_solve, power iteration,
+ * lambda_max):
+ *   NFM_FP32       CUDA-core FP32 (default),
+ *   NFM_TC_BF16X3  5th-generation tensor cores, operands split x = hi + lo in
+ *                  BF16 and D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated
+ *                  in FP32 (relative error ~1e-5),
+ *   NFM_TC_FP16X3  the same with FP16 halves and the residual scaled per pair
+ *                  by a power of two (relative error ~1e-6).
+ * The forward operator is FP32 in every mode.  Errors: NFM_ERR_ARG. */
+enum { NFM_FP32 = 0, NFM_TC_BF16X3 = 1, NFM_TC_FP16X3 = 2 };
+int nfm_set_precision(nfm_ctx* ctx, int mode);
+
 /* Minibatch forward operator y = A_B s (Eq. 2 rows of the listed pairs).
  *   pairs [n_pairs] int32 (device), s [N] complex64, y [n_pairs*K] complex64.
  * y must not alias s.  Uses library-owned scratch (allocated on first need). */

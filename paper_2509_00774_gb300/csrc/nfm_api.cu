@@ -81,6 +81,12 @@ struct nfm_ctx {
     size_t hperm_cap = 0;
     void* d_prox_partial = nullptr;
     size_t prox_partial_cap = 0;
+    void* d_bmat = nullptr;
+    size_t bmat_cap = 0;
+    void* d_bscale = nullptr;
+    size_t bscale_cap = 0;
+    int precision = NFM_FP32;
+    bool adj_tc_attr[2][MAX_K1 + 1] = {};
 
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -268,9 +274,39 @@ int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s
     return NFM_OK;
 }
 
+int enqueue_adjoint_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r, float2* g_out, float2* s,
+                       float step, float alpha)
+{
+    const int K1 = ctx->K1;
+    const bool f16 = ctx->precision == NFM_TC_FP16X3;
+    const size_t smem = adj_tc_smem_bytes(ADJ_TC_PCHUNK);
+    if (!ctx->adj_tc_attr[f16][K1]) {
+        NFM_CK(cudaFuncSetAttribute(adj_tc_kernel_ptr(K1, f16), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ctx->smem_optin));
+        ctx->adj_tc_attr[f16][K1] = true;
+    }
+    NFM_TRY(ensure(ctx, &ctx->d_bmat, &ctx->bmat_cap, adj_tc_bmat_bytes(n_pairs)));
+    NFM_TRY(ensure(ctx, &ctx->d_bscale, &ctx->bscale_cap, (size_t)n_pairs * sizeof(float)));
+    AdjArgs a;
+    a.pairs = pairs;
+    a.n_pairs = n_pairs;
+    a.r = r;
+    a.g_out = g_out;
+    a.s = s;
+    a.step = step;
+    a.alpha = alpha;
+    a.pchunk = ADJ_TC_PCHUNK;
+    const int e0 = prof_mark(ctx);
+    NFM_CK(launch_adjoint_tc(op_desc(ctx), a, f16, r, (unsigned char*)ctx->d_bmat, (float*)ctx->d_bscale, smem,
+                             ctx->stream));
+    prof_pair(ctx, 2, e0, prof_mark(ctx));
+    return NFM_OK;
+}
+
 int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r, float2* g_out, float2* s,
                     float step, float alpha)
 {
+    if (ctx->precision != NFM_FP32) return enqueue_adjoint_tc(ctx, pairs, n_pairs, r, g_out, s, step, alpha);
     const int K1 = ctx->K1;
     size_t smem = adj_smem_bytes(K1, ADJ_PCHUNK);
     if (!ctx->adj_attr[K1]) {
@@ -300,6 +336,7 @@ int check_flags(nfm_ctx* ctx)
     if (flags) {
         NFM_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
         if (flags & ERRF_PAIR) return fail(ctx, NFM_ERR_ARG, "a pair index was outside [0, P)");
+        if (flags & ERRF_TIMEOUT) return fail(ctx, NFM_ERR_TIMEOUT, "a bounded wait on the tensor core gave up");
         return fail(ctx, NFM_ERR_NUMERIC, "device flag 0x%x", flags);
     }
     return NFM_OK;
@@ -370,7 +407,7 @@ void nfm_destroy(nfm_ctx* ctx)
     else cudaDeviceSynchronize();
     void* ps[] = {ctx->d_ant, ctx->d_ant_xyz, ctx->d_pulse, ctx->d_pairs_all, ctx->d_err, ctx->d_red,
                   ctx->d_partial, ctx->d_resid, ctx->d_v, ctx->d_g, ctx->d_y, ctx->d_hy, ctx->d_hs, ctx->d_hperm,
-                  ctx->d_prox_partial};
+                  ctx->d_prox_partial, ctx->d_bmat, ctx->d_bscale};
     for (void* p : ps) free_ptr(p);
     for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
     delete ctx;
@@ -525,6 +562,15 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     ctx->gd = gd;
     ctx->ph = ph;
     ctx->has_geom = true;
+    return NFM_OK;
+}
+
+int nfm_set_precision(nfm_ctx* ctx, int mode)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    if (mode != NFM_FP32 && mode != NFM_TC_BF16X3 && mode != NFM_TC_FP16X3)
+        return fail(ctx, NFM_ERR_ARG, "unknown precision mode %d", mode);
+    ctx->precision = mode;
     return NFM_OK;
 }
 

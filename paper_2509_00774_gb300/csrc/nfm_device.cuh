@@ -71,7 +71,7 @@ struct OpDesc {
     int* err;              // device error flags
 };
 
-enum : int { ERRF_PAIR = 1 };
+enum : int { ERRF_PAIR = 1, ERRF_TIMEOUT = 2 };
 
 __device__ __forceinline__ float frac_turns(float x) { return x - rintf(x); }
 

@@ -47,6 +47,7 @@ struct AntSetup {
 };
 
 constexpr int FWD_PC = 8;         // pairs per forward CTA
+constexpr int ADJ_TC_PCHUNK = 8;  // pairs whose tensor-core B operands a CTA holds at once
 constexpr int ADJ_THREADS = 128;  // one 8x4x4 tile: two voxels per thread, pairs split in two halves
 constexpr int ADJ_PCHUNK = 32;
 
@@ -77,6 +78,12 @@ cudaError_t launch_fwd_partial(const OpDesc& op, const FwdArgs& a, dim3 grid, in
                                cudaStream_t st);
 cudaError_t launch_fwd_reduce(const OpDesc& op, const ReduceArgs& a, cudaStream_t st);
 cudaError_t launch_adjoint(const OpDesc& op, const AdjArgs& a, size_t smem, cudaStream_t st);
+// tensor-core adjoint: prep kernel (B operands of every pair into bmat) + tcgen05 kernel
+size_t adj_tc_smem_bytes(int pchunk);
+size_t adj_tc_bmat_bytes(int n_pairs);
+const void* adj_tc_kernel_ptr(int K1, bool f16);
+cudaError_t launch_adjoint_tc(const OpDesc& op, const AdjArgs& a, bool f16, const float2* r, unsigned char* bmat,
+                              float* inv_scale, size_t smem, cudaStream_t st);
 cudaError_t launch_ant_setup(const GridDesc& g, const AntSetup& a, cudaStream_t st);
 
 // FP64 reductions (deterministic: fixed grid, fixed tree)

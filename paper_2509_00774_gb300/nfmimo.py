@@ -52,6 +52,7 @@ def load_library(path: str | None = None):
         "nfm_last_error": (ctypes.c_char_p, [vp]),
         "nfm_set_stream": (i, [vp, vp]),
         "nfm_set_geometry": (i, [vp, vp, i, vp, i, vp, i, vp, ctypes.POINTER(_Grid), d]),
+        "nfm_set_precision": (i, [vp, i]),
         "nfm_dims": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                          ctypes.POINTER(ctypes.c_longlong)]),
         "nfm_forward": (i, [vp, vp, i, vp, vp]),
@@ -161,6 +162,12 @@ class Context:
         self.T, self.R, self.K, self.N = tx.shape[0], rx.shape[0], fr.shape[0], g.N
         self.P = self.T * self.R
         self.M = self.P * self.K
+
+    PRECISION = {"fp32": 0, "tc_bf16x3": 1, "tc_fp16x3": 2}
+
+    def set_precision(self, mode):
+        """Adjoint arithmetic: "fp32" (CUDA cores), "tc_bf16x3" or "tc_fp16x3" (tensor cores)."""
+        self._check(self._lib.nfm_set_precision(self._h, self.PRECISION[mode] if isinstance(mode, str) else int(mode)))
 
     def dims(self):
         T, R, K, N = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()

@@ -1,0 +1,97 @@
+"""Tensor-core (tcgen05) adjoint A_B^H r with BF16x3 and FP16x3 operand splits against the FP64
+oracle, and SPGM driven by it.
+
+Tolerances: the split keeps each operand to ~2^-16 (BF16 halves) or ~2^-22 (FP16 halves) relative,
+and the neglected lo*lo product is of the same order, so the BF16x3 adjoint is held to relative l2
+1e-4 (the split tensor-core bound stated for this method's GPU form) and FP16x3 to the FP32 bound 1e-5;
+worst element 5x the bound times the rms, as for the FP32 path.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, nmse
+from paper_2509_00774_gb300 import inputs as I
+from paper_2509_00774_gb300 import workloads as W
+from tests.gpu_helpers import NMSE_TOL, OBJ_TOL, make_ctx, term_scale, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"tc_bf16x3": 1e-4, "tc_fp16x3": 1e-5}
+
+
+def _c64(z):
+    return np.asarray(z, dtype=np.complex64).astype(np.complex128)
+
+
+def _check(got, want, tol, scale=None, what=""):
+    err = got - want
+    ref = np.abs(want) if scale is None else scale
+    rel = np.linalg.norm(err) / np.linalg.norm(ref)
+    worst = np.max(np.abs(err)) / (np.linalg.norm(ref) / np.sqrt(ref.size))
+    print(f"[parity] {what}: n={err.size} rel_l2={rel:.2e} worst/rms={worst:.2e}")
+    assert rel <= tol and worst <= 5 * tol, (what, rel, worst)
+
+
+def _adjoint_case(geom, pairs, mode, seed, cols=None, dense_scale=True):
+    o = Oracle(geom)
+    ctx = make_ctx(geom)
+    ctx.set_precision(mode)
+    rows = o.rows_of_pairs(pairs)
+    r = _c64(I.complex_gaussian(rows.size, seed))
+    g = to_host(ctx.adjoint(to_dev(pairs, "int32"), to_dev(r)))
+    cols = np.arange(geom.N) if cols is None else cols
+    want = o.adjoint(r, rows=rows, cols=cols)
+    scale = term_scale(o.dense(rows, cols).T, r) if dense_scale else None
+    _check(g[cols], want, TOL[mode], scale, f"{mode} adjoint")
+
+
+@pytest.mark.parametrize("mode", ["tc_bf16x3", "tc_fp16x3"])
+@pytest.mark.parametrize("pairs", [[5], [3, 12, 0, 7], list(range(16)), [15, 14, 13, 2, 2, 9, 1, 8, 4, 6, 11]])
+def test_tc_adjoint_small(mode, pairs):
+    _adjoint_case(W.small_T4R4_K16_16x16x8().geom, np.array(pairs), mode, seed=60)
+
+
+@pytest.mark.parametrize("mode", ["tc_bf16x3", "tc_fp16x3"])
+@pytest.mark.parametrize("case", range(4))
+def test_tc_adjoint_ragged(mode, case):
+    from tests.test_gpu_operator import RAGGED, _ragged_geom
+    T, R, K, dims = RAGGED[[0, 1, 3, 4][case]]
+    geom = _ragged_geom(T, R, K, dims, pulse=True, seed=case)
+    rng = np.random.default_rng(300 + case)
+    pairs = rng.choice(T * R, size=min(T * R, 9), replace=False)
+    _adjoint_case(geom, pairs, mode, seed=61 + case)
+
+
+@pytest.mark.parametrize("mode", ["tc_bf16x3", "tc_fp16x3"])
+def test_tc_adjoint_mid_and_large_sampled(mode):
+    rng = np.random.default_rng(62)
+    w = W.mid_T16R16_K64_64x64x32()
+    pairs = I.epoch_permutation(w.geom.P, 2, 0)[:16]
+    _adjoint_case(w.geom, pairs, mode, seed=63, cols=np.sort(rng.choice(w.geom.N, 512, replace=False)),
+                  dense_scale=False)
+    w = W.large_T32R32_K128_128x128x64()
+    pairs = I.epoch_permutation(w.geom.P, 2, 0)[:64]
+    _adjoint_case(w.geom, pairs, mode, seed=64, cols=np.sort(rng.choice(w.geom.N, 256, replace=False)),
+                  dense_scale=False)
+
+
+@pytest.mark.parametrize("mode", ["tc_bf16x3", "tc_fp16x3"])
+def test_tc_spgm_small_matches_oracle(mode):
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    y = _c64(I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, 1), w.snr_db))
+    ctx = make_ctx(w.geom)
+    ctx.set_precision(mode)
+    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
+    eta = float(np.float32(1.0 / L))
+    lam = float(np.float32(0.05 * o.lambda_max(y)))
+    s_orc = np.zeros(o.N, dtype=np.complex128)
+    s_gpu = to_dev(np.zeros(o.N))
+    y_dev = to_dev(y)
+    for e in range(w.epochs):
+        perm = I.epoch_permutation(o.P, w.seeds["perm"], e)
+        s_orc = o.spgm_epoch(y, s_orc, perm, 4, eta, lam)
+        ctx.spgm_epoch(y_dev, s_gpu, to_dev(perm, "int32"), 4, eta, lam)
+        assert nmse(to_host(s_gpu), s_orc) <= NMSE_TOL, e
+    F_gpu, F_orc = o.objective(y, to_host(s_gpu), lam), o.objective(y, s_orc, lam)
+    assert abs(F_gpu - F_orc) <= OBJ_TOL * F_orc
