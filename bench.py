@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_bf16x3", "tc_fp16x3"],
                     help="adjoint arithmetic: CUDA-core FP32 or tensor-core split precision")
-    ap.add_argument("--workload", default="mid", choices=["mid", "large"],
-                    help="mid = the headline workload; large = 32 TX x 32 RX, K = 128, N = 1048576")
+    ap.add_argument("--workload", default="mid", choices=["mid", "large", "batched48"],
+                    help="mid = the headline workload; large = 32 TX x 32 RX, K = 128, N = 1048576; "
+                         "batched48 = 48 uneven scenes per epoch through one CUDA graph")
     return ap.parse_args()
 
 
@@ -394,8 +395,80 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batched(args):
+    """48 uneven scenes (grids 32..96, 8..24 TX/RX, 32..96 freqs), one SPGM epoch of all per step."""
+    import numpy as np
+    import torch
+    from paper_2509_00774_gb300 import build as nb
+    from paper_2509_00774_gb300 import inputs as I
+    from paper_2509_00774_gb300 import workloads as W
+    from paper_2509_00774_gb300.nfmimo import Batch, Context
+    nb.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(device=dev)
+    ws = [W.batched_scene(i) for i in range(48)]
+    E = args.warmup + args.steps
+    with torch.cuda.stream(stream):
+        ctxs, ys, ss, perm_bufs, perm_all, etas, lams = [], [], [], [], [], [], []
+        for w in ws:
+            g = w.geom
+            c = Context(0, stream=stream)
+            c.set_precision(args.precision)
+            c.set_geometry(g)
+            allp = torch.arange(g.P, dtype=torch.int32, device=dev)
+            clean = c.forward(allp, torch.from_numpy(w.scene_vector().astype(np.complex64)).to(dev))
+            noise = torch.from_numpy(I.complex_gaussian(g.M, w.seeds["noise"]).astype(np.complex64)).to(dev)
+            sigma = float(torch.sqrt(torch.mean(clean.abs() ** 2) / 10 ** (w.snr_db / 10)))
+            y = clean + sigma * noise
+            v0 = torch.from_numpy(I.complex_gaussian(g.N, w.seeds["power"]).astype(np.complex64)).to(dev)
+            L = c.power_iteration(v0, 10)
+            ctxs.append(c)
+            ys.append(y)
+            ss.append(torch.zeros(g.N, dtype=torch.complex64, device=dev))
+            perm_all.append(torch.from_numpy(np.stack([I.epoch_permutation(g.P, w.seeds["perm"], e)
+                                                       for e in range(E)]).astype(np.int32)).to(dev))
+            perm_bufs.append(torch.empty(g.P, dtype=torch.int32, device=dev))
+            etas.append(1.0 / L)
+            lams.append(0.05 * c.lambda_max(y))
+        bps = [w.pairs_per_batch for w in ws]
+        batch = Batch(ctxs, stream=stream)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+        def set_perms(e):
+            for pb, pa in zip(perm_bufs, perm_all):
+                pb.copy_(pa[e])
+
+        for e in range(args.warmup):
+            set_perms(e)
+            batch.spgm_epoch(ys, ss, perm_bufs, bps, etas, lams)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for k in range(args.steps):
+            set_perms(args.warmup + k)
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            batch.spgm_epoch(ys, ss, perm_bufs, bps, etas, lams)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        total_ms = float(sum(a.elapsed_time(b) for a, b in zip(starts, ends)))
+    pairs = sum(2.0 * w.geom.M * w.geom.N for w in ws)
+    line = {"metric": METRIC, "value": pairs * args.steps / (total_ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched48_uneven", "scenes": len(ws), "pairs_per_step": pairs,
+                       "step": "one SPGM epoch of all 48 scenes (one CUDA graph, a branch per scene)",
+                       "precision": args.precision, "l2": "256 MiB buffer written between timed steps"}}
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def main():
     args = parse()
+    if args.workload == "batched48" and args.impl != "reference":
+        run_batched(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -158,6 +158,25 @@ int nfm_prox_step(nfm_ctx* ctx, const float* s, const float* g, float step, floa
 int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n,
                            const float* grad_out, float* grad_s, float* grad_g, double* grad_scalars);
 
+/* Batched solves of many independent scenes (uneven grids, arrays and K).
+ * A batch holds n_scenes contexts (each with its own geometry, set by
+ * nfm_set_geometry; the batch does not own them) and enqueues on cuda_stream
+ * (caller-owned; NULL = legacy default stream).  nfm_batch_spgm_epoch runs one
+ * SPGM epoch of every scene: scene i uses y[i] [P_i*K_i], s[i] [N_i] (in
+ * place), perm[i] [P_i] (all device pointers), pairs_per_batch[i], eta[i],
+ * lambda[i] (host arrays of length n_scenes).  The first call captures the
+ * epochs of all scenes into one CUDA graph with one concurrent branch per
+ * scene and later calls replay it while every pointer and parameter is the
+ * same as in the captured call (the contents of y, s and perm may change);
+ * any change re-captures.  Profiling must be off in the scene contexts.
+ * Errors: NFM_ERR_ARG, NFM_ERR_STATE (a scene without geometry), NFM_ERR_CUDA. */
+typedef struct nfm_batch nfm_batch;
+int nfm_batch_create(nfm_batch** out, nfm_ctx* const* scenes, int n_scenes, void* cuda_stream);
+void nfm_batch_destroy(nfm_batch* batch);
+int nfm_batch_spgm_epoch(nfm_batch* batch, const float* const* y, float* const* s, const int* const* perm,
+                         const int* pairs_per_batch, const float* eta, const float* lambda);
+const char* nfm_batch_last_error(const nfm_batch* batch);
+
 /* Largest eigenvalue L of A^H A / M by `iters` power iterations from
  * v0 [N] (device, complex64, not modified), with FP64 norms:
  *   v <- A^H A v / ||A^H A v||, then L = ||A v||^2 / (M ||v||^2).

@@ -86,6 +86,7 @@ struct nfm_ctx {
     void* d_bscale = nullptr;
     size_t bscale_cap = 0;
     int precision = NFM_FP32;
+    unsigned long long scratch_gen = 0;   // bumped whenever a scratch buffer is (re)allocated
     bool adj_tc_attr[2][MAX_K1 + 1] = {};
 
     bool prof = false;
@@ -144,6 +145,7 @@ int ensure(nfm_ctx* ctx, void** p, size_t* cap, size_t bytes)
         if (e != cudaSuccess) return fail(ctx, NFM_ERR_CUDA, "cudaFree failed: %s", cudaGetErrorString(e));
     }
     size_t want = bytes < 256 ? 256 : bytes;
+    ++ctx->scratch_gen;
     cudaError_t e = cudaMalloc(p, want);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -947,3 +949,198 @@ extern "C" int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, 
     NFM_CK(launch_fwd_reduce(op, ra, ctx->stream));
     return NFM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched scenes: one CUDA graph per epoch with a concurrent branch per scene.
+struct nfm_batch {
+    std::vector<nfm_ctx*> scenes;
+    cudaStream_t stream = nullptr;          // caller's stream (graph launches)
+    cudaStream_t cap = nullptr;             // capture origin
+    std::vector<cudaStream_t> branch;       // one per scene
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec = nullptr;
+    // arguments of the captured call
+    std::vector<const void*> y, s, perm;
+    std::vector<int> bp;
+    std::vector<float> eta, lam;
+    std::vector<unsigned long long> gen;   // scene scratch generations the graph was captured with
+    std::string err;
+};
+
+namespace {
+
+int bfail(nfm_batch* b, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    b->err = buf;
+    return code;
+}
+
+#define NFM_BCK(call)                                                                         \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bfail(b, NFM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+// Allocate and plan everything an epoch of this scene needs, so that the capture
+// performs no allocation.
+int prepare_epoch(nfm_ctx* ctx, int bp)
+{
+    NFM_TRY(ensure(ctx, &ctx->d_resid, &ctx->resid_cap, (size_t)bp * ctx->K * sizeof(float2)));
+    for (int nb : {bp, ctx->P % bp}) {
+        if (nb <= 0) continue;
+        FwdPlan pl;
+        NFM_TRY(plan_forward(ctx, nb, &pl));
+        NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, pl.partial_bytes));
+        if (ctx->precision != NFM_FP32) {
+            NFM_TRY(ensure(ctx, &ctx->d_bmat, &ctx->bmat_cap, adj_tc_bmat_bytes(nb)));
+            NFM_TRY(ensure(ctx, &ctx->d_bscale, &ctx->bscale_cap, (size_t)nb * sizeof(float)));
+        }
+    }
+    const int K1 = ctx->K1;
+    if (ctx->precision == NFM_FP32 && !ctx->adj_attr[K1]) {
+        NFM_CK(cudaFuncSetAttribute(adj_kernel_ptr(K1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ctx->smem_optin));
+        ctx->adj_attr[K1] = true;
+    }
+    if (ctx->precision != NFM_FP32) {
+        const bool f16 = ctx->precision == NFM_TC_FP16X3;
+        if (!ctx->adj_tc_attr[f16][K1]) {
+            NFM_CK(cudaFuncSetAttribute(adj_tc_kernel_ptr(K1, f16), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ctx->smem_optin));
+            ctx->adj_tc_attr[f16][K1] = true;
+        }
+    }
+    return NFM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nfm_batch_create(nfm_batch** out, nfm_ctx* const* scenes, int n_scenes, void* cuda_stream)
+{
+    if (!out) return NFM_ERR_ARG;
+    *out = nullptr;
+    if (!scenes || n_scenes < 1) return fail(nullptr, NFM_ERR_ARG, "need at least one scene");
+    for (int i = 0; i < n_scenes; ++i)
+        if (!scenes[i]) return fail(nullptr, NFM_ERR_ARG, "scene %d is NULL", i);
+    const int dev = scenes[0]->device;
+    for (int i = 1; i < n_scenes; ++i)
+        if (scenes[i]->device != dev) return fail(nullptr, NFM_ERR_ARG, "all scenes must be on one device");
+    DevGuard guard(dev);
+    nfm_batch* b = new nfm_batch();
+    b->scenes.assign(scenes, scenes + n_scenes);
+    b->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    b->branch.assign(n_scenes, nullptr);
+    b->join.assign(n_scenes, nullptr);
+    for (int i = 0; i < n_scenes && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        nfm_batch_destroy(b);
+        return fail(nullptr, NFM_ERR_CUDA, "batch streams/events: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return NFM_OK;
+}
+
+void nfm_batch_destroy(nfm_batch* b)
+{
+    if (!b) return;
+    DevGuard guard(b->scenes.empty() ? 0 : b->scenes[0]->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaStream_t st : b->branch)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join)
+        if (ev) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+const char* nfm_batch_last_error(const nfm_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+int nfm_batch_spgm_epoch(nfm_batch* b, const float* const* y, float* const* s, const int* const* perm,
+                         const int* pairs_per_batch, const float* eta, const float* lambda)
+{
+    if (!b) return NFM_ERR_ARG;
+    const int n = (int)b->scenes.size();
+    if (!y || !s || !perm || !pairs_per_batch || !eta || !lambda) return bfail(b, NFM_ERR_ARG, "NULL argument array");
+    DevGuard guard(b->scenes[0]->device);
+    bool same = b->exec != nullptr;
+    for (int i = 0; i < n; ++i) {
+        nfm_ctx* c = b->scenes[i];
+        if (!c->has_geom) return bfail(b, NFM_ERR_STATE, "scene %d has no geometry", i);
+        if (c->prof) return bfail(b, NFM_ERR_STATE, "scene %d has profiling enabled", i);
+        if (pairs_per_batch[i] < 1) return bfail(b, NFM_ERR_ARG, "scene %d: pairs_per_batch < 1", i);
+        if (!(eta[i] > 0) || !std::isfinite(eta[i]) || !(lambda[i] >= 0) || !std::isfinite(lambda[i]))
+            return bfail(b, NFM_ERR_ARG, "scene %d: bad eta/lambda", i);
+        if (!y[i] || !s[i] || !perm[i]) return bfail(b, NFM_ERR_ARG, "scene %d: NULL vector", i);
+        if (same && (b->y[i] != y[i] || b->s[i] != s[i] || b->perm[i] != perm[i] || b->bp[i] != pairs_per_batch[i] ||
+                     b->eta[i] != eta[i] || b->lam[i] != lambda[i] || b->gen[i] != c->scratch_gen))
+            same = false;
+    }
+    if (!same) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        for (int i = 0; i < n; ++i) {
+            int r = prepare_epoch(b->scenes[i], pairs_per_batch[i]);
+            if (r != NFM_OK) return bfail(b, r, "scene %d: %s", i, b->scenes[i]->err.c_str());
+        }
+        NFM_BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = NFM_OK;
+        cudaError_t e = cudaEventRecord(b->fork, b->cap);
+        for (int i = 0; i < n && e == cudaSuccess && rc == NFM_OK; ++i) {
+            nfm_ctx* c = b->scenes[i];
+            e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+            if (e != cudaSuccess) break;
+            cudaStream_t saved = c->stream;
+            c->stream = b->branch[i];
+            rc = spgm_epoch_impl(c, (const float2*)y[i], (float2*)s[i], perm[i], pairs_per_batch[i], eta[i], lambda[i]);
+            c->stream = saved;
+            if (rc != NFM_OK) break;
+            e = cudaEventRecord(b->join[i], b->branch[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[i], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+        if (rc != NFM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return bfail(b, rc, "capture: %s", b->scenes[0]->err.c_str());
+        }
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return bfail(b, NFM_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return bfail(b, NFM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+        b->y.assign(y, y + n);
+        b->s.assign((const void* const*)s, (const void* const*)s + n);
+        b->perm.assign((const void* const*)perm, (const void* const*)perm + n);
+        b->bp.assign(pairs_per_batch, pairs_per_batch + n);
+        b->eta.assign(eta, eta + n);
+        b->lam.assign(lambda, lambda + n);
+        b->gen.resize(n);
+        for (int i = 0; i < n; ++i) b->gen[i] = b->scenes[i]->scratch_gen;
+    }
+    NFM_BCK(cudaGraphLaunch(b->exec, b->stream));
+    return NFM_OK;
+}
+
+}  // extern "C"

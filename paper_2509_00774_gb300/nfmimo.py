@@ -70,6 +70,11 @@ def load_library(path: str | None = None):
         "nfm_lambda_max": (i, [vp, vp, ctypes.POINTER(d)]),
         "nfm_synchronize": (i, [vp]),
         "nfm_profile_enable": (i, [vp, i]),
+        "nfm_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]),
+        "nfm_batch_destroy": (None, [vp]),
+        "nfm_batch_spgm_epoch": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(i), ctypes.POINTER(f), ctypes.POINTER(f)]),
+        "nfm_batch_last_error": (ctypes.c_char_p, [vp]),
         "nfm_profile_report": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
     }
     for name, (res, args) in sig.items():
@@ -302,3 +307,48 @@ class Context:
         cnt = (ctypes.c_longlong * n)()
         self._check(self._lib.nfm_profile_report(self._h, ms, cnt, n))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(self.PROFILE_KINDS)}
+
+
+class Batch:
+    """nfm_batch: one SPGM epoch of many scenes (each a Context with its own geometry) per call,
+    run as one CUDA graph with a concurrent branch per scene."""
+
+    def __init__(self, contexts, stream=None):
+        import torch
+        self._lib = load_library()
+        self.contexts = list(contexts)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.contexts[0].device)
+        self._stream = stream
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.handle.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        rc = self._lib.nfm_batch_create(ctypes.byref(h), arr, len(self.contexts), ctypes.c_void_p(stream.cuda_stream))
+        if rc != NFM_OK:
+            raise NfmError(rc, self._lib.nfm_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nfm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spgm_epoch(self, ys, ss, perms, pairs_per_batch, etas, lams):
+        """ys, ss, perms: per-scene device tensors (complex64, complex64 in/out, int32)."""
+        import torch
+        n = len(self.contexts)
+        P = ctypes.c_void_p
+        def ptrs(ts, dt, name):
+            return (P * n)(*[_ptr(t, dt, name, self.contexts[0].device).value for t in ts])
+        bp = (ctypes.c_int * n)(*[int(x) for x in pairs_per_batch])
+        et = (ctypes.c_float * n)(*[float(x) for x in etas])
+        la = (ctypes.c_float * n)(*[float(x) for x in lams])
+        rc = self._lib.nfm_batch_spgm_epoch(self._h, ptrs(ys, torch.complex64, "y"), ptrs(ss, torch.complex64, "s"),
+                                            ptrs(perms, torch.int32, "perm"), bp, et, la)
+        if rc != NFM_OK:
+            raise NfmError(rc, self._lib.nfm_batch_last_error(self._h).decode())

@@ -35,11 +35,15 @@ def test_binding_covers_the_boundary():
     for n in _declared():
         assert getattr(lib, n).argtypes is not None or n == "nfm_destroy", n
     ctx_methods = {m for m in dir(nfmimo.Context) if not m.startswith("_")}
+    batch_methods = {m for m in dir(nfmimo.Batch) if not m.startswith("_")}
     for n in _declared():
         short = n[len("nfm_"):]
-        if short in ("create", "destroy", "last_error"):
+        if short in ("create", "destroy", "last_error", "batch_create", "batch_destroy", "batch_last_error"):
             continue
-        assert short in ctx_methods, short
+        if short.startswith("batch_"):
+            assert short[len("batch_"):] in batch_methods, short
+        else:
+            assert short in ctx_methods, short
 
 
 def test_create_without_gpu_fails_cleanly():
