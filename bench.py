@@ -61,6 +61,22 @@ def dist_env():
     return rank, world, local
 
 
+def ranks_max(x: float, device="cpu") -> float:
+    """Maximum of x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pairs_per_step: float, steps: int, world: int, max_seconds: float) -> float:
+    """Whole-job G pairs/s: every rank runs its own replica of the same workload (weak scaling)."""
+    return pairs_per_step * steps * world / max_seconds / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -307,13 +323,9 @@ def run_ours(args):
         time.sleep(0.25)
         sampler.stop()
         step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-        total_ms = float(sum(step_ms))
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = ranks_max(float(sum(step_ms)), dev)
         pairs_per_step = 2.0 * geom.M * geom.N
-        value = pairs_per_step * args.steps * world / (total_ms * 1e-3) / 1e9
+        value = job_throughput(pairs_per_step, args.steps, world, total_ms * 1e-3)
 
         # end to end through the host-buffer entry point (copies inside the timed region)
         y_host = torch.empty(geom.M, dtype=torch.complex64, pin_memory=True)
@@ -328,12 +340,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for k in range(e2e_steps):
             ctx.spgm_epochs_host(y_host, s_host, perms_host[k % E:k % E + 1], bp, eta, lam)
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e_value = pairs_per_step * e2e_steps * world / e2e_s / 1e9
+        e2e_s = ranks_max(time.perf_counter() - t0, dev)
+        e2e_value = job_throughput(pairs_per_step, e2e_steps, world, e2e_s)
         h2d = geom.M * 8 + geom.N * 8 + geom.P * 4
         d2h = geom.N * 8
 

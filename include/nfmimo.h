@@ -132,6 +132,16 @@ int nfm_spgm_epoch(nfm_ctx* ctx, const float* y, float* s, const int* perm, int 
 int nfm_spgm_epochs_host(nfm_ctx* ctx, const float* y_host, float* s_host, const int* perms_host,
                          int n_epochs, int pairs_per_batch, float eta, float lambda);
 
+/* SPGM iteration on a Cartesian minibatch (Sec. IV-A: B = #f x #Tx x #Rx
+ * rows): the rows of the listed pairs at the frequencies k with
+ * freq_mask[k] != 0 (device uint8 [K]; n_freq = number of nonzero entries, so
+ * B = n_pairs * n_freq).  The forward runs over all K frequencies of the pairs
+ * and the residual of unselected rows is set to 0, so the adjoint is exactly
+ * A_B^H (A_B s - y_B).  For the paper's composition pass the pairs of #Tx
+ * transmitters x #Rx receivers. */
+int nfm_spgm_step_freqs(nfm_ctx* ctx, const float* y, float* s, const int* pairs, int n_pairs,
+                        const unsigned char* freq_mask, int n_freq, float eta, float lambda);
+
 /* One full-batch PGM iteration (Sec. IV, Eq. 5): nfm_spgm_step with every
  * pair in index order, B = M rows.  y [P*K], s [N] (in place), device. */
 int nfm_pgm_step(nfm_ctx* ctx, const float* y, float* s, float eta, float lambda);

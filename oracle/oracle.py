@@ -189,6 +189,16 @@ class Oracle:
         res = self.forward(s, rows=rows) - np.asarray(y)[rows]
         return self.adjoint(res, rows=rows) / rows.size
 
+    def rows_gradient(self, y, s, rows) -> np.ndarray:
+        """grad of (1/B) sum_{m in rows} D_m(s) = A_rows^H (A_rows s - y_rows) / B   (Eq. 6, any row set)."""
+        rows = np.asarray(rows, dtype=np.int64)
+        res = self.forward(s, rows=rows) - np.asarray(y)[rows]
+        return self.adjoint(res, rows=rows) / rows.size
+
+    def spgm_step_rows(self, y, s, rows, eta, lam) -> np.ndarray:
+        """SPGM iteration (Eq. 5) with the minibatch gradient over an explicit row set."""
+        return prox_l1(s - eta * self.rows_gradient(y, s, rows), lam * eta)
+
     def pgm_step(self, y, s, eta, lam) -> np.ndarray:
         """One PGM fixed-point iteration (Eq. 5), full batch."""
         return prox_l1(s - eta * self.full_gradient(y, s), lam * eta)

@@ -241,9 +241,9 @@ int plan_forward(nfm_ctx* ctx, int n_pairs, FwdPlan* pl)
     return NFM_OK;
 }
 
-// out[b*K + k] = (A_B s)[b, k] (- y_obs[pair_b*K + k] if y_obs)
+// out[b*K + k] = (A_B s)[b, k] (- y_obs[pair_b*K + k] if y_obs; 0 where fmask[k] == 0)
 int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
-                    float2* out)
+                    float2* out, const unsigned char* fmask = nullptr)
 {
     FwdPlan pl;
     NFM_TRY(plan_forward(ctx, n_pairs, &pl));
@@ -268,6 +268,7 @@ int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s
     ra.n_out = n_pairs * ctx->K;
     ra.pairs = pairs;
     ra.y_obs = y_obs;
+    ra.fmask = fmask;
     ra.out = out;
     NFM_CK(launch_fwd_reduce(op, ra, ctx->stream));
     const int e2 = prof_mark(ctx);
@@ -660,6 +661,27 @@ int nfm_spgm_epochs_host(nfm_ctx* ctx, const float* y_host, float* s_host, const
     return check_flags(ctx);
 }
 
+int nfm_spgm_step_freqs(nfm_ctx* ctx, const float* y, float* s, const int* pairs, int n_pairs,
+                        const unsigned char* freq_mask, int n_freq, float eta, float lambda)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
+    if (n_freq < 1 || n_freq > ctx->K) return fail(ctx, NFM_ERR_ARG, "n_freq must be in [1, K]");
+    if (!(eta > 0) || !std::isfinite(eta)) return fail(ctx, NFM_ERR_ARG, "eta must be finite and > 0");
+    if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(ctx, NFM_ERR_ARG, "lambda must be finite and >= 0");
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, pairs, "pairs", 4));
+    NFM_TRY(check_ptr(ctx, freq_mask, "freq_mask", 1));
+    NFM_TRY(ensure(ctx, &ctx->d_resid, &ctx->resid_cap, (size_t)n_pairs * ctx->K * sizeof(float2)));
+    float2* r = (float2*)ctx->d_resid;
+    NFM_TRY(enqueue_forward(ctx, pairs, n_pairs, (const float2*)s, (const float2*)y, r, freq_mask));
+    const double B = (double)n_pairs * n_freq;
+    return enqueue_adjoint(ctx, pairs, n_pairs, r, nullptr, (float2*)s, (float)(eta / B),
+                           (float)((double)eta * lambda));
+}
+
 int nfm_pgm_step(nfm_ctx* ctx, const float* y, float* s, float eta, float lambda)
 {
     NFM_TRY(require_geom(ctx));
@@ -945,6 +967,7 @@ extern "C" int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, 
     ra.n_out = n_pairs * ctx->K;
     ra.pairs = pairs;
     ra.y_obs = nullptr;
+    ra.fmask = nullptr;
     ra.out = (float2*)y;
     NFM_CK(launch_fwd_reduce(op, ra, ctx->stream));
     return NFM_OK;

@@ -23,6 +23,7 @@ struct ReduceArgs {
     int n_out;               // n_pairs * K
     const int* pairs;        // [n_pairs] (only read when y_obs != nullptr)
     const float2* y_obs;     // full measurement vector [P*K] or nullptr
+    const unsigned char* fmask;  // [K]: rows with fmask[k] == 0 get a zero residual (nullptr = all rows)
     float2* out;             // [n_pairs * K]
 };
 

@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(1024) fwd_reduce_kernel(OpDesc op, ReduceArgs 
             float2 yo = a.y_obs[(size_t)pair * op.K + k];
             t.x -= yo.x;
             t.y -= yo.y;
+            if (a.fmask && !a.fmask[k]) t = make_float2(0.f, 0.f);
         }
         a.out[o] = t;
     }

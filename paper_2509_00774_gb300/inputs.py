@@ -157,6 +157,31 @@ def epoch_permutation(P: int, seed: int, epoch: int) -> np.ndarray:
     return np.asarray(perm, dtype=np.int32)
 
 
+def _draw_subset(n: int, k: int, state: int):
+    """k distinct indices of range(n) by a partial Fisher-Yates shuffle (SplitMix64 draws)."""
+    idx = list(range(n))
+    for i in range(k):
+        state, x = splitmix64_next(state)
+        u = (x >> 11) * (1.0 / 9007199254740992.0)
+        j = i + int(u * (n - i))
+        idx[i], idx[j] = idx[j], idx[i]
+    return sorted(idx[:k]), state
+
+
+def cartesian_minibatch(T: int, R: int, K: int, n_tx: int, n_rx: int, n_f: int, seed: int, it: int):
+    """Minibatch of composition (#f, #Tx, #Rx) (Sec. IV-A): n_tx transmitters, n_rx receivers and
+    n_f frequencies drawn without replacement for iteration `it`.  Returns (pairs int32 [n_tx*n_rx],
+    frequency mask uint8 [K]); B = n_f * n_tx * n_rx rows."""
+    state = (seed ^ ((_GOLDEN * (it + 1)) & _M64) ^ 0x5DEECE66D) & _M64
+    txs, state = _draw_subset(T, n_tx, state)
+    rxs, state = _draw_subset(R, n_rx, state)
+    fs, state = _draw_subset(K, n_f, state)
+    pairs = np.array([t * R + r for t in txs for r in rxs], dtype=np.int32)
+    mask = np.zeros(K, dtype=np.uint8)
+    mask[fs] = 1
+    return pairs, mask
+
+
 def complex_gaussian(n: int, seed: int) -> np.ndarray:
     """Standard circular complex Gaussian draws with E|g|^2 = 1 (complex128)."""
     rng = np.random.default_rng(seed)

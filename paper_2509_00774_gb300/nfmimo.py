@@ -62,6 +62,7 @@ def load_library(path: str | None = None):
         "nfm_spgm_epoch": (i, [vp, vp, vp, vp, i, f, f]),
         "nfm_spgm_epochs_host": (i, [vp, vp, vp, vp, i, i, f, f]),
         "nfm_pgm_step": (i, [vp, vp, vp, f, f]),
+        "nfm_spgm_step_freqs": (i, [vp, vp, vp, vp, i, vp, i, f, f]),
         "nfm_solve": (i, [vp, vp, vp, vp, i, i, f, f, d, ctypes.POINTER(i), ctypes.POINTER(d)]),
         "nfm_prox_step": (i, [vp, vp, vp, f, f, ctypes.c_longlong, vp]),
         "nfm_prox_step_backward": (i, [vp, vp, vp, f, f, ctypes.c_longlong, vp, vp, vp, vp]),
@@ -245,6 +246,15 @@ class Context:
             self._h, hp(y_host, np.complex64, "y_host"), hp(s_host, np.complex64, "s_host"),
             hp(perms, np.int32, "perms_host"), n_epochs, int(pairs_per_batch), float(eta), float(lam)))
         return s_host
+
+    def spgm_step_freqs(self, y, s, pairs, freq_mask, eta, lam):
+        """SPGM step on the rows (pairs x selected frequencies); freq_mask: uint8 device tensor [K]."""
+        import torch
+        n_freq = int(freq_mask.count_nonzero())
+        self._check(self._lib.nfm_spgm_step_freqs(
+            self._h, self._c(y, "y"), self._c(s, "s"), self._i(pairs, "pairs"), pairs.numel(),
+            _ptr(freq_mask, torch.uint8, "freq_mask", self.device), n_freq, float(eta), float(lam)))
+        return s
 
     def pgm_step(self, y, s, eta, lam):
         """One full-batch PGM iteration (every pair), s updated in place."""

@@ -118,6 +118,27 @@ def test_solve_termination_rule():
     assert nmse(to_host(s_gpu), ref) <= NMSE_TOL
 
 
+@pytest.mark.parametrize("comp", [(4, 2, 3), (16, 4, 4), (1, 1, 1)])
+def test_cartesian_minibatch_steps_match_oracle(comp):
+    """Minibatches of composition (#f, #Tx, #Rx) (Sec. IV-A) on the small workload."""
+    n_f, n_t, n_r = comp
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
+    eta = float(np.float32(0.5 / L))
+    lam = float(np.float32(0.05 * o.lambda_max(y)))
+    s_orc = np.zeros(o.N, dtype=np.complex128)
+    s_gpu = to_dev(np.zeros(o.N))
+    y_dev = to_dev(y)
+    import torch
+    for it in range(12):
+        pairs, mask = I.cartesian_minibatch(o.T, o.R, o.K, n_t, n_r, n_f, seed=4, it=it)
+        rows = np.array([p * o.K + k for p in pairs for k in np.flatnonzero(mask)])
+        s_orc = o.spgm_step_rows(y, s_orc, rows, eta, lam)
+        ctx.spgm_step_freqs(y_dev, s_gpu, to_dev(pairs, "int32"), torch.from_numpy(mask).cuda(), eta, lam)
+        assert nmse(to_host(s_gpu), s_orc) <= NMSE_TOL, it
+
+
 def test_spgm_host_buffers_match_device():
     w, o, y = _small_problem()
     ctx = make_ctx(w.geom)

@@ -72,3 +72,17 @@ def test_grid_positions():
     assert np.allclose(pos[0], [-0.05, -0.05, 0.25])
     assert np.allclose(pos[-1], [-0.05 + 15 * 0.1 / 16, -0.05 + 15 * 0.1 / 16, 0.29])
     assert np.allclose(pos[17], [-0.05 + 0.1 / 16, -0.05 + 0.1 / 16, 0.25])
+
+
+def test_cartesian_minibatch_composition():
+    for it in range(20):
+        pairs, mask = I.cartesian_minibatch(16, 9, 11, 4, 3, 4, seed=3, it=it)
+        assert pairs.dtype == np.int32 and pairs.size == 12 and len(set(pairs.tolist())) == 12
+        assert mask.dtype == np.uint8 and mask.sum() == 4 and mask.size == 11
+        tx = sorted({p // 9 for p in pairs.tolist()})
+        rx = sorted({p % 9 for p in pairs.tolist()})
+        assert len(tx) == 4 and len(rx) == 3
+        assert all(t * 9 + r in pairs for t in tx for r in rx)     # full Cartesian product
+    a = I.cartesian_minibatch(16, 9, 11, 4, 3, 4, seed=3, it=5)
+    b = I.cartesian_minibatch(16, 9, 11, 4, 3, 4, seed=3, it=5)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

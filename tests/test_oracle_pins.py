@@ -231,6 +231,21 @@ def test_minibatch_gradient_is_unbiased():
     assert np.linalg.norm(np.mean(gs, axis=0) - full) <= 1e-12 * np.linalg.norm(full)
 
 
+def test_rows_gradient_all_rows_is_full_gradient():
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    s = I.complex_gaussian(o.N, 33) * 0.1
+    y = I.complex_gaussian(o.M, 34)
+    full = o.full_gradient(y, s)
+    assert np.linalg.norm(o.rows_gradient(y, s, np.arange(o.M)) - full) <= 1e-13 * np.linalg.norm(full)
+    # a Cartesian minibatch: rows (pair, k) for the chosen pairs and frequencies, against the dense matrix
+    pairs, mask = I.cartesian_minibatch(o.T, o.R, o.K, 2, 3, 5, seed=1, it=0)
+    rows = np.array([p * o.K + k for p in pairs for k in np.flatnonzero(mask)])
+    A = o.dense(rows, np.arange(o.N))
+    want = A.conj().T @ (A @ s - y[rows]) / rows.size
+    assert np.linalg.norm(o.rows_gradient(y, s, rows) - want) <= 1e-12 * np.linalg.norm(want)
+
+
 def test_spgm_epoch_equals_sequence_of_steps():
     w = W.small_T4R4_K16_16x16x8()
     o = Oracle(w.geom)
