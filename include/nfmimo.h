@@ -103,6 +103,14 @@ int nfm_dims(const nfm_ctx* ctx, int* T, int* R, int* K, long long* N);
 enum { NFM_FP32 = 0, NFM_TC_BF16X3 = 1, NFM_TC_FP16X3 = 2 };
 int nfm_set_precision(nfm_ctx* ctx, int mode);
 
+/* Regulariser of Eq. 3 (Sec. III uses l1 and notes the method extends to
+ * other functionals): R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 (elastic net;
+ * default w1 = 1, w2 = 0, the paper's l1; w1 = 0 is Tikhonov).  Its prox,
+ * used by every SPGM/PGM step, is
+ *   prox(z) = z max(0, 1 - eta lambda w1/|z|) / (1 + eta lambda w2),
+ * and nfm_objective adds lambda R(s).  Weights finite, >= 0, not both 0. */
+int nfm_set_regularizer(nfm_ctx* ctx, double w1, double w2);
+
 /* Minibatch forward operator y = A_B s (Eq. 2 rows of the listed pairs).
  *   pairs [n_pairs] int32 (device), s [N] complex64, y [n_pairs*K] complex64.
  * y must not alias s.  Uses library-owned scratch (allocated on first need). */
@@ -193,8 +201,8 @@ const char* nfm_batch_last_error(const nfm_batch* batch);
  * Writes *L_out (host) and synchronises.  The SPGM step is eta = 1/L. */
 int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out);
 
-/* Objective of Eq. 3 with Eq. 4 and the l1 term, accumulated in FP64:
- *   F(s) = ||y - A s||^2 / (2M) + lambda sum_n |s_n|.
+/* Objective of Eq. 3 with Eq. 4 and the regulariser, accumulated in FP64:
+ *   F(s) = ||y - A s||^2 / (2M) + lambda R(s)   (R = sum_n |s_n| by default).
  * y [P*K], s [N] device.  Writes *F_out (host) and synchronises. */
 int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, double* F_out);
 

@@ -101,8 +101,10 @@ def _cplx(z):
 class Oracle:
     """FP64 operator on one geometry (an `inputs.Geometry`)."""
 
-    def __init__(self, geom):
+    def __init__(self, geom, w1: float = 1.0, w2: float = 0.0):
+        """w1, w2: regulariser R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 (w2 = 0: the paper's l1)."""
         self.geom = geom
+        self.w1, self.w2 = float(w1), float(w2)
         self.T, self.R, self.K = geom.T, geom.R, geom.K
         self.P, self.M, self.N = geom.P, geom.M, geom.N
         self._tx = np.ascontiguousarray(geom.tx, dtype=np.float64)
@@ -175,9 +177,18 @@ class Oracle:
         res = np.asarray(y) - self.forward(s)
         return float(np.vdot(res, res).real) / (2.0 * self.M)
 
+    def regulariser(self, s) -> float:
+        """R(s) = w1 sum |s_n| + (w2/2) sum |s_n|^2   (Sec. III; l1 when w2 = 0)."""
+        s = np.asarray(s)
+        return self.w1 * float(np.sum(np.abs(s))) + 0.5 * self.w2 * float(np.vdot(s, s).real)
+
+    def prox(self, z, alpha_eta):
+        """prox of (eta lambda) R at z, alpha_eta = eta lambda."""
+        return prox_l1(z, alpha_eta * self.w1) / (1.0 + alpha_eta * self.w2)
+
     def objective(self, y, s, lam) -> float:
-        """D(s) + lambda R(s), R(s) = sum |s_n|   (Eq. 3, Eq. 4)."""
-        return self.data_fidelity(y, s) + lam * float(np.sum(np.abs(s)))
+        """D(s) + lambda R(s)   (Eq. 3, Eq. 4)."""
+        return self.data_fidelity(y, s) + lam * self.regulariser(s)
 
     def full_gradient(self, y, s) -> np.ndarray:
         """grad D(s) = A^H (A s - y) / M."""
@@ -197,15 +208,15 @@ class Oracle:
 
     def spgm_step_rows(self, y, s, rows, eta, lam) -> np.ndarray:
         """SPGM iteration (Eq. 5) with the minibatch gradient over an explicit row set."""
-        return prox_l1(s - eta * self.rows_gradient(y, s, rows), lam * eta)
+        return self.prox(s - eta * self.rows_gradient(y, s, rows), lam * eta)
 
     def pgm_step(self, y, s, eta, lam) -> np.ndarray:
         """One PGM fixed-point iteration (Eq. 5), full batch."""
-        return prox_l1(s - eta * self.full_gradient(y, s), lam * eta)
+        return self.prox(s - eta * self.full_gradient(y, s), lam * eta)
 
     def spgm_step(self, y, s, pairs, eta, lam) -> np.ndarray:
         """One SPGM iteration: Eq. 5 with the minibatch gradient of Eq. 6."""
-        return prox_l1(s - eta * self.minibatch_gradient(y, s, pairs), lam * eta)
+        return self.prox(s - eta * self.minibatch_gradient(y, s, pairs), lam * eta)
 
     def spgm_epoch(self, y, s, perm, pairs_per_batch, eta, lam) -> np.ndarray:
         """One pass over a permutation of the pairs in chunks of B_p pairs."""

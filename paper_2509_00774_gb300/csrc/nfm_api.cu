@@ -86,6 +86,7 @@ struct nfm_ctx {
     void* d_bscale = nullptr;
     size_t bscale_cap = 0;
     int precision = NFM_FP32;
+    double reg_w1 = 1.0, reg_w2 = 0.0;    // R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2
     unsigned long long scratch_gen = 0;   // bumped whenever a scratch buffer is (re)allocated
     bool adj_tc_attr[2][MAX_K1 + 1] = {};
 
@@ -278,7 +279,7 @@ int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s
 }
 
 int enqueue_adjoint_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r, float2* g_out, float2* s,
-                       float step, float alpha)
+                       float step, float alpha, float shrink)
 {
     const int K1 = ctx->K1;
     const bool f16 = ctx->precision == NFM_TC_FP16X3;
@@ -298,6 +299,7 @@ int enqueue_adjoint_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2
     a.s = s;
     a.step = step;
     a.alpha = alpha;
+    a.shrink = shrink;
     a.pchunk = ADJ_TC_PCHUNK;
     const int e0 = prof_mark(ctx);
     NFM_CK(launch_adjoint_tc(op_desc(ctx), a, f16, r, (unsigned char*)ctx->d_bmat, (float*)ctx->d_bscale, smem,
@@ -307,9 +309,9 @@ int enqueue_adjoint_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2
 }
 
 int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r, float2* g_out, float2* s,
-                    float step, float alpha)
+                    float step, float alpha, float shrink = 1.0f)
 {
-    if (ctx->precision != NFM_FP32) return enqueue_adjoint_tc(ctx, pairs, n_pairs, r, g_out, s, step, alpha);
+    if (ctx->precision != NFM_FP32) return enqueue_adjoint_tc(ctx, pairs, n_pairs, r, g_out, s, step, alpha, shrink);
     const int K1 = ctx->K1;
     size_t smem = adj_smem_bytes(K1, ADJ_PCHUNK);
     if (!ctx->adj_attr[K1]) {
@@ -325,6 +327,7 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
     a.s = s;
     a.step = step;
     a.alpha = alpha;
+    a.shrink = shrink;
     a.pchunk = ADJ_PCHUNK;
     const int e0 = prof_mark(ctx);
     NFM_CK(launch_adjoint(op_desc(ctx), a, smem, ctx->stream));
@@ -352,7 +355,9 @@ int spgm_step_impl(nfm_ctx* ctx, const float2* y, float2* s, const int* pairs, i
     float2* r = (float2*)ctx->d_resid;
     NFM_TRY(enqueue_forward(ctx, pairs, n_pairs, s, y, r));
     const double B = (double)n_pairs * ctx->K;
-    NFM_TRY(enqueue_adjoint(ctx, pairs, n_pairs, r, nullptr, s, (float)(eta / B), (float)((double)eta * lambda)));
+    NFM_TRY(enqueue_adjoint(ctx, pairs, n_pairs, r, nullptr, s, (float)(eta / B),
+                            (float)((double)eta * lambda * ctx->reg_w1),
+                            (float)(1.0 / (1.0 + (double)eta * lambda * ctx->reg_w2))));
     return NFM_OK;
 }
 
@@ -568,6 +573,16 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     return NFM_OK;
 }
 
+int nfm_set_regularizer(nfm_ctx* ctx, double w1, double w2)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    if (!(w1 >= 0) || !(w2 >= 0) || !std::isfinite(w1) || !std::isfinite(w2) || (w1 == 0 && w2 == 0))
+        return fail(ctx, NFM_ERR_ARG, "regularizer weights must be finite, >= 0 and not both 0");
+    ctx->reg_w1 = w1;
+    ctx->reg_w2 = w2;
+    return NFM_OK;
+}
+
 int nfm_set_precision(nfm_ctx* ctx, int mode)
 {
     if (!ctx) return NFM_ERR_ARG;
@@ -679,7 +694,8 @@ int nfm_spgm_step_freqs(nfm_ctx* ctx, const float* y, float* s, const int* pairs
     NFM_TRY(enqueue_forward(ctx, pairs, n_pairs, (const float2*)s, (const float2*)y, r, freq_mask));
     const double B = (double)n_pairs * n_freq;
     return enqueue_adjoint(ctx, pairs, n_pairs, r, nullptr, (float2*)s, (float)(eta / B),
-                           (float)((double)eta * lambda));
+                           (float)((double)eta * lambda * ctx->reg_w1),
+                           (float)(1.0 / (1.0 + (double)eta * lambda * ctx->reg_w2)));
 }
 
 int nfm_pgm_step(nfm_ctx* ctx, const float* y, float* s, float eta, float lambda)
@@ -819,12 +835,16 @@ int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, d
     NFM_TRY(enqueue_forward(ctx, ctx->d_pairs_all, ctx->P, (const float2*)s, (const float2*)y, res));
     NFM_CK(launch_norm2(res, ctx->M, part, sc + 4, st));
     NFM_CK(launch_abs_sum((const float2*)s, ctx->N, part, sc + 5, st));
-    NFM_CK(launch_axpby(sc + 4, 1.0 / (2.0 * (double)ctx->M), sc + 5, lambda, sc + 6, st));
-    double F = 0;
+    NFM_CK(launch_axpby(sc + 4, 1.0 / (2.0 * (double)ctx->M), sc + 5, lambda * ctx->reg_w1, sc + 6, st));
+    double F = 0, s2 = 0;
     NFM_CK(cudaMemcpyAsync(&F, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (ctx->reg_w2 != 0.0) {
+        NFM_CK(launch_norm2((const float2*)s, ctx->N, part, sc + 2, st));
+        NFM_CK(cudaMemcpyAsync(&s2, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     NFM_CK(st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize());
     NFM_TRY(check_flags(ctx));
-    *F_out = F;
+    *F_out = F + 0.5 * lambda * ctx->reg_w2 * s2;
     return NFM_OK;
 }
 

@@ -34,7 +34,8 @@ struct AdjArgs {
     float2* g_out;           // [N] plain adjoint output, or nullptr
     float2* s;               // [N] SPGM iterate updated in place, or nullptr
     float step;              // eta / B
-    float alpha;             // eta * lambda
+    float alpha;             // eta * lambda * w1 (soft-threshold level)
+    float shrink;            // 1 / (1 + eta * lambda * w2) (elastic-net scaling; 1 for plain l1)
     int pchunk;              // pairs staged in shared memory per round
 };
 

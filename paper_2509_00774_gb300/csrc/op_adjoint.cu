@@ -1,7 +1,9 @@
 // Minibatch adjoint g = A_B^H r on CUDA cores, optionally fused with the SPGM
 // gradient step and the complex soft-threshold (Eq. 5 with the Eq. 6 gradient):
 //
-//     s_n <- prox_alpha( s_n - (eta/B) g_n ),  prox(z) = z max(0, 1 - alpha/|z|).
+//     s_n <- prox( s_n - (eta/B) g_n ),  prox(z) = z max(0, 1 - alpha/|z|) / (1 + eta lambda w2)
+//
+// (alpha = eta lambda w1; w2 = 0 is the paper's l1 prox).
 //
 // One CTA = one 8x4x4 voxel tile, 128 threads: two voxels per thread (z layers
 // lz and lz+2) and the minibatch pairs split by parity between two thread
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_kernel(OpDesc op, AdjArgs a)
             float mag = sqrtf(zr * zr + zi * zi);
             float2 out = make_float2(0.f, 0.f);
             if (mag > a.alpha) {
-                float sc = 1.0f - a.alpha / mag;
+                float sc = (1.0f - a.alpha / mag) * a.shrink;
                 out = make_float2(zr * sc, zi * sc);
             }
             a.s[n] = out;

@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(128) adj_tc_kernel(OpDesc op, AdjArgs a, const
         const float mag = sqrtf(zr * zr + zi * zi);
         float2 out = make_float2(0.f, 0.f);
         if (mag > a.alpha) {
-            const float f = 1.0f - a.alpha / mag;
+            const float f = (1.0f - a.alpha / mag) * a.shrink;
             out = make_float2(zr * f, zi * f);
         }
         a.s[n] = out;

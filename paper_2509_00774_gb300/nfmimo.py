@@ -53,6 +53,7 @@ def load_library(path: str | None = None):
         "nfm_set_stream": (i, [vp, vp]),
         "nfm_set_geometry": (i, [vp, vp, i, vp, i, vp, i, vp, ctypes.POINTER(_Grid), d]),
         "nfm_set_precision": (i, [vp, i]),
+        "nfm_set_regularizer": (i, [vp, d, d]),
         "nfm_dims": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                          ctypes.POINTER(ctypes.c_longlong)]),
         "nfm_forward": (i, [vp, vp, i, vp, vp]),
@@ -174,6 +175,10 @@ class Context:
     def set_precision(self, mode):
         """Adjoint arithmetic: "fp32" (CUDA cores), "tc_bf16x3" or "tc_fp16x3" (tensor cores)."""
         self._check(self._lib.nfm_set_precision(self._h, self.PRECISION[mode] if isinstance(mode, str) else int(mode)))
+
+    def set_regularizer(self, w1=1.0, w2=0.0):
+        """R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 for every SPGM/PGM step and the objective."""
+        self._check(self._lib.nfm_set_regularizer(self._h, float(w1), float(w2)))
 
     def dims(self):
         T, R, K, N = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()

@@ -139,6 +139,29 @@ def test_cartesian_minibatch_steps_match_oracle(comp):
         assert nmse(to_host(s_gpu), s_orc) <= NMSE_TOL, it
 
 
+@pytest.mark.parametrize("w1,w2", [(1.0, 0.5), (0.0, 3.0)])
+def test_elastic_net_and_tikhonov_spgm_match_oracle(w1, w2):
+    """Other regularisers (Sec. III): R = w1 ||s||_1 + (w2/2)||s||^2, 10 epochs on the small workload."""
+    w, _, y = _small_problem()
+    o = Oracle(w.geom, w1=w1, w2=w2)
+    ctx = make_ctx(w.geom)
+    ctx.set_regularizer(w1, w2)
+    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
+    eta = float(np.float32(1.0 / L))
+    lam = float(np.float32(0.05 * o.lambda_max(y)))
+    s_orc = np.zeros(o.N, dtype=np.complex128)
+    s_gpu = to_dev(np.zeros(o.N))
+    y_dev = to_dev(y)
+    for e in range(10):
+        perm = I.epoch_permutation(o.P, w.seeds["perm"], e)
+        s_orc = o.spgm_epoch(y, s_orc, perm, 4, eta, lam)
+        ctx.spgm_epoch(y_dev, s_gpu, to_dev(perm, "int32"), 4, eta, lam)
+        assert nmse(to_host(s_gpu), s_orc) <= NMSE_TOL, e
+    F_gpu = ctx.objective(y_dev, s_gpu, lam)
+    F_orc = o.objective(y, to_host(s_gpu), lam)
+    assert abs(F_gpu - F_orc) <= 1e-5 * F_orc
+
+
 def test_spgm_host_buffers_match_device():
     w, o, y = _small_problem()
     ctx = make_ctx(w.geom)

@@ -208,6 +208,40 @@ def test_pgm_monotone_and_kkt_fixed_point():
     assert _kkt_violation(A, o.M, y, s, lam) < 1e-6
 
 
+def test_elastic_net_prox_hand_case_and_kkt():
+    """R = w1 ||s||_1 + (w2/2)||s||^2: prox is the soft threshold then 1/(1 + eta lambda w2);
+    the PGM fixed point satisfies the KKT conditions with the dense-matrix gradient."""
+    w = W.small_T4R4_K16_16x16x8()
+    grid = I.Grid(-0.03, -0.03, 0.25, 0.02, 0.02, 0.02, 4, 4, 3)
+    geom = I.Geometry(w.geom.tx, w.geom.rx, w.geom.freq, grid)
+    o = Oracle(geom, w1=1.0, w2=0.4)
+    z = np.array([3 + 4j, 0.5 + 0j])
+    out = o.prox(z, 2.5)                  # threshold 2.5, scale 1/(1 + 2.5*0.4) = 1/2
+    assert out[0] == 0.75 + 1j and out[1] == 0
+    A = o.dense(np.arange(o.M), np.arange(o.N))
+    y = I.add_noise(A @ I.point_scene(grid, 5, 0), I.complex_gaussian(o.M, 1), 30.0)
+    L = float(np.linalg.eigvalsh(A.conj().T @ A / o.M)[-1])
+    lam = 0.05 * o.lambda_max(y)
+    s = np.zeros(o.N, dtype=np.complex128)
+    F = [o.objective(y, s, lam)]
+    for _ in range(1000):
+        s = o.pgm_step(y, s, 1.0 / L, lam)
+        F.append(o.objective(y, s, lam))
+    assert np.all(np.diff(F) <= 1e-12 * F[0])
+    g = A.conj().T @ (A @ s - y) / o.M
+    nz = np.abs(s) > 0
+    v_nz = np.max(np.abs(g[nz] + lam * (s[nz] / np.abs(s[nz]) + 0.4 * s[nz])))
+    v_z = np.max(np.maximum(np.abs(g[~nz]) - lam, 0.0)) if (~nz).any() else 0.0
+    assert max(v_nz, v_z) / lam < 1e-6
+    # Tikhonov only (w1 = 0): the PGM fixed point solves (A^H A/M + lam w2 I) s = A^H y / M
+    t = Oracle(geom, w1=0.0, w2=2.0)
+    s = np.zeros(o.N, dtype=np.complex128)
+    for _ in range(2000):
+        s = t.pgm_step(y, s, 1.0 / L, lam)
+    exact = np.linalg.solve(A.conj().T @ A / o.M + lam * 2.0 * np.eye(o.N), A.conj().T @ y / o.M)
+    assert np.linalg.norm(s - exact) <= 1e-8 * np.linalg.norm(exact)
+
+
 def test_lambda_max_gives_zero_solution():
     w = W.small_T4R4_K16_16x16x8()
     o = Oracle(w.geom)
