@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_bf16x3", "tc_fp16x3"],
                     help="adjoint arithmetic: CUDA-core FP32 or tensor-core split precision")
+    ap.add_argument("--nonuniform", action="store_true",
+                    help="jitter the frequencies off the uniform grid (general-frequency kernels)")
     ap.add_argument("--workload", default="mid", choices=["mid", "large", "batched48"],
                     help="mid = the headline workload; large = 32 TX x 32 RX, K = 128, N = 1048576; "
                          "batched48 = 48 uneven scenes per epoch through one CUDA graph")
@@ -278,6 +280,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     w = W.mid_T16R16_K64_64x64x32() if args.workload == "mid" else W.large_T32R32_K128_128x128x64()
+    if args.nonuniform:
+        f = w.geom.freq
+        step = (f[-1] - f[0]) / (f.size - 1)
+        w.geom.freq = f + np.random.default_rng(5).uniform(-0.3, 0.3, f.size) * step
     geom = w.geom
     with torch.cuda.stream(stream):
         ctx = Context(local, stream=stream)
@@ -382,7 +388,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "T": geom.T, "R": geom.R, "K": geom.K, "N": geom.N, "M": geom.M,
+        "config": {"workload": w.name + ("_jittered_freqs" if args.nonuniform else ""), "T": geom.T, "R": geom.R, "K": geom.K, "N": geom.N, "M": geom.M,
                    "pairs_per_batch": bp, "minibatches_per_step": geom.P // bp, "step": "one SPGM epoch",
                    "operator": "forward: fp32 cuda-core three-term phasor recurrence; adjoint: " +
                                ("fp32 cuda-core Horner" if args.precision == "fp32" else

@@ -67,8 +67,11 @@ int nfm_set_stream(nfm_ctx* ctx, void* cuda_stream);
 /* Geometry of the observation model (Sec. II, Eq. 1-2).
  *   tx_xyz [T][3], rx_xyz [R][3]: HOST FP64 antenna positions (the paper puts
  *     them on z = 0; any z is accepted).
- *   freq_hz [K]: HOST FP64 frequencies; they must be equally spaced (the
- *     operator advances the phase by a fixed step per frequency).  1 <= K <= 128.
+ *   freq_hz [K]: HOST FP64 frequencies, 1 <= K <= 128.  Equally spaced lists use
+ *     the phasor-recurrence kernels (and allow the tensor-core adjoint); any
+ *     other list uses the general-frequency kernels, which evaluate every
+ *     element's phase from FP64 per-(antenna, voxel tile, frequency) tables
+ *     (slower; FP32 only; nfm_forward_noalloc rejects such a geometry).
  *   pulse_re_im [K][2]: HOST complex p(f_k), or NULL for p = 1.
  *   grid: the voxel grid (HOST struct).  N = nx ny nz < 2^31.
  *   c: propagation speed (m/s), > 0.
@@ -77,8 +80,8 @@ int nfm_set_stream(nfm_ctx* ctx, void* cuda_stream);
  * Copies what it
  * needs (the caller may free its arrays on return), builds the per-(antenna,
  * voxel-tile) FP64 tables on the device and synchronises the stream.
- * Errors: NFM_ERR_ARG (sizes, non-finite values, non-uniform frequencies,
- * antenna on a voxel), NFM_ERR_NOMEM, NFM_ERR_CUDA. */
+ * Errors: NFM_ERR_ARG (sizes, non-finite values, antenna on a voxel),
+ * NFM_ERR_NOMEM, NFM_ERR_CUDA. */
 int nfm_set_geometry(nfm_ctx* ctx,
                      const double* tx_xyz, int T,
                      const double* rx_xyz, int R,

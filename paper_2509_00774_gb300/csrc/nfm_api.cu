@@ -58,6 +58,9 @@ struct nfm_ctx {
 
     AntTile* d_ant = nullptr;
     double* d_ant_xyz = nullptr;
+    bool uniform = true;          // equally spaced frequencies (recurrence / tensor-core paths)
+    float* d_antk = nullptr;      // general frequencies: [(T+R) * n_tiles * K] reduced phases
+    float2* d_fkc = nullptr;      // general frequencies: f_k / c as hi + lo
     float2* d_pulse = nullptr;
     int* d_pairs_all = nullptr;
     int* d_err = nullptr;
@@ -243,9 +246,62 @@ int plan_forward(nfm_ctx* ctx, int n_pairs, FwdPlan* pl)
 }
 
 // out[b*K + k] = (A_B s)[b, k] (- y_obs[pair_b*K + k] if y_obs; 0 where fmask[k] == 0)
+void plan_forward_general(const nfm_ctx* ctx, int n_pairs, FwdPlan* plp)
+{
+    FwdPlan& pl = *plp;
+    pl.n_groups = (n_pairs + FWD_PC - 1) / FWD_PC;
+    pl.n_slots = pl.n_groups * FWD_PC;
+    long long G = (long long)ctx->num_sms * 4;
+    long long nch = (G + pl.n_groups - 1) / pl.n_groups;
+    if (nch > ctx->gd.n_tiles) nch = ctx->gd.n_tiles;
+    if (nch > 65535) nch = 65535;
+    if (nch < 1) nch = 1;
+    pl.n_chunks = (int)nch;
+    pl.base = ctx->gd.n_tiles / pl.n_chunks;
+    pl.rem = ctx->gd.n_tiles % pl.n_chunks;
+    pl.partial_bytes = (size_t)pl.n_chunks * pl.n_slots * ctx->K * sizeof(float2);
+}
+
+int enqueue_forward_general(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
+                            float2* out, const unsigned char* fmask)
+{
+    FwdPlan pl;
+    plan_forward_general(ctx, n_pairs, &pl);
+    NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, pl.partial_bytes));
+    OpDesc op = op_desc(ctx);
+    GenDesc gdsc{ctx->d_antk, ctx->d_fkc};
+    FwdArgs a;
+    a.pairs = pairs;
+    a.n_pairs = n_pairs;
+    a.s = s;
+    a.partial = (float2*)ctx->d_partial;
+    a.n_slots = pl.n_slots;
+    a.VS = 1;
+    a.tiles_base = pl.base;
+    a.tiles_rem = pl.rem;
+    const int e0 = prof_mark(ctx);
+    NFM_CK(launch_fwd_general(op, gdsc, a, dim3(pl.n_groups, pl.n_chunks), ctx->stream));
+    const int e1 = prof_mark(ctx);
+    ReduceArgs ra;
+    ra.partial = (const float2*)ctx->d_partial;
+    ra.n_chunks = pl.n_chunks;
+    ra.n_slots = pl.n_slots;
+    ra.n_out = n_pairs * ctx->K;
+    ra.pairs = pairs;
+    ra.y_obs = y_obs;
+    ra.fmask = fmask;
+    ra.out = out;
+    NFM_CK(launch_fwd_reduce(op, ra, ctx->stream));
+    const int e2 = prof_mark(ctx);
+    prof_pair(ctx, 0, e0, e1);
+    prof_pair(ctx, 1, e1, e2);
+    return NFM_OK;
+}
+
 int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
                     float2* out, const unsigned char* fmask = nullptr)
 {
+    if (!ctx->uniform) return enqueue_forward_general(ctx, pairs, n_pairs, s, y_obs, out, fmask);
     FwdPlan pl;
     NFM_TRY(plan_forward(ctx, n_pairs, &pl));
     NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, pl.partial_bytes));
@@ -311,6 +367,25 @@ int enqueue_adjoint_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2
 int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r, float2* g_out, float2* s,
                     float step, float alpha, float shrink = 1.0f)
 {
+    if (!ctx->uniform) {
+        if (ctx->precision != NFM_FP32)
+            return fail(ctx, NFM_ERR_ARG, "the tensor-core adjoint needs equally spaced frequencies");
+        AdjArgs a;
+        a.pairs = pairs;
+        a.n_pairs = n_pairs;
+        a.r = r;
+        a.g_out = g_out;
+        a.s = s;
+        a.step = step;
+        a.alpha = alpha;
+        a.shrink = shrink;
+        a.pchunk = GEN_ADJ_PCHUNK;
+        GenDesc gdsc{ctx->d_antk, ctx->d_fkc};
+        const int e0 = prof_mark(ctx);
+        NFM_CK(launch_adj_general(op_desc(ctx), gdsc, a, ctx->stream));
+        prof_pair(ctx, 2, e0, prof_mark(ctx));
+        return NFM_OK;
+    }
     if (ctx->precision != NFM_FP32) return enqueue_adjoint_tc(ctx, pairs, n_pairs, r, g_out, s, step, alpha, shrink);
     const int K1 = ctx->K1;
     size_t smem = adj_smem_bytes(K1, ADJ_PCHUNK);
@@ -413,7 +488,7 @@ void nfm_destroy(nfm_ctx* ctx)
     DevGuard guard(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
-    void* ps[] = {ctx->d_ant, ctx->d_ant_xyz, ctx->d_pulse, ctx->d_pairs_all, ctx->d_err, ctx->d_red,
+    void* ps[] = {ctx->d_ant, ctx->d_ant_xyz, ctx->d_pulse, ctx->d_antk, ctx->d_fkc, ctx->d_pairs_all, ctx->d_err, ctx->d_red,
                   ctx->d_partial, ctx->d_resid, ctx->d_v, ctx->d_g, ctx->d_y, ctx->d_hy, ctx->d_hs, ctx->d_hperm,
                   ctx->d_prox_partial, ctx->d_bmat, ctx->d_bscale};
     for (void* p : ps) free_ptr(p);
@@ -462,11 +537,10 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
             if (!std::isfinite(pulse_re_im[k])) return fail(ctx, NFM_ERR_ARG, "non-finite pulse spectrum");
     const double f0 = freq_hz[0];
     const double df = K > 1 ? (freq_hz[K - 1] - freq_hz[0]) / (K - 1) : 0.0;
+    bool uniform = true;
     for (int k = 0; k < K; ++k) {
         double want = f0 + k * df;
-        if (std::fabs(freq_hz[k] - want) > 1e-9 * std::fabs(freq_hz[K - 1]))
-            return fail(ctx, NFM_ERR_ARG, "frequencies must be equally spaced (f[%d] off by %g Hz)", k,
-                        freq_hz[k] - want);
+        if (std::fabs(freq_hz[k] - want) > 1e-9 * std::fabs(freq_hz[K - 1])) uniform = false;
     }
     // smallest antenna-voxel distance (distance to the grid's bounding box)
     const double lo[3] = {g.x0, g.y0, g.z0};
@@ -489,6 +563,10 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     free_ptr(ctx->d_ant_xyz);
     free_ptr(ctx->d_pulse);
     free_ptr(ctx->d_pairs_all);
+    free_ptr(ctx->d_antk);
+    free_ptr(ctx->d_fkc);
+    ctx->d_antk = nullptr;
+    ctx->d_fkc = nullptr;
     ctx->d_ant = nullptr;
     ctx->d_ant_xyz = nullptr;
     ctx->d_pulse = nullptr;
@@ -554,6 +632,28 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     as.dfc2 = K2 * df / c;
     as.out = ctx->d_ant;
     NFM_CK(launch_ant_setup(gd, as, ctx->stream));
+    if (!uniform) {
+        // general frequencies: FP64 reduced phases per (antenna, tile, k) and f_k / c split hi + lo
+        double* hfk = new double[K];
+        float* hfkc = new float[2 * K];
+        for (int k = 0; k < K; ++k) {
+            hfk[k] = freq_hz[k] / c;
+            hfkc[2 * k] = (float)hfk[k];
+            hfkc[2 * k + 1] = (float)(hfk[k] - (double)hfkc[2 * k]);
+        }
+        double* d_fk = nullptr;
+        e = cudaMalloc((void**)&ctx->d_antk, (size_t)n_ant * gd.n_tiles * K * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_fkc, (size_t)K * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&d_fk, (size_t)K * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemcpy(d_fk, hfk, K * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->d_fkc, hfkc, K * sizeof(float2), cudaMemcpyHostToDevice);
+        delete[] hfk;
+        delete[] hfkc;
+        if (e == cudaSuccess) e = launch_antk_setup(gd, as, d_fk, K, ctx->d_antk, ctx->stream);
+        if (e == cudaSuccess) e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
+        free_ptr(d_fk);
+        if (e != cudaSuccess) return fail(ctx, NFM_ERR_CUDA, "general-frequency tables: %s", cudaGetErrorString(e));
+    }
     NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
 
     ctx->T = T;
@@ -569,6 +669,7 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     ctx->df = df;
     ctx->gd = gd;
     ctx->ph = ph;
+    ctx->uniform = uniform;
     ctx->has_geom = true;
     return NFM_OK;
 }
@@ -952,6 +1053,8 @@ extern "C" int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, 
     NFM_TRY(check_ptr(ctx, pairs, "pairs", 4));
     NFM_TRY(check_ptr(ctx, s, "s", 8));
     NFM_TRY(check_ptr(ctx, y, "y", 8));
+    if (!ctx->uniform)
+        return fail(ctx, NFM_ERR_ARG, "the allocation-free forward needs equally spaced frequencies");
     if ((size_t)n_pairs * ctx->K > NOALLOC_SCRATCH_ELEMS)
         return fail(ctx, NFM_ERR_ARG, "n_pairs * K = %lld exceeds the allocation-free limit %zu",
                     (long long)n_pairs * ctx->K, NOALLOC_SCRATCH_ELEMS);
@@ -1039,7 +1142,10 @@ int prepare_epoch(nfm_ctx* ctx, int bp)
     for (int nb : {bp, ctx->P % bp}) {
         if (nb <= 0) continue;
         FwdPlan pl;
-        NFM_TRY(plan_forward(ctx, nb, &pl));
+        if (ctx->uniform)
+            NFM_TRY(plan_forward(ctx, nb, &pl));
+        else
+            plan_forward_general(ctx, nb, &pl);
         NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, pl.partial_bytes));
         if (ctx->precision != NFM_FP32) {
             NFM_TRY(ensure(ctx, &ctx->d_bmat, &ctx->bmat_cap, adj_tc_bmat_bytes(nb)));

@@ -48,6 +48,19 @@ struct AntSetup {
     AntTile* out;            // [n_ant * n_tiles]
 };
 
+constexpr int GEN_MAX_K = 128;    // frequencies of the general-frequency path
+constexpr int GEN_ADJ_PCHUNK = 16;
+// Arbitrary frequency lists: per-(antenna, tile, k) reduced phases and f_k / c (hi + lo).
+struct GenDesc {
+    const float* antk;       // [(T + R) * n_tiles * K]
+    const float2* fkc;       // [K]
+};
+cudaError_t launch_antk_setup(const GridDesc& g, const AntSetup& a, const double* fk_over_c, int K, float* out,
+                              cudaStream_t st);
+cudaError_t launch_fwd_general(const OpDesc& op, const GenDesc& gd, const FwdArgs& a, dim3 grid, cudaStream_t st);
+cudaError_t launch_adj_general(const OpDesc& op, const GenDesc& gd, const AdjArgs& a, cudaStream_t st);
+const void* fwd_general_ptr();
+
 constexpr int FWD_PC = 8;         // pairs per forward CTA
 constexpr int ADJ_TC_PCHUNK = 8;  // pairs whose tensor-core B operands a CTA holds at once
 constexpr int ADJ_THREADS = 128;  // one 8x4x4 tile: two voxels per thread, pairs split in two halves

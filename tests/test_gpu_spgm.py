@@ -217,7 +217,7 @@ def test_invalid_geometry_rejected():
     w = W.small_T4R4_K16_16x16x8()
     g = w.geom
     ctx = Context(0)
-    bad_freq = I.Geometry(g.tx, g.rx, np.array([72e9, 73e9, 75e9]), g.grid)
+    bad_freq = I.Geometry(g.tx, g.rx, np.array([72e9, -73e9, 75e9]), g.grid)
     too_many = I.Geometry(g.tx, g.rx, I.uniform_freqs(70e9, 80e9, 129), g.grid)
     inside = I.Geometry(np.array([[0.0, 0.0, 0.27]]), g.rx, g.freq, g.grid)
     for bad in (bad_freq, too_many, inside):
