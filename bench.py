@@ -50,7 +50,9 @@ def parse():
                     help="adjoint arithmetic: CUDA-core FP32 or tensor-core split precision")
     ap.add_argument("--nonuniform", action="store_true",
                     help="jitter the frequencies off the uniform grid (general-frequency kernels)")
-    ap.add_argument("--workload", default="mid", choices=["mid", "large", "batched48"],
+    ap.add_argument("--study-rho", type=float, nargs="+", default=[0.3, 0.1, 0.03],
+                    help="paper_like study: step sizes as eta * L")
+    ap.add_argument("--workload", default="mid", choices=["mid", "large", "batched48", "paper_like"],
                     help="mid = the headline workload; large = 32 TX x 32 RX, K = 128, N = 1048576; "
                          "batched48 = 48 uneven scenes per epoch through one CUDA graph")
     return ap.parse_args()
@@ -478,10 +480,151 @@ def run_batched(args):
     batch.close()
 
 
+def run_paper_like(args):
+    """Synthetic analogue of the paper's Sec. V study (Figs. 1-4) on a scene of the measured data
+    set's shape (16 TX x 9 RX spirals, 11 frequencies 4-16 GHz, 61 x 61 x 21 voxels).
+
+    PGM and SPGM with Cartesian minibatches (#f, #Tx, #Rx) run until the change in reflectivity
+    magnitudes relative to the peak magnitude, max_n | |s_n(k+1)| - |s_n(k)| | / max_n |s_n(k+1)|,
+    drops below 1e-3 (relative, since the synthetic data's scale is not the measured set's).  The
+    statistic is taken once every c iterations (c = ceil(M / B), about one pass over the rows)
+    over that chunk's last iteration and read one chunk later, so a run stops at most 2c - 1
+    iterations after the rule first holds.  PSNR over
+    normalised magnitudes against the PGM reconstruction, as in Fig. 4, and against PGM run to a
+    relative change of 1e-6 (the fixed point); PGM* is PGM stopped at the (4, 4, 3) run's wall
+    time, as in Fig. 1(e).  Device microseconds per iteration are timed separately, without checks.  The minibatch draws are generated before the
+    timed region (they are inputs); wall time covers the GPU work and its launches."""
+    import numpy as np
+    import torch
+    from paper_2509_00774_gb300 import build as nb
+    from paper_2509_00774_gb300 import inputs as I
+    from paper_2509_00774_gb300 import metrics
+    from paper_2509_00774_gb300 import workloads as W
+    from paper_2509_00774_gb300.nfmimo import Context
+    nb.build()
+    dev = torch.device("cuda", 0)
+    w = W.paper_like_T16R9_K11_61x61x21()
+    g = w.geom
+    ctx = Context(0)
+    ctx.set_geometry(g)
+    allp = torch.arange(g.P, dtype=torch.int32, device=dev)
+    clean = ctx.forward(allp, torch.from_numpy(w.scene_vector().astype(np.complex64)).to(dev))
+    noise = torch.from_numpy(I.complex_gaussian(g.M, w.seeds["noise"]).astype(np.complex64)).to(dev)
+    y = clean + float(torch.sqrt(torch.mean(clean.abs() ** 2) / 10 ** (w.snr_db / 10))) * noise
+    L = ctx.power_iteration(torch.from_numpy(I.complex_gaussian(g.N, 3).astype(np.complex64)).to(dev), 50)
+    lam = 0.05 * ctx.lambda_max(y)
+    tol = 1e-3
+    comps = [(4, 4, 3), (2, 4, 3), (4, 8, 6), (11, 4, 3), (11, 16, 9)]
+    out = {"study": "pgm_vs_spgm_cartesian", "workload": w.name, "M": g.M, "N": g.N, "L": L,
+           "lambda": lam, "tol_magnitude_change": tol, "runs": []}
+
+    def solve(eta, comp, max_iters, fixed_iters=None, tol_override=None):
+        nf, ntx, nrx = comp
+        full = comp == (g.K, g.T, g.R)
+        B = nf * ntx * nrx
+        c = 1 if full else -(-g.M // B)
+        n_draw = 0 if full else min(max_iters, 1 << 16)
+        if not full:
+            draws = [I.cartesian_minibatch(g.T, g.R, g.K, ntx, nrx, nf, seed=13, it=i) for i in range(n_draw)]
+            pairs = torch.from_numpy(np.stack([d[0] for d in draws])).to(dev)
+            masks = torch.from_numpy(np.stack([d[1] for d in draws])).to(dev)
+        s = torch.zeros(g.N, dtype=torch.complex64, device=dev)
+        prev = torch.empty_like(s)
+        stat = torch.empty(2, dtype=torch.float32, pin_memory=True)
+        ev = [torch.cuda.Event(), torch.cuda.Event()]
+        limit = fixed_iters if fixed_iters is not None else (max_iters if full else n_draw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = 0
+        chunk = 0
+        change = float("inf")
+        while k < limit:
+            n = min(c, limit - k)
+            for j in range(n):
+                if j == n - 1 and fixed_iters is None:
+                    prev.copy_(s)
+                if full:
+                    ctx.pgm_step(y, s, eta, lam)
+                else:
+                    ctx.spgm_step_freqs(y, s, pairs[k], masks[k], eta, lam, n_freq=nf)
+                k += 1
+            if fixed_iters is None:
+                # relative change of the chunk's last iteration, copied back without a stall; the
+                # previous chunk's value is read while this chunk runs (the run stops one chunk late)
+                m = s.abs()
+                rel = (m - prev.abs()).abs().max() / m.max().clamp_min(1e-30)
+                stat[chunk % 2].copy_(rel, non_blocking=True)
+                ev[chunk % 2].record()
+                if chunk > 0:
+                    ev[(chunk - 1) % 2].synchronize()
+                    change = float(stat[(chunk - 1) % 2])
+                    if change < (tol if tol_override is None else tol_override):
+                        break
+                chunk += 1
+        torch.cuda.synchronize()
+        return s.cpu().numpy(), time.perf_counter() - t0, k, change
+
+    def device_us_per_iter(eta, comp, n):
+        """Device time of n back-to-back iterations (no termination checks), CUDA events."""
+        nf, ntx, nrx = comp
+        full = comp == (g.K, g.T, g.R)
+        if not full:
+            draws = [I.cartesian_minibatch(g.T, g.R, g.K, ntx, nrx, nf, seed=29, it=i) for i in range(n)]
+            pairs = torch.from_numpy(np.stack([d[0] for d in draws])).to(dev)
+            masks = torch.from_numpy(np.stack([d[1] for d in draws])).to(dev)
+        s = torch.zeros(g.N, dtype=torch.complex64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for i in range(n):
+            if full:
+                ctx.pgm_step(y, s, eta, lam)
+            else:
+                ctx.spgm_step_freqs(y, s, pairs[i], masks[i], eta, lam, n_freq=nf)
+        e1.record()
+        torch.cuda.synchronize()
+        return 1e3 * e0.elapsed_time(e1) / n
+
+    pgm_comp = (g.K, g.T, g.R)
+    for comp in comps:                      # warm-up: module loading and first launches
+        solve(0.1 / L, comp, 8, fixed_iters=4)
+    out["device_us_per_iteration"] = {
+        "x".join(map(str, comp)): device_us_per_iter(0.1 / L, comp, 200 if comp == pgm_comp else 2000)
+        for comp in comps}
+    for rho in args.study_rho:
+        eta = rho / L
+        s_fp, _, k_fp, ch_fp = solve(eta, pgm_comp, 40000, tol_override=1e-6)
+        s_pgm, t_pgm, k_pgm, ch_pgm = solve(eta, pgm_comp, 200000)
+        row = {"eta_times_L": rho, "eta": eta, "alpha": eta * lam,
+               "pgm_fixed_point": {"iterations": k_fp, "last_change": ch_fp, "tol": 1e-6},
+               "pgm": {"iterations": k_pgm, "seconds": t_pgm, "last_change": ch_pgm,
+                       "psnr_vs_fixed_point_db": metrics.psnr_magnitude(s_pgm, s_fp)}, "spgm": []}
+        t443 = None
+        for comp in comps[:-1]:
+            s_, t_, k_, ch_ = solve(eta, comp, 1 << 16)
+            row["spgm"].append({"composition_f_tx_rx": list(comp), "B": comp[0] * comp[1] * comp[2],
+                                "iterations": k_, "seconds": t_, "last_change": ch_,
+                                "converged": ch_ < tol, "speedup_vs_pgm": t_pgm / t_,
+                                "psnr_vs_pgm_db": metrics.psnr_magnitude(s_, s_pgm),
+                                "psnr_vs_fixed_point_db": metrics.psnr_magnitude(s_, s_fp)})
+            if comp == (4, 4, 3):
+                t443 = t_
+        k_star = max(1, int(k_pgm * t443 / t_pgm))
+        s_star, t_star, _, _ = solve(eta, pgm_comp, k_star, fixed_iters=k_star)
+        row["pgm_star"] = {"iterations": k_star, "seconds": t_star,
+                           "psnr_vs_pgm_db": metrics.psnr_magnitude(s_star, s_pgm)}
+        out["runs"].append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "batched48" and args.impl != "reference":
         run_batched(args)
+        return
+    if args.workload == "paper_like":
+        run_paper_like(args)
         return
     if args.impl == "reference":
         run_reference(args)

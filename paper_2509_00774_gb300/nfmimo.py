@@ -252,10 +252,12 @@ class Context:
             hp(perms, np.int32, "perms_host"), n_epochs, int(pairs_per_batch), float(eta), float(lam)))
         return s_host
 
-    def spgm_step_freqs(self, y, s, pairs, freq_mask, eta, lam):
-        """SPGM step on the rows (pairs x selected frequencies); freq_mask: uint8 device tensor [K]."""
+    def spgm_step_freqs(self, y, s, pairs, freq_mask, eta, lam, n_freq=None):
+        """SPGM step on the rows (pairs x selected frequencies); freq_mask: uint8 device tensor [K].
+        n_freq (the number of set mask entries) is counted on the device when not given."""
         import torch
-        n_freq = int(freq_mask.count_nonzero())
+        if n_freq is None:
+            n_freq = int(freq_mask.count_nonzero())
         self._check(self._lib.nfm_spgm_step_freqs(
             self._h, self._c(y, "y"), self._c(s, "s"), self._i(pairs, "pairs"), pairs.numel(),
             _ptr(freq_mask, torch.uint8, "freq_mask", self.device), n_freq, float(eta), float(lam)))

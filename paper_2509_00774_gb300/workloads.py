@@ -79,6 +79,25 @@ def batched_scene(i: int) -> Workload:
                     20.0, 16, 30, _seeds(1000 + 10 * i))
 
 
+def spiral_array(n: int, r_max: float, turns: float, phase0: float = 0.0) -> np.ndarray:
+    """n antennas on an Archimedean spiral in the z = 0 plane (radius up to r_max)."""
+    t = np.arange(n) / max(n - 1, 1)
+    ang = phase0 + 2 * np.pi * turns * t
+    r = r_max * (0.15 + 0.85 * t)
+    return np.stack([r * np.cos(ang), r * np.sin(ang), np.zeros(n)], 1)
+
+
+def paper_like_T16R9_K11_61x61x21() -> Workload:
+    """Shape of the paper's experiment (Sec. V): 16 TX and 9 RX on spirals, 11 equally spaced
+    frequencies in 4-16 GHz (M = 1584), a 30 x 30 x 10 cm scene sampled at 0.5 cm (61 x 61 x 21,
+    N = 78141) about 0.5 m in front of the array.  Antenna positions and the scene are synthetic."""
+    tx = spiral_array(16, 0.18, 1.5, 0.0)
+    rx = spiral_array(9, 0.12, 1.25, 0.7)
+    grid = I.Grid(-0.15, -0.15, 0.45, 0.005, 0.005, 0.005, 61, 61, 21)
+    geom = I.Geometry(tx, rx, I.uniform_freqs(4e9, 16e9, 11), grid)
+    return Workload("paper_like_T16R9_K11_61x61x21", geom, "height", 200, 20.0, 12, 400, _seeds(0))
+
+
 WORKLOADS = {
     "small": small_T4R4_K16_16x16x8,
     "mid": mid_T16R16_K64_64x64x32,

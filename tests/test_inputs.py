@@ -86,3 +86,20 @@ def test_cartesian_minibatch_composition():
     a = I.cartesian_minibatch(16, 9, 11, 4, 3, 4, seed=3, it=5)
     b = I.cartesian_minibatch(16, 9, 11, 4, 3, 4, seed=3, it=5)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_metrics_closed_forms():
+    from paper_2509_00774_gb300 import metrics
+    ref = np.array([1.0, 0.5, 0.0, 0.25])
+    a = np.array([1.0, 0.5, 0.1, 0.25])
+    assert abs(metrics.psnr_magnitude(a, ref) - 10 * np.log10(400.0)) < 1e-12
+    assert abs(metrics.nmse(a, ref) - 0.01 / 1.3125) < 1e-15
+    assert metrics.psnr_magnitude(2 * ref, ref) == float("inf")     # scale-invariant
+
+
+def test_paper_like_workload_shape():
+    w = W.paper_like_T16R9_K11_61x61x21()
+    g = w.geom
+    assert (g.T, g.R, g.K, g.grid.nx, g.grid.ny, g.grid.nz) == (16, 9, 11, 61, 61, 21)
+    assert g.M == 1584 and g.N == 78141
+    assert np.all(g.tx[:, 2] == 0) and np.all(g.rx[:, 2] == 0)
