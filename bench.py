@@ -52,7 +52,10 @@ def parse():
                     help="jitter the frequencies off the uniform grid (general-frequency kernels)")
     ap.add_argument("--study-rho", type=float, nargs="+", default=[0.3, 0.1, 0.03],
                     help="paper_like study: step sizes as eta * L")
-    ap.add_argument("--workload", default="mid", choices=["mid", "large", "batched48", "paper_like"],
+    ap.add_argument("--study", default=None, choices=["paper_like", "time_to_nmse"],
+                    help="run a study instead of the bench line: the Sec. V PGM vs SPGM comparison on a "
+                         "paper-shaped scene, or SPGM time to the oracle's NMSE (small and mid workloads)")
+    ap.add_argument("--workload", default="mid", choices=["mid", "large", "batched48"],
                     help="mid = the headline workload; large = 32 TX x 32 RX, K = 128, N = 1048576; "
                          "batched48 = 48 uneven scenes per epoch through one CUDA graph")
     return ap.parse_args()
@@ -221,6 +224,137 @@ def cpu_baseline(w, y_np, eta, lam, seconds):
     return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{done} SPGM minibatch step(s) of the workload ({bp} pairs x {w.geom.K} freqs x "
                       f"{w.geom.N} voxels, forward + adjoint + prox) in FP64 on {cores} host threads, {dt:.1f} s"}
+
+
+def time_to_oracle_nmse(include_mid=False, nmse_tol=1e-4):
+    """SPGM time to the FP64 oracle's reconstruction within NMSE <= nmse_tol, per precision form.
+
+    Small workload (4 TX x 4 RX, 16 freqs, 16x16x8 voxels, 4 pairs per minibatch, 30 epochs): the
+    oracle runs the 30 epochs; each GPU form runs the same seeded epochs with CUDA events around
+    every epoch, and the time to target is the summed epoch time up to the first epoch whose iterate
+    is within nmse_tol of the oracle's final one.  y, eta = 1/L (50 power iterations) and lambda come
+    from the oracle.  The batched form solves 8 such scenes (other seeds) per CUDA graph; its time is
+    per scene.  With include_mid, the mid workload's first 3 epochs (eta from the oracle's bound
+    ||A||_F^2/M on L) are compared the same way.
+    """
+    import dataclasses
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2509_00774_gb300 import inputs as I
+    from paper_2509_00774_gb300 import metrics
+    from paper_2509_00774_gb300 import workloads as W
+    from paper_2509_00774_gb300.nfmimo import Batch, Context
+    oracle.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def problem(w, power_its):
+        o = oracle.Oracle(w.geom)
+        y = I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db)
+        y = y.astype(np.complex64).astype(np.complex128)
+        L = (o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), power_its) if power_its
+             else o.frobenius_bound())
+        return o, y, float(np.float32(1.0 / L)), float(np.float32(0.05 * o.lambda_max(y)))
+
+    def oracle_run(o, w, y, eta, lam, epochs):
+        s = np.zeros(o.N, dtype=np.complex128)
+        t0 = time.perf_counter()
+        for e in range(epochs):
+            s = o.spgm_epoch(y, s, I.epoch_permutation(o.P, w.seeds["perm"], e), w.pairs_per_batch, eta, lam)
+        return s, time.perf_counter() - t0
+
+    def gpu_run(w, y, eta, lam, epochs, precision, s_ref):
+        g = w.geom
+        ctx = Context(dev.index)
+        ctx.set_precision(precision)
+        ctx.set_geometry(g)
+        y_d = torch.from_numpy(y.astype(np.complex64)).to(dev)
+        perms = torch.from_numpy(np.stack([I.epoch_permutation(g.P, w.seeds["perm"], e)
+                                           for e in range(epochs)]).astype(np.int32)).to(dev)
+        scratch = torch.zeros(g.N, dtype=torch.complex64, device=dev)
+        for e in range(min(3, epochs)):                      # warm-up on a scratch iterate
+            ctx.spgm_epoch(y_d, scratch, perms[e], w.pairs_per_batch, eta, lam)
+        s = torch.zeros(g.N, dtype=torch.complex64, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * epochs)]
+        snaps = []
+        torch.cuda.synchronize()
+        for e in range(epochs):
+            ev[2 * e].record()
+            ctx.spgm_epoch(y_d, s, perms[e], w.pairs_per_batch, eta, lam)
+            ev[2 * e + 1].record()
+            snaps.append(s.clone())                           # outside the timed events
+        torch.cuda.synchronize()
+        ms = [ev[2 * e].elapsed_time(ev[2 * e + 1]) for e in range(epochs)]
+        errs = [metrics.nmse(x.cpu().numpy(), s_ref) for x in snaps]
+        hit = next((e for e, x in enumerate(errs) if x <= nmse_tol), None)
+        ctx.close()
+        return {"epochs_to_target": None if hit is None else hit + 1,
+                "ms_to_target": None if hit is None else float(sum(ms[:hit + 1])),
+                "ms_all_epochs": float(sum(ms)), "final_nmse": errs[-1]}
+
+    out = {"nmse_tol": nmse_tol, "reference": "FP64 oracle reconstruction after the same epochs"}
+    w = W.small_T4R4_K16_16x16x8()
+    o, y, eta, lam = problem(w, 50)
+    s_ref, t_orc = oracle_run(o, w, y, eta, lam, w.epochs)
+    small = {"workload": w.name, "epochs": w.epochs, "pairs_per_batch": w.pairs_per_batch,
+             "oracle_s": t_orc, "oracle_cores": oracle.get_threads()}
+    for prec in ("fp32", "tc_bf16x3", "tc_fp16x3"):
+        small[prec] = gpu_run(w, y, eta, lam, w.epochs, prec, s_ref)
+    # batched form: 8 scenes of the same geometry with their own seeds, one graph per epoch
+    scenes = [dataclasses.replace(w, seeds={"scene": 50 + 4 * i, "noise": 51 + 4 * i, "perm": 52 + 4 * i,
+                                            "power": 53 + 4 * i}) for i in range(8)]
+    probs = [problem(x, 50) for x in scenes]
+    refs = [oracle_run(p[0], x, p[1], p[2], p[3], w.epochs)[0] for p, x in zip(probs, scenes)]
+    ctxs = []
+    for x in scenes:
+        c = Context(dev.index)
+        c.set_geometry(x.geom)
+        ctxs.append(c)
+    batch = Batch(ctxs)
+    ys = [torch.from_numpy(p[1].astype(np.complex64)).to(dev) for p in probs]
+    perm_all = [torch.from_numpy(np.stack([I.epoch_permutation(w.geom.P, x.seeds["perm"], e)
+                                           for e in range(w.epochs)]).astype(np.int32)).to(dev) for x in scenes]
+    perm_bufs = [torch.empty(w.geom.P, dtype=torch.int32, device=dev) for _ in scenes]
+    bps = [w.pairs_per_batch] * len(scenes)
+    etas = [p[2] for p in probs]
+    lams = [p[3] for p in probs]
+    scratch = [torch.zeros(w.geom.N, dtype=torch.complex64, device=dev) for _ in scenes]
+    for e in range(3):
+        for pb, pa in zip(perm_bufs, perm_all):
+            pb.copy_(pa[e])
+        batch.spgm_epoch(ys, scratch, perm_bufs, bps, etas, lams)
+    ss = [torch.zeros(w.geom.N, dtype=torch.complex64, device=dev) for _ in scenes]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * w.epochs)]
+    snaps = []
+    for e in range(w.epochs):
+        for pb, pa in zip(perm_bufs, perm_all):
+            pb.copy_(pa[e])
+        ev[2 * e].record()
+        batch.spgm_epoch(ys, ss, perm_bufs, bps, etas, lams)
+        ev[2 * e + 1].record()
+        snaps.append([x.clone() for x in ss])
+    torch.cuda.synchronize()
+    ms = [ev[2 * e].elapsed_time(ev[2 * e + 1]) for e in range(w.epochs)]
+    worst = [max(metrics.nmse(x.cpu().numpy(), r) for x, r in zip(sn, refs)) for sn in snaps]
+    hit = next((e for e, x in enumerate(worst) if x <= nmse_tol), None)
+    small["batched_fp32_8_scenes"] = {
+        "epochs_to_target": None if hit is None else hit + 1,
+        "ms_to_target_per_scene": None if hit is None else float(sum(ms[:hit + 1])) / len(scenes),
+        "ms_all_epochs_per_scene": float(sum(ms)) / len(scenes), "final_max_nmse": worst[-1]}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    out["small"] = small
+    if include_mid:
+        w = W.mid_T16R16_K64_64x64x32()
+        o, y, eta, lam = problem(w, 0)
+        s_ref, t_orc = oracle_run(o, w, y, eta, lam, 3)
+        mid = {"workload": w.name, "epochs": 3, "pairs_per_batch": w.pairs_per_batch, "oracle_s": t_orc,
+               "oracle_cores": oracle.get_threads(), "step": "1/L_F, L_F = ||A||_F^2/M (oracle closed form)"}
+        for prec in ("fp32", "tc_bf16x3", "tc_fp16x3"):
+            mid[prec] = gpu_run(w, y, eta, lam, 3, prec, s_ref)
+        out["mid"] = mid
+    return out
 
 
 def run_reference(args):
@@ -406,6 +540,7 @@ def run_ours(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, y.cpu().numpy().astype(np.complex128), eta, lam, args.cpu_seconds)
+        line["time_to_oracle_nmse"] = time_to_oracle_nmse()
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -620,11 +755,16 @@ def run_paper_like(args):
 
 def main():
     args = parse()
+    if args.study == "paper_like":
+        run_paper_like(args)
+        return
+    if args.study == "time_to_nmse":
+        from paper_2509_00774_gb300 import build as nb
+        nb.build()
+        print(json.dumps(time_to_oracle_nmse(include_mid=True)), flush=True)
+        return
     if args.workload == "batched48" and args.impl != "reference":
         run_batched(args)
-        return
-    if args.workload == "paper_like":
-        run_paper_like(args)
         return
     if args.impl == "reference":
         run_reference(args)

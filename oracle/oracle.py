@@ -21,6 +21,7 @@ Readings where the paper is silent (each also listed in the design notes):
     drawn without replacement from a per-epoch permutation; a short last chunk
     uses its own B
   * step eta = 1/L with L = lambda_max(A^H A)/M from a seeded power iteration
+    (or, where that is too slow, from the bound ||A||_F^2/M >= L)
   * lambda = frac * max_n |(A^H y)_n| / M
 """
 from __future__ import annotations
@@ -238,6 +239,23 @@ class Oracle:
             v /= np.linalg.norm(v)
         Av = self.forward(v)
         return float(np.vdot(Av, Av).real) / (self.M * float(np.vdot(v, v).real))
+
+    def frobenius_bound(self) -> float:
+        """||A||_F^2 / M, an upper bound on L = lambda_max(A^H A)/M (the trace bounds the largest
+        eigenvalue of a positive semidefinite matrix).
+
+        From Eq. 2, |A_mn|^2 = |p(f_m)|^2 / ((4 pi)^2 dT^2 dR^2), so the sum over the rows of one
+        voxel factors into (sum_k |p_k|^2)(sum_t 1/dT^2)(sum_r 1/dR^2) / (4 pi)^2.
+        """
+        pos = self.geom.grid.positions()
+        inv_t = np.zeros(self.N)
+        for a in self._tx:
+            inv_t += 1.0 / np.sum((pos - a) ** 2, axis=1)
+        inv_r = np.zeros(self.N)
+        for a in self._rx:
+            inv_r += 1.0 / np.sum((pos - a) ** 2, axis=1)
+        pk = float(self.K) if self._p is None else float(np.sum(self._p ** 2))
+        return pk * float(np.sum(inv_t * inv_r)) / ((4.0 * math.pi) ** 2 * self.M)
 
     def lambda_max(self, y) -> float:
         """max_n |(A^H y)_n| / M: the smallest lambda for which s = 0 is a minimiser."""

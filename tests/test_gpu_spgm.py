@@ -176,26 +176,37 @@ def test_spgm_host_buffers_match_device():
     assert np.array_equal(s_host, s_dev.cpu().numpy())
 
 
-def test_spgm_mid_first_steps():
-    """Mid workload (N = 131072, 16 pairs x 64 frequencies per minibatch): first 3 SPGM steps."""
+def test_spgm_mid_three_epochs():
+    """Mid workload (N = 131072, 16 pairs x 64 frequencies per minibatch): the first three SPGM
+    epochs in full, every iterate of the first epoch and the end of each epoch against the oracle.
+    The step is 1/||A||_F^2 * M (the oracle's closed-form bound on L; a power iteration on this
+    size is too slow for the oracle) and lambda = 0.05 max|A^H y|/M from the oracle."""
     w = W.mid_T16R16_K64_64x64x32()
     o = Oracle(w.geom)
     y = _c64(I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db))
     ctx = make_ctx(w.geom)
-    # step size from the GPU power iteration (checked separately on the small workload)
-    L = ctx.power_iteration(to_dev(_c64(I.complex_gaussian(o.N, w.seeds["power"]))), 20)
-    eta = float(np.float32(1.0 / L))
-    lam = float(np.float32(0.05 * ctx.lambda_max(to_dev(y))))
-    perm = I.epoch_permutation(o.P, w.seeds["perm"], 0)
+    eta = float(np.float32(1.0 / o.frobenius_bound()))
+    lam = float(np.float32(0.05 * o.lambda_max(y)))
     s_orc = np.zeros(o.N, dtype=np.complex128)
     s_gpu = to_dev(np.zeros(o.N))
     y_dev = to_dev(y)
-    for c in range(3):
-        pairs = perm[16 * c:16 * (c + 1)]
-        s_orc = o.spgm_step(y, s_orc, pairs, eta, lam)
-        ctx.spgm_step(y_dev, s_gpu, to_dev(pairs, "int32"), eta, lam)
+    bp = w.pairs_per_batch
+    for e in range(3):
+        perm = I.epoch_permutation(o.P, w.seeds["perm"], e)
+        if e == 0:
+            for c in range(o.P // bp):
+                pairs = perm[bp * c:bp * (c + 1)]
+                s_orc = o.spgm_step(y, s_orc, pairs, eta, lam)
+                ctx.spgm_step(y_dev, s_gpu, to_dev(pairs, "int32"), eta, lam)
+                err = nmse(to_host(s_gpu), s_orc)
+                assert err <= NMSE_TOL, f"step {c}: NMSE {err:.3e}"
+        else:
+            s_orc = o.spgm_epoch(y, s_orc, perm, bp, eta, lam)
+            ctx.spgm_epoch(y_dev, s_gpu, to_dev(perm, "int32"), bp, eta, lam)
         err = nmse(to_host(s_gpu), s_orc)
-        assert err <= NMSE_TOL, f"step {c}: NMSE {err:.3e}"
+        print(f"[parity] mid SPGM epoch {e}: NMSE {err:.3e}")
+        assert err <= NMSE_TOL, f"epoch {e}: NMSE {err:.3e}"
+    assert np.count_nonzero(s_orc) > 0
 
 
 # ---------------------------------------------------------------------------

@@ -314,6 +314,18 @@ def test_power_iteration_matches_eigvalsh():
     assert abs(L500 - lam_top) <= 1e-8 * lam_top
 
 
+@pytest.mark.parametrize("pulse", [False, True])
+def test_frobenius_bound_is_the_dense_trace(pulse):
+    """||A||_F^2 / M from its closed form equals the sum of |A_mn|^2 over the dense matrix, and
+    bounds the top eigenvalue of A^H A / M from above."""
+    o = Oracle(_tiny_random_geom(4, T=3, R=4, K=6, grid=(5, 4, 3), pulse=pulse))
+    A = o.dense(np.arange(o.M), np.arange(o.N))
+    fro = float(np.sum(np.abs(A) ** 2)) / o.M
+    assert abs(o.frobenius_bound() - fro) <= 1e-12 * fro
+    lam_top = float(np.linalg.eigvalsh(A.conj().T @ A / o.M)[-1])
+    assert lam_top <= o.frobenius_bound() * (1 + 1e-12)
+
+
 # ---------------------------------------------------------------------------
 # metrics
 # ---------------------------------------------------------------------------
