@@ -106,6 +106,39 @@ int nfm_dims(const nfm_ctx* ctx, int* T, int* R, int* K, long long* N);
 enum { NFM_FP32 = 0, NFM_TC_BF16X3 = 1, NFM_TC_FP16X3 = 2 };
 int nfm_set_precision(nfm_ctx* ctx, int mode);
 
+/* How the FP32 CUDA-core operator evaluates the frequency dependence of Eq. 2
+ * for equally spaced frequencies f_k = f0 + k df:
+ *   NFM_ALGO_DIRECT     every (row, voxel) term from phasor recurrences over k;
+ *   NFM_ALGO_CHEBYSHEV  per (pair, 8x4x4 voxel tile) the factor
+ *                       exp(-j 2 pi k df delta/c), delta = D - D_tile_centre,
+ *                       is expanded in Chebyshev polynomials of
+ *                       t = delta / xi (|t| <= 0.9):
+ *                         exp(-j z_k t) = sum_{l<L} (-j)^l b_l(z_k) T_l(t),
+ *                       b_0 = J_0, b_l = 2 J_l (Jacobi-Anger), L in {16, ..., 32}
+ *                       chosen at nfm_set_geometry so the dropped tail is below
+ *                       2e-8; per (pair, voxel) the work is L recurrence steps
+ *                       instead of K terms (relative error ~2e-6, as DIRECT);
+ *   NFM_ALGO_AUTO       CHEBYSHEV where the geometry allows it (L <= 32), else
+ *                       DIRECT (default).
+ * Arbitrary frequency lists always use their own kernels; the tensor-core
+ * adjoint modes keep their own generation.  Requesting CHEBYSHEV where L would
+ * exceed 32 makes the operator calls fail with NFM_ERR_ARG. */
+enum { NFM_ALGO_AUTO = 0, NFM_ALGO_DIRECT = 1, NFM_ALGO_CHEBYSHEV = 2 };
+int nfm_set_algorithm(nfm_ctx* ctx, int algo);
+
+/* Which algorithm the operator uses for the current geometry and setting
+ * (NFM_ALGO_DIRECT or NFM_ALGO_CHEBYSHEV), the expansion length L (0 if the
+ * expansion is not available) and z of the highest frequency.  Any pointer
+ * may be NULL.  Errors: NFM_ERR_STATE without a geometry. */
+int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_max);
+
+/* Host-only helper (no GPU needed): the expansion coefficients
+ * out[k*L + l] = b_l(k z_step), l < L, k < K, of
+ *   exp(-j z t) = sum_l (-j)^l b_l(z) T_l(t)   (b_0 = J_0(z), b_l = 2 J_l(z)),
+ * computed in FP64 by Chebyshev-Gauss quadrature with 2L + 64 nodes.
+ * Errors: NFM_ERR_ARG for K < 1, L outside [1, 256], NULL out, non-finite z_step. */
+int nfm_cheb_coefficients(double z_step, int K, int L, double* out);
+
 /* Regulariser of Eq. 3 (Sec. III uses l1 and notes the method extends to
  * other functionals): R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 (elastic net;
  * default w1 = 1, w2 = 0, the paper's l1; w1 = 0 is Tikhonov).  Its prox,

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnfmimo.so")
-SOURCES = ["nfm_api.cu", "op_forward.cu", "op_adjoint.cu", "op_adjoint_tc.cu", "op_misc.cu", "op_prox.cu", "op_general.cu"]
+SOURCES = ["nfm_api.cu", "op_forward.cu", "op_adjoint.cu", "op_adjoint_tc.cu", "op_misc.cu", "op_prox.cu", "op_general.cu",
+           "op_cheb.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -102,6 +102,17 @@ struct nfm_ctx {
     int fwd_occ[MAX_K1 + 1] = {};
     bool fwd_attr[MAX_K1 + 1] = {};
     bool adj_attr[MAX_K1 + 1] = {};
+
+    // Chebyshev expansion of the frequency dependence (equally spaced frequencies)
+    int algorithm = NFM_ALGO_AUTO;
+    float* d_cheb = nullptr;      // [cheb_kpad][cheb_L] b_l(k)
+    int cheb_L = 0;               // 0: not available for this geometry
+    int cheb_kpad = 0;
+    float cheb_tau = 0.f;         // t = tau * delta
+    double cheb_zmax = 0.0;       // z of the highest frequency
+    bool fwd_cheb_attr[CHEB_MAX_L + 1] = {};
+    bool adj_cheb_attr[CHEB_MAX_L + 1] = {};
+    int fwd_cheb_occ[CHEB_MAX_L + 1][4] = {};
 };
 
 namespace {
@@ -214,6 +225,111 @@ void prof_pair(nfm_ctx* ctx, int kind, int a, int b)
     if (ctx->prof && a >= 0 && b >= 0) ctx->pending.push_back({kind, a, b});
 }
 
+// b_l(k), l < L, of exp(-j z t) = sum_l (-j)^l b_l T_l(t) at z = k z_step (b_0 = J_0(z),
+// b_l = 2 J_l(z)), by Chebyshev-Gauss quadrature of (eps_l / pi) int_0^pi e^{-j z cos th} cos(l th) dth
+// with Q = 2L + 64 nodes (exact up to aliasing from degree >= 2Q - L).  FP64, row-major [K][L].
+void cheb_coefficients(double z_step, int K, int L, double* out)
+{
+    const double pi = 3.14159265358979323846;
+    const int Q = 2 * L + 64;
+    std::vector<double> cth(Q), th(Q);
+    for (int q = 0; q < Q; ++q) {
+        th[q] = pi * (q + 0.5) / Q;
+        cth[q] = std::cos(th[q]);
+    }
+    for (int k = 0; k < K; ++k) {
+        const double z = k * z_step;
+        for (int l = 0; l < L; ++l) {
+            double re = 0.0, im = 0.0;
+            for (int q = 0; q < Q; ++q) {
+                const double w = std::cos(l * th[q]);
+                re += std::cos(z * cth[q]) * w;
+                im -= std::sin(z * cth[q]) * w;
+            }
+            const double eps = l == 0 ? 1.0 : 2.0;
+            re *= eps / Q;
+            im *= eps / Q;
+            // a_l = (-j)^l b_l  =>  b_l = Re(j^l a_l)
+            double b;
+            switch (l & 3) {
+            case 0: b = re; break;
+            case 1: b = -im; break;
+            case 2: b = -re; break;
+            default: b = im; break;
+            }
+            out[(size_t)k * L + l] = b;
+        }
+    }
+}
+
+// Chebyshev expansion set-up for equally spaced frequencies: the FP64 range of
+// delta = D - D_c over every (pair, tile), the scale tau with |t| <= 0.9, the
+// number of terms L (tail below 2e-8 at the highest frequency) and the table.
+int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, double df, double c)
+{
+    unsigned long long* d_mx = nullptr;
+    unsigned long long bits = 0;
+    cudaError_t e = cudaMalloc((void**)&d_mx, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_mx, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = launch_cheb_range(gd, as, d_mx, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, d_mx, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
+    free_ptr(d_mx);
+    if (e != cudaSuccess) return fail(ctx, NFM_ERR_CUDA, "expansion range: %s", cudaGetErrorString(e));
+    double dmax;
+    memcpy(&dmax, &bits, sizeof(dmax));
+    const double margin = 0.9;
+    const double span = 2.0 * dmax;                 // |delta| = |d_T - d_cT + d_R - d_cR| <= span
+    if (!(span > 0)) return NFM_OK;                 // degenerate: keep the direct path
+    const double z_step = 2.0 * 3.14159265358979323846 * df * span / (c * margin);
+    const double zmax = z_step * (K - 1);
+    // tail of the expansion at the highest frequency
+    const int LP = 80;
+    std::vector<double> probe(2 * LP);
+    cheb_coefficients(zmax, 2, LP, probe.data());   // rows z = 0 and z = zmax
+    int L = 0;
+    for (int cand = 16; cand <= CHEB_MAX_L; cand += 4) {
+        double tail = 0.0;
+        for (int l = cand; l < LP; ++l) tail += std::fabs(probe[LP + l]);
+        if (tail < 2e-8) {
+            L = cand;
+            break;
+        }
+    }
+    if (L == 0) return NFM_OK;                      // too many terms: the direct path stays
+    const int kpad = (K + 3) & ~3;
+    std::vector<double> b((size_t)K * L);
+    cheb_coefficients(z_step, K, L, b.data());
+    std::vector<float> hb((size_t)kpad * L, 0.f);
+    for (size_t i = 0; i < b.size(); ++i) hb[i] = (float)b[i];
+    e = cudaMalloc((void**)&ctx->d_cheb, hb.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_cheb, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_ptr(ctx->d_cheb);
+        ctx->d_cheb = nullptr;
+        return fail(ctx, NFM_ERR_NOMEM, "expansion table: %s", cudaGetErrorString(e));
+    }
+    ctx->cheb_L = L;
+    ctx->cheb_kpad = kpad;
+    ctx->cheb_tau = (float)(margin / span);
+    ctx->cheb_zmax = zmax;
+    return NFM_OK;
+}
+
+// Whether the Chebyshev kernels run for this context (equally spaced frequencies).
+int use_cheb(nfm_ctx* ctx, bool& on)
+{
+    on = false;
+    if (!ctx->uniform || ctx->algorithm == NFM_ALGO_DIRECT) return NFM_OK;
+    if (ctx->cheb_L == 0) {
+        if (ctx->algorithm == NFM_ALGO_CHEBYSHEV)
+            return fail(ctx, NFM_ERR_ARG, "the Chebyshev expansion needs more than %d terms here", CHEB_MAX_L);
+        return NFM_OK;
+    }
+    on = true;
+    return NFM_OK;
+}
+
 int plan_forward(nfm_ctx* ctx, int n_pairs, FwdPlan* pl)
 {
     const int K1 = ctx->K1;
@@ -298,10 +414,75 @@ int enqueue_forward_general(nfm_ctx* ctx, const int* pairs, int n_pairs, const f
     return NFM_OK;
 }
 
+int enqueue_forward_cheb(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
+                         float2* out, const unsigned char* fmask)
+{
+    const int LT = ctx->cheb_L, KP = ctx->cheb_kpad;
+    int pch = 4, pci = 0;
+    while (pch < CHEB_GROUPS && pch < n_pairs) {
+        pch *= 2;
+        ++pci;
+    }
+    const int TS = CHEB_GROUPS / pch;
+    const size_t smem = fwd_cheb_smem_bytes(LT, KP, pch);
+    if (smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "expansion forward needs %zu B shared memory", smem);
+    const void* fn = fwd_cheb_kernel_ptr(LT);
+    if (!ctx->fwd_cheb_attr[LT]) {
+        NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin));
+        ctx->fwd_cheb_attr[LT] = true;
+    }
+    int& occ = ctx->fwd_cheb_occ[LT][pci];
+    if (occ == 0) {
+        NFM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, CHEB_THREADS, smem));
+        if (occ < 1) occ = 1;
+    }
+    const int n_groups = (n_pairs + pch - 1) / pch;
+    const int n_slots = n_groups * pch;
+    long long G = 2LL * ctx->num_sms * occ;         // about two waves of CTAs
+    long long nch = (G + n_groups - 1) / n_groups;
+    long long max_ch = (ctx->gd.n_tiles + TS - 1) / TS;
+    if (nch > max_ch) nch = max_ch;
+    if (nch > 65535) nch = 65535;
+    if (nch < 1) nch = 1;
+    const size_t partial_bytes = (size_t)nch * n_slots * ctx->K * sizeof(float2);
+    NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, partial_bytes));
+    OpDesc op = op_desc(ctx);
+    ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, KP};
+    FwdArgs a;
+    a.pairs = pairs;
+    a.n_pairs = n_pairs;
+    a.s = s;
+    a.partial = (float2*)ctx->d_partial;
+    a.n_slots = n_slots;
+    a.VS = pch;
+    a.tiles_base = (int)(ctx->gd.n_tiles / nch);
+    a.tiles_rem = (int)(ctx->gd.n_tiles % nch);
+    const int e0 = prof_mark(ctx);
+    NFM_CK(launch_fwd_cheb(op, cd, a, dim3(n_groups, (unsigned)nch), smem, ctx->stream));
+    const int e1 = prof_mark(ctx);
+    ReduceArgs ra;
+    ra.partial = (const float2*)ctx->d_partial;
+    ra.n_chunks = (int)nch;
+    ra.n_slots = n_slots;
+    ra.n_out = n_pairs * ctx->K;
+    ra.pairs = pairs;
+    ra.y_obs = y_obs;
+    ra.fmask = fmask;
+    ra.out = out;
+    NFM_CK(launch_fwd_reduce(op, ra, ctx->stream));
+    const int e2 = prof_mark(ctx);
+    prof_pair(ctx, 0, e0, e1);
+    prof_pair(ctx, 1, e1, e2);
+    return NFM_OK;
+}
+
 int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
                     float2* out, const unsigned char* fmask = nullptr)
 {
     if (!ctx->uniform) return enqueue_forward_general(ctx, pairs, n_pairs, s, y_obs, out, fmask);
+    bool cheb = false;
+    NFM_TRY(use_cheb(ctx, cheb));
+    if (cheb) return enqueue_forward_cheb(ctx, pairs, n_pairs, s, y_obs, out, fmask);
     FwdPlan pl;
     NFM_TRY(plan_forward(ctx, n_pairs, &pl));
     NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, pl.partial_bytes));
@@ -387,6 +568,32 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         return NFM_OK;
     }
     if (ctx->precision != NFM_FP32) return enqueue_adjoint_tc(ctx, pairs, n_pairs, r, g_out, s, step, alpha, shrink);
+    bool cheb = false;
+    NFM_TRY(use_cheb(ctx, cheb));
+    if (cheb) {
+        const int LT = ctx->cheb_L;
+        const size_t smem = adj_cheb_smem_bytes(LT, ctx->cheb_kpad);
+        if (!ctx->adj_cheb_attr[LT]) {
+            NFM_CK(cudaFuncSetAttribute(adj_cheb_kernel_ptr(LT), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ctx->smem_optin));
+            ctx->adj_cheb_attr[LT] = true;
+        }
+        AdjArgs a;
+        a.pairs = pairs;
+        a.n_pairs = n_pairs;
+        a.r = r;
+        a.g_out = g_out;
+        a.s = s;
+        a.step = step;
+        a.alpha = alpha;
+        a.shrink = shrink;
+        a.pchunk = CHEB_ADJ_PCHUNK;
+        ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad};
+        const int e0 = prof_mark(ctx);
+        NFM_CK(launch_adj_cheb(op_desc(ctx), cd, a, smem, ctx->stream));
+        prof_pair(ctx, 2, e0, prof_mark(ctx));
+        return NFM_OK;
+    }
     const int K1 = ctx->K1;
     size_t smem = adj_smem_bytes(K1, ADJ_PCHUNK);
     if (!ctx->adj_attr[K1]) {
@@ -490,7 +697,7 @@ void nfm_destroy(nfm_ctx* ctx)
     else cudaDeviceSynchronize();
     void* ps[] = {ctx->d_ant, ctx->d_ant_xyz, ctx->d_pulse, ctx->d_antk, ctx->d_fkc, ctx->d_pairs_all, ctx->d_err, ctx->d_red,
                   ctx->d_partial, ctx->d_resid, ctx->d_v, ctx->d_g, ctx->d_y, ctx->d_hy, ctx->d_hs, ctx->d_hperm,
-                  ctx->d_prox_partial, ctx->d_bmat, ctx->d_bscale};
+                  ctx->d_prox_partial, ctx->d_bmat, ctx->d_bscale, ctx->d_cheb};
     for (void* p : ps) free_ptr(p);
     for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
     delete ctx;
@@ -565,6 +772,9 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     free_ptr(ctx->d_pairs_all);
     free_ptr(ctx->d_antk);
     free_ptr(ctx->d_fkc);
+    free_ptr(ctx->d_cheb);
+    ctx->d_cheb = nullptr;
+    ctx->cheb_L = 0;
     ctx->d_antk = nullptr;
     ctx->d_fkc = nullptr;
     ctx->d_ant = nullptr;
@@ -654,6 +864,7 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
         free_ptr(d_fk);
         if (e != cudaSuccess) return fail(ctx, NFM_ERR_CUDA, "general-frequency tables: %s", cudaGetErrorString(e));
     }
+    if (uniform) NFM_TRY(setup_cheb(ctx, gd, as, K, df, c));
     NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
 
     ctx->T = T;
@@ -690,6 +901,33 @@ int nfm_set_precision(nfm_ctx* ctx, int mode)
     if (mode != NFM_FP32 && mode != NFM_TC_BF16X3 && mode != NFM_TC_FP16X3)
         return fail(ctx, NFM_ERR_ARG, "unknown precision mode %d", mode);
     ctx->precision = mode;
+    return NFM_OK;
+}
+
+int nfm_set_algorithm(nfm_ctx* ctx, int algo)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    if (algo != NFM_ALGO_AUTO && algo != NFM_ALGO_DIRECT && algo != NFM_ALGO_CHEBYSHEV)
+        return fail(ctx, NFM_ERR_ARG, "unknown algorithm %d", algo);
+    ctx->algorithm = algo;
+    return NFM_OK;
+}
+
+int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_max)
+{
+    NFM_TRY(require_geom(ctx));
+    bool cheb = false;
+    NFM_TRY(use_cheb(ctx, cheb));
+    if (algo_in_use) *algo_in_use = cheb ? NFM_ALGO_CHEBYSHEV : NFM_ALGO_DIRECT;
+    if (n_terms) *n_terms = ctx->cheb_L;
+    if (z_max) *z_max = ctx->cheb_zmax;
+    return NFM_OK;
+}
+
+int nfm_cheb_coefficients(double z_step, int K, int L, double* out)
+{
+    if (K < 1 || L < 1 || L > 256 || !out || !std::isfinite(z_step)) return NFM_ERR_ARG;
+    cheb_coefficients(z_step, K, L, out);
     return NFM_OK;
 }
 

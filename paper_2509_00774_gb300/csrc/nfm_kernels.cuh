@@ -61,6 +61,26 @@ cudaError_t launch_fwd_general(const OpDesc& op, const GenDesc& gd, const FwdArg
 cudaError_t launch_adj_general(const OpDesc& op, const GenDesc& gd, const AdjArgs& a, cudaStream_t st);
 const void* fwd_general_ptr();
 
+// Chebyshev-expansion operator (op_cheb.cu)
+constexpr int CHEB_THREADS = 128;
+constexpr int CHEB_GROUP = 4;                              // lanes per (pair, tile) in the forward
+constexpr int CHEB_GROUPS = CHEB_THREADS / CHEB_GROUP;    // 32
+constexpr int CHEB_ADJ_PCHUNK = 16;                        // pairs staged per adjoint round
+constexpr int CHEB_MAX_L = 32;
+struct ChebDesc {
+    const float* coef;       // [k_pad][L] b_l(k), rows k >= K zero
+    float tau;               // t = tau * delta
+    int L;                   // expansion terms (16, 20, 24, 28 or 32)
+    int k_pad;               // K rounded up to a multiple of 4
+};
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch);
+size_t adj_cheb_smem_bytes(int LT, int k_pad);
+const void* fwd_cheb_kernel_ptr(int LT);
+const void* adj_cheb_kernel_ptr(int LT);
+cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, size_t smem,
+                            cudaStream_t st);
+cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, size_t smem, cudaStream_t st);
+
 constexpr int FWD_PC = 8;         // pairs per forward CTA
 constexpr int ADJ_TC_PCHUNK = 8;  // pairs whose tensor-core B operands a CTA holds at once
 constexpr int ADJ_THREADS = 128;  // one 8x4x4 tile: two voxels per thread, pairs split in two halves
@@ -100,6 +120,8 @@ const void* adj_tc_kernel_ptr(int K1, bool f16);
 cudaError_t launch_adjoint_tc(const OpDesc& op, const AdjArgs& a, bool f16, const float2* r, unsigned char* bmat,
                               float* inv_scale, size_t smem, cudaStream_t st);
 cudaError_t launch_ant_setup(const GridDesc& g, const AntSetup& a, cudaStream_t st);
+// FP64 max over antennas, tiles and voxel slots of | |r_a - r_v| - |r_a - r_c| | (atomicMax on the bits)
+cudaError_t launch_cheb_range(const GridDesc& g, const AntSetup& a, unsigned long long* out, cudaStream_t st);
 
 // FP64 reductions (deterministic: fixed grid, fixed tree)
 constexpr int RED_BLOCKS = 256;

@@ -1,0 +1,460 @@
+// Matrix-free A_B s and A_B^H r (Eq. 2) by a tile-local Chebyshev expansion of
+// the frequency dependence (equally spaced frequencies f_k = f0 + k df).
+//
+// For a (pair, tile) with centre path length D_c and a voxel with path length
+// D = D_c + delta, the element factors as
+//
+//   A_kv = p_k amp_v e^{-j 2 pi f0 D/c} e^{-j 2 pi k df D_c/c} e^{-j z_k t_v},
+//   t_v = delta_v / xi  (|t_v| <= 0.9 for every voxel slot),  z_k = 2 pi k df xi / c,
+//
+// and the last factor has the Jacobi-Anger (Chebyshev) expansion
+//
+//   e^{-j z t} = sum_l (-j)^l b_l(z) T_l(t),   b_0 = J_0(z),  b_l = 2 J_l(z),
+//
+// truncated after L terms (tail below 2e-8).  So per (pair, tile)
+//
+//   forward:  y_k += P_k sum_l (-j)^l b_l(k) m_l,  m_l = sum_v u_v T_l(t_v),
+//             u_v = amp_v s_v e^{-j 2 pi f0 D_v/c},  P_k = e^{-j 2 pi k df D_c/c}
+//   adjoint:  g_v += conj(u'_v) sum_l T_l(t_v) C_l,  C_l = j^l sum_k b_l(k) conj(p_k) r_k conj(P_k),
+//             u'_v = amp_v e^{-j 2 pi f0 D_v/c}.
+//
+// The per-voxel work is L steps of the Chebyshev recurrence T_{l+1} = 2t T_l - T_{l-1}
+// (stable for |t| <= 0.9: rounding grows at most linearly in l) with two FMAs
+// each, instead of K complex terms; the per-(pair, tile) work is 2KL FMAs.
+// b_l(k) is real, so each (k, l) term of the expansion is two FMAs.
+#include "nfm_kernels.cuh"
+
+namespace nfm {
+
+// amplitude, reduced base phase f0 D/c (turns) and delta = D - D_c of one (pair, voxel)
+struct ChebVoxel {
+    float amp, th0, delta;
+};
+
+__device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelOffset& o, const PhaseConsts& ph)
+{
+    float rsT, rsR;
+    const float dT = antenna_delta(pt.vTx, pt.vTy, pt.vTz, pt.dcT, pt.dcT2, o, rsT);
+    const float dR = antenna_delta(pt.vRx, pt.vRy, pt.vRz, pt.dcR, pt.dcR2, o, rsR);
+    ChebVoxel c;
+    c.delta = dT + dR;
+    c.amp = INV_4PI * rsT * rsR;
+    // f0 (D_c + delta)/c with an exact product split: one rounding at |x| <= 1
+    const float p = ph.f0c_hi * c.delta;
+    const float pe = fmaf(ph.f0c_hi, c.delta, -p);
+    const float th = (pt.B + (p - rintf(p))) + fmaf(ph.f0c_lo, c.delta, pe);
+    c.th0 = frac_turns(th);
+    return c;
+}
+
+// (cos, sin)(2 pi k df D_c / c) from the reduced step phase S = S_hi + S_lo of the
+// pair tile: k S_hi split exactly (FMA remainder), so one rounding at |x| <= 1/2.
+__device__ __forceinline__ float2 tile_step_cis(const PairTile& pt, int k)
+{
+    const float kf = (float)k;
+    const float p = kf * pt.S_hi;
+    const float e = fmaf(kf, pt.S_hi, -p);
+    const float ph = (p - rintf(p)) + fmaf(kf, pt.S_lo, e);
+    return cis_turns_sfu(ph);
+}
+
+// ---------------------------------------------------------------------------
+// forward: CTA = CHEB_GROUPS groups of CHEB_GROUP lanes; group = (pair, tile of the stage)
+// ---------------------------------------------------------------------------
+template <int LT>
+__global__ void __launch_bounds__(CHEB_THREADS) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int PCH = a.VS;                    // pairs per CTA (4, 8, 16 or 32)
+    const int TS = CHEB_GROUPS / PCH;        // tiles per stage
+    const int K = op.K;
+    const int KP = cd.k_pad;                 // table rows (multiple of 4, zero rows beyond K)
+    float* coef = reinterpret_cast<float*>(smem);                            // [KP][LT]
+    float2* acc = reinterpret_cast<float2*>(coef + KP * LT);                 // [CHEB_GROUPS][KP]
+    VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + CHEB_GROUPS * KP);  // [TILE_V]
+    float2* s_st = reinterpret_cast<float2*>(voff + TILE_V);                 // [2][TS][TILE_V]
+    AntTile* ant_st = reinterpret_cast<AntTile*>(s_st + 2 * TS * TILE_V);    // [2][CHEB_GROUPS][2]
+    int* pair_s = reinterpret_cast<int*>(ant_st + 2 * CHEB_GROUPS * 2);      // [PCH]
+
+    const int tid = threadIdx.x;
+    const int g = tid / CHEB_GROUP, ln = tid % CHEB_GROUP;
+    const int pl = g % PCH, slot = g / PCH;
+    const unsigned gmask = 0xFu << ((tid % 32) & ~(CHEB_GROUP - 1));
+    const int pair_base = blockIdx.x * PCH;
+    const int chunk = blockIdx.y;
+    const int t_begin = chunk * a.tiles_base + min(chunk, a.tiles_rem);
+    const int t_end = t_begin + a.tiles_base + (chunk < a.tiles_rem ? 1 : 0);
+    const int n_stages = (t_end - t_begin + TS - 1) / TS;
+
+    for (int i = tid; i < KP * LT / 4; i += CHEB_THREADS)
+        reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
+    for (int i = tid; i < CHEB_GROUPS * KP; i += CHEB_THREADS) acc[i] = make_float2(0.f, 0.f);
+    for (int v = tid; v < TILE_V; v += CHEB_THREADS)
+        voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
+    pdl_wait();                              // s and pairs may come from the previous kernel
+    if (tid < PCH) {
+        const int sp = pair_base + tid;
+        pair_s[tid] = sp < a.n_pairs ? a.pairs[sp] : -1;
+    }
+    __syncthreads();
+
+    auto load_stage = [&](int q) {
+        const int buf = q & 1;
+        for (int i = tid; i < TS * TILE_V; i += CHEB_THREADS) {
+            const int sl = i / TILE_V, v = i % TILE_V;
+            const int tile = t_begin + q * TS + sl;
+            bool in = false;
+            const float2* src = a.s;
+            if (tile < t_end) {
+                int tx, ty, tz;
+                tile_coords(op.g, tile, tx, ty, tz);
+                const int ix = tx * TILE_X + v % TILE_X, iy = ty * TILE_Y + (v / TILE_X) % TILE_Y,
+                          iz = tz * TILE_Z + v / (TILE_X * TILE_Y);
+                in = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
+                if (in) src = a.s + ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
+            }
+            cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, src, in);
+        }
+        for (int i = tid; i < CHEB_GROUPS * 6; i += CHEB_THREADS) {   // 2 rows x 48 B per group
+            const int gi = i / 6, part = i % 6;
+            const int tile = t_begin + q * TS + gi / PCH;
+            const int pair = pair_s[gi % PCH];
+            if (tile < t_end && pair >= 0) {
+                const AntTile *at, *ar;
+                pair_rows(op, pair, tile, at, ar);
+                AntTile* dst = ant_st + (buf * CHEB_GROUPS + gi) * 2 + (part < 3 ? 0 : 1);
+                cp_async_16(reinterpret_cast<float4*>(dst) + part % 3,
+                            reinterpret_cast<const float4*>(part < 3 ? at : ar) + part % 3);
+            }
+        }
+        cp_async_commit();
+    };
+
+    if (n_stages > 0) {
+        load_stage(0);
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    for (int q = 0; q < n_stages; ++q) {
+        if (q + 1 < n_stages) load_stage(q + 1);
+        const int buf = q & 1;
+        const int tile = t_begin + q * TS + slot;
+        if (tile < t_end && pair_s[pl] >= 0) {      // uniform over the group's lanes
+            const AntTile* ap = ant_st + (buf * CHEB_GROUPS + g) * 2;
+            const PairTile P = fold_pair_tile(ap[0], ap[1]);
+            const float2* sb = s_st + (buf * TS + slot) * TILE_V;
+            float mr[LT], mi[LT];
+#pragma unroll
+            for (int l = 0; l < LT; ++l) mr[l] = mi[l] = 0.f;
+#pragma unroll 2
+            for (int i = 0; i < TILE_V / CHEB_GROUP; ++i) {
+                const int v = ln + CHEB_GROUP * i;
+                const float2 sv = sb[v];
+                const ChebVoxel cv = cheb_voxel(P, voff[v], op.ph);
+                const float2 c0 = cis_turns_sfu(cv.th0);
+                const float2 u = cmul_conj(make_float2(cv.amp * sv.x, cv.amp * sv.y), c0);
+                const float t = cv.delta * cd.tau;
+                const float t2 = t + t;
+                mr[0] += u.x;
+                mi[0] += u.y;
+                mr[1] = fmaf(u.x, t, mr[1]);
+                mi[1] = fmaf(u.y, t, mi[1]);
+                float Tp = 1.f, Tc = t;
+#pragma unroll
+                for (int l = 2; l < LT; ++l) {
+                    const float Tn = fmaf(t2, Tc, -Tp);
+                    mr[l] = fmaf(u.x, Tn, mr[l]);
+                    mi[l] = fmaf(u.y, Tn, mi[l]);
+                    Tp = Tc;
+                    Tc = Tn;
+                }
+            }
+            // all-reduce over the group's lanes (the same sum order in every lane)
+#pragma unroll
+            for (int l = 0; l < LT; ++l) {
+                mr[l] += __shfl_xor_sync(gmask, mr[l], 1);
+                mi[l] += __shfl_xor_sync(gmask, mi[l], 1);
+                mr[l] += __shfl_xor_sync(gmask, mr[l], 2);
+                mi[l] += __shfl_xor_sync(gmask, mi[l], 2);
+            }
+            // expansion: lane ln owns k = ln + 4 j; (-j)^l applied by permuting re/im
+            float2* accg = acc + g * KP;
+            for (int k0 = ln; k0 < K; k0 += 2 * CHEB_GROUP) {
+                const int k1 = k0 + CHEB_GROUP;          // may be >= K: zero table row, not stored
+                const float* b0 = coef + k0 * LT;
+                const float* b1 = coef + min(k1, KP - 1) * LT;
+                float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
+#pragma unroll
+                for (int l = 0; l < LT; l += 4) {
+                    const float4 x = *reinterpret_cast<const float4*>(b0 + l);
+                    const float4 y = *reinterpret_cast<const float4*>(b1 + l);
+                    sr0 = fmaf(x.x, mr[l], sr0);
+                    si0 = fmaf(x.x, mi[l], si0);
+                    sr1 = fmaf(y.x, mr[l], sr1);
+                    si1 = fmaf(y.x, mi[l], si1);
+                    sr0 = fmaf(x.y, mi[l + 1], sr0);
+                    si0 = fmaf(-x.y, mr[l + 1], si0);
+                    sr1 = fmaf(y.y, mi[l + 1], sr1);
+                    si1 = fmaf(-y.y, mr[l + 1], si1);
+                    sr0 = fmaf(-x.z, mr[l + 2], sr0);
+                    si0 = fmaf(-x.z, mi[l + 2], si0);
+                    sr1 = fmaf(-y.z, mr[l + 2], sr1);
+                    si1 = fmaf(-y.z, mi[l + 2], si1);
+                    sr0 = fmaf(-x.w, mi[l + 3], sr0);
+                    si0 = fmaf(x.w, mr[l + 3], si0);
+                    sr1 = fmaf(-y.w, mi[l + 3], sr1);
+                    si1 = fmaf(y.w, mr[l + 3], si1);
+                }
+                {
+                    const float2 c = tile_step_cis(P, k0);      // P_k = (c.x, -c.y)
+                    float2 av = accg[k0];
+                    av.x += fmaf(c.x, sr0, c.y * si0);
+                    av.y += fmaf(c.x, si0, -c.y * sr0);
+                    accg[k0] = av;
+                }
+                if (k1 < K) {
+                    const float2 c = tile_step_cis(P, k1);
+                    float2 av = accg[k1];
+                    av.x += fmaf(c.x, sr1, c.y * si1);
+                    av.y += fmaf(c.x, si1, -c.y * sr1);
+                    accg[k1] = av;
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    pdl_launch_dependents();
+
+    // sum the stage slots of each pair in slot order and write the chunk partial
+    for (int o = tid; o < PCH * K; o += CHEB_THREADS) {
+        const int p = o / K, k = o - (o / K) * K;
+        const int sp = pair_base + p;
+        if (sp >= a.n_pairs) continue;
+        float2 sum = acc[p * KP + k];
+        for (int sl = 1; sl < TS; ++sl) {
+            const float2 x = acc[(sl * PCH + p) * KP + k];
+            sum.x += x.x;
+            sum.y += x.y;
+        }
+        a.partial[((size_t)chunk * a.n_slots + sp) * K + k] = sum;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint: CTA = one voxel tile, thread = voxel; pairs in chunks of CHEB_ADJ_PCHUNK
+// ---------------------------------------------------------------------------
+template <int LT>
+__global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int K = op.K;
+    const int KP = cd.k_pad;
+    float* coef = reinterpret_cast<float*>(smem);                          // [KP][LT]
+    float2* rp = reinterpret_cast<float2*>(coef + KP * LT);               // [PCH][KP]
+    float2* Cs = rp + CHEB_ADJ_PCHUNK * KP;                                 // [PCH][LT]
+    PairTile* pt = reinterpret_cast<PairTile*>(Cs + CHEB_ADJ_PCHUNK * LT);  // [PCH]
+
+    const int tile = blockIdx.x;
+    const int tid = threadIdx.x;
+    int tx, ty, tz;
+    tile_coords(op.g, tile, tx, ty, tz);
+    const int lx = tid % TILE_X, ly = (tid / TILE_X) % TILE_Y, lz = tid / (TILE_X * TILE_Y);
+    const VoxelOffset o = voxel_offset(op.g, lx, ly, lz);
+    for (int i = tid; i < KP * LT / 4; i += CHEB_THREADS)
+        reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
+    constexpr int LQ = LT / 4;
+    float gr = 0.f, gi = 0.f;
+    pdl_wait();                              // r comes from the previous kernel
+
+    for (int c0 = 0; c0 < a.n_pairs; c0 += CHEB_ADJ_PCHUNK) {
+        const int nc = min(CHEB_ADJ_PCHUNK, a.n_pairs - c0);
+        __syncthreads();
+        if (tid < nc) pt[tid] = load_pair_tile(op, a.pairs[c0 + tid], tile);
+        __syncthreads();
+        // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c}
+        for (int e = tid; e < nc * K; e += CHEB_THREADS) {
+            const int j = e / K, k = e - (e / K) * K;
+            float2 v = a.r[(size_t)(c0 + j) * K + k];
+            if (op.pulse) v = cmul_conj(v, op.pulse[k]);
+            rp[j * KP + k] = cmul(v, tile_step_cis(pt[j], k));
+        }
+        __syncthreads();
+        // C_l = j^l sum_k b_l(k) r'_k, four l per task
+        for (int e = tid; e < nc * LQ; e += CHEB_THREADS) {
+            const int j = e / LQ, l = 4 * (e - (e / LQ) * LQ);
+            const float2* rj = rp + j * KP;
+            float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f, cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
+            for (int k = 0; k < K; ++k) {
+                const float2 rv = rj[k];
+                const float4 b = *reinterpret_cast<const float4*>(coef + k * LT + l);
+                cr0 = fmaf(b.x, rv.x, cr0);
+                ci0 = fmaf(b.x, rv.y, ci0);
+                cr1 = fmaf(b.y, rv.x, cr1);
+                ci1 = fmaf(b.y, rv.y, ci1);
+                cr2 = fmaf(b.z, rv.x, cr2);
+                ci2 = fmaf(b.z, rv.y, ci2);
+                cr3 = fmaf(b.w, rv.x, cr3);
+                ci3 = fmaf(b.w, rv.y, ci3);
+            }
+            float2* Cj = Cs + j * LT + l;      // l % 4 == 0: factors 1, j, -1, -j
+            Cj[0] = make_float2(cr0, ci0);
+            Cj[1] = make_float2(-ci1, cr1);
+            Cj[2] = make_float2(-cr2, -ci2);
+            Cj[3] = make_float2(ci3, -cr3);
+        }
+        __syncthreads();
+        // per voxel: sum over the chunk's pairs of conj(u') sum_l T_l(t) C_l
+        for (int j = 0; j < nc; ++j) {
+            const ChebVoxel cv = cheb_voxel(pt[j], o, op.ph);
+            const float2 c0v = cis_turns_sfu(cv.th0);
+            const float t = cv.delta * cd.tau;
+            const float t2 = t + t;
+            const float4* C = reinterpret_cast<const float4*>(Cs + j * LT);
+            float4 q = C[0];
+            float ar = fmaf(t, q.z, q.x), ai = fmaf(t, q.w, q.y);
+            float Tp = 1.f, Tc = t;
+#pragma unroll
+            for (int l = 2; l < LT; l += 2) {
+                q = C[l / 2];
+                const float Ta = fmaf(t2, Tc, -Tp);
+                const float Tb = fmaf(t2, Ta, -Tc);
+                ar = fmaf(Ta, q.x, ar);
+                ai = fmaf(Ta, q.y, ai);
+                ar = fmaf(Tb, q.z, ar);
+                ai = fmaf(Tb, q.w, ai);
+                Tp = Ta;
+                Tc = Tb;
+            }
+            const float wr = cv.amp * c0v.x, wi = cv.amp * c0v.y;
+            gr = fmaf(wr, ar, fmaf(-wi, ai, gr));
+            gi = fmaf(wr, ai, fmaf(wi, ar, gi));
+        }
+    }
+    pdl_launch_dependents();
+
+    const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
+    if (ix >= op.g.nx || iy >= op.g.ny || iz >= op.g.nz) return;
+    const size_t n = ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
+    if (a.s) {
+        const float2 sv = a.s[n];
+        const float zr = fmaf(-a.step, gr, sv.x);
+        const float zi = fmaf(-a.step, gi, sv.y);
+        const float mag = sqrtf(zr * zr + zi * zi);
+        float2 out = make_float2(0.f, 0.f);
+        if (mag > a.alpha) {
+            const float sc = (1.0f - a.alpha / mag) * a.shrink;
+            out = make_float2(zr * sc, zi * sc);
+        }
+        a.s[n] = out;
+    } else {
+        a.g_out[n] = make_float2(gr, gi);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 range of delta: max over antennas, tiles and the 128 voxel slots of each
+// tile (including slots beyond the grid edge) of | |r_a - r_v| - |r_a - r_c| |
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) cheb_range_kernel(GridDesc g, AntSetup a, unsigned long long* out)
+{
+    __shared__ double red[256];
+    double mx = 0.0;
+    const long long total = (long long)a.n_ant * g.n_tiles;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ant = (int)(i / g.n_tiles);
+        const int tile = (int)(i - (long long)ant * g.n_tiles);
+        int tx, ty, tz;
+        tile_coords(g, tile, tx, ty, tz);
+        const double ax = a.ant_xyz[3 * ant], ay = a.ant_xyz[3 * ant + 1], az = a.ant_xyz[3 * ant + 2];
+        const double cx = a.x0 + (tx * TILE_X + 0.5 * (TILE_X - 1)) * a.dx;
+        const double cy = a.y0 + (ty * TILE_Y + 0.5 * (TILE_Y - 1)) * a.dy;
+        const double cz = a.z0 + (tz * TILE_Z + 0.5 * (TILE_Z - 1)) * a.dz;
+        const double dc = sqrt((ax - cx) * (ax - cx) + (ay - cy) * (ay - cy) + (az - cz) * (az - cz));
+        for (int v = 0; v < TILE_V; ++v) {
+            const double px = a.x0 + (tx * TILE_X + v % TILE_X) * a.dx;
+            const double py = a.y0 + (ty * TILE_Y + (v / TILE_X) % TILE_Y) * a.dy;
+            const double pz = a.z0 + (tz * TILE_Z + v / (TILE_X * TILE_Y)) * a.dz;
+            const double d = sqrt((ax - px) * (ax - px) + (ay - py) * (ay - py) + (az - pz) * (az - pz));
+            mx = fmax(mx, fabs(d - dc));
+        }
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    // non-negative doubles order like their bit patterns
+    if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch)
+{
+    const int TS = CHEB_GROUPS / pch;
+    return (size_t)k_pad * LT * sizeof(float) + (size_t)CHEB_GROUPS * k_pad * sizeof(float2) +
+           TILE_V * sizeof(VoxelOffset) + (size_t)2 * TS * TILE_V * sizeof(float2) +
+           (size_t)2 * CHEB_GROUPS * 2 * sizeof(AntTile) + (size_t)pch * sizeof(int);
+}
+
+size_t adj_cheb_smem_bytes(int LT, int k_pad)
+{
+    return (size_t)k_pad * LT * sizeof(float) + (size_t)CHEB_ADJ_PCHUNK * k_pad * sizeof(float2) +
+           (size_t)CHEB_ADJ_PCHUNK * LT * sizeof(float2) + (size_t)CHEB_ADJ_PCHUNK * sizeof(PairTile);
+}
+
+const void* fwd_cheb_kernel_ptr(int LT)
+{
+    switch (LT) {
+    case 16: return (const void*)fwd_cheb_kernel<16>;
+    case 20: return (const void*)fwd_cheb_kernel<20>;
+    case 24: return (const void*)fwd_cheb_kernel<24>;
+    case 28: return (const void*)fwd_cheb_kernel<28>;
+    case 32: return (const void*)fwd_cheb_kernel<32>;
+    default: return nullptr;
+    }
+}
+
+const void* adj_cheb_kernel_ptr(int LT)
+{
+    switch (LT) {
+    case 16: return (const void*)adj_cheb_kernel<16>;
+    case 20: return (const void*)adj_cheb_kernel<20>;
+    case 24: return (const void*)adj_cheb_kernel<24>;
+    case 28: return (const void*)adj_cheb_kernel<28>;
+    case 32: return (const void*)adj_cheb_kernel<32>;
+    default: return nullptr;
+    }
+}
+
+cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, size_t smem,
+                            cudaStream_t st)
+{
+    const void* fn = fwd_cheb_kernel_ptr(cd.L);
+    if (!fn) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&op, (void*)&cd, (void*)&a};
+    return launch_pdl(fn, grid, dim3(CHEB_THREADS), smem, st, args);
+}
+
+cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, size_t smem, cudaStream_t st)
+{
+    const void* fn = adj_cheb_kernel_ptr(cd.L);
+    if (!fn) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&op, (void*)&cd, (void*)&a};
+    return launch_pdl(fn, dim3(op.g.n_tiles), dim3(CHEB_THREADS), smem, st, args);
+}
+
+cudaError_t launch_cheb_range(const GridDesc& g, const AntSetup& a, unsigned long long* out, cudaStream_t st)
+{
+    long long total = (long long)a.n_ant * g.n_tiles;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 2048) blocks = 2048;
+    cheb_range_kernel<<<blocks, 256, 0, st>>>(g, a, out);
+    return cudaGetLastError();
+}
+
+}  // namespace nfm

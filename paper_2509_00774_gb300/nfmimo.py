@@ -53,6 +53,9 @@ def load_library(path: str | None = None):
         "nfm_set_stream": (i, [vp, vp]),
         "nfm_set_geometry": (i, [vp, vp, i, vp, i, vp, i, vp, ctypes.POINTER(_Grid), d]),
         "nfm_set_precision": (i, [vp, i]),
+        "nfm_set_algorithm": (i, [vp, i]),
+        "nfm_algorithm_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]),
+        "nfm_cheb_coefficients": (i, [d, i, i, vp]),
         "nfm_set_regularizer": (i, [vp, d, d]),
         "nfm_dims": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                          ctypes.POINTER(ctypes.c_longlong)]),
@@ -85,6 +88,16 @@ def load_library(path: str | None = None):
         fn.argtypes = args
     _lib = L
     return L
+
+
+def cheb_coefficients(z_step: float, K: int, L: int):
+    """FP64 table b[k, l] = b_l(k z_step) of exp(-j z t) = sum_l (-j)^l b_l(z) T_l(t) (host only)."""
+    import numpy as np
+    out = np.zeros((int(K), int(L)), dtype=np.float64)
+    rc = load_library().nfm_cheb_coefficients(float(z_step), int(K), int(L), out.ctypes.data_as(ctypes.c_void_p))
+    if rc != NFM_OK:
+        raise NfmError(rc, "nfm_cheb_coefficients: invalid arguments")
+    return out
 
 
 def _ptr(t, dtype, name, device=None):
@@ -175,6 +188,20 @@ class Context:
     def set_precision(self, mode):
         """Adjoint arithmetic: "fp32" (CUDA cores), "tc_bf16x3" or "tc_fp16x3" (tensor cores)."""
         self._check(self._lib.nfm_set_precision(self._h, self.PRECISION[mode] if isinstance(mode, str) else int(mode)))
+
+    ALGORITHM = {"auto": 0, "direct": 1, "chebyshev": 2}
+
+    def set_algorithm(self, algo):
+        """Frequency evaluation of the FP32 operator: "auto", "direct" or "chebyshev"."""
+        self._check(self._lib.nfm_set_algorithm(self._h, self.ALGORITHM[algo] if isinstance(algo, str) else int(algo)))
+
+    def algorithm_info(self):
+        """(algorithm in use: "direct" | "chebyshev", expansion length L, z of the highest frequency)."""
+        a, n, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self._lib.nfm_algorithm_info(self._h, ctypes.byref(a), ctypes.byref(n), ctypes.byref(z)))
+        return {1: "direct", 2: "chebyshev"}[a.value], n.value, z.value
+
+    cheb_coefficients = staticmethod(cheb_coefficients)
 
     def set_regularizer(self, w1=1.0, w2=0.0):
         """R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 for every SPGM/PGM step and the objective."""

@@ -58,10 +58,18 @@ def assert_close_operator(got, want, what="", scale=None):
     return rel, worst
 
 
-def make_ctx(geom):
+# operator algorithm for make_ctx ("auto" unless a test module parametrizes it)
+ALGORITHM = "auto"
+
+
+def make_ctx(geom, algorithm=None):
     from paper_2509_00774_gb300.nfmimo import Context
     ctx = Context(0)
     ctx.set_geometry(geom)
+    algo = algorithm or ALGORITHM
+    ctx.set_algorithm(algo)
+    if algo != "auto":
+        assert ctx.algorithm_info()[0] == algo
     return ctx
 
 

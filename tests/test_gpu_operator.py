@@ -11,9 +11,18 @@ import oracle
 from oracle import Oracle
 from paper_2509_00774_gb300 import inputs as I
 from paper_2509_00774_gb300 import workloads as W
+from tests import gpu_helpers
 from tests.gpu_helpers import assert_close_operator, make_ctx, term_scale, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, params=["chebyshev", "direct"])
+def operator_algorithm(request):
+    """Every test of this module runs with both FP32 operator algorithms."""
+    gpu_helpers.ALGORITHM = request.param
+    yield request.param
+    gpu_helpers.ALGORITHM = "auto"
 
 
 def _c64(z):
