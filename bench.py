@@ -33,8 +33,17 @@ UNIT = "G pairs/s"
 # Algorithmic work per (row, voxel) element: one complex multiply-accumulate plus
 # one complex phasor step of the frequency recurrence = 8 FP32 FMA-pipe
 # lane-instructions, counted as 16 flops (an FMA-pipe instruction = 2 flops).
-FLOPS_PER_PAIR = 16.0
+FLOPS_PER_PAIR = 16.0          # direct recurrence: flops per (row, voxel) element
 FP32_LANES_PER_SM = 128
+CHEB_GEOM_OPS = 42             # expansion: FP32/SFU ops of geometry and base phase per (pair, voxel)
+
+
+def cheb_flops_per_pair_voxel(L, K):
+    """Algorithmic FP32 work of the expansion operator per (pair, voxel): L Chebyshev recurrence
+    steps with a complex-by-real accumulation (3L FMAs), the per-(pair, tile) expansion over the
+    128 voxels of a tile (2KL FMAs / 128) and the geometry (two distances, amplitude, base phase:
+    CHEB_GEOM_OPS ops), counted as 2 flops per FMA-pipe operation."""
+    return 2.0 * (3 * L + 2.0 * K * L / 128.0 + CHEB_GEOM_OPS)
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -52,6 +61,9 @@ def parse():
                     help="jitter the frequencies off the uniform grid (general-frequency kernels)")
     ap.add_argument("--study-rho", type=float, nargs="+", default=[0.3, 0.1, 0.03],
                     help="paper_like study: step sizes as eta * L")
+    ap.add_argument("--algorithm", default="auto", choices=["auto", "direct", "chebyshev"],
+                    help="FP32 operator algorithm for equally spaced frequencies")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default forward launch shape")
     ap.add_argument("--study", default=None, choices=["paper_like", "time_to_nmse"],
                     help="run a study instead of the bench line: the Sec. V PGM vs SPGM comparison on a "
                          "paper-shaped scene, or SPGM time to the oracle's NMSE (small and mid workloads)")
@@ -173,7 +185,9 @@ def build_problem(torch, ctx, w, seed_offset):
     return y, 1.0 / L, lam
 
 
-KERNEL_SOURCES = {"fwd_partial_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_forward.cu"),
+KERNEL_SOURCES = {"fwd_cheb_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_cheb.cu"),
+                  "adj_cheb_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_cheb.cu"),
+                  "fwd_partial_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_forward.cu"),
                   "adj_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_adjoint.cu"),
                   "adj_tc_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_adjoint_tc.cu")}
 
@@ -424,7 +438,10 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         ctx = Context(local, stream=stream)
         ctx.set_precision(args.precision)
+        ctx.set_algorithm(args.algorithm)
         y, eta, lam = build_problem(torch, ctx, w, seed_offset=rank)
+        algo, cheb_L, cheb_zmax = ctx.algorithm_info()
+        shape = ctx.autotune(w.pairs_per_batch) if (algo == "chebyshev" and not args.no_autotune) else None
         E = args.warmup + args.steps
         perms = np.stack([I.epoch_permutation(geom.P, w.seeds["perm"] + 1000 * rank, e) for e in range(E)])
         perms_d = torch.from_numpy(perms.astype(np.int32)).to(dev)
@@ -497,26 +514,40 @@ def run_ours(args):
     fp32_peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     kernels = {}
     elems = bp * geom.K * geom.N        # (row, voxel) pairs per forward / adjoint launch
+    cheb = algo == "chebyshev"
+    flops_per_launch = (cheb_flops_per_pair_voxel(cheb_L, geom.K) * bp * geom.N if cheb
+                        else FLOPS_PER_PAIR * elems)
     for kind, (ms, n) in prof.items():
         if n == 0:
             continue
         avg_ms = ms / n
         entry = {"launches": n, "total_ms": ms, "avg_us": avg_ms * 1e3}
-        if kind in ("forward_partial", "adjoint"):
-            tf = FLOPS_PER_PAIR * elems / (avg_ms * 1e-3) / 1e12
-            entry.update({"gpairs_per_s": elems / (avg_ms * 1e-3) / 1e9, "tflops": tf})
+        if kind in ("forward_partial", "adjoint") and not (kind == "adjoint" and cheb and args.precision != "fp32"):
+            tf = flops_per_launch / (avg_ms * 1e-3) / 1e12
+            entry.update({"gpairs_per_s": elems / (avg_ms * 1e-3) / 1e9, "tflops": tf,
+                          "direct_equivalent_tflops": FLOPS_PER_PAIR * elems / (avg_ms * 1e-3) / 1e12})
+        elif kind == "adjoint":
+            entry.update({"gpairs_per_s": elems / (avg_ms * 1e-3) / 1e9,
+                          "tflops": FLOPS_PER_PAIR * elems / (avg_ms * 1e-3) / 1e12})
         kernels[kind] = entry
     dom = max(("forward_partial", "adjoint"), key=lambda k: kernels.get(k, {}).get("total_ms", 0.0))
     dk = kernels[dom]
-    kname = {"forward_partial": "fwd_partial_kernel",
-             "adjoint": "adj_kernel" if args.precision == "fp32" else "adj_tc_kernel"}[dom]
+    kname = {"forward_partial": "fwd_cheb_kernel" if cheb else "fwd_partial_kernel",
+             "adjoint": ("adj_cheb_kernel" if cheb else "adj_kernel") if args.precision == "fp32"
+             else "adj_tc_kernel"}[dom]
+    if cheb and not (dom == "adjoint" and args.precision != "fp32"):
+        work = (f"{cheb_flops_per_pair_voxel(cheb_L, geom.K):.0f} flops per (pair, voxel) = 2 x (3L recurrence/accumulate "
+                f"FMAs + 2KL/128 expansion FMAs + {CHEB_GEOM_OPS} geometry ops), L = {cheb_L}, K = {geom.K}; "
+                f"{bp * geom.N} (pair, voxel) = {elems} (row, voxel) per launch")
+    else:
+        work = (f"{FLOPS_PER_PAIR:.0f} flops = 8 FP32 FMA-pipe lane-instructions (complex MAC + phasor step) "
+                f"per (row, voxel) pair, {elems} pairs per launch")
     roofline = {"bound": "alu", "kernel": kname, "achieved": dk["tflops"], "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": dk["tflops"] / fp32_peak_tflops,
                 "traffic": traffic_for(kname),
                 "peak_source": f"FP32 FMA lanes: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} x 2 flops x "
                                f"{sm_mhz:.0f} MHz (sm_max_mhz, {peak_src})",
-                "work": f"{FLOPS_PER_PAIR:.0f} flops = 8 FP32 FMA-pipe lane-instructions (complex MAC + phasor step) "
-                        f"per (row, voxel) pair, {elems} pairs per launch",
+                "work": work,
                 "timing": f"CUDA events around every launch over {prof_steps} epochs run right after the timed region"}
     launches = sum(kernels.get(k, {}).get("launches", 0) for k in ("forward_partial", "forward_reduce", "adjoint"))
     launches = launches * args.steps // prof_steps      # per timed region (same kernels every epoch)
@@ -526,9 +557,11 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name + ("_jittered_freqs" if args.nonuniform else ""), "T": geom.T, "R": geom.R, "K": geom.K, "N": geom.N, "M": geom.M,
                    "pairs_per_batch": bp, "minibatches_per_step": geom.P // bp, "step": "one SPGM epoch",
-                   "operator": "forward: fp32 cuda-core three-term phasor recurrence; adjoint: " +
-                               ("fp32 cuda-core Horner" if args.precision == "fp32" else
-                                f"tcgen05 {args.precision[3:]} split, FP32 accumulate in TMEM"),
+                   "operator": (f"fp32 cuda-core tile-local Chebyshev expansion, L = {cheb_L}" if cheb else
+                                "forward: fp32 cuda-core three-term phasor recurrence; adjoint: fp32 cuda-core Horner") +
+                               ("" if args.precision == "fp32" else
+                                f"; adjoint: tcgen05 {args.precision[3:]} split, FP32 accumulate in TMEM"),
+                   "forward_launch_shape": shape,
                    "l2": "256 MiB buffer written between timed steps, outside the timed events",
                    "eta": eta, "lambda": lam, "parallelism": f"replicas x{world}"},
         "roofline": roofline,
@@ -566,6 +599,7 @@ def run_batched(args):
             g = w.geom
             c = Context(0, stream=stream)
             c.set_precision(args.precision)
+            c.set_algorithm(args.algorithm)
             c.set_geometry(g)
             allp = torch.arange(g.P, dtype=torch.int32, device=dev)
             clean = c.forward(allp, torch.from_numpy(w.scene_vector().astype(np.complex64)).to(dev))
@@ -582,6 +616,8 @@ def run_batched(args):
             perm_bufs.append(torch.empty(g.P, dtype=torch.int32, device=dev))
             etas.append(1.0 / L)
             lams.append(0.05 * c.lambda_max(y))
+            if not args.no_autotune and c.algorithm_info()[0] == "chebyshev":
+                c.autotune(w.pairs_per_batch)
         bps = [w.pairs_per_batch for w in ws]
         batch = Batch(ctxs, stream=stream)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)

@@ -132,6 +132,18 @@ int nfm_set_algorithm(nfm_ctx* ctx, int algo);
  * may be NULL.  Errors: NFM_ERR_STATE without a geometry. */
 int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_max);
 
+/* Autotuner for the expansion forward (no counterpart in the paper): times
+ * the candidate launch shapes (64 or 128 threads per CTA, 4..32 pairs per
+ * CTA, one, two or four waves of tile chunks) on minibatches of n_pairs pairs
+ * of the current geometry (pairs 0..n_pairs-1, a zero scene, 3 timed launches
+ * each) and keeps the fastest for every later call with n_pairs pairs.  The
+ * shape changes the order of the FP32 partial sums, so results are
+ * reproducible for a given shape, not across shapes; contexts that are never
+ * tuned use a fixed default.  Synchronises the stream.  Writes the chosen
+ * shape (any pointer may be NULL).  Errors: NFM_ERR_ARG (n_pairs outside
+ * [1, P]), NFM_ERR_STATE (no geometry, or the expansion is not in use). */
+int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads, int* pairs_per_cta, int* chunks);
+
 /* Host-only helper (no GPU needed): the expansion coefficients
  * out[k*L + l] = b_l(k z_step), l < L, k < K, of
  *   exp(-j z t) = sum_l (-j)^l b_l(z) T_l(t)   (b_0 = J_0(z), b_l = 2 J_l(z)),

@@ -112,7 +112,9 @@ struct nfm_ctx {
     double cheb_zmax = 0.0;       // z of the highest frequency
     bool fwd_cheb_attr[CHEB_MAX_L + 1] = {};
     bool adj_cheb_attr[CHEB_MAX_L + 1] = {};
-    int fwd_cheb_occ[CHEB_MAX_L + 1][4] = {};
+    // launch shapes of the expansion forward chosen by nfm_autotune, per minibatch size
+    struct FwdShape { int n_pairs, threads, pch, chunks; };
+    std::vector<FwdShape> fwd_tuned;
 };
 
 namespace {
@@ -414,56 +416,91 @@ int enqueue_forward_general(nfm_ctx* ctx, const int* pairs, int n_pairs, const f
     return NFM_OK;
 }
 
-int enqueue_forward_cheb(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
-                         float2* out, const unsigned char* fmask)
+// Launch shape of the expansion forward: CTA size, pairs per CTA and tile chunks.
+struct ChebShape {
+    int threads, pch, n_groups, n_slots;
+    long long nch;
+    size_t smem;
+};
+
+// Default shape (threads = 128, pairs per CTA = the power of two >= n_pairs in [4, 32], about
+// `waves` CTAs per resident slot), or the one given.
+int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int pch, double waves, long long chunks, ChebShape* sh)
 {
     const int LT = ctx->cheb_L, KP = ctx->cheb_kpad;
-    int pch = 4, pci = 0;
-    while (pch < CHEB_GROUPS && pch < n_pairs) {
-        pch *= 2;
-        ++pci;
+    const int ng = threads / CHEB_GROUP;
+    if (pch <= 0) {
+        pch = 4;
+        while (pch < ng && pch < n_pairs) pch *= 2;
     }
-    const int TS = CHEB_GROUPS / pch;
-    const size_t smem = fwd_cheb_smem_bytes(LT, KP, pch);
-    if (smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "expansion forward needs %zu B shared memory", smem);
+    if (ng % pch != 0) return fail(ctx, NFM_ERR_ARG, "pairs per CTA %d does not divide %d groups", pch, ng);
+    const int TS = ng / pch;
+    sh->threads = threads;
+    sh->pch = pch;
+    sh->smem = fwd_cheb_smem_bytes(LT, KP, pch, threads);
+    if (sh->smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "expansion forward needs %zu B shared memory", sh->smem);
     const void* fn = fwd_cheb_kernel_ptr(LT);
     if (!ctx->fwd_cheb_attr[LT]) {
         NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin));
         ctx->fwd_cheb_attr[LT] = true;
     }
-    int& occ = ctx->fwd_cheb_occ[LT][pci];
-    if (occ == 0) {
-        NFM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, CHEB_THREADS, smem));
+    sh->n_groups = (n_pairs + pch - 1) / pch;
+    sh->n_slots = sh->n_groups * pch;
+    long long nch = chunks;
+    if (nch <= 0) {
+        int occ = 0;
+        NFM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, sh->smem));
         if (occ < 1) occ = 1;
+        const long long G = (long long)(waves * ctx->num_sms * occ);
+        nch = (G + sh->n_groups - 1) / sh->n_groups;
     }
-    const int n_groups = (n_pairs + pch - 1) / pch;
-    const int n_slots = n_groups * pch;
-    long long G = 2LL * ctx->num_sms * occ;         // about two waves of CTAs
-    long long nch = (G + n_groups - 1) / n_groups;
-    long long max_ch = (ctx->gd.n_tiles + TS - 1) / TS;
+    const long long max_ch = (ctx->gd.n_tiles + TS - 1) / TS;
     if (nch > max_ch) nch = max_ch;
     if (nch > 65535) nch = 65535;
     if (nch < 1) nch = 1;
-    const size_t partial_bytes = (size_t)nch * n_slots * ctx->K * sizeof(float2);
+    sh->nch = nch;
+    return NFM_OK;
+}
+
+int launch_cheb_forward_shape(nfm_ctx* ctx, const ChebShape& sh, const int* pairs, int n_pairs, const float2* s)
+{
+    const size_t partial_bytes = (size_t)sh.nch * sh.n_slots * ctx->K * sizeof(float2);
     NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, partial_bytes));
-    OpDesc op = op_desc(ctx);
-    ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, KP};
+    ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, ctx->cheb_L, ctx->cheb_kpad};
     FwdArgs a;
     a.pairs = pairs;
     a.n_pairs = n_pairs;
     a.s = s;
     a.partial = (float2*)ctx->d_partial;
-    a.n_slots = n_slots;
-    a.VS = pch;
-    a.tiles_base = (int)(ctx->gd.n_tiles / nch);
-    a.tiles_rem = (int)(ctx->gd.n_tiles % nch);
+    a.n_slots = sh.n_slots;
+    a.VS = sh.pch;
+    a.tiles_base = (int)(ctx->gd.n_tiles / sh.nch);
+    a.tiles_rem = (int)(ctx->gd.n_tiles % sh.nch);
+    NFM_CK(launch_fwd_cheb(op_desc(ctx), cd, a, dim3(sh.n_groups, (unsigned)sh.nch), sh.threads, sh.smem,
+                           ctx->stream));
+    return NFM_OK;
+}
+
+int enqueue_forward_cheb(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
+                         float2* out, const unsigned char* fmask)
+{
+    ChebShape sh;
+    bool tuned = false;
+    for (const auto& t : ctx->fwd_tuned)
+        if (t.n_pairs == n_pairs) {
+            NFM_TRY(cheb_shape(ctx, n_pairs, t.threads, t.pch, 0.0, t.chunks, &sh));
+            tuned = true;
+            break;
+        }
+    if (!tuned) NFM_TRY(cheb_shape(ctx, n_pairs, CHEB_THREADS, 0, 2.0, 0, &sh));
     const int e0 = prof_mark(ctx);
-    NFM_CK(launch_fwd_cheb(op, cd, a, dim3(n_groups, (unsigned)nch), smem, ctx->stream));
+    NFM_TRY(launch_cheb_forward_shape(ctx, sh, pairs, n_pairs, s));
     const int e1 = prof_mark(ctx);
+    OpDesc op = op_desc(ctx);
     ReduceArgs ra;
     ra.partial = (const float2*)ctx->d_partial;
-    ra.n_chunks = (int)nch;
-    ra.n_slots = n_slots;
+    ra.n_chunks = (int)sh.nch;
+    ra.n_slots = sh.n_slots;
     ra.n_out = n_pairs * ctx->K;
     ra.pairs = pairs;
     ra.y_obs = y_obs;
@@ -775,6 +812,7 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     free_ptr(ctx->d_cheb);
     ctx->d_cheb = nullptr;
     ctx->cheb_L = 0;
+    ctx->fwd_tuned.clear();
     ctx->d_antk = nullptr;
     ctx->d_fkc = nullptr;
     ctx->d_ant = nullptr;
@@ -921,6 +959,69 @@ int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_m
     if (algo_in_use) *algo_in_use = cheb ? NFM_ALGO_CHEBYSHEV : NFM_ALGO_DIRECT;
     if (n_terms) *n_terms = ctx->cheb_L;
     if (z_max) *z_max = ctx->cheb_zmax;
+    return NFM_OK;
+}
+
+int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads_out, int* pairs_per_cta_out, int* chunks_out)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (n_pairs < 1 || n_pairs > ctx->P) return fail(ctx, NFM_ERR_ARG, "n_pairs = %d outside [1, P]", n_pairs);
+    bool cheb = false;
+    NFM_TRY(use_cheb(ctx, cheb));
+    if (!cheb) return fail(ctx, NFM_ERR_STATE, "the autotuner covers the expansion forward only");
+    for (size_t i = 0; i < ctx->fwd_tuned.size(); ++i)
+        if (ctx->fwd_tuned[i].n_pairs == n_pairs) {
+            ctx->fwd_tuned.erase(ctx->fwd_tuned.begin() + i);
+            break;
+        }
+    NFM_TRY(ensure(ctx, &ctx->d_v, &ctx->v_cap, (size_t)ctx->N * sizeof(float2)));
+    NFM_CK(cudaMemsetAsync(ctx->d_v, 0, (size_t)ctx->N * sizeof(float2), ctx->stream));
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    cudaEvent_t e0, e1;
+    NFM_CK(cudaEventCreate(&e0));
+    NFM_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    ChebShape best_sh{};
+    const double waves[3] = {1.0, 2.0, 4.0};
+    int rc = NFM_OK;
+    for (int threads : {64, 128}) {
+        const int ng = threads / CHEB_GROUP;
+        for (int pch = 4; pch <= ng && rc == NFM_OK; pch *= 2) {
+            if (pch / 2 >= n_pairs && pch > 4) break;        // all groups beyond the pairs would idle
+            for (double w : waves) {
+                ChebShape sh;
+                rc = cheb_shape(ctx, n_pairs, threads, pch, w, 0, &sh);
+                if (rc != NFM_OK) break;
+                rc = launch_cheb_forward_shape(ctx, sh, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v);
+                if (rc != NFM_OK) break;
+                if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = NFM_ERR_CUDA; break; }
+                for (int r = 0; r < 3 && rc == NFM_OK; ++r)
+                    rc = launch_cheb_forward_shape(ctx, sh, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v);
+                if (rc != NFM_OK) break;
+                float ms = 0.f;
+                if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    rc = fail(ctx, NFM_ERR_CUDA, "autotuner timing failed");
+                    break;
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_sh = sh;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->prof = prof;
+    NFM_TRY(rc);
+    NFM_TRY(check_flags(ctx));
+    ctx->fwd_tuned.push_back({n_pairs, best_sh.threads, best_sh.pch, (int)best_sh.nch});
+    if (threads_out) *threads_out = best_sh.threads;
+    if (pairs_per_cta_out) *pairs_per_cta_out = best_sh.pch;
+    if (chunks_out) *chunks_out = (int)best_sh.nch;
     return NFM_OK;
 }
 

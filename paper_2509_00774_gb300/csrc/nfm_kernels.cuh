@@ -73,12 +73,13 @@ struct ChebDesc {
     int L;                   // expansion terms (16, 20, 24, 28 or 32)
     int k_pad;               // K rounded up to a multiple of 4
 };
-size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch);
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads);
 size_t adj_cheb_smem_bytes(int LT, int k_pad);
 const void* fwd_cheb_kernel_ptr(int LT);
 const void* adj_cheb_kernel_ptr(int LT);
-cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, size_t smem,
-                            cudaStream_t st);
+// threads: 64 or 128 (16 or 32 groups); a.VS = pairs per CTA, a power of two dividing threads / 4
+cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
+                            size_t smem, cudaStream_t st);
 cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, size_t smem, cudaStream_t st);
 
 constexpr int FWD_PC = 8;         // pairs per forward CTA

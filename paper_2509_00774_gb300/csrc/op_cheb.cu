@@ -59,22 +59,25 @@ __device__ __forceinline__ float2 tile_step_cis(const PairTile& pt, int k)
 }
 
 // ---------------------------------------------------------------------------
-// forward: CTA = CHEB_GROUPS groups of CHEB_GROUP lanes; group = (pair, tile of the stage)
+// forward: CTA = ng = blockDim.x / CHEB_GROUP groups of CHEB_GROUP lanes; group = (pair, tile of
+// the stage); PCH pairs per CTA and TS = ng / PCH tiles per stage
 // ---------------------------------------------------------------------------
 template <int LT>
-__global__ void __launch_bounds__(CHEB_THREADS) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
+__global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int PCH = a.VS;                    // pairs per CTA (4, 8, 16 or 32)
-    const int TS = CHEB_GROUPS / PCH;        // tiles per stage
+    const int ng = blockDim.x / CHEB_GROUP;  // groups per CTA (16 or 32)
+    const int PCH = a.VS;                    // pairs per CTA (4 ... ng, power of two)
+    const int TS = ng / PCH;                 // tiles per stage
     const int K = op.K;
     const int KP = cd.k_pad;                 // table rows (multiple of 4, zero rows beyond K)
+    const int AS = KP + 4;                   // accumulator row stride (float2): 8 groups x 4 lanes on distinct banks
     float* coef = reinterpret_cast<float*>(smem);                            // [KP][LT]
-    float2* acc = reinterpret_cast<float2*>(coef + KP * LT);                 // [CHEB_GROUPS][KP]
-    VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + CHEB_GROUPS * KP);  // [TILE_V]
+    float2* acc = reinterpret_cast<float2*>(coef + KP * LT);                 // [ng][AS]
+    VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + ng * AS);       // [TILE_V]
     float2* s_st = reinterpret_cast<float2*>(voff + TILE_V);                 // [2][TS][TILE_V]
-    AntTile* ant_st = reinterpret_cast<AntTile*>(s_st + 2 * TS * TILE_V);    // [2][CHEB_GROUPS][2]
-    int* pair_s = reinterpret_cast<int*>(ant_st + 2 * CHEB_GROUPS * 2);      // [PCH]
+    AntTile* ant_st = reinterpret_cast<AntTile*>(s_st + 2 * TS * TILE_V);    // [2][ng][2]
+    int* pair_s = reinterpret_cast<int*>(ant_st + 2 * ng * 2);               // [PCH]
 
     const int tid = threadIdx.x;
     const int g = tid / CHEB_GROUP, ln = tid % CHEB_GROUP;
@@ -86,10 +89,11 @@ __global__ void __launch_bounds__(CHEB_THREADS) fwd_cheb_kernel(OpDesc op, ChebD
     const int t_end = t_begin + a.tiles_base + (chunk < a.tiles_rem ? 1 : 0);
     const int n_stages = (t_end - t_begin + TS - 1) / TS;
 
-    for (int i = tid; i < KP * LT / 4; i += CHEB_THREADS)
+    const int nt = blockDim.x;
+    for (int i = tid; i < KP * LT / 4; i += nt)
         reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
-    for (int i = tid; i < CHEB_GROUPS * KP; i += CHEB_THREADS) acc[i] = make_float2(0.f, 0.f);
-    for (int v = tid; v < TILE_V; v += CHEB_THREADS)
+    for (int i = tid; i < ng * AS; i += nt) acc[i] = make_float2(0.f, 0.f);
+    for (int v = tid; v < TILE_V; v += nt)
         voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
     pdl_wait();                              // s and pairs may come from the previous kernel
     if (tid < PCH) {
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(CHEB_THREADS) fwd_cheb_kernel(OpDesc op, ChebD
 
     auto load_stage = [&](int q) {
         const int buf = q & 1;
-        for (int i = tid; i < TS * TILE_V; i += CHEB_THREADS) {
+        for (int i = tid; i < TS * TILE_V; i += nt) {
             const int sl = i / TILE_V, v = i % TILE_V;
             const int tile = t_begin + q * TS + sl;
             bool in = false;
@@ -115,14 +119,14 @@ __global__ void __launch_bounds__(CHEB_THREADS) fwd_cheb_kernel(OpDesc op, ChebD
             }
             cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, src, in);
         }
-        for (int i = tid; i < CHEB_GROUPS * 6; i += CHEB_THREADS) {   // 2 rows x 48 B per group
+        for (int i = tid; i < ng * 6; i += nt) {   // 2 rows x 48 B per group
             const int gi = i / 6, part = i % 6;
             const int tile = t_begin + q * TS + gi / PCH;
             const int pair = pair_s[gi % PCH];
             if (tile < t_end && pair >= 0) {
                 const AntTile *at, *ar;
                 pair_rows(op, pair, tile, at, ar);
-                AntTile* dst = ant_st + (buf * CHEB_GROUPS + gi) * 2 + (part < 3 ? 0 : 1);
+                AntTile* dst = ant_st + (buf * ng + gi) * 2 + (part < 3 ? 0 : 1);
                 cp_async_16(reinterpret_cast<float4*>(dst) + part % 3,
                             reinterpret_cast<const float4*>(part < 3 ? at : ar) + part % 3);
             }
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(CHEB_THREADS) fwd_cheb_kernel(OpDesc op, ChebD
         const int buf = q & 1;
         const int tile = t_begin + q * TS + slot;
         if (tile < t_end && pair_s[pl] >= 0) {      // uniform over the group's lanes
-            const AntTile* ap = ant_st + (buf * CHEB_GROUPS + g) * 2;
+            const AntTile* ap = ant_st + (buf * ng + g) * 2;
             const PairTile P = fold_pair_tile(ap[0], ap[1]);
             const float2* sb = s_st + (buf * TS + slot) * TILE_V;
             float mr[LT], mi[LT];
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(CHEB_THREADS) fwd_cheb_kernel(OpDesc op, ChebD
                 mi[l] += __shfl_xor_sync(gmask, mi[l], 2);
             }
             // expansion: lane ln owns k = ln + 4 j; (-j)^l applied by permuting re/im
-            float2* accg = acc + g * KP;
+            float2* accg = acc + g * AS;
             for (int k0 = ln; k0 < K; k0 += 2 * CHEB_GROUP) {
                 const int k1 = k0 + CHEB_GROUP;          // may be >= K: zero table row, not stored
                 const float* b0 = coef + k0 * LT;
@@ -227,13 +231,13 @@ __global__ void __launch_bounds__(CHEB_THREADS) fwd_cheb_kernel(OpDesc op, ChebD
     pdl_launch_dependents();
 
     // sum the stage slots of each pair in slot order and write the chunk partial
-    for (int o = tid; o < PCH * K; o += CHEB_THREADS) {
+    for (int o = tid; o < PCH * K; o += nt) {
         const int p = o / K, k = o - (o / K) * K;
         const int sp = pair_base + p;
         if (sp >= a.n_pairs) continue;
-        float2 sum = acc[p * KP + k];
+        float2 sum = acc[p * AS + k];
         for (int sl = 1; sl < TS; ++sl) {
-            const float2 x = acc[(sl * PCH + p) * KP + k];
+            const float2 x = acc[(sl * PCH + p) * AS + k];
             sum.x += x.x;
             sum.y += x.y;
         }
@@ -251,8 +255,9 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
     const int K = op.K;
     const int KP = cd.k_pad;
     float* coef = reinterpret_cast<float*>(smem);                          // [KP][LT]
-    float2* rp = reinterpret_cast<float2*>(coef + KP * LT);               // [PCH][KP]
-    float2* Cs = rp + CHEB_ADJ_PCHUNK * KP;                                 // [PCH][LT]
+    const int RS = KP + 2;                   // r' row stride (float2), staggers the banks
+    float2* rp = reinterpret_cast<float2*>(coef + KP * LT);               // [PCH][RS]
+    float2* Cs = rp + CHEB_ADJ_PCHUNK * RS;                                 // [PCH][LT]
     PairTile* pt = reinterpret_cast<PairTile*>(Cs + CHEB_ADJ_PCHUNK * LT);  // [PCH]
 
     const int tile = blockIdx.x;
@@ -277,13 +282,13 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
             const int j = e / K, k = e - (e / K) * K;
             float2 v = a.r[(size_t)(c0 + j) * K + k];
             if (op.pulse) v = cmul_conj(v, op.pulse[k]);
-            rp[j * KP + k] = cmul(v, tile_step_cis(pt[j], k));
+            rp[j * RS + k] = cmul(v, tile_step_cis(pt[j], k));
         }
         __syncthreads();
         // C_l = j^l sum_k b_l(k) r'_k, four l per task
         for (int e = tid; e < nc * LQ; e += CHEB_THREADS) {
             const int j = e / LQ, l = 4 * (e - (e / LQ) * LQ);
-            const float2* rj = rp + j * KP;
+            const float2* rj = rp + j * RS;
             float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f, cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
             for (int k = 0; k < K; ++k) {
                 const float2 rv = rj[k];
@@ -393,17 +398,18 @@ __global__ void __launch_bounds__(256) cheb_range_kernel(GridDesc g, AntSetup a,
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch)
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads)
 {
-    const int TS = CHEB_GROUPS / pch;
-    return (size_t)k_pad * LT * sizeof(float) + (size_t)CHEB_GROUPS * k_pad * sizeof(float2) +
+    const int ng = threads / CHEB_GROUP;
+    const int TS = ng / pch;
+    return (size_t)k_pad * LT * sizeof(float) + (size_t)ng * (k_pad + 4) * sizeof(float2) +
            TILE_V * sizeof(VoxelOffset) + (size_t)2 * TS * TILE_V * sizeof(float2) +
-           (size_t)2 * CHEB_GROUPS * 2 * sizeof(AntTile) + (size_t)pch * sizeof(int);
+           (size_t)2 * ng * 2 * sizeof(AntTile) + (size_t)pch * sizeof(int);
 }
 
 size_t adj_cheb_smem_bytes(int LT, int k_pad)
 {
-    return (size_t)k_pad * LT * sizeof(float) + (size_t)CHEB_ADJ_PCHUNK * k_pad * sizeof(float2) +
+    return (size_t)k_pad * LT * sizeof(float) + (size_t)CHEB_ADJ_PCHUNK * (k_pad + 2) * sizeof(float2) +
            (size_t)CHEB_ADJ_PCHUNK * LT * sizeof(float2) + (size_t)CHEB_ADJ_PCHUNK * sizeof(PairTile);
 }
 
@@ -431,13 +437,14 @@ const void* adj_cheb_kernel_ptr(int LT)
     }
 }
 
-cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, size_t smem,
-                            cudaStream_t st)
+cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
+                            size_t smem, cudaStream_t st)
 {
     const void* fn = fwd_cheb_kernel_ptr(cd.L);
-    if (!fn) return cudaErrorInvalidValue;
+    if (!fn || (threads != 64 && threads != 128)) return cudaErrorInvalidValue;
+    if (a.VS < 1 || (threads / CHEB_GROUP) % a.VS != 0) return cudaErrorInvalidValue;
     void* args[] = {(void*)&op, (void*)&cd, (void*)&a};
-    return launch_pdl(fn, grid, dim3(CHEB_THREADS), smem, st, args);
+    return launch_pdl(fn, grid, dim3(threads), smem, st, args);
 }
 
 cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, size_t smem, cudaStream_t st)

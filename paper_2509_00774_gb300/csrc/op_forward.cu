@@ -289,17 +289,20 @@ cudaError_t launch_fwd_partial(const OpDesc& op, const FwdArgs& a, dim3 grid, in
 
 // Sum the chunk partials in chunk order (fixed), apply p(f_k), and optionally
 // subtract the observed rows: out[slot*K + k] = p_k sum_c partial[c][slot][k] - y[pair*K + k].
-__global__ void __launch_bounds__(1024) fwd_reduce_kernel(OpDesc op, ReduceArgs a)
+// CTA = RED_OUT outputs x 32 chunk lanes; lane y sums chunks y, y+32, ... in that
+// order, then the 32 lane sums are added in lane order.
+constexpr int RED_OUT = 4;
+__global__ void __launch_bounds__(RED_OUT * 32) fwd_reduce_kernel(OpDesc op, ReduceArgs a)
 {
     constexpr int UN = 8;                 // loads in flight per thread
-    __shared__ float2 red[32][33];
-    const int o = blockIdx.x * 32 + threadIdx.x;
+    __shared__ float2 red[32][RED_OUT + 1];
+    const int ox = threadIdx.x % RED_OUT, cy = threadIdx.x / RED_OUT;
+    const int o = blockIdx.x * RED_OUT + ox;
     const size_t stride = (size_t)a.n_slots * op.K;
     pdl_wait();
     float2 s = make_float2(0.f, 0.f);
     if (o < a.n_out) {
-        // chunk lane y sums chunks y, y+32, ... in that order
-        for (int c0 = threadIdx.y; c0 < a.n_chunks; c0 += 32 * UN) {
+        for (int c0 = cy; c0 < a.n_chunks; c0 += 32 * UN) {
             float2 x[UN];
 #pragma unroll
             for (int u = 0; u < UN; ++u) {
@@ -313,16 +316,16 @@ __global__ void __launch_bounds__(1024) fwd_reduce_kernel(OpDesc op, ReduceArgs 
             }
         }
     }
-    red[threadIdx.y][threadIdx.x] = s;
+    red[cy][ox] = s;
     __syncthreads();
-    if (threadIdx.y == 0 && o < a.n_out) {
-        float2 t = red[0][threadIdx.x];
+    if (cy == 0 && o < a.n_out) {
+        float2 t = red[0][ox];
 #pragma unroll
         for (int y = 1; y < 32; ++y) {
-            t.x += red[y][threadIdx.x].x;
-            t.y += red[y][threadIdx.x].y;
+            t.x += red[y][ox].x;
+            t.y += red[y][ox].y;
         }
-        int k = o % op.K;
+        const int k = o % op.K;
         if (op.pulse) t = cmul(op.pulse[k], t);
         if (a.y_obs) {
             int pair = a.pairs[o / op.K];
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(1024) fwd_reduce_kernel(OpDesc op, ReduceArgs 
                 atomicOr(op.err, ERRF_PAIR);
                 pair = 0;
             }
-            float2 yo = a.y_obs[(size_t)pair * op.K + k];
+            const float2 yo = a.y_obs[(size_t)pair * op.K + k];
             t.x -= yo.x;
             t.y -= yo.y;
             if (a.fmask && !a.fmask[k]) t = make_float2(0.f, 0.f);
@@ -342,10 +345,9 @@ __global__ void __launch_bounds__(1024) fwd_reduce_kernel(OpDesc op, ReduceArgs 
 
 cudaError_t launch_fwd_reduce(const OpDesc& op, const ReduceArgs& a, cudaStream_t st)
 {
-    dim3 block(32, 32);
-    dim3 grid((a.n_out + 31) / 32);
+    dim3 grid((a.n_out + RED_OUT - 1) / RED_OUT);
     void* args[] = {(void*)&op, (void*)&a};
-    return launch_pdl((const void*)fwd_reduce_kernel, grid, block, 0, st, args);
+    return launch_pdl((const void*)fwd_reduce_kernel, grid, dim3(RED_OUT * 32), 0, st, args);
 }
 
 }  // namespace nfm

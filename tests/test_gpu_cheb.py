@@ -61,3 +61,25 @@ def test_spgm_small_both_algorithms(algo):
     err = nmse(to_host(s_gpu), s_orc)
     print(f"[parity] SPGM small ({algo}): NMSE {err:.2e}")
     assert err <= NMSE_TOL
+
+
+def test_autotuned_shape_keeps_parity():
+    """After nfm_autotune the forward runs with the chosen launch shape: still within the operator
+    tolerance of the oracle on sampled rows, and reproducible from call to call."""
+    from oracle import Oracle
+    from tests.gpu_helpers import assert_close_operator
+    w = W.mid_T16R16_K64_64x64x32()
+    o = Oracle(w.geom)
+    ctx = make_ctx(w.geom)
+    shape = ctx.autotune(16)
+    print(f"[cheb] autotuned shape for 16 pairs: {shape}")
+    assert shape["threads"] in (64, 128) and shape["chunks"] >= 1
+    pairs = I.epoch_permutation(w.geom.P, 6, 0)[:16]
+    s = I.complex_gaussian(w.geom.N, 61).astype(np.complex64).astype(np.complex128)
+    pd, sd = to_dev(pairs, "int32"), to_dev(s)
+    y1 = to_host(ctx.forward(pd, sd))
+    y2 = to_host(ctx.forward(pd, sd))
+    assert np.array_equal(y1, y2)
+    rows = o.rows_of_pairs(pairs)
+    idx = np.sort(np.random.default_rng(62).choice(rows.size, 64, replace=False))
+    assert_close_operator(y1[idx], o.forward(s, rows=rows[idx]), "forward (autotuned)")
