@@ -133,8 +133,9 @@ int nfm_set_algorithm(nfm_ctx* ctx, int algo);
 int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_max);
 
 /* Autotuner for the expansion forward (no counterpart in the paper): times
- * the candidate launch shapes (64 or 128 threads per CTA, 4..32 pairs per
- * CTA, one, two or four waves of tile chunks) on minibatches of n_pairs pairs
+ * the candidate launch shapes (4 or 8 lanes per (pair, tile), 64 or 128
+ * threads per CTA, 4..32 pairs per CTA, one, two or four waves of tile
+ * chunks) on minibatches of n_pairs pairs
  * of the current geometry (pairs 0..n_pairs-1, a zero scene, 3 timed launches
  * each) and keeps the fastest for every later call with n_pairs pairs.  The
  * shape changes the order of the FP32 partial sums, so results are
@@ -142,7 +143,7 @@ int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_m
  * tuned use a fixed default.  Synchronises the stream.  Writes the chosen
  * shape (any pointer may be NULL).  Errors: NFM_ERR_ARG (n_pairs outside
  * [1, P]), NFM_ERR_STATE (no geometry, or the expansion is not in use). */
-int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads, int* pairs_per_cta, int* chunks);
+int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads, int* lanes_per_group, int* pairs_per_cta, int* chunks);
 
 /* Host-only helper (no GPU needed): the expansion coefficients
  * out[k*L + l] = b_l(k z_step), l < L, k < K, of

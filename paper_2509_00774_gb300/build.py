@@ -19,6 +19,9 @@ LIB = os.path.join(HERE, "libnfmimo.so")
 SOURCES = ["nfm_api.cu", "op_forward.cu", "op_adjoint.cu", "op_adjoint_tc.cu", "op_misc.cu", "op_prox.cu", "op_general.cu",
            "op_cheb.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# per-file extra flags: the expansion kernels handle no subnormal values (distances, unit phasors,
+# Chebyshev values in [-1, 1]); flushing them lets rsqrt / reciprocal skip their subnormal paths
+FILE_FLAGS = {"op_cheb.cu": ["-ftz=true"]}
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
@@ -52,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc()] + ARCH + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc()] + ARCH + flags + FILE_FLAGS.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

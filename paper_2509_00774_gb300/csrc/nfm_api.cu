@@ -110,10 +110,10 @@ struct nfm_ctx {
     int cheb_kpad = 0;
     float cheb_tau = 0.f;         // t = tau * delta
     double cheb_zmax = 0.0;       // z of the highest frequency
-    bool fwd_cheb_attr[CHEB_MAX_L + 1] = {};
+    bool fwd_cheb_attr[CHEB_MAX_L + 1][2] = {};
     bool adj_cheb_attr[CHEB_MAX_L + 1] = {};
     // launch shapes of the expansion forward chosen by nfm_autotune, per minibatch size
-    struct FwdShape { int n_pairs, threads, pch, chunks; };
+    struct FwdShape { int n_pairs, threads, group, pch, chunks; };
     std::vector<FwdShape> fwd_tuned;
 };
 
@@ -418,17 +418,18 @@ int enqueue_forward_general(nfm_ctx* ctx, const int* pairs, int n_pairs, const f
 
 // Launch shape of the expansion forward: CTA size, pairs per CTA and tile chunks.
 struct ChebShape {
-    int threads, pch, n_groups, n_slots;
+    int threads, group, pch, n_groups, n_slots;
     long long nch;
     size_t smem;
 };
 
-// Default shape (threads = 128, pairs per CTA = the power of two >= n_pairs in [4, 32], about
-// `waves` CTAs per resident slot), or the one given.
-int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int pch, double waves, long long chunks, ChebShape* sh)
+// Default shape (threads = 128, 4 lanes per (pair, tile), pairs per CTA = the power of two >=
+// n_pairs in [4, 32], about `waves` CTAs per resident slot), or the one given.
+int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int group, int pch, double waves, long long chunks,
+               ChebShape* sh)
 {
     const int LT = ctx->cheb_L, KP = ctx->cheb_kpad;
-    const int ng = threads / CHEB_GROUP;
+    const int ng = threads / group;
     if (pch <= 0) {
         pch = 4;
         while (pch < ng && pch < n_pairs) pch *= 2;
@@ -436,13 +437,15 @@ int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int pch, double waves, lo
     if (ng % pch != 0) return fail(ctx, NFM_ERR_ARG, "pairs per CTA %d does not divide %d groups", pch, ng);
     const int TS = ng / pch;
     sh->threads = threads;
+    sh->group = group;
     sh->pch = pch;
-    sh->smem = fwd_cheb_smem_bytes(LT, KP, pch, threads);
+    sh->smem = fwd_cheb_smem_bytes(LT, KP, pch, threads, group);
     if (sh->smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "expansion forward needs %zu B shared memory", sh->smem);
-    const void* fn = fwd_cheb_kernel_ptr(LT);
-    if (!ctx->fwd_cheb_attr[LT]) {
+    const void* fn = fwd_cheb_kernel_ptr(LT, group);
+    if (!fn) return fail(ctx, NFM_ERR_ARG, "no expansion forward for L = %d, group %d", LT, group);
+    if (!ctx->fwd_cheb_attr[LT][group == 8]) {
         NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin));
-        ctx->fwd_cheb_attr[LT] = true;
+        ctx->fwd_cheb_attr[LT][group == 8] = true;
     }
     sh->n_groups = (n_pairs + pch - 1) / pch;
     sh->n_slots = sh->n_groups * pch;
@@ -476,8 +479,8 @@ int launch_cheb_forward_shape(nfm_ctx* ctx, const ChebShape& sh, const int* pair
     a.VS = sh.pch;
     a.tiles_base = (int)(ctx->gd.n_tiles / sh.nch);
     a.tiles_rem = (int)(ctx->gd.n_tiles % sh.nch);
-    NFM_CK(launch_fwd_cheb(op_desc(ctx), cd, a, dim3(sh.n_groups, (unsigned)sh.nch), sh.threads, sh.smem,
-                           ctx->stream));
+    NFM_CK(launch_fwd_cheb(op_desc(ctx), cd, a, dim3(sh.n_groups, (unsigned)sh.nch), sh.threads, sh.group,
+                           sh.smem, ctx->stream));
     return NFM_OK;
 }
 
@@ -488,11 +491,11 @@ int enqueue_forward_cheb(nfm_ctx* ctx, const int* pairs, int n_pairs, const floa
     bool tuned = false;
     for (const auto& t : ctx->fwd_tuned)
         if (t.n_pairs == n_pairs) {
-            NFM_TRY(cheb_shape(ctx, n_pairs, t.threads, t.pch, 0.0, t.chunks, &sh));
+            NFM_TRY(cheb_shape(ctx, n_pairs, t.threads, t.group, t.pch, 0.0, t.chunks, &sh));
             tuned = true;
             break;
         }
-    if (!tuned) NFM_TRY(cheb_shape(ctx, n_pairs, CHEB_THREADS, 0, 2.0, 0, &sh));
+    if (!tuned) NFM_TRY(cheb_shape(ctx, n_pairs, CHEB_THREADS, CHEB_GROUP, 0, 2.0, 0, &sh));
     const int e0 = prof_mark(ctx);
     NFM_TRY(launch_cheb_forward_shape(ctx, sh, pairs, n_pairs, s));
     const int e1 = prof_mark(ctx);
@@ -962,7 +965,8 @@ int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_m
     return NFM_OK;
 }
 
-int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads_out, int* pairs_per_cta_out, int* chunks_out)
+int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads_out, int* group_out, int* pairs_per_cta_out,
+                 int* chunks_out)
 {
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
@@ -986,29 +990,34 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads_out, int* pairs_per_cta
     ChebShape best_sh{};
     const double waves[3] = {1.0, 2.0, 4.0};
     int rc = NFM_OK;
-    for (int threads : {64, 128}) {
-        const int ng = threads / CHEB_GROUP;
-        for (int pch = 4; pch <= ng && rc == NFM_OK; pch *= 2) {
-            if (pch / 2 >= n_pairs && pch > 4) break;        // all groups beyond the pairs would idle
-            for (double w : waves) {
-                ChebShape sh;
-                rc = cheb_shape(ctx, n_pairs, threads, pch, w, 0, &sh);
-                if (rc != NFM_OK) break;
-                rc = launch_cheb_forward_shape(ctx, sh, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v);
-                if (rc != NFM_OK) break;
-                if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) { rc = NFM_ERR_CUDA; break; }
-                for (int r = 0; r < 3 && rc == NFM_OK; ++r)
+    for (int group : {4, 8}) {
+        for (int threads : {64, 128}) {
+            const int ng = threads / group;
+            for (int pch = 4; pch <= ng && rc == NFM_OK; pch *= 2) {
+                if (pch / 2 >= n_pairs && pch > 4) break;        // all groups beyond the pairs would idle
+                for (double w : waves) {
+                    ChebShape sh;
+                    rc = cheb_shape(ctx, n_pairs, threads, group, pch, w, 0, &sh);
+                    if (rc != NFM_OK) break;
                     rc = launch_cheb_forward_shape(ctx, sh, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v);
-                if (rc != NFM_OK) break;
-                float ms = 0.f;
-                if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                    rc = fail(ctx, NFM_ERR_CUDA, "autotuner timing failed");
-                    break;
-                }
-                if (ms < best) {
-                    best = ms;
-                    best_sh = sh;
+                    if (rc != NFM_OK) break;
+                    if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) {
+                        rc = fail(ctx, NFM_ERR_CUDA, "autotuner event failed");
+                        break;
+                    }
+                    for (int r = 0; r < 3 && rc == NFM_OK; ++r)
+                        rc = launch_cheb_forward_shape(ctx, sh, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v);
+                    if (rc != NFM_OK) break;
+                    float ms = 0.f;
+                    if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        rc = fail(ctx, NFM_ERR_CUDA, "autotuner timing failed");
+                        break;
+                    }
+                    if (ms < best) {
+                        best = ms;
+                        best_sh = sh;
+                    }
                 }
             }
         }
@@ -1018,7 +1027,8 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads_out, int* pairs_per_cta
     ctx->prof = prof;
     NFM_TRY(rc);
     NFM_TRY(check_flags(ctx));
-    ctx->fwd_tuned.push_back({n_pairs, best_sh.threads, best_sh.pch, (int)best_sh.nch});
+    ctx->fwd_tuned.push_back({n_pairs, best_sh.threads, best_sh.group, best_sh.pch, (int)best_sh.nch});
+    if (group_out) *group_out = best_sh.group;
     if (threads_out) *threads_out = best_sh.threads;
     if (pairs_per_cta_out) *pairs_per_cta_out = best_sh.pch;
     if (chunks_out) *chunks_out = (int)best_sh.nch;

@@ -73,13 +73,14 @@ struct ChebDesc {
     int L;                   // expansion terms (16, 20, 24, 28 or 32)
     int k_pad;               // K rounded up to a multiple of 4
 };
-size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads);
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group);
 size_t adj_cheb_smem_bytes(int LT, int k_pad);
-const void* fwd_cheb_kernel_ptr(int LT);
+const void* fwd_cheb_kernel_ptr(int LT, int group);
 const void* adj_cheb_kernel_ptr(int LT);
-// threads: 64 or 128 (16 or 32 groups); a.VS = pairs per CTA, a power of two dividing threads / 4
+// threads: 64 or 128; group: 4 or 8 lanes per (pair, tile); a.VS = pairs per CTA, a power of two
+// dividing threads / group
 cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
-                            size_t smem, cudaStream_t st);
+                            int group, size_t smem, cudaStream_t st);
 cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, size_t smem, cudaStream_t st);
 
 constexpr int FWD_PC = 8;         // pairs per forward CTA

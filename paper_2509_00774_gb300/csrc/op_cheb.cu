@@ -58,20 +58,30 @@ __device__ __forceinline__ float2 tile_step_cis(const PairTile& pt, int k)
     return cis_turns_sfu(ph);
 }
 
+// The same phasor from the Taylor-series cis_turns (error ~1e-7), for a step that a recurrence repeats.
+__device__ __forceinline__ float2 tile_step_cis_exact(const PairTile& pt, int k)
+{
+    const float kf = (float)k;
+    const float p = kf * pt.S_hi;
+    const float e = fmaf(kf, pt.S_hi, -p);
+    const float ph = (p - rintf(p)) + fmaf(kf, pt.S_lo, e);
+    return cis_turns(ph);
+}
+
 // ---------------------------------------------------------------------------
-// forward: CTA = ng = blockDim.x / CHEB_GROUP groups of CHEB_GROUP lanes; group = (pair, tile of
-// the stage); PCH pairs per CTA and TS = ng / PCH tiles per stage
+// forward: CTA = ng = blockDim.x / G groups of G lanes (G = 4 or 8); group = (pair, tile of the
+// stage); PCH pairs per CTA and TS = ng / PCH tiles per stage
 // ---------------------------------------------------------------------------
-template <int LT>
+template <int LT, int G>
 __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int ng = blockDim.x / CHEB_GROUP;  // groups per CTA (16 or 32)
-    const int PCH = a.VS;                    // pairs per CTA (4 ... ng, power of two)
+    const int ng = blockDim.x / G;           // groups per CTA
+    const int PCH = a.VS;                    // pairs per CTA (power of two dividing ng)
     const int TS = ng / PCH;                 // tiles per stage
     const int K = op.K;
     const int KP = cd.k_pad;                 // table rows (multiple of 4, zero rows beyond K)
-    const int AS = KP + 4;                   // accumulator row stride (float2): 8 groups x 4 lanes on distinct banks
+    const int AS = KP + 4;                   // accumulator row stride (float2), staggers the banks
     float* coef = reinterpret_cast<float*>(smem);                            // [KP][LT]
     float2* acc = reinterpret_cast<float2*>(coef + KP * LT);                 // [ng][AS]
     VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + ng * AS);       // [TILE_V]
@@ -80,29 +90,45 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
     int* pair_s = reinterpret_cast<int*>(ant_st + 2 * ng * 2);               // [PCH]
 
     const int tid = threadIdx.x;
-    const int g = tid / CHEB_GROUP, ln = tid % CHEB_GROUP;
+    const int nt = blockDim.x;
+    const int g = tid / G, ln = tid % G;
     const int pl = g % PCH, slot = g / PCH;
-    const unsigned gmask = 0xFu << ((tid % 32) & ~(CHEB_GROUP - 1));
+    const unsigned gmask = ((1u << G) - 1u) << ((tid % 32) & ~(G - 1));
     const int pair_base = blockIdx.x * PCH;
     const int chunk = blockIdx.y;
     const int t_begin = chunk * a.tiles_base + min(chunk, a.tiles_rem);
     const int t_end = t_begin + a.tiles_base + (chunk < a.tiles_rem ? 1 : 0);
     const int n_stages = (t_end - t_begin + TS - 1) / TS;
 
-    const int nt = blockDim.x;
+    // Constants and the pair list: no kernel of this library writes them, so they are read
+    // before the wait on the previous kernel (which may still be running its tail).
     for (int i = tid; i < KP * LT / 4; i += nt)
         reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
     for (int i = tid; i < ng * AS; i += nt) acc[i] = make_float2(0.f, 0.f);
     for (int v = tid; v < TILE_V; v += nt)
         voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
-    pdl_wait();                              // s and pairs may come from the previous kernel
     if (tid < PCH) {
         const int sp = pair_base + tid;
         pair_s[tid] = sp < a.n_pairs ? a.pairs[sp] : -1;
     }
     __syncthreads();
 
-    auto load_stage = [&](int q) {
+    auto load_geom = [&](int q) {                 // the two antenna-tile rows of every group
+        const int buf = q & 1;
+        for (int i = tid; i < ng * 6; i += nt) {  // 2 rows x 48 B per group
+            const int gi = i / 6, part = i % 6;
+            const int tile = t_begin + q * TS + gi / PCH;
+            const int pair = pair_s[gi % PCH];
+            if (tile < t_end && pair >= 0) {
+                const AntTile *at, *ar;
+                pair_rows(op, pair, tile, at, ar);
+                AntTile* dst = ant_st + (buf * ng + gi) * 2 + (part < 3 ? 0 : 1);
+                cp_async_16(reinterpret_cast<float4*>(dst) + part % 3,
+                            reinterpret_cast<const float4*>(part < 3 ? at : ar) + part % 3);
+            }
+        }
+    };
+    auto load_s = [&](int q) {                    // the stage's scene values (zero outside the grid)
         const int buf = q & 1;
         for (int i = tid; i < TS * TILE_V; i += nt) {
             const int sl = i / TILE_V, v = i % TILE_V;
@@ -119,28 +145,22 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
             }
             cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, src, in);
         }
-        for (int i = tid; i < ng * 6; i += nt) {   // 2 rows x 48 B per group
-            const int gi = i / 6, part = i % 6;
-            const int tile = t_begin + q * TS + gi / PCH;
-            const int pair = pair_s[gi % PCH];
-            if (tile < t_end && pair >= 0) {
-                const AntTile *at, *ar;
-                pair_rows(op, pair, tile, at, ar);
-                AntTile* dst = ant_st + (buf * ng + gi) * 2 + (part < 3 ? 0 : 1);
-                cp_async_16(reinterpret_cast<float4*>(dst) + part % 3,
-                            reinterpret_cast<const float4*>(part < 3 ? at : ar) + part % 3);
-            }
-        }
-        cp_async_commit();
     };
 
+    if (n_stages > 0) load_geom(0);
+    pdl_wait();                              // s may come from the previous kernel
     if (n_stages > 0) {
-        load_stage(0);
+        load_s(0);
+        cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
     }
     for (int q = 0; q < n_stages; ++q) {
-        if (q + 1 < n_stages) load_stage(q + 1);
+        if (q + 1 < n_stages) {
+            load_geom(q + 1);
+            load_s(q + 1);
+            cp_async_commit();
+        }
         const int buf = q & 1;
         const int tile = t_begin + q * TS + slot;
         if (tile < t_end && pair_s[pl] >= 0) {      // uniform over the group's lanes
@@ -151,8 +171,8 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
 #pragma unroll
             for (int l = 0; l < LT; ++l) mr[l] = mi[l] = 0.f;
 #pragma unroll 2
-            for (int i = 0; i < TILE_V / CHEB_GROUP; ++i) {
-                const int v = ln + CHEB_GROUP * i;
+            for (int i = 0; i < TILE_V / G; ++i) {
+                const int v = ln + G * i;
                 const float2 sv = sb[v];
                 const ChebVoxel cv = cheb_voxel(P, voff[v], op.ph);
                 const float2 c0 = cis_turns_sfu(cv.th0);
@@ -175,16 +195,21 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
             }
             // all-reduce over the group's lanes (the same sum order in every lane)
 #pragma unroll
-            for (int l = 0; l < LT; ++l) {
-                mr[l] += __shfl_xor_sync(gmask, mr[l], 1);
-                mi[l] += __shfl_xor_sync(gmask, mi[l], 1);
-                mr[l] += __shfl_xor_sync(gmask, mr[l], 2);
-                mi[l] += __shfl_xor_sync(gmask, mi[l], 2);
+            for (int w = 1; w < G; w *= 2) {
+#pragma unroll
+                for (int l = 0; l < LT; ++l) {
+                    mr[l] += __shfl_xor_sync(gmask, mr[l], w);
+                    mi[l] += __shfl_xor_sync(gmask, mi[l], w);
+                }
             }
-            // expansion: lane ln owns k = ln + 4 j; (-j)^l applied by permuting re/im
+            // expansion: lane ln owns k = ln + G j; (-j)^l applied by permuting re/im.  The tile
+            // phasors P_k = e^{-j 2 pi k df D_c/c} of the lane's k advance by W = P_{2G} (Taylor
+            // phasor, error ~1e-7, at most K/(2G) steps) from directly evaluated starts.
             float2* accg = acc + g * AS;
-            for (int k0 = ln; k0 < K; k0 += 2 * CHEB_GROUP) {
-                const int k1 = k0 + CHEB_GROUP;          // may be >= K: zero table row, not stored
+            float2 c0 = tile_step_cis(P, ln), c1 = tile_step_cis(P, ln + G);
+            const float2 W = tile_step_cis_exact(P, 2 * G);
+            for (int k0 = ln; k0 < K; k0 += 2 * G) {
+                const int k1 = k0 + G;                   // may be >= K: zero table row, not stored
                 const float* b0 = coef + k0 * LT;
                 const float* b1 = coef + min(k1, KP - 1) * LT;
                 float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
@@ -209,20 +234,20 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
                     sr1 = fmaf(-y.w, mi[l + 3], sr1);
                     si1 = fmaf(y.w, mr[l + 3], si1);
                 }
-                {
-                    const float2 c = tile_step_cis(P, k0);      // P_k = (c.x, -c.y)
+                {                                        // y_k += P_k S_k, P_k = (c.x, -c.y)
                     float2 av = accg[k0];
-                    av.x += fmaf(c.x, sr0, c.y * si0);
-                    av.y += fmaf(c.x, si0, -c.y * sr0);
+                    av.x += fmaf(c0.x, sr0, c0.y * si0);
+                    av.y += fmaf(c0.x, si0, -c0.y * sr0);
                     accg[k0] = av;
                 }
                 if (k1 < K) {
-                    const float2 c = tile_step_cis(P, k1);
                     float2 av = accg[k1];
-                    av.x += fmaf(c.x, sr1, c.y * si1);
-                    av.y += fmaf(c.x, si1, -c.y * sr1);
+                    av.x += fmaf(c1.x, sr1, c1.y * si1);
+                    av.y += fmaf(c1.x, si1, -c1.y * sr1);
                     accg[k1] = av;
                 }
+                c0 = cmul(c0, W);
+                c1 = cmul(c1, W);
             }
         }
         cp_async_wait_all();
@@ -231,17 +256,18 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
     pdl_launch_dependents();
 
     // sum the stage slots of each pair in slot order and write the chunk partial
-    for (int o = tid; o < PCH * K; o += nt) {
-        const int p = o / K, k = o - (o / K) * K;
+    for (int p = 0; p < PCH; ++p) {
         const int sp = pair_base + p;
-        if (sp >= a.n_pairs) continue;
-        float2 sum = acc[p * AS + k];
-        for (int sl = 1; sl < TS; ++sl) {
-            const float2 x = acc[(sl * PCH + p) * AS + k];
-            sum.x += x.x;
-            sum.y += x.y;
+        if (sp >= a.n_pairs) break;
+        for (int k = tid; k < K; k += nt) {
+            float2 sum = acc[p * AS + k];
+            for (int sl = 1; sl < TS; ++sl) {
+                const float2 x = acc[(sl * PCH + p) * AS + k];
+                sum.x += x.x;
+                sum.y += x.y;
+            }
+            a.partial[((size_t)chunk * a.n_slots + sp) * K + k] = sum;
         }
-        a.partial[((size_t)chunk * a.n_slots + sp) * K + k] = sum;
     }
 }
 
@@ -269,20 +295,33 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
     for (int i = tid; i < KP * LT / 4; i += CHEB_THREADS)
         reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
     constexpr int LQ = LT / 4;
+    // (pair, k) items of the r' stage: threads split as (CHEB_THREADS / K) pairs x K frequencies
+    // when K <= CHEB_THREADS, else every thread strides over k of each pair
+    const bool kfit = K <= CHEB_THREADS;
+    const int j_step = kfit ? CHEB_THREADS / K : 1;
+    const int j_first = kfit ? (tid / K < j_step ? tid / K : 1 << 30) : 0;
+    const int k_first = kfit ? tid % K : tid;
+    const int k_step = kfit ? K : CHEB_THREADS;
     float gr = 0.f, gi = 0.f;
+    // the pair list and the geometry tables are never written by this library's kernels, so the
+    // first chunk's pair tiles are read before the wait on the previous kernel
+    if (tid < min(CHEB_ADJ_PCHUNK, a.n_pairs)) pt[tid] = load_pair_tile(op, a.pairs[tid], tile);
     pdl_wait();                              // r comes from the previous kernel
 
     for (int c0 = 0; c0 < a.n_pairs; c0 += CHEB_ADJ_PCHUNK) {
         const int nc = min(CHEB_ADJ_PCHUNK, a.n_pairs - c0);
-        __syncthreads();
-        if (tid < nc) pt[tid] = load_pair_tile(op, a.pairs[c0 + tid], tile);
+        if (c0 > 0) {
+            __syncthreads();
+            if (tid < nc) pt[tid] = load_pair_tile(op, a.pairs[c0 + tid], tile);
+        }
         __syncthreads();
         // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c}
-        for (int e = tid; e < nc * K; e += CHEB_THREADS) {
-            const int j = e / K, k = e - (e / K) * K;
-            float2 v = a.r[(size_t)(c0 + j) * K + k];
-            if (op.pulse) v = cmul_conj(v, op.pulse[k]);
-            rp[j * RS + k] = cmul(v, tile_step_cis(pt[j], k));
+        for (int j = j_first; j < nc; j += j_step) {
+            for (int k = k_first; k < K; k += k_step) {
+                float2 v = a.r[(size_t)(c0 + j) * K + k];
+                if (op.pulse) v = cmul_conj(v, op.pulse[k]);
+                rp[j * RS + k] = cmul(v, tile_step_cis(pt[j], k));
+            }
         }
         __syncthreads();
         // C_l = j^l sum_k b_l(k) r'_k, four l per task
@@ -309,11 +348,21 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
             Cj[3] = make_float2(ci3, -cr3);
         }
         __syncthreads();
-        // per voxel: sum over the chunk's pairs of conj(u') sum_l T_l(t) C_l
-        for (int j = 0; j < nc; ++j) {
+        // per voxel: sum over the chunk's pairs of conj(u') sum_l T_l(t) C_l; the geometry of pair
+        // j+1 is computed next to the recurrence of pair j (independent instructions)
+        auto stage_pair = [&](int j, float2& w, float& t) {
             const ChebVoxel cv = cheb_voxel(pt[j], o, op.ph);
             const float2 c0v = cis_turns_sfu(cv.th0);
-            const float t = cv.delta * cd.tau;
+            w = make_float2(cv.amp * c0v.x, cv.amp * c0v.y);
+            t = cv.delta * cd.tau;
+        };
+        float2 w;
+        float t;
+        stage_pair(0, w, t);
+        for (int j = 0; j < nc; ++j) {
+            float2 wn;
+            float tn;
+            stage_pair(min(j + 1, nc - 1), wn, tn);
             const float t2 = t + t;
             const float4* C = reinterpret_cast<const float4*>(Cs + j * LT);
             float4 q = C[0];
@@ -331,9 +380,10 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
                 Tp = Ta;
                 Tc = Tb;
             }
-            const float wr = cv.amp * c0v.x, wi = cv.amp * c0v.y;
-            gr = fmaf(wr, ar, fmaf(-wi, ai, gr));
-            gi = fmaf(wr, ai, fmaf(wi, ar, gi));
+            gr = fmaf(w.x, ar, fmaf(-w.y, ai, gr));
+            gi = fmaf(w.x, ai, fmaf(w.y, ar, gi));
+            w = wn;
+            t = tn;
         }
     }
     pdl_launch_dependents();
@@ -398,9 +448,9 @@ __global__ void __launch_bounds__(256) cheb_range_kernel(GridDesc g, AntSetup a,
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads)
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group)
 {
-    const int ng = threads / CHEB_GROUP;
+    const int ng = threads / group;
     const int TS = ng / pch;
     return (size_t)k_pad * LT * sizeof(float) + (size_t)ng * (k_pad + 4) * sizeof(float2) +
            TILE_V * sizeof(VoxelOffset) + (size_t)2 * TS * TILE_V * sizeof(float2) +
@@ -413,16 +463,24 @@ size_t adj_cheb_smem_bytes(int LT, int k_pad)
            (size_t)CHEB_ADJ_PCHUNK * LT * sizeof(float2) + (size_t)CHEB_ADJ_PCHUNK * sizeof(PairTile);
 }
 
-const void* fwd_cheb_kernel_ptr(int LT)
+template <int G>
+const void* fwd_cheb_ptr_g(int LT)
 {
     switch (LT) {
-    case 16: return (const void*)fwd_cheb_kernel<16>;
-    case 20: return (const void*)fwd_cheb_kernel<20>;
-    case 24: return (const void*)fwd_cheb_kernel<24>;
-    case 28: return (const void*)fwd_cheb_kernel<28>;
-    case 32: return (const void*)fwd_cheb_kernel<32>;
+    case 16: return (const void*)fwd_cheb_kernel<16, G>;
+    case 20: return (const void*)fwd_cheb_kernel<20, G>;
+    case 24: return (const void*)fwd_cheb_kernel<24, G>;
+    case 28: return (const void*)fwd_cheb_kernel<28, G>;
+    case 32: return (const void*)fwd_cheb_kernel<32, G>;
     default: return nullptr;
     }
+}
+
+const void* fwd_cheb_kernel_ptr(int LT, int group)
+{
+    if (group == 4) return fwd_cheb_ptr_g<4>(LT);
+    if (group == 8) return fwd_cheb_ptr_g<8>(LT);
+    return nullptr;
 }
 
 const void* adj_cheb_kernel_ptr(int LT)
@@ -438,11 +496,11 @@ const void* adj_cheb_kernel_ptr(int LT)
 }
 
 cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
-                            size_t smem, cudaStream_t st)
+                            int group, size_t smem, cudaStream_t st)
 {
-    const void* fn = fwd_cheb_kernel_ptr(cd.L);
+    const void* fn = fwd_cheb_kernel_ptr(cd.L, group);
     if (!fn || (threads != 64 && threads != 128)) return cudaErrorInvalidValue;
-    if (a.VS < 1 || (threads / CHEB_GROUP) % a.VS != 0) return cudaErrorInvalidValue;
+    if (a.VS < 1 || (threads / group) % a.VS != 0) return cudaErrorInvalidValue;
     void* args[] = {(void*)&op, (void*)&cd, (void*)&a};
     return launch_pdl(fn, grid, dim3(threads), smem, st, args);
 }

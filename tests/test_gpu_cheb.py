@@ -73,7 +73,7 @@ def test_autotuned_shape_keeps_parity():
     ctx = make_ctx(w.geom)
     shape = ctx.autotune(16)
     print(f"[cheb] autotuned shape for 16 pairs: {shape}")
-    assert shape["threads"] in (64, 128) and shape["chunks"] >= 1
+    assert shape["threads"] in (64, 128) and shape["lanes_per_group"] in (4, 8) and shape["chunks"] >= 1
     pairs = I.epoch_permutation(w.geom.P, 6, 0)[:16]
     s = I.complex_gaussian(w.geom.N, 61).astype(np.complex64).astype(np.complex128)
     pd, sd = to_dev(pairs, "int32"), to_dev(s)
