@@ -241,3 +241,20 @@ def test_invalid_geometry_rejected():
     ctx.set_geometry(g)
     with pytest.raises(NfmError):
         ctx.spgm_step(to_dev(np.zeros(g.M)), to_dev(np.zeros(g.N)), to_dev(np.array([0]), "int32"), -1.0, 0.1)
+
+
+def test_empty_minibatch_rejected():
+    """A minibatch of zero pairs is an argument error for every operator entry point (host check,
+    nothing is launched); the context stays usable."""
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    empty = to_dev(np.array([], dtype=np.int32), "int32")
+    s = to_dev(np.zeros(o.N))
+    for call in (lambda: ctx.forward(empty, s, to_dev(np.zeros(1))),
+                 lambda: ctx.adjoint(empty, to_dev(np.zeros(1)), to_dev(np.zeros(o.N))),
+                 lambda: ctx.spgm_step(to_dev(y), s, empty, 1e-3, 1e-3)):
+        with pytest.raises(NfmError) as ei:
+            call()
+        assert ei.value.code == -1
+    g = to_host(ctx.adjoint(to_dev(np.arange(16), "int32"), to_dev(np.zeros(o.M))))
+    assert np.all(g == 0)
