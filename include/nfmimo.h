@@ -112,11 +112,11 @@ int nfm_set_precision(nfm_ctx* ctx, int mode);
  *   NFM_ALGO_CHEBYSHEV  per (pair, 8x4x4 voxel tile) the factor
  *                       exp(-j 2 pi k df delta/c), delta = D - D_tile_centre,
  *                       is expanded in Chebyshev polynomials of
- *                       t = delta / xi (|t| <= 0.9):
+ *                       t = delta / xi (|t| <= 0.95):
  *                         exp(-j z_k t) = sum_{l<L} (-j)^l b_l(z_k) T_l(t),
- *                       b_0 = J_0, b_l = 2 J_l (Jacobi-Anger), L in {16, ..., 32}
- *                       chosen at nfm_set_geometry so the dropped tail is below
- *                       2e-8; per (pair, voxel) the work is L recurrence steps
+ *                       b_0 = J_0, b_l = 2 J_l (Jacobi-Anger), L even in
+ *                       [16, 32] chosen at nfm_set_geometry so the dropped tail
+ *                       is below 1e-7; per (pair, voxel) the work is L recurrence steps
  *                       instead of K terms (relative error ~2e-6, as DIRECT);
  *   NFM_ALGO_AUTO       CHEBYSHEV where the geometry allows it (L <= 32), else
  *                       DIRECT (default).

@@ -265,8 +265,8 @@ void cheb_coefficients(double z_step, int K, int L, double* out)
 }
 
 // Chebyshev expansion set-up for equally spaced frequencies: the FP64 range of
-// delta = D - D_c over every (pair, tile), the scale tau with |t| <= 0.9, the
-// number of terms L (tail below 2e-8 at the highest frequency) and the table.
+// delta = D - D_c over every (pair, tile), the scale tau with |t| <= 0.95, the
+// number of terms L (even, tail below 1e-7 at the highest frequency) and the table.
 int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, double df, double c)
 {
     unsigned long long* d_mx = nullptr;
@@ -280,7 +280,7 @@ int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, doub
     if (e != cudaSuccess) return fail(ctx, NFM_ERR_CUDA, "expansion range: %s", cudaGetErrorString(e));
     double dmax;
     memcpy(&dmax, &bits, sizeof(dmax));
-    const double margin = 0.9;
+    const double margin = 0.95;
     const double span = 2.0 * dmax;                 // |delta| = |d_T - d_cT + d_R - d_cR| <= span
     if (!(span > 0)) return NFM_OK;                 // degenerate: keep the direct path
     const double z_step = 2.0 * 3.14159265358979323846 * df * span / (c * margin);
@@ -290,20 +290,22 @@ int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, doub
     std::vector<double> probe(2 * LP);
     cheb_coefficients(zmax, 2, LP, probe.data());   // rows z = 0 and z = zmax
     int L = 0;
-    for (int cand = 16; cand <= CHEB_MAX_L; cand += 4) {
+    for (int cand = 16; cand <= CHEB_MAX_L; cand += 2) {
         double tail = 0.0;
         for (int l = cand; l < LP; ++l) tail += std::fabs(probe[LP + l]);
-        if (tail < 2e-8) {
+        if (tail < 1e-7) {
             L = cand;
             break;
         }
     }
     if (L == 0) return NFM_OK;                      // too many terms: the direct path stays
     const int kpad = (K + 3) & ~3;
+    const int ls = (L + 3) & ~3;                    // table row stride, zero beyond L
     std::vector<double> b((size_t)K * L);
     cheb_coefficients(z_step, K, L, b.data());
-    std::vector<float> hb((size_t)kpad * L, 0.f);
-    for (size_t i = 0; i < b.size(); ++i) hb[i] = (float)b[i];
+    std::vector<float> hb((size_t)kpad * ls, 0.f);
+    for (int k = 0; k < K; ++k)
+        for (int l = 0; l < L; ++l) hb[(size_t)k * ls + l] = (float)b[(size_t)k * L + l];
     e = cudaMalloc((void**)&ctx->d_cheb, hb.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d_cheb, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

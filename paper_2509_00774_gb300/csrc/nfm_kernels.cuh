@@ -68,9 +68,9 @@ constexpr int CHEB_GROUPS = CHEB_THREADS / CHEB_GROUP;    // 32
 constexpr int CHEB_ADJ_PCHUNK = 16;                        // pairs staged per adjoint round
 constexpr int CHEB_MAX_L = 32;
 struct ChebDesc {
-    const float* coef;       // [k_pad][L] b_l(k), rows k >= K zero
+    const float* coef;       // [k_pad][round4(L)] b_l(k), zero for k >= K or l >= L
     float tau;               // t = tau * delta
-    int L;                   // expansion terms (16, 20, 24, 28 or 32)
+    int L;                   // expansion terms (even, 16 ... 32)
     int k_pad;               // K rounded up to a multiple of 4
 };
 size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group);

@@ -5,13 +5,13 @@
 // D = D_c + delta, the element factors as
 //
 //   A_kv = p_k amp_v e^{-j 2 pi f0 D/c} e^{-j 2 pi k df D_c/c} e^{-j z_k t_v},
-//   t_v = delta_v / xi  (|t_v| <= 0.9 for every voxel slot),  z_k = 2 pi k df xi / c,
+//   t_v = delta_v / xi  (|t_v| <= 0.95 for every voxel slot),  z_k = 2 pi k df xi / c,
 //
 // and the last factor has the Jacobi-Anger (Chebyshev) expansion
 //
 //   e^{-j z t} = sum_l (-j)^l b_l(z) T_l(t),   b_0 = J_0(z),  b_l = 2 J_l(z),
 //
-// truncated after L terms (tail below 2e-8).  So per (pair, tile)
+// truncated after L terms (L even, tail below 1e-7).  So per (pair, tile)
 //
 //   forward:  y_k += P_k sum_l (-j)^l b_l(k) m_l,  m_l = sum_v u_v T_l(t_v),
 //             u_v = amp_v s_v e^{-j 2 pi f0 D_v/c},  P_k = e^{-j 2 pi k df D_c/c}
@@ -19,7 +19,7 @@
 //             u'_v = amp_v e^{-j 2 pi f0 D_v/c}.
 //
 // The per-voxel work is L steps of the Chebyshev recurrence T_{l+1} = 2t T_l - T_{l-1}
-// (stable for |t| <= 0.9: rounding grows at most linearly in l) with two FMAs
+// (stable for |t| <= 0.95: rounding grows at most 3.2 l times) with two FMAs
 // each, instead of K complex terms; the per-(pair, tile) work is 2KL FMAs.
 // b_l(k) is real, so each (k, l) term of the expansion is two FMAs.
 #include "nfm_kernels.cuh"
@@ -75,6 +75,7 @@ __device__ __forceinline__ float2 tile_step_cis_exact(const PairTile& pt, int k)
 template <int LT, int G>
 __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
 {
+    constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
     extern __shared__ __align__(16) unsigned char smem[];
     const int ng = blockDim.x / G;           // groups per CTA
     const int PCH = a.VS;                    // pairs per CTA (power of two dividing ng)
@@ -82,8 +83,8 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
     const int K = op.K;
     const int KP = cd.k_pad;                 // table rows (multiple of 4, zero rows beyond K)
     const int AS = KP + 4;                   // accumulator row stride (float2), staggers the banks
-    float* coef = reinterpret_cast<float*>(smem);                            // [KP][LT]
-    float2* acc = reinterpret_cast<float2*>(coef + KP * LT);                 // [ng][AS]
+    float* coef = reinterpret_cast<float*>(smem);                            // [KP][LS]
+    float2* acc = reinterpret_cast<float2*>(coef + KP * LS);                 // [ng][AS]
     VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + ng * AS);       // [TILE_V]
     float2* s_st = reinterpret_cast<float2*>(voff + TILE_V);                 // [2][TS][TILE_V]
     AntTile* ant_st = reinterpret_cast<AntTile*>(s_st + 2 * TS * TILE_V);    // [2][ng][2]
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
 
     // Constants and the pair list: no kernel of this library writes them, so they are read
     // before the wait on the previous kernel (which may still be running its tail).
-    for (int i = tid; i < KP * LT / 4; i += nt)
+    for (int i = tid; i < KP * LS / 4; i += nt)
         reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
     for (int i = tid; i < ng * AS; i += nt) acc[i] = make_float2(0.f, 0.f);
     for (int v = tid; v < TILE_V; v += nt)
@@ -210,8 +211,8 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
             const float2 W = tile_step_cis_exact(P, 2 * G);
             for (int k0 = ln; k0 < K; k0 += 2 * G) {
                 const int k1 = k0 + G;                   // may be >= K: zero table row, not stored
-                const float* b0 = coef + k0 * LT;
-                const float* b1 = coef + min(k1, KP - 1) * LT;
+                const float* b0 = coef + k0 * LS;
+                const float* b1 = coef + min(k1, KP - 1) * LS;
                 float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
 #pragma unroll
                 for (int l = 0; l < LT; l += 4) {
@@ -225,14 +226,16 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
                     si0 = fmaf(-x.y, mr[l + 1], si0);
                     sr1 = fmaf(y.y, mi[l + 1], sr1);
                     si1 = fmaf(-y.y, mr[l + 1], si1);
-                    sr0 = fmaf(-x.z, mr[l + 2], sr0);
-                    si0 = fmaf(-x.z, mi[l + 2], si0);
-                    sr1 = fmaf(-y.z, mr[l + 2], sr1);
-                    si1 = fmaf(-y.z, mi[l + 2], si1);
-                    sr0 = fmaf(-x.w, mi[l + 3], sr0);
-                    si0 = fmaf(x.w, mr[l + 3], si0);
-                    sr1 = fmaf(-y.w, mi[l + 3], sr1);
-                    si1 = fmaf(y.w, mr[l + 3], si1);
+                    if (l + 2 < LT) {                    // LT is even: l + 2 < LT covers l + 3
+                        sr0 = fmaf(-x.z, mr[l + 2], sr0);
+                        si0 = fmaf(-x.z, mi[l + 2], si0);
+                        sr1 = fmaf(-y.z, mr[l + 2], sr1);
+                        si1 = fmaf(-y.z, mi[l + 2], si1);
+                        sr0 = fmaf(-x.w, mi[l + 3], sr0);
+                        si0 = fmaf(x.w, mr[l + 3], si0);
+                        sr1 = fmaf(-y.w, mi[l + 3], sr1);
+                        si1 = fmaf(y.w, mr[l + 3], si1);
+                    }
                 }
                 {                                        // y_k += P_k S_k, P_k = (c.x, -c.y)
                     float2 av = accg[k0];
@@ -277,14 +280,15 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, Ch
 template <int LT>
 __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
 {
+    constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = op.K;
     const int KP = cd.k_pad;
-    float* coef = reinterpret_cast<float*>(smem);                          // [KP][LT]
+    float* coef = reinterpret_cast<float*>(smem);                          // [KP][LS]
     const int RS = KP + 2;                   // r' row stride (float2), staggers the banks
-    float2* rp = reinterpret_cast<float2*>(coef + KP * LT);               // [PCH][RS]
-    float2* Cs = rp + CHEB_ADJ_PCHUNK * RS;                                 // [PCH][LT]
-    PairTile* pt = reinterpret_cast<PairTile*>(Cs + CHEB_ADJ_PCHUNK * LT);  // [PCH]
+    float2* rp = reinterpret_cast<float2*>(coef + KP * LS);               // [PCH][RS]
+    float2* Cs = rp + CHEB_ADJ_PCHUNK * RS;                                 // [PCH][LS]
+    PairTile* pt = reinterpret_cast<PairTile*>(Cs + CHEB_ADJ_PCHUNK * LS);  // [PCH]
 
     const int tile = blockIdx.x;
     const int tid = threadIdx.x;
@@ -292,9 +296,9 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
     tile_coords(op.g, tile, tx, ty, tz);
     const int lx = tid % TILE_X, ly = (tid / TILE_X) % TILE_Y, lz = tid / (TILE_X * TILE_Y);
     const VoxelOffset o = voxel_offset(op.g, lx, ly, lz);
-    for (int i = tid; i < KP * LT / 4; i += CHEB_THREADS)
+    for (int i = tid; i < KP * LS / 4; i += CHEB_THREADS)
         reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
-    constexpr int LQ = LT / 4;
+    constexpr int LQ = LS / 4;
     // (pair, k) items of the r' stage: threads split as (CHEB_THREADS / K) pairs x K frequencies
     // when K <= CHEB_THREADS, else every thread strides over k of each pair
     const bool kfit = K <= CHEB_THREADS;
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
             float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f, cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
             for (int k = 0; k < K; ++k) {
                 const float2 rv = rj[k];
-                const float4 b = *reinterpret_cast<const float4*>(coef + k * LT + l);
+                const float4 b = *reinterpret_cast<const float4*>(coef + k * LS + l);
                 cr0 = fmaf(b.x, rv.x, cr0);
                 ci0 = fmaf(b.x, rv.y, ci0);
                 cr1 = fmaf(b.y, rv.x, cr1);
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
                 cr3 = fmaf(b.w, rv.x, cr3);
                 ci3 = fmaf(b.w, rv.y, ci3);
             }
-            float2* Cj = Cs + j * LT + l;      // l % 4 == 0: factors 1, j, -1, -j
+            float2* Cj = Cs + j * LS + l;      // l % 4 == 0: factors 1, j, -1, -j
             Cj[0] = make_float2(cr0, ci0);
             Cj[1] = make_float2(-ci1, cr1);
             Cj[2] = make_float2(-cr2, -ci2);
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
             float tn;
             stage_pair(min(j + 1, nc - 1), wn, tn);
             const float t2 = t + t;
-            const float4* C = reinterpret_cast<const float4*>(Cs + j * LT);
+            const float4* C = reinterpret_cast<const float4*>(Cs + j * LS);
             float4 q = C[0];
             float ar = fmaf(t, q.z, q.x), ai = fmaf(t, q.w, q.y);
             float Tp = 1.f, Tc = t;
@@ -452,15 +456,17 @@ size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group)
 {
     const int ng = threads / group;
     const int TS = ng / pch;
-    return (size_t)k_pad * LT * sizeof(float) + (size_t)ng * (k_pad + 4) * sizeof(float2) +
+    const int LS = (LT + 3) & ~3;
+    return (size_t)k_pad * LS * sizeof(float) + (size_t)ng * (k_pad + 4) * sizeof(float2) +
            TILE_V * sizeof(VoxelOffset) + (size_t)2 * TS * TILE_V * sizeof(float2) +
            (size_t)2 * ng * 2 * sizeof(AntTile) + (size_t)pch * sizeof(int);
 }
 
 size_t adj_cheb_smem_bytes(int LT, int k_pad)
 {
-    return (size_t)k_pad * LT * sizeof(float) + (size_t)CHEB_ADJ_PCHUNK * (k_pad + 2) * sizeof(float2) +
-           (size_t)CHEB_ADJ_PCHUNK * LT * sizeof(float2) + (size_t)CHEB_ADJ_PCHUNK * sizeof(PairTile);
+    const int LS = (LT + 3) & ~3;
+    return (size_t)k_pad * LS * sizeof(float) + (size_t)CHEB_ADJ_PCHUNK * (k_pad + 2) * sizeof(float2) +
+           (size_t)CHEB_ADJ_PCHUNK * LS * sizeof(float2) + (size_t)CHEB_ADJ_PCHUNK * sizeof(PairTile);
 }
 
 template <int G>
@@ -468,9 +474,13 @@ const void* fwd_cheb_ptr_g(int LT)
 {
     switch (LT) {
     case 16: return (const void*)fwd_cheb_kernel<16, G>;
+    case 18: return (const void*)fwd_cheb_kernel<18, G>;
     case 20: return (const void*)fwd_cheb_kernel<20, G>;
+    case 22: return (const void*)fwd_cheb_kernel<22, G>;
     case 24: return (const void*)fwd_cheb_kernel<24, G>;
+    case 26: return (const void*)fwd_cheb_kernel<26, G>;
     case 28: return (const void*)fwd_cheb_kernel<28, G>;
+    case 30: return (const void*)fwd_cheb_kernel<30, G>;
     case 32: return (const void*)fwd_cheb_kernel<32, G>;
     default: return nullptr;
     }
@@ -487,9 +497,13 @@ const void* adj_cheb_kernel_ptr(int LT)
 {
     switch (LT) {
     case 16: return (const void*)adj_cheb_kernel<16>;
+    case 18: return (const void*)adj_cheb_kernel<18>;
     case 20: return (const void*)adj_cheb_kernel<20>;
+    case 22: return (const void*)adj_cheb_kernel<22>;
     case 24: return (const void*)adj_cheb_kernel<24>;
+    case 26: return (const void*)adj_cheb_kernel<26>;
     case 28: return (const void*)adj_cheb_kernel<28>;
+    case 30: return (const void*)adj_cheb_kernel<30>;
     case 32: return (const void*)adj_cheb_kernel<32>;
     default: return nullptr;
     }
