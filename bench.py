@@ -247,7 +247,8 @@ def time_to_oracle_nmse(include_mid=False, nmse_tol=1e-4):
     oracle runs the 30 epochs; each GPU form runs the same seeded epochs with CUDA events around
     every epoch, and the time to target is the summed epoch time up to the first epoch whose iterate
     is within nmse_tol of the oracle's final one.  y, eta = 1/L (50 power iterations) and lambda come
-    from the oracle.  The batched form solves 8 such scenes (other seeds) per CUDA graph; its time is
+    from the oracle.  Each context is autotuned for its minibatch size first (launch shape, and the
+    expansion or the direct recurrence, whichever is faster there).  The batched form solves 8 such scenes (other seeds) per CUDA graph; its time is
     per scene.  With include_mid, the mid workload's first 3 epochs (eta from the oracle's bound
     ||A||_F^2/M on L) are compared the same way.
     """
@@ -282,6 +283,9 @@ def time_to_oracle_nmse(include_mid=False, nmse_tol=1e-4):
         ctx = Context(dev.index)
         ctx.set_precision(precision)
         ctx.set_geometry(g)
+        algo = ctx.algorithm_info()[0]
+        if algo == "chebyshev":
+            algo = ctx.autotune(w.pairs_per_batch)["algorithm"]
         y_d = torch.from_numpy(y.astype(np.complex64)).to(dev)
         perms = torch.from_numpy(np.stack([I.epoch_permutation(g.P, w.seeds["perm"], e)
                                            for e in range(epochs)]).astype(np.int32)).to(dev)
@@ -304,7 +308,7 @@ def time_to_oracle_nmse(include_mid=False, nmse_tol=1e-4):
         ctx.close()
         return {"epochs_to_target": None if hit is None else hit + 1,
                 "ms_to_target": None if hit is None else float(sum(ms[:hit + 1])),
-                "ms_all_epochs": float(sum(ms)), "final_nmse": errs[-1]}
+                "ms_all_epochs": float(sum(ms)), "final_nmse": errs[-1], "operator": algo}
 
     out = {"nmse_tol": nmse_tol, "reference": "FP64 oracle reconstruction after the same epochs"}
     w = W.small_T4R4_K16_16x16x8()
@@ -323,6 +327,8 @@ def time_to_oracle_nmse(include_mid=False, nmse_tol=1e-4):
     for x in scenes:
         c = Context(dev.index)
         c.set_geometry(x.geom)
+        if c.algorithm_info()[0] == "chebyshev":
+            c.autotune(w.pairs_per_batch)
         ctxs.append(c)
     batch = Batch(ctxs)
     ys = [torch.from_numpy(p[1].astype(np.complex64)).to(dev) for p in probs]
@@ -442,6 +448,8 @@ def run_ours(args):
         y, eta, lam = build_problem(torch, ctx, w, seed_offset=rank)
         algo, cheb_L, cheb_zmax = ctx.algorithm_info()
         shape = ctx.autotune(w.pairs_per_batch) if (algo == "chebyshev" and not args.no_autotune) else None
+        if shape is not None:
+            algo = shape["algorithm"]          # with "auto" the tuner may keep the direct recurrence
         E = args.warmup + args.steps
         perms = np.stack([I.epoch_permutation(geom.P, w.seeds["perm"] + 1000 * rank, e) for e in range(E)])
         perms_d = torch.from_numpy(perms.astype(np.int32)).to(dev)

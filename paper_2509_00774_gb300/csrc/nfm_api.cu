@@ -113,7 +113,7 @@ struct nfm_ctx {
     bool fwd_cheb_attr[CHEB_MAX_L + 1][2] = {};
     bool adj_cheb_attr[CHEB_MAX_L + 1] = {};
     // launch shapes of the expansion forward chosen by nfm_autotune, per minibatch size
-    struct FwdShape { int n_pairs, threads, group, pch, chunks; };
+    struct FwdShape { int n_pairs, threads, group, pch, chunks; bool direct; };
     std::vector<FwdShape> fwd_tuned;
 };
 
@@ -321,7 +321,7 @@ int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, doub
 }
 
 // Whether the Chebyshev kernels run for this context (equally spaced frequencies).
-int use_cheb(nfm_ctx* ctx, bool& on)
+int use_cheb(nfm_ctx* ctx, bool& on, int n_pairs = -1)
 {
     on = false;
     if (!ctx->uniform || ctx->algorithm == NFM_ALGO_DIRECT) return NFM_OK;
@@ -330,6 +330,9 @@ int use_cheb(nfm_ctx* ctx, bool& on)
             return fail(ctx, NFM_ERR_ARG, "the Chebyshev expansion needs more than %d terms here", CHEB_MAX_L);
         return NFM_OK;
     }
+    if (ctx->algorithm == NFM_ALGO_AUTO && n_pairs > 0)      // the autotuner may have preferred the direct form
+        for (const auto& t : ctx->fwd_tuned)
+            if (t.n_pairs == n_pairs && t.direct) return NFM_OK;
     on = true;
     return NFM_OK;
 }
@@ -523,7 +526,7 @@ int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s
 {
     if (!ctx->uniform) return enqueue_forward_general(ctx, pairs, n_pairs, s, y_obs, out, fmask);
     bool cheb = false;
-    NFM_TRY(use_cheb(ctx, cheb));
+    NFM_TRY(use_cheb(ctx, cheb, n_pairs));
     if (cheb) return enqueue_forward_cheb(ctx, pairs, n_pairs, s, y_obs, out, fmask);
     FwdPlan pl;
     NFM_TRY(plan_forward(ctx, n_pairs, &pl));
@@ -611,7 +614,7 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
     }
     if (ctx->precision != NFM_FP32) return enqueue_adjoint_tc(ctx, pairs, n_pairs, r, g_out, s, step, alpha, shrink);
     bool cheb = false;
-    NFM_TRY(use_cheb(ctx, cheb));
+    NFM_TRY(use_cheb(ctx, cheb, n_pairs));
     if (cheb) {
         const int LT = ctx->cheb_L;
         const size_t smem = adj_cheb_smem_bytes(LT, ctx->cheb_kpad);
@@ -967,8 +970,8 @@ int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_m
     return NFM_OK;
 }
 
-int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads_out, int* group_out, int* pairs_per_cta_out,
-                 int* chunks_out)
+int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out, int* group_out,
+                 int* pairs_per_cta_out, int* chunks_out)
 {
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
@@ -1029,7 +1032,42 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* threads_out, int* group_out, in
     ctx->prof = prof;
     NFM_TRY(rc);
     NFM_TRY(check_flags(ctx));
-    ctx->fwd_tuned.push_back({n_pairs, best_sh.threads, best_sh.group, best_sh.pch, (int)best_sh.nch});
+    ctx->fwd_tuned.push_back({n_pairs, best_sh.threads, best_sh.group, best_sh.pch, (int)best_sh.nch, false});
+    // With NFM_ALGO_AUTO, also time a whole operator pair (forward + residual + adjoint) of the
+    // expansion with the chosen shape against the direct recurrence and keep the faster.
+    bool direct = false;
+    if (ctx->algorithm == NFM_ALGO_AUTO) {
+        NFM_TRY(ensure(ctx, &ctx->d_resid, &ctx->resid_cap, (size_t)n_pairs * ctx->K * sizeof(float2)));
+        NFM_TRY(ensure(ctx, &ctx->d_g, &ctx->g_cap, (size_t)ctx->N * sizeof(float2)));
+        float t_alg[2] = {0.f, 0.f};
+        cudaEvent_t a0, a1;
+        NFM_CK(cudaEventCreate(&a0));
+        NFM_CK(cudaEventCreate(&a1));
+        ctx->prof = false;
+        for (int alg = 0; alg < 2 && rc == NFM_OK; ++alg) {
+            ctx->algorithm = alg == 0 ? NFM_ALGO_CHEBYSHEV : NFM_ALGO_DIRECT;
+            for (int r = 0; r < 4 && rc == NFM_OK; ++r) {
+                if (r == 1 && cudaEventRecord(a0, ctx->stream) != cudaSuccess) rc = NFM_ERR_CUDA;
+                if (rc == NFM_OK)
+                    rc = enqueue_forward(ctx, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v, nullptr,
+                                         (float2*)ctx->d_resid);
+                if (rc == NFM_OK)
+                    rc = enqueue_adjoint(ctx, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_resid,
+                                         (float2*)ctx->d_g, nullptr, 0.f, 0.f);
+            }
+            if (rc == NFM_OK && (cudaEventRecord(a1, ctx->stream) != cudaSuccess || cudaEventSynchronize(a1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&t_alg[alg], a0, a1) != cudaSuccess))
+                rc = fail(ctx, NFM_ERR_CUDA, "autotuner timing failed");
+        }
+        ctx->algorithm = NFM_ALGO_AUTO;
+        ctx->prof = prof;
+        cudaEventDestroy(a0);
+        cudaEventDestroy(a1);
+        NFM_TRY(rc);
+        direct = t_alg[1] < t_alg[0];
+        ctx->fwd_tuned.back().direct = direct;
+    }
+    if (algorithm_out) *algorithm_out = direct ? NFM_ALGO_DIRECT : NFM_ALGO_CHEBYSHEV;
     if (group_out) *group_out = best_sh.group;
     if (threads_out) *threads_out = best_sh.threads;
     if (pairs_per_cta_out) *pairs_per_cta_out = best_sh.pch;

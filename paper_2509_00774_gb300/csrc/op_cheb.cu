@@ -72,8 +72,10 @@ __device__ __forceinline__ float2 tile_step_cis_exact(const PairTile& pt, int k)
 // forward: CTA = ng = blockDim.x / G groups of G lanes (G = 4 or 8); group = (pair, tile of the
 // stage); PCH pairs per CTA and TS = ng / PCH tiles per stage
 // ---------------------------------------------------------------------------
+// 4-lane groups: 96 registers (5 CTAs of 128 threads per SM); 8-lane groups hold half the voxels
+// per lane and are capped at 72 registers (7 CTAs per SM) so nearly twice the warps stay resident.
 template <int LT, int G>
-__global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
+__global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
 {
     constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
     extern __shared__ __align__(16) unsigned char smem[];

@@ -56,7 +56,8 @@ def load_library(path: str | None = None):
         "nfm_set_algorithm": (i, [vp, i]),
         "nfm_algorithm_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]),
         "nfm_cheb_coefficients": (i, [d, i, i, vp]),
-        "nfm_autotune": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "nfm_autotune": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                             ctypes.POINTER(i)]),
         "nfm_set_regularizer": (i, [vp, d, d]),
         "nfm_dims": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                          ctypes.POINTER(ctypes.c_longlong)]),
@@ -205,12 +206,14 @@ class Context:
     cheb_coefficients = staticmethod(cheb_coefficients)
 
     def autotune(self, n_pairs):
-        """Time the expansion forward's launch shapes for n_pairs-pair minibatches and keep the
-        fastest; returns {"threads", "lanes_per_group", "pairs_per_cta", "chunks"}."""
-        t, g, p, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        self._check(self._lib.nfm_autotune(self._h, int(n_pairs), ctypes.byref(t), ctypes.byref(g), ctypes.byref(p),
-                                           ctypes.byref(c)))
-        return {"threads": t.value, "lanes_per_group": g.value, "pairs_per_cta": p.value, "chunks": c.value}
+        """Time the expansion forward's launch shapes (and, with algorithm "auto", the expansion
+        against the direct recurrence) for n_pairs-pair minibatches and keep the fastest; returns
+        {"algorithm", "threads", "lanes_per_group", "pairs_per_cta", "chunks"}."""
+        a, t, g, p, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.nfm_autotune(self._h, int(n_pairs), ctypes.byref(a), ctypes.byref(t), ctypes.byref(g),
+                                           ctypes.byref(p), ctypes.byref(c)))
+        return {"algorithm": {1: "direct", 2: "chebyshev"}[a.value], "threads": t.value, "lanes_per_group": g.value,
+                "pairs_per_cta": p.value, "chunks": c.value}
 
     def set_regularizer(self, w1=1.0, w2=0.0):
         """R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 for every SPGM/PGM step and the objective."""

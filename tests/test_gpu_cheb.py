@@ -83,3 +83,28 @@ def test_autotuned_shape_keeps_parity():
     rows = o.rows_of_pairs(pairs)
     idx = np.sort(np.random.default_rng(62).choice(rows.size, 64, replace=False))
     assert_close_operator(y1[idx], o.forward(s, rows=rows[idx]), "forward (autotuned)")
+
+
+def test_autotuned_small_spgm_matches_oracle():
+    """With "auto", nfm_autotune may keep the direct recurrence for a tiny minibatch; whichever
+    it picks, the 30 SPGM epochs of the small workload still match the oracle."""
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    y = I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db)
+    y = y.astype(np.complex64).astype(np.complex128)
+    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
+    eta = float(np.float32(1.0 / L))
+    lam = float(np.float32(0.05 * o.lambda_max(y)))
+    ctx = make_ctx(w.geom)
+    choice = ctx.autotune(w.pairs_per_batch)
+    print(f"[cheb] small workload autotune: {choice}")
+    s_orc = np.zeros(o.N, dtype=np.complex128)
+    s_gpu = to_dev(np.zeros(o.N))
+    y_dev = to_dev(y)
+    for e in range(w.epochs):
+        perm = I.epoch_permutation(o.P, w.seeds["perm"], e)
+        s_orc = o.spgm_epoch(y, s_orc, perm, w.pairs_per_batch, eta, lam)
+        ctx.spgm_epoch(y_dev, s_gpu, to_dev(perm, "int32"), w.pairs_per_batch, eta, lam)
+    err = nmse(to_host(s_gpu), s_orc)
+    print(f"[parity] SPGM small (autotuned {choice['algorithm']}): NMSE {err:.2e}")
+    assert err <= NMSE_TOL
