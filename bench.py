@@ -214,6 +214,28 @@ def sources_digest(kernel):
     return h.hexdigest()
 
 
+def prox_stream_gbs(torch, ctx, dev, stream, n=1 << 26, reps=10):
+    """HBM rate of the stand-alone gradient-step + prox kernel (the autograd op; inside SPGM the same
+    update is the adjoint's epilogue): 24 bytes per element (read s and g, write out), a 1.5 GB
+    stream, CUDA events on the context stream, best of `reps` launches."""
+    s = torch.randn(n, dtype=torch.complex64, device=dev)
+    g = torch.randn(n, dtype=torch.complex64, device=dev)
+    out = torch.empty_like(s)
+    for _ in range(3):
+        ctx.prox_step(s, g, 0.5, 0.3, out)
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.prox_step(s, g, 0.5, 0.3, out)
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    del s, g, out
+    return {"kernel": "prox_step_vec_kernel", "elements": n, "bytes_per_element": 24,
+            "achieved_gbs": 24.0 * n / best / 1e9, "us_per_launch": best * 1e6}
+
+
 def cpu_baseline(w, y_np, eta, lam, seconds):
     """Time the FP64 oracle on SPGM minibatch steps of the same workload (bounded sample)."""
     import numpy as np
@@ -487,6 +509,7 @@ def run_ours(args):
             ctx.spgm_epoch(y, s, perms_d[args.warmup + k], bp, eta, lam)
         prof = ctx.profile_report()
         ctx.profile_enable(False)
+        hbm = prox_stream_gbs(torch, ctx, dev, stream)
         time.sleep(0.25)
         sampler.stop()
         step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
@@ -574,6 +597,9 @@ def run_ours(args):
                    "eta": eta, "lambda": lam, "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "kernels": kernels,
+        "update_prox_hbm": dict(hbm, peak_gbs=float(peaks.get("hbm_gbs", 6800.0)),
+                                frac=hbm["achieved_gbs"] / float(peaks.get("hbm_gbs", 6800.0)),
+                                peak_source=peak_src),
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps, "api": "nfm_spgm_epochs_host (pinned host buffers)"},
