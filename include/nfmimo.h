@@ -133,18 +133,20 @@ int nfm_set_algorithm(nfm_ctx* ctx, int algo);
 int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_max);
 
 /* Autotuner (no counterpart in the paper) for minibatches of n_pairs pairs of
- * the current geometry: times the launch shapes of the expansion forward
- * (4 or 8 lanes per (pair, tile), 64 or 128 threads per CTA, 4..32 pairs per
- * CTA, one, two or four waves of tile chunks; pairs 0..n_pairs-1, a zero
- * scene, 3 timed launches each) and keeps the fastest; with NFM_ALGO_AUTO it
- * then times a forward + residual + adjoint of the expansion (chosen shape)
- * against the direct recurrence and keeps the faster algorithm for every later
- * call with n_pairs pairs.  The choice changes the order of the FP32 sums, so
- * results are reproducible for a given choice, not across choices; contexts
- * that are never tuned use a fixed default.  Synchronises the stream.  Writes
- * the chosen algorithm (NFM_ALGO_CHEBYSHEV or NFM_ALGO_DIRECT) and forward
- * shape (any pointer may be NULL).  Errors: NFM_ERR_ARG (n_pairs outside
- * [1, P]), NFM_ERR_STATE (no geometry, or the expansion is not in use). */
+ * the current geometry.  Every candidate launch shape of the expansion
+ * forward (4 or 8 lanes per (pair, tile), 64 or 128 threads per CTA, 4..32
+ * pairs per CTA, one, two or four waves of tile chunks) is timed on a whole
+ * operator step as SPGM runs it (forward + residual + adjoint; pairs
+ * 0..n_pairs-1, a zero scene, one warm-up and three timed steps), because the
+ * shape also decides how the dependent launches overlap; the fastest is kept.
+ * With NFM_ALGO_AUTO the same step with the direct recurrence is timed too
+ * and the faster algorithm is kept for every later call with n_pairs pairs.
+ * The choice changes the order of the FP32 sums, so results are reproducible
+ * for a given choice, not across choices; contexts that are never tuned use a
+ * fixed default.  Synchronises the stream.  Writes the chosen algorithm
+ * (NFM_ALGO_CHEBYSHEV or NFM_ALGO_DIRECT) and forward shape (any pointer may
+ * be NULL).  Errors: NFM_ERR_ARG (n_pairs outside [1, P]), NFM_ERR_STATE (no
+ * geometry, or the expansion is not in use). */
 int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm, int* threads, int* lanes_per_group, int* pairs_per_cta,
                  int* chunks);
 

@@ -979,22 +979,47 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out
     bool cheb = false;
     NFM_TRY(use_cheb(ctx, cheb));
     if (!cheb) return fail(ctx, NFM_ERR_STATE, "the autotuner covers the expansion forward only");
-    for (size_t i = 0; i < ctx->fwd_tuned.size(); ++i)
-        if (ctx->fwd_tuned[i].n_pairs == n_pairs) {
-            ctx->fwd_tuned.erase(ctx->fwd_tuned.begin() + i);
-            break;
-        }
+    auto drop_entry = [&]() {
+        for (size_t i = 0; i < ctx->fwd_tuned.size(); ++i)
+            if (ctx->fwd_tuned[i].n_pairs == n_pairs) {
+                ctx->fwd_tuned.erase(ctx->fwd_tuned.begin() + i);
+                return;
+            }
+    };
+    drop_entry();
     NFM_TRY(ensure(ctx, &ctx->d_v, &ctx->v_cap, (size_t)ctx->N * sizeof(float2)));
+    NFM_TRY(ensure(ctx, &ctx->d_resid, &ctx->resid_cap, (size_t)n_pairs * ctx->K * sizeof(float2)));
+    NFM_TRY(ensure(ctx, &ctx->d_g, &ctx->g_cap, (size_t)ctx->N * sizeof(float2)));
     NFM_CK(cudaMemsetAsync(ctx->d_v, 0, (size_t)ctx->N * sizeof(float2), ctx->stream));
     const bool prof = ctx->prof;
+    const int algorithm = ctx->algorithm;
     ctx->prof = false;
     cudaEvent_t e0, e1;
     NFM_CK(cudaEventCreate(&e0));
     NFM_CK(cudaEventCreate(&e1));
+    // One operator step as SPGM runs it (forward + residual reduction + adjoint, dependent launches
+    // overlapping through PDL): one warm-up and three timed repetitions.
+    auto time_step = [&](float& ms) -> int {
+        for (int r = 0; r < 4; ++r) {
+            if (r == 1 && cudaEventRecord(e0, ctx->stream) != cudaSuccess)
+                return fail(ctx, NFM_ERR_CUDA, "autotuner event failed");
+            int q = enqueue_forward(ctx, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v, nullptr,
+                                    (float2*)ctx->d_resid);
+            if (q == NFM_OK)
+                q = enqueue_adjoint(ctx, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_resid, (float2*)ctx->d_g,
+                                    nullptr, 0.f, 0.f);
+            if (q != NFM_OK) return q;
+        }
+        if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            return fail(ctx, NFM_ERR_CUDA, "autotuner timing failed");
+        return NFM_OK;
+    };
     float best = 1e30f;
     ChebShape best_sh{};
     const double waves[3] = {1.0, 2.0, 4.0};
     int rc = NFM_OK;
+    ctx->algorithm = NFM_ALGO_CHEBYSHEV;
     for (int group : {4, 8}) {
         for (int threads : {64, 128}) {
             const int ng = threads / group;
@@ -1004,21 +1029,11 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out
                     ChebShape sh;
                     rc = cheb_shape(ctx, n_pairs, threads, group, pch, w, 0, &sh);
                     if (rc != NFM_OK) break;
-                    rc = launch_cheb_forward_shape(ctx, sh, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v);
-                    if (rc != NFM_OK) break;
-                    if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) {
-                        rc = fail(ctx, NFM_ERR_CUDA, "autotuner event failed");
-                        break;
-                    }
-                    for (int r = 0; r < 3 && rc == NFM_OK; ++r)
-                        rc = launch_cheb_forward_shape(ctx, sh, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v);
-                    if (rc != NFM_OK) break;
+                    drop_entry();
+                    ctx->fwd_tuned.push_back({n_pairs, sh.threads, sh.group, sh.pch, (int)sh.nch, false});
                     float ms = 0.f;
-                    if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                        rc = fail(ctx, NFM_ERR_CUDA, "autotuner timing failed");
-                        break;
-                    }
+                    rc = time_step(ms);
+                    if (rc != NFM_OK) break;
                     if (ms < best) {
                         best = ms;
                         best_sh = sh;
@@ -1027,46 +1042,27 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out
             }
         }
     }
+    drop_entry();
+    if (rc == NFM_OK)
+        ctx->fwd_tuned.push_back({n_pairs, best_sh.threads, best_sh.group, best_sh.pch, (int)best_sh.nch, false});
+    // With NFM_ALGO_AUTO, the same step with the direct recurrence; the faster algorithm is kept.
+    bool direct = false;
+    if (rc == NFM_OK && algorithm == NFM_ALGO_AUTO) {
+        float t_direct = 0.f;
+        ctx->algorithm = NFM_ALGO_DIRECT;
+        rc = time_step(t_direct);
+        if (rc == NFM_OK) {
+            direct = t_direct < best;
+            ctx->fwd_tuned.back().direct = direct;
+        }
+    }
+    ctx->algorithm = algorithm;
+    ctx->prof = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->prof = prof;
+    if (rc != NFM_OK) drop_entry();
     NFM_TRY(rc);
     NFM_TRY(check_flags(ctx));
-    ctx->fwd_tuned.push_back({n_pairs, best_sh.threads, best_sh.group, best_sh.pch, (int)best_sh.nch, false});
-    // With NFM_ALGO_AUTO, also time a whole operator pair (forward + residual + adjoint) of the
-    // expansion with the chosen shape against the direct recurrence and keep the faster.
-    bool direct = false;
-    if (ctx->algorithm == NFM_ALGO_AUTO) {
-        NFM_TRY(ensure(ctx, &ctx->d_resid, &ctx->resid_cap, (size_t)n_pairs * ctx->K * sizeof(float2)));
-        NFM_TRY(ensure(ctx, &ctx->d_g, &ctx->g_cap, (size_t)ctx->N * sizeof(float2)));
-        float t_alg[2] = {0.f, 0.f};
-        cudaEvent_t a0, a1;
-        NFM_CK(cudaEventCreate(&a0));
-        NFM_CK(cudaEventCreate(&a1));
-        ctx->prof = false;
-        for (int alg = 0; alg < 2 && rc == NFM_OK; ++alg) {
-            ctx->algorithm = alg == 0 ? NFM_ALGO_CHEBYSHEV : NFM_ALGO_DIRECT;
-            for (int r = 0; r < 4 && rc == NFM_OK; ++r) {
-                if (r == 1 && cudaEventRecord(a0, ctx->stream) != cudaSuccess) rc = NFM_ERR_CUDA;
-                if (rc == NFM_OK)
-                    rc = enqueue_forward(ctx, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_v, nullptr,
-                                         (float2*)ctx->d_resid);
-                if (rc == NFM_OK)
-                    rc = enqueue_adjoint(ctx, ctx->d_pairs_all, n_pairs, (const float2*)ctx->d_resid,
-                                         (float2*)ctx->d_g, nullptr, 0.f, 0.f);
-            }
-            if (rc == NFM_OK && (cudaEventRecord(a1, ctx->stream) != cudaSuccess || cudaEventSynchronize(a1) != cudaSuccess ||
-                                 cudaEventElapsedTime(&t_alg[alg], a0, a1) != cudaSuccess))
-                rc = fail(ctx, NFM_ERR_CUDA, "autotuner timing failed");
-        }
-        ctx->algorithm = NFM_ALGO_AUTO;
-        ctx->prof = prof;
-        cudaEventDestroy(a0);
-        cudaEventDestroy(a1);
-        NFM_TRY(rc);
-        direct = t_alg[1] < t_alg[0];
-        ctx->fwd_tuned.back().direct = direct;
-    }
     if (algorithm_out) *algorithm_out = direct ? NFM_ALGO_DIRECT : NFM_ALGO_CHEBYSHEV;
     if (group_out) *group_out = best_sh.group;
     if (threads_out) *threads_out = best_sh.threads;

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
 // adjoint: CTA = one voxel tile, thread = voxel; pairs in chunks of CHEB_ADJ_PCHUNK
 // ---------------------------------------------------------------------------
 template <int LT>
-__global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
+__global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
 {
     constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
     extern __shared__ __align__(16) unsigned char smem[];
@@ -370,13 +370,18 @@ __global__ void __launch_bounds__(CHEB_THREADS) adj_cheb_kernel(OpDesc op, ChebD
             float tn;
             stage_pair(min(j + 1, nc - 1), wn, tn);
             const float t2 = t + t;
+            // the pair's coefficients are read into registers first, so the recurrence below
+            // does not wait on shared-memory latency term by term
             const float4* C = reinterpret_cast<const float4*>(Cs + j * LS);
-            float4 q = C[0];
+            float4 cr[LT / 2];
+#pragma unroll
+            for (int i = 0; i < LT / 2; ++i) cr[i] = C[i];
+            float4 q = cr[0];
             float ar = fmaf(t, q.z, q.x), ai = fmaf(t, q.w, q.y);
             float Tp = 1.f, Tc = t;
 #pragma unroll
             for (int l = 2; l < LT; l += 2) {
-                q = C[l / 2];
+                q = cr[l / 2];
                 const float Ta = fmaf(t2, Tc, -Tp);
                 const float Tb = fmaf(t2, Ta, -Tc);
                 ar = fmaf(Ta, q.x, ar);
