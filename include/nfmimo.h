@@ -137,8 +137,9 @@ int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_m
  * forward (4 or 8 lanes per (pair, tile), 64 or 128 threads per CTA, 4..32
  * pairs per CTA, one, two or four waves of tile chunks) is timed on a whole
  * operator step as SPGM runs it (forward + residual + adjoint; pairs
- * 0..n_pairs-1, a zero scene, one warm-up and three timed steps), because the
- * shape also decides how the dependent launches overlap; the fastest is kept.
+ * 0..n_pairs-1, a zero scene, one warm-up and six timed steps), because the
+ * shape also decides how the dependent launches overlap; the three fastest are
+ * timed again twice over twelve steps and the lowest time decides.
  * With NFM_ALGO_AUTO the same step with the direct recurrence is timed too
  * and the faster algorithm is kept for every later call with n_pairs pairs.
  * The choice changes the order of the FP32 sums, so results are reproducible
