@@ -408,9 +408,10 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = W.mid_T16R16_K64_64x64x32()
+    w = W.large_T32R32_K128_128x128x64() if args.workload == "large" else W.mid_T16R16_K64_64x64x32()
     oracle.build()
     o = oracle.Oracle(w.geom)
+    cores = oracle.get_threads()
     y = I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db)
     eta, lam = 1.0 / 70.0, 0.05 * 1e-3
     perm = I.epoch_permutation(o.P, w.seeds["perm"], 0)
@@ -426,12 +427,14 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     per_step = 2.0 * bp * o.K * o.N
     value = per_step * args.steps / dt / 1e9
-    cores = oracle.get_threads()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "pairs_per_batch": bp, "step": "one SPGM minibatch step (16 pairs x 64 freqs)"},
+        "config": {"workload": w.name, "T": o.T, "R": o.R, "K": o.K, "N": o.N, "M": o.M, "pairs_per_batch": bp,
+                   "minibatches_per_step": 1,
+                   "step": f"one SPGM minibatch step ({bp} pairs x {o.K} freqs, forward + adjoint + prox) in FP64",
+                   "parallelism": f"{cores} host threads (OpenMP)"},
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} SPGM minibatch steps on {cores} host threads"},
