@@ -108,3 +108,45 @@ def test_autotuned_small_spgm_matches_oracle():
     err = nmse(to_host(s_gpu), s_orc)
     print(f"[parity] SPGM small (autotuned {choice['algorithm']}): NMSE {err:.2e}")
     assert err <= NMSE_TOL
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_geometries_match_oracle(seed):
+    """Random arrays, bands, frequency counts (1..128), grids and minibatches: the expansion operator
+    (default launch shape, then the autotuned one) against the oracle on sampled rows and voxels."""
+    from tests.gpu_helpers import assert_close_operator
+    rng = np.random.default_rng(1000 + seed)
+    T, R = int(rng.integers(1, 10)), int(rng.integers(1, 10))
+    K = int(rng.choice([1, 2, 3, 5, 11, 17, 31, 64, 77, 128]))
+    nx, ny, nz = (int(v) for v in rng.integers(3, 21, 3))
+    d = float(rng.uniform(0.002, 0.008))
+    f_lo = float(rng.uniform(4e9, 70e9))
+    f_hi = f_lo + float(rng.uniform(0.5e9, 12e9))
+    tx = np.concatenate([rng.uniform(-0.2, 0.2, (T, 2)), np.zeros((T, 1))], 1)
+    rx = np.concatenate([rng.uniform(-0.2, 0.2, (R, 2)), np.zeros((R, 1))], 1)
+    grid = I.Grid(-nx * d / 2, -ny * d / 2, float(rng.uniform(0.2, 0.6)), d, d, d * 0.8, nx, ny, nz)
+    pulse = (rng.standard_normal(K) + 1j * rng.standard_normal(K)) if seed % 2 else None
+    geom = I.Geometry(tx, rx, I.uniform_freqs(f_lo, f_hi, K), grid, pulse=pulse)
+    o = Oracle(geom)
+    ctx = make_ctx(geom)
+    algo, L, zmax = ctx.algorithm_info()
+    n_pairs = int(rng.integers(1, geom.P + 1))
+    pairs = rng.choice(geom.P, n_pairs, replace=n_pairs > geom.P)
+    s = (I.complex_gaussian(geom.N, seed + 7)).astype(np.complex64).astype(np.complex128)
+    r = (I.complex_gaussian(n_pairs * K, seed + 8)).astype(np.complex64).astype(np.complex128)
+    rows = o.rows_of_pairs(pairs)
+    ridx = np.sort(rng.choice(rows.size, min(rows.size, 48), replace=False))
+    cols = np.sort(rng.choice(geom.N, min(geom.N, 256), replace=False))
+    want_y = o.forward(s, rows=rows[ridx])
+    want_g = o.adjoint(r, rows=rows, cols=cols)
+    for tuned in (False, True):
+        if tuned and algo == "chebyshev":
+            ctx.autotune(n_pairs)
+        y = to_host(ctx.forward(to_dev(pairs, "int32"), to_dev(s)))
+        g = to_host(ctx.adjoint(to_dev(pairs, "int32"), to_dev(r)))
+        print(f"[cheb] seed {seed}: T{T} R{R} K{K} grid {nx}x{ny}x{nz} pairs {n_pairs} {algo} L={L} "
+              f"z_max={zmax:.2f} tuned={tuned}")
+        scale_y = np.sqrt((np.abs(o.dense(rows[ridx], np.arange(geom.N))) ** 2) @ (np.abs(s) ** 2))
+        scale_g = np.sqrt((np.abs(o.dense(rows, cols).T) ** 2) @ (np.abs(r) ** 2))
+        assert_close_operator(y[ridx], want_y, "forward", scale_y)
+        assert_close_operator(g[cols], want_g, "adjoint", scale_g)
