@@ -102,7 +102,11 @@ int nfm_dims(const nfm_ctx* ctx, int* T, int* R, int* K, long long* N);
  *                  in FP32 (relative error ~1e-5),
  *   NFM_TC_FP16X3  the same with FP16 halves and the residual scaled per pair
  *                  by a power of two (relative error ~1e-6).
- * The forward operator is FP32 in every mode.  Errors: NFM_ERR_ARG. */
+ * With the Chebyshev expansion in use (see nfm_set_algorithm) the tensor cores
+ * run the adjoint's coefficient contraction C[(tile, pair), l] = sum_k r'_k b_l(k)
+ * and the per-voxel Chebyshev sum stays FP32; otherwise they run the
+ * frequency-split phasor GEMM.  The forward operator is FP32 in every mode.
+ * Errors: NFM_ERR_ARG. */
 enum { NFM_FP32 = 0, NFM_TC_BF16X3 = 1, NFM_TC_FP16X3 = 2 };
 int nfm_set_precision(nfm_ctx* ctx, int mode);
 

@@ -1,0 +1,51 @@
+// Per-(pair, voxel) geometry of the Chebyshev-expansion operator and the
+// tile phasor P_k = exp(-j 2 pi k df D_c / c) (shared by the CUDA-core and the
+// tensor-core kernels of the expansion).
+#pragma once
+#include "nfm_device.cuh"
+
+namespace nfm {
+
+// amplitude, reduced base phase f0 D/c (turns) and delta = D - D_c of one (pair, voxel)
+struct ChebVoxel {
+    float amp, th0, delta;
+};
+
+__device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelOffset& o, const PhaseConsts& ph)
+{
+    float rsT, rsR;
+    const float dT = antenna_delta(pt.vTx, pt.vTy, pt.vTz, pt.dcT, pt.dcT2, o, rsT);
+    const float dR = antenna_delta(pt.vRx, pt.vRy, pt.vRz, pt.dcR, pt.dcR2, o, rsR);
+    ChebVoxel c;
+    c.delta = dT + dR;
+    c.amp = INV_4PI * rsT * rsR;
+    // f0 (D_c + delta)/c with an exact product split: one rounding at |x| <= 1
+    const float p = ph.f0c_hi * c.delta;
+    const float pe = fmaf(ph.f0c_hi, c.delta, -p);
+    const float th = (pt.B + (p - rintf(p))) + fmaf(ph.f0c_lo, c.delta, pe);
+    c.th0 = frac_turns(th);
+    return c;
+}
+
+// (cos, sin)(2 pi k df D_c / c) from the reduced step phase S = S_hi + S_lo of the
+// pair tile: k S_hi split exactly (FMA remainder), so one rounding at |x| <= 1/2.
+__device__ __forceinline__ float2 tile_step_cis(const PairTile& pt, int k)
+{
+    const float kf = (float)k;
+    const float p = kf * pt.S_hi;
+    const float e = fmaf(kf, pt.S_hi, -p);
+    const float ph = (p - rintf(p)) + fmaf(kf, pt.S_lo, e);
+    return cis_turns_sfu(ph);
+}
+
+// The same phasor from the Taylor-series cis_turns (error ~1e-7), for a step that a recurrence repeats.
+__device__ __forceinline__ float2 tile_step_cis_exact(const PairTile& pt, int k)
+{
+    const float kf = (float)k;
+    const float p = kf * pt.S_hi;
+    const float e = fmaf(kf, pt.S_hi, -p);
+    const float ph = (p - rintf(p)) + fmaf(kf, pt.S_lo, e);
+    return cis_turns(ph);
+}
+
+}  // namespace nfm

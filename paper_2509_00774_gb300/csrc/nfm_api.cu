@@ -113,6 +113,7 @@ struct nfm_ctx {
     double cheb_zmax = 0.0;       // z of the highest frequency
     bool fwd_cheb_attr[CHEB_MAX_L + 1][2] = {};
     bool adj_cheb_attr[CHEB_MAX_L + 1] = {};
+    bool adj_cheb_tc_attr[2][CHEB_MAX_L + 1] = {};
     // launch shapes of the expansion forward chosen by nfm_autotune, per minibatch size
     struct FwdShape { int n_pairs, threads, group, pch, chunks; bool direct; };
     std::vector<FwdShape> fwd_tuned;
@@ -613,9 +614,36 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         prof_pair(ctx, 2, e0, prof_mark(ctx));
         return NFM_OK;
     }
-    if (ctx->precision != NFM_FP32) return enqueue_adjoint_tc(ctx, pairs, n_pairs, r, g_out, s, step, alpha, shrink);
     bool cheb = false;
     NFM_TRY(use_cheb(ctx, cheb, n_pairs));
+    if (ctx->precision != NFM_FP32) {
+        if (!cheb) return enqueue_adjoint_tc(ctx, pairs, n_pairs, r, g_out, s, step, alpha, shrink);
+        // expansion adjoint with its coefficient stage on the tensor cores
+        const bool f16 = ctx->precision == NFM_TC_FP16X3;
+        const int LT = ctx->cheb_L;
+        const size_t smem = adj_cheb_tc_smem_bytes(ctx->K);
+        if (smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "tensor-core expansion needs %zu B shared memory", smem);
+        if (!ctx->adj_cheb_tc_attr[f16][LT]) {
+            NFM_CK(cudaFuncSetAttribute(adj_cheb_tc_kernel_ptr(LT, f16), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ctx->smem_optin));
+            ctx->adj_cheb_tc_attr[f16][LT] = true;
+        }
+        AdjArgs a;
+        a.pairs = pairs;
+        a.n_pairs = n_pairs;
+        a.r = r;
+        a.g_out = g_out;
+        a.s = s;
+        a.step = step;
+        a.alpha = alpha;
+        a.shrink = shrink;
+        a.pchunk = 16;
+        ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad};
+        const int e0 = prof_mark(ctx);
+        NFM_CK(launch_adj_cheb_tc(op_desc(ctx), cd, a, f16, smem, ctx->stream));
+        prof_pair(ctx, 2, e0, prof_mark(ctx));
+        return NFM_OK;
+    }
     if (cheb) {
         const int LT = ctx->cheb_L;
         const size_t smem = adj_cheb_smem_bytes(LT, ctx->cheb_kpad);

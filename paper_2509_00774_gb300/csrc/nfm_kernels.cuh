@@ -82,6 +82,11 @@ const void* adj_cheb_kernel_ptr(int LT);
 cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
                             int group, size_t smem, cudaStream_t st);
 cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, size_t smem, cudaStream_t st);
+// tensor-core (tcgen05) coefficient stage of the expansion adjoint (op_cheb_tc.cu), K <= 128, L <= 32
+size_t adj_cheb_tc_smem_bytes(int K);
+const void* adj_cheb_tc_kernel_ptr(int LT, bool f16);
+cudaError_t launch_adj_cheb_tc(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, bool f16, size_t smem,
+                               cudaStream_t st);
 
 constexpr int FWD_PC = 8;         // pairs per forward CTA
 constexpr int ADJ_TC_PCHUNK = 8;  // pairs whose tensor-core B operands a CTA holds at once

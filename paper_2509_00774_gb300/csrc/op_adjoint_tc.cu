@@ -21,98 +21,19 @@
 // Operands use the no-swizzle K-major layout: 8-row x 16-byte core matrices,
 // core matrices along K 128 B apart (LBO), along M/N 256 B apart (SBO).
 #include "nfm_kernels.cuh"
-
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
+#include "tc_ptx.cuh"
 
 namespace nfm {
 
 namespace {
+
+using namespace tc;
 
 constexpr int TC_M = 128;
 constexpr int TC_N = 16;
 constexpr int TC_KSTEP_BYTES_A = TC_M * 16 * 2;    // 4096: one K step (16 elements) of A
 constexpr int TC_KSTEP_BYTES_B = TC_N * 16 * 2;    // 512
 constexpr int TC_B_PAIR_BYTES = 2 * 2 * TC_KSTEP_BYTES_B;   // [split][kstep] = 2048
-constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;      // bounded mbarrier spin
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() { asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for phase `parity` of bar; false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
-{
-    for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor: no swizzle, K-major, LBO = 128 B, SBO = 256 B.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)(256u >> 4) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version of the 5th-generation tensor core
-    return d;                 // base offset 0, layout type 0 (no swizzle)
-}
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16 (or F16), both K-major, M = 128, N = 16.
 template <bool F16>
@@ -120,41 +41,6 @@ __host__ __device__ constexpr uint32_t tc_idesc()
 {
     return (1u << 4) | ((F16 ? 0u : 1u) << 7) | ((F16 ? 0u : 1u) << 10) | ((uint32_t)(TC_N >> 3) << 17) |
            ((uint32_t)(TC_M >> 4) << 24);
-}
-
-// byte offset of element (row, kk) (kk < 16) in one K step of a K-major no-swizzle operand
-__device__ __forceinline__ uint32_t kmaj_off(int row, int kk)
-{
-    return (uint32_t)((row >> 3) * 256 + (kk >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
-}
-
-// Two FP32 values -> one 32-bit register of two 16-bit values, the first in the
-// low half (lower address).  cvt packs its first source into the upper half.
-template <bool F16>
-__device__ __forceinline__ uint32_t pack2(float a, float b)
-{
-    uint32_t u;
-    if (F16)
-        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(b), "f"(a));
-    else
-        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(b), "f"(a));
-    return u;
-}
-template <bool F16>
-__device__ __forceinline__ float2 unpack2(uint32_t u)
-{
-    if (F16)
-        return make_float2(__half2float(__ushort_as_half((unsigned short)(u & 0xFFFFu))),
-                           __half2float(__ushort_as_half((unsigned short)(u >> 16))));
-    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
-}
-// x = hi + lo (both rounded to the 16-bit type), for two values
-template <bool F16>
-__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo)
-{
-    hi = pack2<F16>(a, b);
-    const float2 h = unpack2<F16>(hi);
-    lo = pack2<F16>(a - h.x, b - h.y);
 }
 
 }  // namespace

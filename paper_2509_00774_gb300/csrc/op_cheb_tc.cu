@@ -1,0 +1,321 @@
+// Tensor-core (tcgen05) form of the Chebyshev-expansion adjoint (the precision
+// modes NFM_TC_BF16X3 / NFM_TC_FP16X3 for equally spaced frequencies).
+//
+// The expansion adjoint (op_cheb.cu) needs, per (pair j, tile t), the
+// coefficients
+//
+//     C_l = j^l sum_k b_l(k) r'_k,   r'_k = conj(p_k) r_jk e^{+j 2 pi k df D_c(j, t)/c},
+//
+// a dense contraction over the K frequencies with a real, constant b.  For four
+// tiles and a chunk of 16 pairs it is one real GEMM D = A B^T:
+//
+//     A[(t, j, c), k] = Re / Im r'_k (c = 0 / 1)   M = 128 rows (4 tiles x 16 pairs x 2)
+//     B[l, k]         = b_l(k)                     N = 32 (l < L, zero rows above)
+//     D[(t, j, c), l] = sum_k A B                  K = the frequencies (multiple of 16, zero padded)
+//
+// Both operands are split x = hi + lo in BF16 (or FP16, r' scaled per pair by a
+// power of two) and D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in FP32 in
+// tensor memory (3 tcgen05.mma of M128 N32 K16 per K step, one thread issues,
+// completion through tcgen05.commit -> mbarrier with a bounded wait).  Warps 0-3
+// read D back (lane = row) into shared memory; the per-voxel part, sum_l T_l(t)
+// C_l with the Chebyshev recurrence and the fused step/prox epilogue, stays on
+// the CUDA cores exactly as in the FP32 expansion adjoint.
+//
+// CTA = 4 tiles = 512 threads (thread = voxel).  Operands use the no-swizzle
+// K-major layout of tc_ptx.cuh.
+#include "nfm_kernels.cuh"
+#include "cheb_device.cuh"
+#include "tc_ptx.cuh"
+
+namespace nfm {
+
+namespace {
+
+using namespace tc;
+
+constexpr int CTC_TILES = 4;                       // tiles per CTA
+constexpr int CTC_THREADS = CTC_TILES * TILE_V;    // 512
+constexpr int CTC_PCH = 16;                        // pairs per chunk
+constexpr int CTC_M = CTC_TILES * CTC_PCH * 2;     // 128 rows (tile, pair, re/im)
+constexpr int CTC_N = 32;                          // l, L <= 32
+constexpr int CTC_KSTEP_A = CTC_M * 16 * 2;        // 4096 bytes: one K step of A
+constexpr int CTC_KSTEP_B = CTC_N * 16 * 2;        // 1024 bytes: one K step of B
+constexpr int CTC_MAX_KS = GEN_MAX_K / 16;         // 8 K steps (K <= 128)
+
+template <bool F16>
+__host__ __device__ constexpr uint32_t ctc_idesc()
+{
+    return (1u << 4) | ((F16 ? 0u : 1u) << 7) | ((F16 ? 0u : 1u) << 10) | ((uint32_t)(CTC_N >> 3) << 17) |
+           ((uint32_t)(CTC_M >> 4) << 24);
+}
+
+struct CtcSmem {   // byte offsets of the dynamic shared-memory regions (KS = K steps)
+    int a, b, pt, craw, scale, bar, tslot, total;
+    __host__ __device__ CtcSmem(int KS)
+    {
+        a = 0;                                            // [split 2][KS][4096]
+        b = a + 2 * KS * CTC_KSTEP_A;                     // [split 2][KS][1024]
+        pt = b + 2 * KS * CTC_KSTEP_B;                    // [4 tiles][16 pairs] PairTile
+        craw = pt + CTC_TILES * CTC_PCH * (int)sizeof(PairTile);   // [4][16][32] float2 (D_re, D_im)
+        scale = craw + CTC_TILES * CTC_PCH * CTC_N * (int)sizeof(float2);   // [16] float
+        bar = scale + CTC_PCH * (int)sizeof(float);       // one mbarrier (8-byte aligned)
+        tslot = bar + 8;
+        total = tslot + 16;
+    }
+};
+
+}  // namespace
+
+template <int LT, bool F16>
+__global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
+{
+    constexpr int LS = (LT + 3) & ~3;        // table row stride of the coefficient table
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int K = op.K;
+    const int KS = (K + 15) / 16;
+    const CtcSmem L(KS);
+    unsigned char* As = smem + L.a;
+    unsigned char* Bs = smem + L.b;
+    PairTile* pt = reinterpret_cast<PairTile*>(smem + L.pt);
+    float2* craw = reinterpret_cast<float2*>(smem + L.craw);
+    float* scale = reinterpret_cast<float*>(smem + L.scale);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tslot);
+
+    const int tid = threadIdx.x;
+    const int warp = tid / 32;
+    const int t4 = tid / TILE_V;             // tile of this thread within the CTA
+    const int v = tid % TILE_V;              // voxel within the tile
+    const int tile = blockIdx.x * CTC_TILES + t4;
+    const bool tile_ok = tile < op.g.n_tiles;
+    int tx = 0, ty = 0, tz = 0;
+    if (tile_ok) tile_coords(op.g, tile, tx, ty, tz);
+    const int lx = v % TILE_X, ly = (v / TILE_X) % TILE_Y, lz = v / (TILE_X * TILE_Y);
+    const VoxelOffset o = voxel_offset(op.g, lx, ly, lz);
+    constexpr uint32_t IDESC = ctc_idesc<F16>();
+
+    if (warp == 0) {
+        tmem_alloc(tslot, 32);
+        tmem_relinquish();
+    }
+    if (tid == 0) mbar_init(bar, 1);
+    // B = the coefficient table b_l(k), rows l (zero for l >= LT), two k per 32-bit word
+    for (int e = tid; e < CTC_N * KS * 8; e += CTC_THREADS) {
+        const int l = e / (KS * 8), kp = e - (e / (KS * 8)) * (KS * 8);
+        const int k = 2 * kp;
+        const float b0 = (l < LT && k < K) ? cd.coef[k * LS + l] : 0.f;
+        const float b1 = (l < LT && k + 1 < K) ? cd.coef[(k + 1) * LS + l] : 0.f;
+        uint32_t hi, lo;
+        split2<F16>(b0, b1, hi, lo);
+        const int s = k / 16, kk = k % 16;
+        *reinterpret_cast<uint32_t*>(Bs + 0 * KS * CTC_KSTEP_B + s * CTC_KSTEP_B + kmaj_off(l, kk)) = hi;
+        *reinterpret_cast<uint32_t*>(Bs + 1 * KS * CTC_KSTEP_B + s * CTC_KSTEP_B + kmaj_off(l, kk)) = lo;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    bool ok = true;
+    float gr = 0.f, gi = 0.f;
+
+    for (int c0 = 0, chunk = 0; c0 < a.n_pairs; c0 += CTC_PCH, ++chunk) {
+        const int nc = min(CTC_PCH, a.n_pairs - c0);
+        // pair tiles of the chunk (geometry only: no kernel of this library writes it)
+        if (tid < CTC_TILES * CTC_PCH) {
+            const int tt = tid / CTC_PCH, j = tid % CTC_PCH;
+            const int til = blockIdx.x * CTC_TILES + tt;
+            if (j < nc && til < op.g.n_tiles) pt[tid] = load_pair_tile(op, a.pairs[c0 + j], til);
+        }
+        if (c0 == 0) pdl_wait();             // r comes from the previous kernel
+        // FP16: per-pair power-of-two scale so that |Re r'|, |Im r'| <= |r'| < 1
+        if (F16) {
+            for (int j = warp; j < CTC_PCH; j += CTC_THREADS / 32) {
+                float m = 0.f;
+                if (j < nc)
+                    for (int k = tid % 32; k < K; k += 32) {
+                        float2 r = a.r[(size_t)(c0 + j) * K + k];
+                        if (op.pulse) r = cmul_conj(r, op.pulse[k]);
+                        m = fmaxf(m, sqrtf(r.x * r.x + r.y * r.y));   // |r'| = |conj(p) r|
+                    }
+                for (int w = 16; w > 0; w >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, w));
+                if (tid % 32 == 0) {
+                    float sc = 1.0f;
+                    if (m > 0.f) {
+                        int ex;
+                        frexpf(m, &ex);
+                        sc = ldexpf(1.0f, -ex);
+                    }
+                    scale[j] = sc;
+                }
+            }
+        }
+        __syncthreads();
+        // A = r' rows (tile, pair, re/im), two k per 32-bit word
+        for (int e = tid; e < CTC_TILES * CTC_PCH * KS * 8; e += CTC_THREADS) {
+            const int kp = e % (KS * 8);
+            const int tj = e / (KS * 8);
+            const int tt = tj / CTC_PCH, j = tj % CTC_PCH;
+            const int k = 2 * kp;
+            float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+            if (j < nc && blockIdx.x * CTC_TILES + tt < op.g.n_tiles) {
+                const PairTile& P = pt[tt * CTC_PCH + j];
+                const float sc = F16 ? scale[j] : 1.0f;
+                if (k < K) {
+                    float2 r = a.r[(size_t)(c0 + j) * K + k];
+                    if (op.pulse) r = cmul_conj(r, op.pulse[k]);
+                    v0 = cmul(r, tile_step_cis(P, k));
+                    v0.x *= sc;
+                    v0.y *= sc;
+                }
+                if (k + 1 < K) {
+                    float2 r = a.r[(size_t)(c0 + j) * K + k + 1];
+                    if (op.pulse) r = cmul_conj(r, op.pulse[k + 1]);
+                    v1 = cmul(r, tile_step_cis(P, k + 1));
+                    v1.x *= sc;
+                    v1.y *= sc;
+                }
+            }
+            uint32_t hre, lre, him, lim;
+            split2<F16>(v0.x, v1.x, hre, lre);
+            split2<F16>(v0.y, v1.y, him, lim);
+            const int row = (tt * CTC_PCH + j) * 2;
+            const int s = k / 16, kk = k % 16;
+            unsigned char* a0 = As + s * CTC_KSTEP_A;
+            *reinterpret_cast<uint32_t*>(a0 + kmaj_off(row, kk)) = hre;
+            *reinterpret_cast<uint32_t*>(a0 + kmaj_off(row + 1, kk)) = him;
+            *reinterpret_cast<uint32_t*>(a0 + KS * CTC_KSTEP_A + kmaj_off(row, kk)) = lre;
+            *reinterpret_cast<uint32_t*>(a0 + KS * CTC_KSTEP_A + kmaj_off(row + 1, kk)) = lim;
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
+            for (int s = 0; s < KS; ++s) {
+                const uint64_t ahi = smem_desc(a_base + s * CTC_KSTEP_A);
+                const uint64_t alo = smem_desc(a_base + (KS + s) * CTC_KSTEP_A);
+                const uint64_t bhi = smem_desc(b_base + s * CTC_KSTEP_B);
+                const uint64_t blo = smem_desc(b_base + (KS + s) * CTC_KSTEP_B);
+                tc_mma(tbase, ahi, bhi, IDESC, s > 0 ? 1u : 0u);
+                tc_mma(tbase, ahi, blo, IDESC, 1u);
+                tc_mma(tbase, alo, bhi, IDESC, 1u);
+            }
+            tc_commit(bar);
+        }
+        if (!mbar_wait(bar, (uint32_t)(chunk & 1))) ok = false;
+        tc_fence_after();
+        if (warp < 4) {                      // lanes 32 warp .. : rows (tile, pair, re/im)
+            float d[32];
+            tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16), d);
+            const int row = tid;             // tid < 128
+            const int tt = row / (2 * CTC_PCH), j = (row / 2) % CTC_PCH, c = row & 1;
+            const float inv = F16 ? 1.0f / scale[j] : 1.0f;
+            float* dst = reinterpret_cast<float*>(craw + (tt * CTC_PCH + j) * CTC_N) + c;
+#pragma unroll
+            for (int l = 0; l < CTC_N; ++l) dst[2 * l] = d[l] * inv;
+        }
+        tc_fence_before();
+        __syncthreads();
+        // per voxel: sum over the chunk's pairs of conj(u') sum_l T_l(t) j^l (D_re + j D_im)_l
+        if (tile_ok) {
+            for (int j = 0; j < nc; ++j) {
+                const ChebVoxel cv = cheb_voxel(pt[t4 * CTC_PCH + j], o, op.ph);
+                const float2 c0v = cis_turns_sfu(cv.th0);
+                const float t = cv.delta * cd.tau, t2 = t + t;
+                const float4* C = reinterpret_cast<const float4*>(craw + (t4 * CTC_PCH + j) * CTC_N);
+                float4 q = C[0];                 // (D_0, D_1): factors 1 and j
+                float ar = fmaf(t, -q.w, q.x), ai = fmaf(t, q.z, q.y);
+                float Tp = 1.f, Tc = t;
+#pragma unroll
+                for (int l = 2; l < LT; l += 2) {
+                    q = C[l / 2];                // (D_l, D_l+1)
+                    const float Ta = fmaf(t2, Tc, -Tp);
+                    const float Tb = fmaf(t2, Ta, -Tc);
+                    if ((l & 3) == 0) {          // factors 1 and j
+                        ar = fmaf(Ta, q.x, ar);
+                        ai = fmaf(Ta, q.y, ai);
+                        ar = fmaf(Tb, -q.w, ar);
+                        ai = fmaf(Tb, q.z, ai);
+                    } else {                     // factors -1 and -j
+                        ar = fmaf(Ta, -q.x, ar);
+                        ai = fmaf(Ta, -q.y, ai);
+                        ar = fmaf(Tb, q.w, ar);
+                        ai = fmaf(Tb, -q.z, ai);
+                    }
+                    Tp = Ta;
+                    Tc = Tb;
+                }
+                const float wr = cv.amp * c0v.x, wi = cv.amp * c0v.y;
+                gr = fmaf(wr, ar, fmaf(-wi, ai, gr));
+                gi = fmaf(wr, ai, fmaf(wi, ar, gi));
+            }
+        }
+        __syncthreads();                     // craw, pt and A are rewritten by the next chunk
+    }
+    pdl_launch_dependents();
+    if (!ok && tid == 0) atomicOr(op.err, ERRF_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 32);
+    }
+
+    if (!tile_ok) return;
+    const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
+    if (ix >= op.g.nx || iy >= op.g.ny || iz >= op.g.nz) return;
+    const size_t n = ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
+    if (a.s) {
+        const float2 sv = a.s[n];
+        const float zr = fmaf(-a.step, gr, sv.x), zi = fmaf(-a.step, gi, sv.y);
+        const float mag = sqrtf(zr * zr + zi * zi);
+        float2 out = make_float2(0.f, 0.f);
+        if (mag > a.alpha) {
+            const float f = (1.0f - a.alpha / mag) * a.shrink;
+            out = make_float2(zr * f, zi * f);
+        }
+        a.s[n] = out;
+    } else {
+        a.g_out[n] = make_float2(gr, gi);
+    }
+}
+
+size_t adj_cheb_tc_smem_bytes(int K)
+{
+    return (size_t)CtcSmem((K + 15) / 16).total;
+}
+
+template <bool F16>
+static const void* adj_cheb_tc_ptr_f(int LT)
+{
+    switch (LT) {
+    case 16: return (const void*)adj_cheb_tc_kernel<16, F16>;
+    case 18: return (const void*)adj_cheb_tc_kernel<18, F16>;
+    case 20: return (const void*)adj_cheb_tc_kernel<20, F16>;
+    case 22: return (const void*)adj_cheb_tc_kernel<22, F16>;
+    case 24: return (const void*)adj_cheb_tc_kernel<24, F16>;
+    case 26: return (const void*)adj_cheb_tc_kernel<26, F16>;
+    case 28: return (const void*)adj_cheb_tc_kernel<28, F16>;
+    case 30: return (const void*)adj_cheb_tc_kernel<30, F16>;
+    case 32: return (const void*)adj_cheb_tc_kernel<32, F16>;
+    default: return nullptr;
+    }
+}
+
+const void* adj_cheb_tc_kernel_ptr(int LT, bool f16)
+{
+    return f16 ? adj_cheb_tc_ptr_f<true>(LT) : adj_cheb_tc_ptr_f<false>(LT);
+}
+
+cudaError_t launch_adj_cheb_tc(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, bool f16, size_t smem,
+                               cudaStream_t st)
+{
+    const void* fn = adj_cheb_tc_kernel_ptr(cd.L, f16);
+    if (!fn || op.K > GEN_MAX_K || cd.L > CTC_N) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&op, (void*)&cd, (void*)&a};
+    const unsigned grid = (unsigned)((op.g.n_tiles + CTC_TILES - 1) / CTC_TILES);
+    return launch_pdl(fn, dim3(grid), dim3(CTC_THREADS), smem, st, args);
+}
+
+}  // namespace nfm
