@@ -185,11 +185,13 @@ def build_problem(torch, ctx, w, seed_offset):
     return y, 1.0 / L, lam
 
 
-KERNEL_SOURCES = {"fwd_cheb_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_cheb.cu"),
-                  "adj_cheb_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_cheb.cu"),
+KERNEL_SOURCES = {"fwd_cheb_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "cheb_device.cuh", "op_cheb.cu"),
+                  "adj_cheb_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "cheb_device.cuh", "op_cheb.cu"),
+                  "adj_cheb_tc_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "cheb_device.cuh", "tc_ptx.cuh",
+                                         "op_cheb_tc.cu"),
                   "fwd_partial_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_forward.cu"),
                   "adj_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_adjoint.cu"),
-                  "adj_tc_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_adjoint_tc.cu")}
+                  "adj_tc_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "tc_ptx.cuh", "op_adjoint_tc.cu")}
 
 
 def traffic_for(kernel):
@@ -556,7 +558,7 @@ def run_ours(args):
             continue
         avg_ms = ms / n
         entry = {"launches": n, "total_ms": ms, "avg_us": avg_ms * 1e3}
-        if kind in ("forward_partial", "adjoint") and not (kind == "adjoint" and cheb and args.precision != "fp32"):
+        if kind in ("forward_partial", "adjoint") and (cheb or kind == "forward_partial" or args.precision == "fp32"):
             tf = flops_per_launch / (avg_ms * 1e-3) / 1e12
             entry.update({"gpairs_per_s": elems / (avg_ms * 1e-3) / 1e9, "tflops": tf,
                           "direct_equivalent_tflops": FLOPS_PER_PAIR * elems / (avg_ms * 1e-3) / 1e12})
@@ -568,11 +570,13 @@ def run_ours(args):
     dk = kernels[dom]
     kname = {"forward_partial": "fwd_cheb_kernel" if cheb else "fwd_partial_kernel",
              "adjoint": ("adj_cheb_kernel" if cheb else "adj_kernel") if args.precision == "fp32"
-             else "adj_tc_kernel"}[dom]
-    if cheb and not (dom == "adjoint" and args.precision != "fp32"):
+             else ("adj_cheb_tc_kernel" if cheb else "adj_tc_kernel")}[dom]
+    if cheb:
         work = (f"{cheb_flops_per_pair_voxel(cheb_L, geom.K):.0f} flops per (pair, voxel) = 2 x (3L recurrence/accumulate "
                 f"FMAs + 2KL/128 expansion FMAs + {CHEB_GEOM_OPS} geometry ops), L = {cheb_L}, K = {geom.K}; "
-                f"{bp * geom.N} (pair, voxel) = {elems} (row, voxel) per launch")
+                f"{bp * geom.N} (pair, voxel) = {elems} (row, voxel) per launch" +
+                ("" if args.precision == "fp32" or dom != "adjoint" else
+                 "; the 2KL/128 coefficient FMAs run on tcgen05, the rest on the FP32 lanes"))
     else:
         work = (f"{FLOPS_PER_PAIR:.0f} flops = 8 FP32 FMA-pipe lane-instructions (complex MAC + phasor step) "
                 f"per (row, voxel) pair, {elems} pairs per launch")
