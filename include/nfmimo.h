@@ -114,14 +114,17 @@ int nfm_set_precision(nfm_ctx* ctx, int mode);
  * for equally spaced frequencies f_k = f0 + k df:
  *   NFM_ALGO_DIRECT     every (row, voxel) term from phasor recurrences over k;
  *   NFM_ALGO_CHEBYSHEV  per (pair, 8x4x4 voxel tile) the factor
- *                       exp(-j 2 pi k df delta/c), delta = D - D_tile_centre,
+ *                       exp(-j 2 pi (k - k_c) df delta/c), delta = D - D_tile_centre,
+ *                       k_c = (K - 1)/2 the band centre (the phase
+ *                       2 pi (f_0 D_c + f_c delta)/c is evaluated directly),
  *                       is expanded in Chebyshev polynomials of
  *                       t = delta / xi (|t| <= 0.95):
  *                         exp(-j z_k t) = sum_{l<L} (-j)^l b_l(z_k) T_l(t),
  *                       b_0 = J_0, b_l = 2 J_l (Jacobi-Anger), L even in
- *                       [16, 32] chosen at nfm_set_geometry so the dropped tail
- *                       is below 1e-7; per (pair, voxel) the work is L recurrence steps
- *                       instead of K terms (relative error ~2e-6, as DIRECT);
+ *                       [10, 32] chosen at nfm_set_geometry so the dropped tail
+ *                       is below 1e-7 at the band edges; per (pair, voxel) the work is
+ *                       L recurrence steps instead of K terms (relative error ~2e-6,
+ *                       as DIRECT);
  *   NFM_ALGO_AUTO       CHEBYSHEV where the geometry allows it (L <= 32), else
  *                       DIRECT (default).
  * Arbitrary frequency lists always use their own kernels; the tensor-core
@@ -132,14 +135,16 @@ int nfm_set_algorithm(nfm_ctx* ctx, int algo);
 
 /* Which algorithm the operator uses for the current geometry and setting
  * (NFM_ALGO_DIRECT or NFM_ALGO_CHEBYSHEV), the expansion length L (0 if the
- * expansion is not available) and z of the highest frequency.  Any pointer
+ * expansion is not available) and the largest |z_k| (the band edges).  Any pointer
  * may be NULL.  Errors: NFM_ERR_STATE without a geometry. */
 int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_max);
 
 /* Autotuner (no counterpart in the paper) for minibatches of n_pairs pairs of
  * the current geometry.  Every candidate launch shape of the expansion
  * forward (4 or 8 lanes per (pair, tile), 64 or 128 threads per CTA, 4..32
- * pairs per CTA, one, two or four waves of tile chunks) is timed on a whole
+ * pairs per CTA, one, two or four waves of tile chunks, and one wave of
+ * (occupancy - 1) or occupancy CTAs on every SM with chunks that may be
+ * shorter than a stage of tiles) is timed on a whole
  * operator step as SPGM runs it (forward + residual + adjoint; pairs
  * 0..n_pairs-1, a zero scene, one warm-up and six timed steps), because the
  * shape also decides how the dependent launches overlap; the three fastest are
@@ -156,11 +161,13 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm, int* threads, int* l
                  int* chunks);
 
 /* Host-only helper (no GPU needed): the expansion coefficients
- * out[k*L + l] = b_l(k z_step), l < L, k < K, of
+ * out[k*L + l] = b_l((k - k_center) z_step), l < L, k < K, of
  *   exp(-j z t) = sum_l (-j)^l b_l(z) T_l(t)   (b_0 = J_0(z), b_l = 2 J_l(z)),
- * computed in FP64 by Chebyshev-Gauss quadrature with 2L + 64 nodes.
- * Errors: NFM_ERR_ARG for K < 1, L outside [1, 256], NULL out, non-finite z_step. */
-int nfm_cheb_coefficients(double z_step, int K, int L, double* out);
+ * computed in FP64 by Chebyshev-Gauss quadrature with 2L + 64 nodes.  The
+ * operator's table is this one with k_center = (K - 1)/2.
+ * Errors: NFM_ERR_ARG for K < 1, L outside [1, 256], NULL out, non-finite
+ * z_step or k_center. */
+int nfm_cheb_coefficients(double z_step, double k_center, int K, int L, double* out);
 
 /* Regulariser of Eq. 3 (Sec. III uses l1 and notes the method extends to
  * other functionals): R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 (elastic net;

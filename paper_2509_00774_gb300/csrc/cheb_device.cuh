@@ -6,12 +6,15 @@
 
 namespace nfm {
 
-// amplitude, reduced base phase f0 D/c (turns) and delta = D - D_c of one (pair, voxel)
+// amplitude, reduced base phase (f_0 D_c + f_c delta)/c (turns) and delta = D - D_c of one (pair, voxel).
+// With f_k = f_0 + k df and the band centre f_c = f_0 + k_c df,
+//   f_k D = f_0 D_c + f_c delta + k df D_c + (k - k_c) df delta,
+// so the phase left to the expansion, (k - k_c) df delta / c, is centred on zero over the band.
 struct ChebVoxel {
     float amp, th0, delta;
 };
 
-__device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelOffset& o, const PhaseConsts& ph)
+__device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelOffset& o, float fc_hi, float fc_lo)
 {
     float rsT, rsR;
     const float dT = antenna_delta(pt.vTx, pt.vTy, pt.vTz, pt.dcT, pt.dcT2, o, rsT);
@@ -19,10 +22,10 @@ __device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelO
     ChebVoxel c;
     c.delta = dT + dR;
     c.amp = INV_4PI * rsT * rsR;
-    // f0 (D_c + delta)/c with an exact product split: one rounding at |x| <= 1
-    const float p = ph.f0c_hi * c.delta;
-    const float pe = fmaf(ph.f0c_hi, c.delta, -p);
-    const float th = (pt.B + (p - rintf(p))) + fmaf(ph.f0c_lo, c.delta, pe);
+    // B = f_0 D_c / c (reduced) plus f_c delta / c with an exact product split: one rounding at |x| <= 1
+    const float p = fc_hi * c.delta;
+    const float pe = fmaf(fc_hi, c.delta, -p);
+    const float th = (pt.B + (p - rintf(p))) + fmaf(fc_lo, c.delta, pe);
     c.th0 = frac_turns(th);
     return c;
 }

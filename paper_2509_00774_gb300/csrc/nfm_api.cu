@@ -110,7 +110,8 @@ struct nfm_ctx {
     int cheb_L = 0;               // 0: not available for this geometry
     int cheb_kpad = 0;
     float cheb_tau = 0.f;         // t = tau * delta
-    double cheb_zmax = 0.0;       // z of the highest frequency
+    double cheb_zmax = 0.0;       // largest |z_k| (the band edges)
+    float cheb_fc_hi = 0.f, cheb_fc_lo = 0.f;   // band centre f_c / c, hi + lo
     bool fwd_cheb_attr[CHEB_MAX_L + 1][2] = {};
     bool adj_cheb_attr[CHEB_MAX_L + 1] = {};
     bool adj_cheb_tc_attr[2][CHEB_MAX_L + 1] = {};
@@ -232,7 +233,7 @@ void prof_pair(nfm_ctx* ctx, int kind, int a, int b)
 // b_l(k), l < L, of exp(-j z t) = sum_l (-j)^l b_l T_l(t) at z = k z_step (b_0 = J_0(z),
 // b_l = 2 J_l(z)), by Chebyshev-Gauss quadrature of (eps_l / pi) int_0^pi e^{-j z cos th} cos(l th) dth
 // with Q = 2L + 64 nodes (exact up to aliasing from degree >= 2Q - L).  FP64, row-major [K][L].
-void cheb_coefficients(double z_step, int K, int L, double* out)
+void cheb_coefficients(double z_step, double k_center, int K, int L, double* out)
 {
     const double pi = 3.14159265358979323846;
     const int Q = 2 * L + 64;
@@ -242,7 +243,7 @@ void cheb_coefficients(double z_step, int K, int L, double* out)
         cth[q] = std::cos(th[q]);
     }
     for (int k = 0; k < K; ++k) {
-        const double z = k * z_step;
+        const double z = (k - k_center) * z_step;
         for (int l = 0; l < L; ++l) {
             double re = 0.0, im = 0.0;
             for (int q = 0; q < Q; ++q) {
@@ -268,8 +269,10 @@ void cheb_coefficients(double z_step, int K, int L, double* out)
 
 // Chebyshev expansion set-up for equally spaced frequencies: the FP64 range of
 // delta = D - D_c over every (pair, tile), the scale tau with |t| <= 0.95, the
-// number of terms L (even, tail below 1e-7 at the highest frequency) and the table.
-int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, double df, double c)
+// band centre k_c = (K - 1)/2 (the expansion covers e^{-j z_k t} with
+// z_k = (k - k_c) z_step, |z_k| <= z_step (K - 1)/2), the number of terms L
+// (even, tail below 1e-7 at the band edges) and the table.
+int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, double f0, double df, double c)
 {
     unsigned long long* d_mx = nullptr;
     unsigned long long bits = 0;
@@ -286,13 +289,14 @@ int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, doub
     const double span = 2.0 * dmax;                 // |delta| = |d_T - d_cT + d_R - d_cR| <= span
     if (!(span > 0)) return NFM_OK;                 // degenerate: keep the direct path
     const double z_step = 2.0 * 3.14159265358979323846 * df * span / (c * margin);
-    const double zmax = z_step * (K - 1);
-    // tail of the expansion at the highest frequency
+    const double k_center = 0.5 * (K - 1);
+    const double zmax = z_step * k_center;
+    // tail of the expansion at the band edges (|z| = zmax; |b_l(-z)| = |b_l(z)|)
     const int LP = 80;
     std::vector<double> probe(2 * LP);
-    cheb_coefficients(zmax, 2, LP, probe.data());   // rows z = 0 and z = zmax
+    cheb_coefficients(zmax, 0.0, 2, LP, probe.data());   // rows z = 0 and z = zmax
     int L = 0;
-    for (int cand = 16; cand <= CHEB_MAX_L; cand += 2) {
+    for (int cand = CHEB_MIN_L; cand <= CHEB_MAX_L; cand += 2) {
         double tail = 0.0;
         for (int l = cand; l < LP; ++l) tail += std::fabs(probe[LP + l]);
         if (tail < 1e-7) {
@@ -304,7 +308,7 @@ int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, doub
     const int kpad = (K + 3) & ~3;
     const int ls = (L + 3) & ~3;                    // table row stride, zero beyond L
     std::vector<double> b((size_t)K * L);
-    cheb_coefficients(z_step, K, L, b.data());
+    cheb_coefficients(z_step, k_center, K, L, b.data());
     std::vector<float> hb((size_t)kpad * ls, 0.f);
     for (int k = 0; k < K; ++k)
         for (int l = 0; l < L; ++l) hb[(size_t)k * ls + l] = (float)b[(size_t)k * L + l];
@@ -319,6 +323,9 @@ int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, doub
     ctx->cheb_kpad = kpad;
     ctx->cheb_tau = (float)(margin / span);
     ctx->cheb_zmax = zmax;
+    const double fcc = (f0 + k_center * df) / c;
+    ctx->cheb_fc_hi = (float)fcc;
+    ctx->cheb_fc_lo = (float)(fcc - (double)ctx->cheb_fc_hi);
     return NFM_OK;
 }
 
@@ -428,10 +435,13 @@ struct ChebShape {
     int threads, group, pch, n_groups, n_slots;
     long long nch;
     size_t smem;
+    int occ;                 // resident CTAs per SM (0 when the chunk count was given)
 };
 
 // Default shape (threads = 128, 4 lanes per (pair, tile), pairs per CTA = the power of two >=
-// n_pairs in [4, 32], about `waves` CTAs per resident slot), or the one given.
+// n_pairs in [4, 32], about `waves` CTAs per resident slot, at least one full stage of tiles per
+// chunk), or the one given (`chunks` > 0: any count up to one tile per chunk; a chunk shorter than a
+// stage leaves the stage's remaining slots idle).
 int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int group, int pch, double waves, long long chunks,
                ChebShape* sh)
 {
@@ -456,16 +466,19 @@ int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int group, int pch, doubl
     }
     sh->n_groups = (n_pairs + pch - 1) / pch;
     sh->n_slots = sh->n_groups * pch;
+    sh->occ = 0;                             // queried only for the default chunk count
     long long nch = chunks;
     if (nch <= 0) {
         int occ = 0;
         NFM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, sh->smem));
         if (occ < 1) occ = 1;
+        sh->occ = occ;
         const long long G = (long long)(waves * ctx->num_sms * occ);
         nch = (G + sh->n_groups - 1) / sh->n_groups;
+        const long long max_ch = (ctx->gd.n_tiles + TS - 1) / TS;
+        if (nch > max_ch) nch = max_ch;
     }
-    const long long max_ch = (ctx->gd.n_tiles + TS - 1) / TS;
-    if (nch > max_ch) nch = max_ch;
+    if (nch > ctx->gd.n_tiles) nch = ctx->gd.n_tiles;
     if (nch > 65535) nch = 65535;
     if (nch < 1) nch = 1;
     sh->nch = nch;
@@ -476,7 +489,7 @@ int launch_cheb_forward_shape(nfm_ctx* ctx, const ChebShape& sh, const int* pair
 {
     const size_t partial_bytes = (size_t)sh.nch * sh.n_slots * ctx->K * sizeof(float2);
     NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, partial_bytes));
-    ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, ctx->cheb_L, ctx->cheb_kpad};
+    ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, ctx->cheb_L, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
     FwdArgs a;
     a.pairs = pairs;
     a.n_pairs = n_pairs;
@@ -638,7 +651,7 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         a.alpha = alpha;
         a.shrink = shrink;
         a.pchunk = 16;
-        ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad};
+        ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
         const int e0 = prof_mark(ctx);
         NFM_CK(launch_adj_cheb_tc(op_desc(ctx), cd, a, f16, smem, ctx->stream));
         prof_pair(ctx, 2, e0, prof_mark(ctx));
@@ -662,7 +675,7 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         a.alpha = alpha;
         a.shrink = shrink;
         a.pchunk = CHEB_ADJ_PCHUNK;
-        ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad};
+        ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
         const int e0 = prof_mark(ctx);
         NFM_CK(launch_adj_cheb(op_desc(ctx), cd, a, smem, ctx->stream));
         prof_pair(ctx, 2, e0, prof_mark(ctx));
@@ -939,7 +952,7 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
         free_ptr(d_fk);
         if (e != cudaSuccess) return fail(ctx, NFM_ERR_CUDA, "general-frequency tables: %s", cudaGetErrorString(e));
     }
-    if (uniform) NFM_TRY(setup_cheb(ctx, gd, as, K, df, c));
+    if (uniform) NFM_TRY(setup_cheb(ctx, gd, as, K, f0, df, c));
     NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
 
     ctx->T = T;
@@ -1055,9 +1068,19 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out
             const int ng = threads / group;
             for (int pch = 4; pch <= ng && rc == NFM_OK; pch *= 2) {
                 if (pch / 2 >= n_pairs && pch > 4) break;        // all groups beyond the pairs would idle
-                for (double w : waves) {
+                // waves of whole-stage chunks, then one wave of (occ - 1) or occ CTAs on every SM with
+                // chunks that may be shorter than a stage (even work per SM when stages are coarse)
+                for (int cand = 0; cand < 5 && rc == NFM_OK; ++cand) {
                     ChebShape sh;
-                    rc = cheb_shape(ctx, n_pairs, threads, group, pch, w, 0, &sh);
+                    if (cand < 3) {
+                        rc = cheb_shape(ctx, n_pairs, threads, group, pch, waves[cand], 0, &sh);
+                    } else {
+                        rc = cheb_shape(ctx, n_pairs, threads, group, pch, 1.0, 0, &sh);
+                        const long long per_sm = sh.occ - (cand == 3 ? 1 : 0);
+                        const long long want = (per_sm * ctx->num_sms + sh.n_groups - 1) / sh.n_groups;
+                        if (rc != NFM_OK || per_sm < 1 || want <= sh.nch) continue;   // covered above
+                        rc = cheb_shape(ctx, n_pairs, threads, group, pch, 0.0, want, &sh);
+                    }
                     if (rc != NFM_OK) break;
                     drop_entry();
                     ctx->fwd_tuned.push_back({n_pairs, sh.threads, sh.group, sh.pch, (int)sh.nch, false});
@@ -1113,10 +1136,10 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out
     return NFM_OK;
 }
 
-int nfm_cheb_coefficients(double z_step, int K, int L, double* out)
+int nfm_cheb_coefficients(double z_step, double k_center, int K, int L, double* out)
 {
-    if (K < 1 || L < 1 || L > 256 || !out || !std::isfinite(z_step)) return NFM_ERR_ARG;
-    cheb_coefficients(z_step, K, L, out);
+    if (K < 1 || L < 1 || L > 256 || !out || !std::isfinite(z_step) || !std::isfinite(k_center)) return NFM_ERR_ARG;
+    cheb_coefficients(z_step, k_center, K, L, out);
     return NFM_OK;
 }
 

@@ -66,12 +66,14 @@ constexpr int CHEB_THREADS = 128;
 constexpr int CHEB_GROUP = 4;                              // lanes per (pair, tile) in the forward
 constexpr int CHEB_GROUPS = CHEB_THREADS / CHEB_GROUP;    // 32
 constexpr int CHEB_ADJ_PCHUNK = 16;                        // pairs staged per adjoint round
+constexpr int CHEB_MIN_L = 10;
 constexpr int CHEB_MAX_L = 32;
 struct ChebDesc {
-    const float* coef;       // [k_pad][round4(L)] b_l(k), zero for k >= K or l >= L
+    const float* coef;       // [k_pad][round4(L)] b_l(z_k), z_k = (k - k_c) z_step; zero for k >= K or l >= L
     float tau;               // t = tau * delta
-    int L;                   // expansion terms (even, 16 ... 32)
+    int L;                   // expansion terms (even, 10 ... 32)
     int k_pad;               // K rounded up to a multiple of 4
+    float fc_hi, fc_lo;      // f_c / c (cycles per metre) as hi + lo, f_c = f_0 + k_c df the band centre
 };
 size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group);
 size_t adj_cheb_smem_bytes(int LT, int k_pad);

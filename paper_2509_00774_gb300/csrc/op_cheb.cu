@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
             for (int i = 0; i < TILE_V / G; ++i) {
                 const int v = ln + G * i;
                 const float2 sv = sb[v];
-                const ChebVoxel cv = cheb_voxel(P, voff[v], op.ph);
+                const ChebVoxel cv = cheb_voxel(P, voff[v], cd.fc_hi, cd.fc_lo);
                 const float2 c0 = cis_turns_sfu(cv.th0);
                 const float2 u = cmul_conj(make_float2(cv.amp * sv.x, cv.amp * sv.y), c0);
                 const float t = cv.delta * cd.tau;
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
         // per voxel: sum over the chunk's pairs of conj(u') sum_l T_l(t) C_l; the geometry of pair
         // j+1 is computed next to the recurrence of pair j (independent instructions)
         auto stage_pair = [&](int j, float2& w, float& t) {
-            const ChebVoxel cv = cheb_voxel(pt[j], o, op.ph);
+            const ChebVoxel cv = cheb_voxel(pt[j], o, cd.fc_hi, cd.fc_lo);
             const float2 c0v = cis_turns_sfu(cv.th0);
             w = make_float2(cv.amp * c0v.x, cv.amp * c0v.y);
             t = cv.delta * cd.tau;
@@ -439,6 +439,9 @@ template <int G>
 const void* fwd_cheb_ptr_g(int LT)
 {
     switch (LT) {
+    case 10: return (const void*)fwd_cheb_kernel<10, G>;
+    case 12: return (const void*)fwd_cheb_kernel<12, G>;
+    case 14: return (const void*)fwd_cheb_kernel<14, G>;
     case 16: return (const void*)fwd_cheb_kernel<16, G>;
     case 18: return (const void*)fwd_cheb_kernel<18, G>;
     case 20: return (const void*)fwd_cheb_kernel<20, G>;
@@ -462,6 +465,9 @@ const void* fwd_cheb_kernel_ptr(int LT, int group)
 const void* adj_cheb_kernel_ptr(int LT)
 {
     switch (LT) {
+    case 10: return (const void*)adj_cheb_kernel<10>;
+    case 12: return (const void*)adj_cheb_kernel<12>;
+    case 14: return (const void*)adj_cheb_kernel<14>;
     case 16: return (const void*)adj_cheb_kernel<16>;
     case 18: return (const void*)adj_cheb_kernel<18>;
     case 20: return (const void*)adj_cheb_kernel<20>;

@@ -41,6 +41,8 @@ constexpr int CTC_N = 32;                          // l, L <= 32
 constexpr int CTC_KSTEP_A = CTC_M * 16 * 2;        // 4096 bytes: one K step of A
 constexpr int CTC_KSTEP_B = CTC_N * 16 * 2;        // 1024 bytes: one K step of B
 constexpr int CTC_MAX_KS = GEN_MAX_K / 16;         // 8 K steps (K <= 128)
+constexpr int CTC_CRS = CTC_N + 2;                 // float2 row stride of the read-back D (16-byte rows,
+                                                   // two rows per bank group: 2-way stores, not 16-way)
 
 template <bool F16>
 __host__ __device__ constexpr uint32_t ctc_idesc()
@@ -56,8 +58,8 @@ struct CtcSmem {   // byte offsets of the dynamic shared-memory regions (KS = K 
         a = 0;                                            // [split 2][KS][4096]
         b = a + 2 * KS * CTC_KSTEP_A;                     // [split 2][KS][1024]
         pt = b + 2 * KS * CTC_KSTEP_B;                    // [4 tiles][16 pairs] PairTile
-        craw = pt + CTC_TILES * CTC_PCH * (int)sizeof(PairTile);   // [4][16][32] float2 (D_re, D_im)
-        scale = craw + CTC_TILES * CTC_PCH * CTC_N * (int)sizeof(float2);   // [16] float
+        craw = pt + CTC_TILES * CTC_PCH * (int)sizeof(PairTile);   // [4][16][CTC_CRS] float2 (D_re, D_im)
+        scale = craw + CTC_TILES * CTC_PCH * CTC_CRS * (int)sizeof(float2);   // [16] float
         bar = scale + CTC_PCH * (int)sizeof(float);       // one mbarrier (8-byte aligned)
         tslot = bar + 8;
         total = tslot + 16;
@@ -99,9 +101,12 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
         tmem_relinquish();
     }
     if (tid == 0) mbar_init(bar, 1);
-    // B = the coefficient table b_l(k), rows l (zero for l >= LT), two k per 32-bit word
+    // B = the coefficient table b_l(k), rows l (zero for l >= LT), two k per 32-bit word.  A row's
+    // words sit in 4 banks of the K-major layout, so the lanes of a warp take 8 rows x 4 words.
     for (int e = tid; e < CTC_N * KS * 8; e += CTC_THREADS) {
-        const int l = e / (KS * 8), kp = e - (e / (KS * 8)) * (KS * 8);
+        const int eh = e >> 5;
+        const int l = (eh / (KS * 2)) * 8 + ((e >> 2) & 7);
+        const int kp = (eh % (KS * 2)) * 4 + (e & 3);
         const int k = 2 * kp;
         const float b0 = (l < LT && k < K) ? cd.coef[k * LS + l] : 0.f;
         const float b1 = (l < LT && k + 1 < K) ? cd.coef[(k + 1) * LS + l] : 0.f;
@@ -150,10 +155,11 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
             }
         }
         __syncthreads();
-        // A = r' rows (tile, pair, re/im), two k per 32-bit word
+        // A = r' rows (tile, pair, re/im), two k per 32-bit word; lanes take 8 (tile, pair) x 4 words
         for (int e = tid; e < CTC_TILES * CTC_PCH * KS * 8; e += CTC_THREADS) {
-            const int kp = e % (KS * 8);
-            const int tj = e / (KS * 8);
+            const int eh = e >> 5;
+            const int tj = (eh / (KS * 2)) * 8 + ((e >> 2) & 7);
+            const int kp = (eh % (KS * 2)) * 4 + (e & 3);
             const int tt = tj / CTC_PCH, j = tj % CTC_PCH;
             const int k = 2 * kp;
             float2 v0 = make_float2(0.f, 0.f), v1 = v0;
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
             const int row = tid;             // tid < 128
             const int tt = row / (2 * CTC_PCH), j = (row / 2) % CTC_PCH, c = row & 1;
             const float inv = F16 ? 1.0f / scale[j] : 1.0f;
-            float* dst = reinterpret_cast<float*>(craw + (tt * CTC_PCH + j) * CTC_N) + c;
+            float* dst = reinterpret_cast<float*>(craw + (tt * CTC_PCH + j) * CTC_CRS) + c;
 #pragma unroll
             for (int l = 0; l < CTC_N; ++l) dst[2 * l] = d[l] * inv;
         }
@@ -220,10 +226,10 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
         // per voxel: sum over the chunk's pairs of conj(u') sum_l T_l(t) j^l (D_re + j D_im)_l
         if (tile_ok) {
             for (int j = 0; j < nc; ++j) {
-                const ChebVoxel cv = cheb_voxel(pt[t4 * CTC_PCH + j], o, op.ph);
+                const ChebVoxel cv = cheb_voxel(pt[t4 * CTC_PCH + j], o, cd.fc_hi, cd.fc_lo);
                 const float2 c0v = cis_turns_sfu(cv.th0);
                 const float t = cv.delta * cd.tau, t2 = t + t;
-                const float4* C = reinterpret_cast<const float4*>(craw + (t4 * CTC_PCH + j) * CTC_N);
+                const float4* C = reinterpret_cast<const float4*>(craw + (t4 * CTC_PCH + j) * CTC_CRS);
                 float4 q = C[0];                 // (D_0, D_1): factors 1 and j
                 float ar = fmaf(t, -q.w, q.x), ai = fmaf(t, q.z, q.y);
                 float Tp = 1.f, Tc = t;
@@ -290,6 +296,9 @@ template <bool F16>
 static const void* adj_cheb_tc_ptr_f(int LT)
 {
     switch (LT) {
+    case 10: return (const void*)adj_cheb_tc_kernel<10, F16>;
+    case 12: return (const void*)adj_cheb_tc_kernel<12, F16>;
+    case 14: return (const void*)adj_cheb_tc_kernel<14, F16>;
     case 16: return (const void*)adj_cheb_tc_kernel<16, F16>;
     case 18: return (const void*)adj_cheb_tc_kernel<18, F16>;
     case 20: return (const void*)adj_cheb_tc_kernel<20, F16>;

@@ -55,7 +55,7 @@ def load_library(path: str | None = None):
         "nfm_set_precision": (i, [vp, i]),
         "nfm_set_algorithm": (i, [vp, i]),
         "nfm_algorithm_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]),
-        "nfm_cheb_coefficients": (i, [d, i, i, vp]),
+        "nfm_cheb_coefficients": (i, [d, d, i, i, vp]),
         "nfm_autotune": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                              ctypes.POINTER(i)]),
         "nfm_set_regularizer": (i, [vp, d, d]),
@@ -92,11 +92,13 @@ def load_library(path: str | None = None):
     return L
 
 
-def cheb_coefficients(z_step: float, K: int, L: int):
-    """FP64 table b[k, l] = b_l(k z_step) of exp(-j z t) = sum_l (-j)^l b_l(z) T_l(t) (host only)."""
+def cheb_coefficients(z_step: float, K: int, L: int, k_center: float = 0.0):
+    """FP64 table b[k, l] = b_l((k - k_center) z_step) of exp(-j z t) = sum_l (-j)^l b_l(z) T_l(t)
+    (host only)."""
     import numpy as np
     out = np.zeros((int(K), int(L)), dtype=np.float64)
-    rc = load_library().nfm_cheb_coefficients(float(z_step), int(K), int(L), out.ctypes.data_as(ctypes.c_void_p))
+    rc = load_library().nfm_cheb_coefficients(float(z_step), float(k_center), int(K), int(L),
+                                              out.ctypes.data_as(ctypes.c_void_p))
     if rc != NFM_OK:
         raise NfmError(rc, "nfm_cheb_coefficients: invalid arguments")
     return out

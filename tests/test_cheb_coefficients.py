@@ -17,11 +17,12 @@ def nfm():
     return nfmimo
 
 
-@pytest.mark.parametrize("z_step,K,L", [(0.0, 1, 16), (0.12, 64, 24), (0.045, 128, 20), (1.1, 11, 32)])
-def test_table_equals_bessel(nfm, z_step, K, L):
+@pytest.mark.parametrize("z_step,K,L,kc", [(0.0, 1, 16, 0.0), (0.12, 64, 24, 0.0), (0.045, 128, 20, 0.0),
+                                           (1.1, 11, 32, 0.0), (0.12, 64, 16, 31.5), (0.3, 11, 12, 5.0)])
+def test_table_equals_bessel(nfm, z_step, K, L, kc):
     special = pytest.importorskip("scipy.special")
-    b = nfm.cheb_coefficients(z_step, K, L)
-    z = z_step * np.arange(K)[:, None]
+    b = nfm.cheb_coefficients(z_step, K, L, kc)
+    z = z_step * (np.arange(K)[:, None] - kc)
     l = np.arange(L)[None, :]
     want = np.where(l == 0, 1.0, 2.0) * special.jv(l, z)
     assert np.max(np.abs(b - want)) <= 1e-13
@@ -38,8 +39,17 @@ def test_series_reproduces_exponential(nfm):
     assert np.max(np.abs(series - exact)) <= 1e-9
 
 
+def test_centred_table_mirrors(nfm):
+    """J_l(-z) = (-1)^l J_l(z): a table centred on the band is mirror-symmetric up to (-1)^l."""
+    b = nfm.cheb_coefficients(0.2, 64, 20, 31.5)
+    sign = (-1.0) ** np.arange(20)
+    assert np.max(np.abs(b[::-1] - b * sign[None, :])) <= 1e-14
+
+
 def test_invalid_arguments(nfm):
     with pytest.raises(nfm.NfmError):
         nfm.cheb_coefficients(0.1, 0, 16)
     with pytest.raises(nfm.NfmError):
         nfm.cheb_coefficients(float("nan"), 4, 16)
+    with pytest.raises(nfm.NfmError):
+        nfm.cheb_coefficients(0.1, 4, 16, float("inf"))

@@ -19,7 +19,7 @@ def test_workloads_select_the_expansion(name):
     ctx = make_ctx(w.geom)
     algo, L, zmax = ctx.algorithm_info()
     print(f"[cheb] {name}: {algo}, L = {L}, z_max = {zmax:.2f}")
-    assert algo == "chebyshev" and L % 2 == 0 and 16 <= L <= 32
+    assert algo == "chebyshev" and L % 2 == 0 and 10 <= L <= 32
     assert zmax < L                         # the series needs more terms than z
 
 
