@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--algorithm", default="auto", choices=["auto", "direct", "chebyshev"],
                     help="FP32 operator algorithm for equally spaced frequencies")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default forward launch shape")
+    ap.add_argument("--forward-shape", default=None, metavar="T,G,P,C",
+                    help="apply this expansion-forward launch shape (threads, lanes per group, pairs per CTA, "
+                         "chunks) instead of autotuning, e.g. one an earlier run printed")
     ap.add_argument("--study", default=None, choices=["paper_like", "time_to_nmse"],
                     help="run a study instead of the bench line: the Sec. V PGM vs SPGM comparison on a "
                          "paper-shaped scene, or SPGM time to the oracle's NMSE (small and mid workloads)")
@@ -474,7 +477,13 @@ def run_ours(args):
         ctx.set_algorithm(args.algorithm)
         y, eta, lam = build_problem(torch, ctx, w, seed_offset=rank)
         algo, cheb_L, cheb_zmax = ctx.algorithm_info()
-        shape = ctx.autotune(w.pairs_per_batch) if (algo == "chebyshev" and not args.no_autotune) else None
+        shape = None
+        if algo == "chebyshev" and args.forward_shape:
+            t, g, p, c = (int(x) for x in args.forward_shape.split(","))
+            shape = {"algorithm": "chebyshev", "threads": t, "lanes_per_group": g, "pairs_per_cta": p, "chunks": c}
+            ctx.set_forward_shape(w.pairs_per_batch, shape)
+        elif algo == "chebyshev" and not args.no_autotune:
+            shape = ctx.autotune(w.pairs_per_batch)
         if shape is not None:
             algo = shape["algorithm"]          # with "auto" the tuner may keep the direct recurrence
         E = args.warmup + args.steps

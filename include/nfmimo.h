@@ -160,6 +160,19 @@ int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_m
 int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm, int* threads, int* lanes_per_group, int* pairs_per_cta,
                  int* chunks);
 
+/* Apply a forward launch shape for minibatches of n_pairs pairs without
+ * timing anything (for example one that nfm_autotune returned in an earlier
+ * run): threads 64 or 128, lanes_per_group 4 or 8, pairs_per_cta a power of
+ * two in [4, threads / lanes_per_group], chunks in [1, number of 8x4x4 voxel
+ * tiles].  algorithm NFM_ALGO_DIRECT keeps the direct recurrence for that
+ * minibatch size under NFM_ALGO_AUTO (the shape is then ignored).  Replaces
+ * any earlier shape for n_pairs.  Errors: NFM_ERR_ARG (a value outside those
+ * ranges, n_pairs outside [1, P], or a shape that needs more shared memory
+ * than the device has), NFM_ERR_STATE (no geometry, or the expansion is not
+ * available). */
+int nfm_set_forward_shape(nfm_ctx* ctx, int n_pairs, int algorithm, int threads, int lanes_per_group,
+                          int pairs_per_cta, int chunks);
+
 /* Host-only helper (no GPU needed): the expansion coefficients
  * out[k*L + l] = b_l((k - k_center) z_step), l < L, k < K, of
  *   exp(-j z t) = sum_l (-j)^l b_l(z) T_l(t)   (b_0 = J_0(z), b_l = 2 J_l(z)),

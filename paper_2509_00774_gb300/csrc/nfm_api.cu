@@ -233,6 +233,14 @@ void prof_pair(nfm_ctx* ctx, int kind, int a, int b)
 // b_l(k), l < L, of exp(-j z t) = sum_l (-j)^l b_l T_l(t) at z = k z_step (b_0 = J_0(z),
 // b_l = 2 J_l(z)), by Chebyshev-Gauss quadrature of (eps_l / pi) int_0^pi e^{-j z cos th} cos(l th) dth
 // with Q = 2L + 64 nodes (exact up to aliasing from degree >= 2Q - L).  FP64, row-major [K][L].
+// Multiplier of the division n / d = (n * m) >> 40 (0 <= n < 2^24, 1 <= d < 2^16): m = floor(2^40 / d) + 1
+// = 2^40/d + e with 0 < e <= 1, so n m / 2^40 = n/d + n e / 2^40 and the added n e / 2^40 < 1/d keeps the
+// floor exact (Granlund and Montgomery, division by invariant integers using multiplication).
+unsigned long long tile_div_magic(int d)
+{
+    return ((1ull << 40) / (unsigned long long)d) + 1ull;
+}
+
 void cheb_coefficients(double z_step, double k_center, int K, int L, double* out)
 {
     const double pi = 3.14159265358979323846;
@@ -879,6 +887,11 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     gd.tiles_y = (g.ny + TILE_Y - 1) / TILE_Y;
     gd.tiles_z = (g.nz + TILE_Z - 1) / TILE_Z;
     gd.n_tiles = gd.tiles_x * gd.tiles_y * gd.tiles_z;
+    gd.mx = gd.my = 0;
+    if (gd.n_tiles < (1 << 24) && gd.tiles_x < (1 << 16) && gd.tiles_y < (1 << 16)) {
+        gd.mx = tile_div_magic(gd.tiles_x);
+        gd.my = tile_div_magic(gd.tiles_y);
+    }
     auto split = [](double x, float& h, float& l) {
         h = (float)x;
         l = (float)(x - (double)h);
@@ -1133,6 +1146,32 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out
     if (threads_out) *threads_out = best_sh.threads;
     if (pairs_per_cta_out) *pairs_per_cta_out = best_sh.pch;
     if (chunks_out) *chunks_out = (int)best_sh.nch;
+    return NFM_OK;
+}
+
+int nfm_set_forward_shape(nfm_ctx* ctx, int n_pairs, int algorithm, int threads, int lanes_per_group,
+                          int pairs_per_cta, int chunks)
+{
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (n_pairs < 1 || n_pairs > ctx->P) return fail(ctx, NFM_ERR_ARG, "n_pairs = %d outside [1, P]", n_pairs);
+    if (ctx->cheb_L == 0 || !ctx->uniform) return fail(ctx, NFM_ERR_STATE, "the expansion is not available here");
+    if (algorithm != NFM_ALGO_CHEBYSHEV && algorithm != NFM_ALGO_DIRECT)
+        return fail(ctx, NFM_ERR_ARG, "algorithm must be NFM_ALGO_CHEBYSHEV or NFM_ALGO_DIRECT");
+    if (threads != 64 && threads != 128) return fail(ctx, NFM_ERR_ARG, "threads must be 64 or 128");
+    if (lanes_per_group != 4 && lanes_per_group != 8) return fail(ctx, NFM_ERR_ARG, "lanes_per_group must be 4 or 8");
+    const int ng = threads / lanes_per_group;
+    if (pairs_per_cta < 4 || pairs_per_cta > ng || (pairs_per_cta & (pairs_per_cta - 1)))
+        return fail(ctx, NFM_ERR_ARG, "pairs_per_cta must be a power of two in [4, %d]", ng);
+    if (chunks < 1 || chunks > ctx->gd.n_tiles) return fail(ctx, NFM_ERR_ARG, "chunks outside [1, %d]", ctx->gd.n_tiles);
+    ChebShape sh;
+    NFM_TRY(cheb_shape(ctx, n_pairs, threads, lanes_per_group, pairs_per_cta, 0.0, chunks, &sh));
+    for (size_t i = 0; i < ctx->fwd_tuned.size(); ++i)
+        if (ctx->fwd_tuned[i].n_pairs == n_pairs) {
+            ctx->fwd_tuned.erase(ctx->fwd_tuned.begin() + i);
+            break;
+        }
+    ctx->fwd_tuned.push_back({n_pairs, sh.threads, sh.group, sh.pch, (int)sh.nch, algorithm == NFM_ALGO_DIRECT});
     return NFM_OK;
 }
 

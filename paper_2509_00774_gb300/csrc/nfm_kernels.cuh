@@ -75,6 +75,12 @@ struct ChebDesc {
     int k_pad;               // K rounded up to a multiple of 4
     float fc_hi, fc_lo;      // f_c / c (cycles per metre) as hi + lo, f_c = f_0 + k_c df the band centre
 };
+// Shared-memory row stride (floats) of the forward's coefficient table: round4(L), plus 4 where that is a
+// multiple of 16, so that the 4 rows a lane group reads at once start in different banks.
+__host__ __device__ constexpr int fwd_coef_stride(int LT)
+{
+    return ((LT + 3) & ~3) % 16 == 0 ? ((LT + 3) & ~3) + 4 : ((LT + 3) & ~3);
+}
 size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group);
 size_t adj_cheb_smem_bytes(int LT, int k_pad);
 const void* fwd_cheb_kernel_ptr(int LT, int group);

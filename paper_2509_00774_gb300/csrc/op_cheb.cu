@@ -37,6 +37,7 @@ template <int LT, int G>
 __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
 {
     constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
+    constexpr int LSS = fwd_coef_stride(LT); // its row stride in shared memory
     extern __shared__ __align__(16) unsigned char smem[];
     const int ng = blockDim.x / G;           // groups per CTA
     const int PCH = a.VS;                    // pairs per CTA (power of two dividing ng)
@@ -44,8 +45,8 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     const int K = op.K;
     const int KP = cd.k_pad;                 // table rows (multiple of 4, zero rows beyond K)
     const int AS = KP + 4;                   // accumulator row stride (float2), staggers the banks
-    float* coef = reinterpret_cast<float*>(smem);                            // [KP][LS]
-    float2* acc = reinterpret_cast<float2*>(coef + KP * LS);                 // [ng][AS]
+    float* coef = reinterpret_cast<float*>(smem);                            // [KP][LSS]
+    float2* acc = reinterpret_cast<float2*>(coef + KP * LSS);                // [ng][AS]
     VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + ng * AS);       // [TILE_V]
     float2* s_st = reinterpret_cast<float2*>(voff + TILE_V);                 // [2][TS][TILE_V]
     AntTile* ant_st = reinterpret_cast<AntTile*>(s_st + 2 * TS * TILE_V);    // [2][ng][2]
@@ -65,7 +66,8 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     // Constants and the pair list: no kernel of this library writes them, so they are read
     // before the wait on the previous kernel (which may still be running its tail).
     for (int i = tid; i < KP * LS / 4; i += nt)
-        reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
+        reinterpret_cast<float4*>(coef)[(i / (LS / 4)) * (LSS / 4) + i % (LS / 4)] =
+            reinterpret_cast<const float4*>(cd.coef)[i];
     for (int i = tid; i < ng * AS; i += nt) acc[i] = make_float2(0.f, 0.f);
     for (int v = tid; v < TILE_V; v += nt)
         voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
@@ -172,8 +174,8 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
             const float2 W = tile_step_cis_exact(P, 2 * G);
             for (int k0 = ln; k0 < K; k0 += 2 * G) {
                 const int k1 = k0 + G;                   // may be >= K: zero table row, not stored
-                const float* b0 = coef + k0 * LS;
-                const float* b1 = coef + min(k1, KP - 1) * LS;
+                const float* b0 = coef + k0 * LSS;
+                const float* b1 = coef + min(k1, KP - 1) * LSS;
                 float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
 #pragma unroll
                 for (int l = 0; l < LT; l += 4) {
@@ -272,6 +274,11 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     // first chunk's pair tiles are read before the wait on the previous kernel
     if (tid < min(CHEB_ADJ_PCHUNK, a.n_pairs)) pt[tid] = load_pair_tile(op, a.pairs[tid], tile);
     pdl_wait();                              // r comes from the previous kernel
+    // the voxel's iterate for the fused update, loaded now so that its latency overlaps the r copies
+    const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
+    const bool in_grid = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
+    const size_t n = in_grid ? ((size_t)iz * op.g.ny + iy) * op.g.nx + ix : 0;
+    const float2 s_old = (a.s && in_grid) ? a.s[n] : make_float2(0.f, 0.f);
 
     for (int c0 = 0; c0 < a.n_pairs; c0 += CHEB_ADJ_PCHUNK) {
         const int nc = min(CHEB_ADJ_PCHUNK, a.n_pairs - c0);
@@ -279,11 +286,18 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
             __syncthreads();
             if (tid < nc) pt[tid] = load_pair_tile(op, a.pairs[c0 + tid], tile);
         }
+        // the chunk's residual rows into rp: every thread issues all its copies before it waits, so the
+        // loads overlap (one L2 round trip instead of one per element); it transforms the same elements
+        for (int j = j_first; j < nc; j += j_step)
+            for (int k = k_first; k < K; k += k_step)
+                cp_async_8(rp + j * RS + k, a.r + (size_t)(c0 + j) * K + k, true);
+        cp_async_commit();
+        cp_async_wait_all();
         __syncthreads();
         // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c}
         for (int j = j_first; j < nc; j += j_step) {
             for (int k = k_first; k < K; k += k_step) {
-                float2 v = a.r[(size_t)(c0 + j) * K + k];
+                float2 v = rp[j * RS + k];
                 if (op.pulse) v = cmul_conj(v, op.pulse[k]);
                 rp[j * RS + k] = cmul(v, tile_step_cis(pt[j], k));
             }
@@ -358,11 +372,9 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     }
     pdl_launch_dependents();
 
-    const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
-    if (ix >= op.g.nx || iy >= op.g.ny || iz >= op.g.nz) return;
-    const size_t n = ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
+    if (!in_grid) return;
     if (a.s) {
-        const float2 sv = a.s[n];
+        const float2 sv = s_old;
         const float zr = fmaf(-a.step, gr, sv.x);
         const float zi = fmaf(-a.step, gi, sv.y);
         const float mag = sqrtf(zr * zr + zi * zi);
@@ -422,8 +434,7 @@ size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group)
 {
     const int ng = threads / group;
     const int TS = ng / pch;
-    const int LS = (LT + 3) & ~3;
-    return (size_t)k_pad * LS * sizeof(float) + (size_t)ng * (k_pad + 4) * sizeof(float2) +
+    return (size_t)k_pad * fwd_coef_stride(LT) * sizeof(float) + (size_t)ng * (k_pad + 4) * sizeof(float2) +
            TILE_V * sizeof(VoxelOffset) + (size_t)2 * TS * TILE_V * sizeof(float2) +
            (size_t)2 * ng * 2 * sizeof(AntTile) + (size_t)pch * sizeof(int);
 }

@@ -56,6 +56,7 @@ def load_library(path: str | None = None):
         "nfm_set_algorithm": (i, [vp, i]),
         "nfm_algorithm_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]),
         "nfm_cheb_coefficients": (i, [d, d, i, i, vp]),
+        "nfm_set_forward_shape": (i, [vp, i, i, i, i, i, i]),
         "nfm_autotune": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                              ctypes.POINTER(i)]),
         "nfm_set_regularizer": (i, [vp, d, d]),
@@ -216,6 +217,14 @@ class Context:
                                            ctypes.byref(p), ctypes.byref(c)))
         return {"algorithm": {1: "direct", 2: "chebyshev"}[a.value], "threads": t.value, "lanes_per_group": g.value,
                 "pairs_per_cta": p.value, "chunks": c.value}
+
+    def set_forward_shape(self, n_pairs, shape):
+        """Apply a forward launch shape for n_pairs-pair minibatches without timing (e.g. a dict that
+        autotune returned earlier: "algorithm", "threads", "lanes_per_group", "pairs_per_cta", "chunks")."""
+        algo = {"chebyshev": 2, "direct": 1}[shape.get("algorithm", "chebyshev")]
+        self._check(self._lib.nfm_set_forward_shape(self._h, int(n_pairs), algo, int(shape["threads"]),
+                                                    int(shape["lanes_per_group"]), int(shape["pairs_per_cta"]),
+                                                    int(shape["chunks"])))
 
     def set_regularizer(self, w1=1.0, w2=0.0):
         """R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 for every SPGM/PGM step and the objective."""

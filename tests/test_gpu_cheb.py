@@ -178,3 +178,29 @@ def test_spgm_step_matches_composed_calls(name):
     rel = np.linalg.norm(a - b) / np.linalg.norm(b)
     print(f"[cheb] {name}: fused SPGM step vs composed calls rel_l2 = {rel:.2e}")
     assert rel <= 1e-5
+
+
+def test_set_forward_shape_applies_and_validates():
+    """A stored launch shape is applied without timing: same results as the autotuned forward with
+    that shape, and out-of-range shapes are rejected."""
+    from paper_2509_00774_gb300.nfmimo import NfmError
+    w = W.mid_T16R16_K64_64x64x32()
+    pairs = to_dev(I.epoch_permutation(w.geom.P, 6, 0)[:16], "int32")
+    s = to_dev(I.complex_gaussian(w.geom.N, 63))
+    tuned = make_ctx(w.geom, algorithm="chebyshev")
+    shape = tuned.autotune(16)
+    y_tuned = to_host(tuned.forward(pairs, s))
+    ctx = make_ctx(w.geom, algorithm="chebyshev")
+    ctx.set_forward_shape(16, shape)
+    assert np.array_equal(to_host(ctx.forward(pairs, s)), y_tuned)
+    for bad in ({"threads": 96, "lanes_per_group": 4, "pairs_per_cta": 4, "chunks": 8},
+                {"threads": 128, "lanes_per_group": 4, "pairs_per_cta": 6, "chunks": 8},
+                {"threads": 128, "lanes_per_group": 4, "pairs_per_cta": 4, "chunks": 0},
+                {"threads": 128, "lanes_per_group": 4, "pairs_per_cta": 4, "chunks": 10 ** 6}):
+        with pytest.raises(NfmError):
+            ctx.set_forward_shape(16, bad)
+    balanced = {"threads": 128, "lanes_per_group": 4, "pairs_per_cta": 4, "chunks": 1000}   # < 1 stage per chunk
+    ctx.set_forward_shape(16, balanced)
+    y_b = to_host(ctx.forward(pairs, s))
+    rel = np.linalg.norm(y_b - y_tuned) / np.linalg.norm(y_tuned)
+    assert rel <= 1e-6
