@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + ng * AS);       // [TILE_V]
     float2* s_st = reinterpret_cast<float2*>(voff + TILE_V);                 // [2][TS][TILE_V]
     AntTile* ant_st = reinterpret_cast<AntTile*>(s_st + 2 * TS * TILE_V);    // [2][ng][2]
-    int* pair_s = reinterpret_cast<int*>(ant_st + 2 * ng * 2);               // [PCH]
+    int* pair_s = reinterpret_cast<int*>(ant_st + 2 * ng * 2);               // [PCH] pair or -1
 
     const int tid = threadIdx.x;
     const int nt = blockDim.x;
@@ -64,16 +64,21 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     const int n_stages = (t_end - t_begin + TS - 1) / TS;
 
     // Constants and the pair list: no kernel of this library writes them, so they are read
-    // before the wait on the previous kernel (which may still be running its tail).
+    // before the wait on the previous kernel (which may still be running its tail).  (Plain loads:
+    // asynchronous copies of the table measured slower here.)
     for (int i = tid; i < KP * LS / 4; i += nt)
         reinterpret_cast<float4*>(coef)[(i / (LS / 4)) * (LSS / 4) + i % (LS / 4)] =
             reinterpret_cast<const float4*>(cd.coef)[i];
-    for (int i = tid; i < ng * AS; i += nt) acc[i] = make_float2(0.f, 0.f);
     for (int v = tid; v < TILE_V; v += nt)
         voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
     if (tid < PCH) {
         const int sp = pair_base + tid;
-        pair_s[tid] = sp < a.n_pairs ? a.pairs[sp] : -1;
+        int pair = sp < a.n_pairs ? a.pairs[sp] : -1;
+        if (sp < a.n_pairs && (pair < 0 || pair >= op.P)) {   // flagged; pair 0 keeps every access in bounds
+            atomicOr(op.err, ERRF_PAIR);
+            pair = 0;
+        }
+        pair_s[tid] = pair;
     }
     __syncthreads();
 
@@ -94,20 +99,19 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     };
     auto load_s = [&](int q) {                    // the stage's scene values (zero outside the grid)
         const int buf = q & 1;
-        for (int i = tid; i < TS * TILE_V; i += nt) {
-            const int sl = i / TILE_V, v = i % TILE_V;
+        for (int sl = 0; sl < TS; ++sl) {
             const int tile = t_begin + q * TS + sl;
-            bool in = false;
-            const float2* src = a.s;
-            if (tile < t_end) {
-                int tx, ty, tz;
-                tile_coords(op.g, tile, tx, ty, tz);
-                const int ix = tx * TILE_X + v % TILE_X, iy = ty * TILE_Y + (v / TILE_X) % TILE_Y,
-                          iz = tz * TILE_Z + v / (TILE_X * TILE_Y);
-                in = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
-                if (in) src = a.s + ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
+            if (tile >= t_end) break;             // slots past the chunk stay idle
+            int tx, ty, tz;
+            tile_coords(op.g, tile, tx, ty, tz);
+            const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TILE_Z;
+            const bool full = x0 + TILE_X <= op.g.nx && y0 + TILE_Y <= op.g.ny && z0 + TILE_Z <= op.g.nz;
+            for (int v = tid; v < TILE_V; v += nt) {
+                const int ix = x0 + v % TILE_X, iy = y0 + (v / TILE_X) % TILE_Y, iz = z0 + v / (TILE_X * TILE_Y);
+                const bool in = full || (ix < op.g.nx && iy < op.g.ny && iz < op.g.nz);
+                const float2* src = in ? a.s + ((size_t)iz * op.g.ny + iy) * op.g.nx + ix : a.s;
+                cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, src, in);
             }
-            cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, src, in);
         }
     };
 
@@ -200,16 +204,20 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
                         si1 = fmaf(y.w, mr[l + 3], si1);
                     }
                 }
-                {                                        // y_k += P_k S_k, P_k = (c.x, -c.y)
-                    float2 av = accg[k0];
-                    av.x += fmaf(c0.x, sr0, c0.y * si0);
-                    av.y += fmaf(c0.x, si0, -c0.y * sr0);
+                {                                        // y_k (+)= P_k S_k, P_k = (c.x, -c.y)
+                    float2 av = make_float2(fmaf(c0.x, sr0, c0.y * si0), fmaf(c0.x, si0, -c0.y * sr0));
+                    if (q > 0) {                         // the first stage writes, later stages add
+                        av.x += accg[k0].x;
+                        av.y += accg[k0].y;
+                    }
                     accg[k0] = av;
                 }
                 if (k1 < K) {
-                    float2 av = accg[k1];
-                    av.x += fmaf(c1.x, sr1, c1.y * si1);
-                    av.y += fmaf(c1.x, si1, -c1.y * sr1);
+                    float2 av = make_float2(fmaf(c1.x, sr1, c1.y * si1), fmaf(c1.x, si1, -c1.y * sr1));
+                    if (q > 0) {
+                        av.x += accg[k1].x;
+                        av.y += accg[k1].y;
+                    }
                     accg[k1] = av;
                 }
                 c0 = cmul(c0, W);
@@ -221,13 +229,15 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     }
     pdl_launch_dependents();
 
-    // sum the stage slots of each pair in slot order and write the chunk partial
+    // sum the live stage slots of each pair in slot order and write the chunk partial (every pair
+    // and tile of the chunk wrote its row in the first stage)
+    const int live_slots = min(TS, t_end - t_begin);
     for (int p = 0; p < PCH; ++p) {
         const int sp = pair_base + p;
         if (sp >= a.n_pairs) break;
         for (int k = tid; k < K; k += nt) {
             float2 sum = acc[p * AS + k];
-            for (int sl = 1; sl < TS; ++sl) {
+            for (int sl = 1; sl < live_slots; ++sl) {
                 const float2 x = acc[(sl * PCH + p) * AS + k];
                 sum.x += x.x;
                 sum.y += x.y;
