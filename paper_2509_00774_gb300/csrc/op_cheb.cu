@@ -262,6 +262,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     float2* rp = reinterpret_cast<float2*>(coef + KP * LS);               // [PCH][RS]
     float2* Cs = rp + CHEB_ADJ_PCHUNK * RS;                                 // [PCH][LS]
     PairTile* pt = reinterpret_cast<PairTile*>(Cs + CHEB_ADJ_PCHUNK * LS);  // [PCH]
+    float2* w16 = reinterpret_cast<float2*>(pt + CHEB_ADJ_PCHUNK);          // [PCH] e^{+j 2 pi 16 df D_c/c}
 
     const int tile = blockIdx.x;
     const int tid = threadIdx.x;
@@ -282,7 +283,10 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     float gr = 0.f, gi = 0.f;
     // the pair list and the geometry tables are never written by this library's kernels, so the
     // first chunk's pair tiles are read before the wait on the previous kernel
-    if (tid < min(CHEB_ADJ_PCHUNK, a.n_pairs)) pt[tid] = load_pair_tile(op, a.pairs[tid], tile);
+    if (tid < min(CHEB_ADJ_PCHUNK, a.n_pairs)) {
+        pt[tid] = load_pair_tile(op, a.pairs[tid], tile);
+        w16[tid] = tile_step_cis_exact(pt[tid], 16);
+    }
     pdl_wait();                              // r comes from the previous kernel
     // the voxel's iterate for the fused update, loaded now so that its latency overlaps the r copies
     const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
@@ -294,7 +298,10 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
         const int nc = min(CHEB_ADJ_PCHUNK, a.n_pairs - c0);
         if (c0 > 0) {
             __syncthreads();
-            if (tid < nc) pt[tid] = load_pair_tile(op, a.pairs[c0 + tid], tile);
+            if (tid < nc) {
+                pt[tid] = load_pair_tile(op, a.pairs[c0 + tid], tile);
+                w16[tid] = tile_step_cis_exact(pt[tid], 16);
+            }
         }
         // the chunk's residual rows into rp: every thread issues all its copies before it waits, so the
         // loads overlap (one L2 round trip instead of one per element); it transforms the same elements
@@ -304,12 +311,19 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
-        // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c}
-        for (int j = j_first; j < nc; j += j_step) {
-            for (int k = k_first; k < K; k += k_step) {
+        // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c}: 16 threads per pair take k = k0 + 16 m; the phasor
+        // starts from the SFU and advances by the pair's exact 16-step phasor (from the SFU again every
+        // 8 steps, so at most 7 rounded products accumulate)
+        for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16) {
+            const int k0 = tid % 16;
+            const PairTile& P = pt[j];
+            const float2 W = w16[j];
+            float2 c = make_float2(1.f, 0.f);
+            for (int k = k0, m = 0; k < K; k += 16, ++m) {
+                c = (m & 7) == 0 ? tile_step_cis(P, k) : cmul(c, W);
                 float2 v = rp[j * RS + k];
                 if (op.pulse) v = cmul_conj(v, op.pulse[k]);
-                rp[j * RS + k] = cmul(v, tile_step_cis(pt[j], k));
+                rp[j * RS + k] = cmul(v, c);
             }
         }
         __syncthreads();
@@ -453,7 +467,8 @@ size_t adj_cheb_smem_bytes(int LT, int k_pad)
 {
     const int LS = (LT + 3) & ~3;
     return (size_t)k_pad * LS * sizeof(float) + (size_t)CHEB_ADJ_PCHUNK * (k_pad + 2) * sizeof(float2) +
-           (size_t)CHEB_ADJ_PCHUNK * LS * sizeof(float2) + (size_t)CHEB_ADJ_PCHUNK * sizeof(PairTile);
+           (size_t)CHEB_ADJ_PCHUNK * LS * sizeof(float2) + (size_t)CHEB_ADJ_PCHUNK * sizeof(PairTile) +
+           (size_t)CHEB_ADJ_PCHUNK * sizeof(float2);
 }
 
 template <int G>
