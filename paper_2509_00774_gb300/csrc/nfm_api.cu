@@ -233,12 +233,14 @@ void prof_pair(nfm_ctx* ctx, int kind, int a, int b)
 // b_l(k), l < L, of exp(-j z t) = sum_l (-j)^l b_l T_l(t) at z = k z_step (b_0 = J_0(z),
 // b_l = 2 J_l(z)), by Chebyshev-Gauss quadrature of (eps_l / pi) int_0^pi e^{-j z cos th} cos(l th) dth
 // with Q = 2L + 64 nodes (exact up to aliasing from degree >= 2Q - L).  FP64, row-major [K][L].
-// Multiplier of the division n / d = (n * m) >> 40 (0 <= n < 2^24, 1 <= d < 2^16): m = floor(2^40 / d) + 1
-// = 2^40/d + e with 0 < e <= 1, so n m / 2^40 = n/d + n e / 2^40 and the added n e / 2^40 < 1/d keeps the
-// floor exact (Granlund and Montgomery, division by invariant integers using multiplication).
-unsigned long long tile_div_magic(int d)
+// Multiplier of the division n / d = umulhi(n, m) = floor(n m / 2^32) for 0 <= n < n_max: m = floor(2^32/d) + 1
+// = 2^32/d + e with 0 < e <= 1, so n m / 2^32 = n/d + n e / 2^32, and the added n e / 2^32 < 1/d keeps the
+// floor exact while n_max d <= 2^32 (Granlund and Montgomery, division by invariant integers using
+// multiplication).  0 (plain division) when that bound fails or d = 1 (m would not fit 32 bits).
+unsigned tile_div_magic(long long n_max, int d)
 {
-    return ((1ull << 40) / (unsigned long long)d) + 1ull;
+    if (d < 2 || n_max * (long long)d > (1ll << 32)) return 0u;
+    return (unsigned)((1ull << 32) / (unsigned long long)d + 1ull);
 }
 
 void cheb_coefficients(double z_step, double k_center, int K, int L, double* out)
@@ -887,11 +889,8 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     gd.tiles_y = (g.ny + TILE_Y - 1) / TILE_Y;
     gd.tiles_z = (g.nz + TILE_Z - 1) / TILE_Z;
     gd.n_tiles = gd.tiles_x * gd.tiles_y * gd.tiles_z;
-    gd.mx = gd.my = 0;
-    if (gd.n_tiles < (1 << 24) && gd.tiles_x < (1 << 16) && gd.tiles_y < (1 << 16)) {
-        gd.mx = tile_div_magic(gd.tiles_x);
-        gd.my = tile_div_magic(gd.tiles_y);
-    }
+    gd.mx = tile_div_magic(gd.n_tiles, gd.tiles_x);
+    gd.my = tile_div_magic(gd.n_tiles, gd.tiles_y);
     auto split = [](double x, float& h, float& l) {
         h = (float)x;
         l = (float)(x - (double)h);

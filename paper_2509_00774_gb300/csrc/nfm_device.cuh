@@ -53,9 +53,9 @@ struct GridDesc {
     int tiles_x, tiles_y, tiles_z;
     int n_tiles;
     float dx_hi, dx_lo, dy_hi, dy_lo, dz_hi, dz_lo;
-    // n / tiles_x = (n * mx) >> 40 and n / tiles_y = (n * my) >> 40 for 0 <= n < 2^24 (division by an
-    // invariant integer with a rounded-up reciprocal: exact while n * divisor < 2^40); 0 = divide
-    unsigned long long mx, my;
+    // n / tiles_x = umulhi(n, mx) and n / tiles_y = umulhi(n, my) for 0 <= n < n_tiles (division by an
+    // invariant integer with a rounded-up reciprocal: exact while n * divisor < 2^32); 0 = divide
+    unsigned mx, my;
 };
 
 struct PhaseConsts {
@@ -209,9 +209,9 @@ __device__ __forceinline__ PVGeom pair_voxel(const PairTile& pt, const VoxelOffs
 
 __device__ __forceinline__ void tile_coords(const GridDesc& g, int tile, int& tx, int& ty, int& tz)
 {
-    const int rest = g.mx ? (int)(((unsigned long long)tile * g.mx) >> 40) : tile / g.tiles_x;
+    const int rest = g.mx ? (int)__umulhi((unsigned)tile, g.mx) : tile / g.tiles_x;
     tx = tile - rest * g.tiles_x;
-    tz = g.my ? (int)(((unsigned long long)rest * g.my) >> 40) : rest / g.tiles_y;
+    tz = g.my ? (int)__umulhi((unsigned)rest, g.my) : rest / g.tiles_y;
     ty = rest - tz * g.tiles_y;
 }
 

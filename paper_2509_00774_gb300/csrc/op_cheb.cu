@@ -97,6 +97,12 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
             }
         }
     };
+    // offset of this thread's voxel slot(s) within a tile in the scene vector (grid rows of nx,
+    // planes of nx ny); a full tile's values are then one add away from its origin
+    const int plane = op.g.nx * op.g.ny;
+    auto slot_offset = [&](int v) {
+        return (v / (TILE_X * TILE_Y)) * plane + ((v / TILE_X) % TILE_Y) * op.g.nx + v % TILE_X;
+    };
     auto load_s = [&](int q) {                    // the stage's scene values (zero outside the grid)
         const int buf = q & 1;
         for (int sl = 0; sl < TS; ++sl) {
@@ -106,11 +112,14 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
             tile_coords(op.g, tile, tx, ty, tz);
             const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TILE_Z;
             const bool full = x0 + TILE_X <= op.g.nx && y0 + TILE_Y <= op.g.ny && z0 + TILE_Z <= op.g.nz;
+            const float2* origin = a.s + ((size_t)z0 * op.g.ny + y0) * op.g.nx + x0;
             for (int v = tid; v < TILE_V; v += nt) {
-                const int ix = x0 + v % TILE_X, iy = y0 + (v / TILE_X) % TILE_Y, iz = z0 + v / (TILE_X * TILE_Y);
-                const bool in = full || (ix < op.g.nx && iy < op.g.ny && iz < op.g.nz);
-                const float2* src = in ? a.s + ((size_t)iz * op.g.ny + iy) * op.g.nx + ix : a.s;
-                cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, src, in);
+                bool in = full;
+                if (!full) {
+                    const int ix = x0 + v % TILE_X, iy = y0 + (v / TILE_X) % TILE_Y, iz = z0 + v / (TILE_X * TILE_Y);
+                    in = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
+                }
+                cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, in ? origin + slot_offset(v) : a.s, in);
             }
         }
     };
@@ -230,19 +239,27 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     pdl_launch_dependents();
 
     // sum the live stage slots of each pair in slot order and write the chunk partial (every pair
-    // and tile of the chunk wrote its row in the first stage)
+    // and tile of the chunk wrote its row in the first stage); the threads split as (nt / K) pairs
+    // x K frequencies when K <= nt
     const int live_slots = min(TS, t_end - t_begin);
-    for (int p = 0; p < PCH; ++p) {
+    const bool kfit = K <= nt;
+    const int p_step = kfit ? nt / K : 1;
+    const int p_first = kfit ? (tid / K < p_step ? tid / K : PCH) : 0;
+    const int k_first = kfit ? tid % K : tid, k_step = kfit ? K : nt;
+    for (int p = p_first; p < PCH; p += p_step) {
         const int sp = pair_base + p;
         if (sp >= a.n_pairs) break;
-        for (int k = tid; k < K; k += nt) {
-            float2 sum = acc[p * AS + k];
+        float2* out = a.partial + ((size_t)chunk * a.n_slots + sp) * K;
+        for (int k = k_first; k < K; k += k_step) {
+            const float2* col = acc + p * AS + k;
+            float2 sum = col[0];
+#pragma unroll 4
             for (int sl = 1; sl < live_slots; ++sl) {
-                const float2 x = acc[(sl * PCH + p) * AS + k];
+                const float2 x = col[sl * PCH * AS];
                 sum.x += x.x;
                 sum.y += x.y;
             }
-            a.partial[((size_t)chunk * a.n_slots + sp) * K + k] = sum;
+            out[k] = sum;
         }
     }
 }
