@@ -290,13 +290,6 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     for (int i = tid; i < KP * LS / 4; i += CHEB_THREADS)
         reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
     constexpr int LQ = LS / 4;
-    // (pair, k) items of the r' stage: threads split as (CHEB_THREADS / K) pairs x K frequencies
-    // when K <= CHEB_THREADS, else every thread strides over k of each pair
-    const bool kfit = K <= CHEB_THREADS;
-    const int j_step = kfit ? CHEB_THREADS / K : 1;
-    const int j_first = kfit ? (tid / K < j_step ? tid / K : 1 << 30) : 0;
-    const int k_first = kfit ? tid % K : tid;
-    const int k_step = kfit ? K : CHEB_THREADS;
     float gr = 0.f, gi = 0.f;
     // the pair list and the geometry tables are never written by this library's kernels, so the
     // first chunk's pair tiles are read before the wait on the previous kernel
@@ -320,27 +313,32 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
                 w16[tid] = tile_step_cis_exact(pt[tid], 16);
             }
         }
-        // the chunk's residual rows into rp: every thread issues all its copies before it waits, so the
-        // loads overlap (one L2 round trip instead of one per element); it transforms the same elements
-        for (int j = j_first; j < nc; j += j_step)
-            for (int k = k_first; k < K; k += k_step)
-                cp_async_8(rp + j * RS + k, a.r + (size_t)(c0 + j) * K + k, true);
+        // The chunk's residual rows into rp, 16 threads per pair taking k = k0 + 16 m: every thread issues
+        // all its copies before it waits, so the loads overlap (one L2 round trip), and later transforms
+        // the same elements.
+        const int k0 = tid % 16;
+        for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16) {
+            const float2* src = a.r + (size_t)(c0 + j) * K;
+            for (int k = k0; k < K; k += 16) cp_async_8(rp + j * RS + k, src + k, true);
+        }
         cp_async_commit();
         cp_async_wait_all();
-        __syncthreads();
-        // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c}: 16 threads per pair take k = k0 + 16 m; the phasor
-        // starts from the SFU and advances by the pair's exact 16-step phasor (from the SFU again every
-        // 8 steps, so at most 7 rounded products accumulate)
+        __syncthreads();                     // pt and w16 of this chunk
+        // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c}: the phasor starts from the SFU and advances by the
+        // pair's exact 16-step phasor, restarted from the SFU every 8 steps (at most 7 rounded products)
         for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16) {
-            const int k0 = tid % 16;
             const PairTile& P = pt[j];
             const float2 W = w16[j];
-            float2 c = make_float2(1.f, 0.f);
-            for (int k = k0, m = 0; k < K; k += 16, ++m) {
-                c = (m & 7) == 0 ? tile_step_cis(P, k) : cmul(c, W);
-                float2 v = rp[j * RS + k];
-                if (op.pulse) v = cmul_conj(v, op.pulse[k]);
-                rp[j * RS + k] = cmul(v, c);
+            float2* row = rp + j * RS;
+            for (int kb = k0; kb < K; kb += 16 * 8) {
+                float2 c = tile_step_cis(P, kb);
+                const int kend = min(K, kb + 16 * 8);
+                for (int k = kb; k < kend; k += 16) {
+                    float2 v = row[k];
+                    if (op.pulse) v = cmul_conj(v, op.pulse[k]);
+                    row[k] = cmul(v, c);
+                    c = cmul(c, W);
+                }
             }
         }
         __syncthreads();
