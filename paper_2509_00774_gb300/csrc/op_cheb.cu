@@ -2,21 +2,26 @@
 // the frequency dependence (equally spaced frequencies f_k = f0 + k df).
 //
 // For a (pair, tile) with centre path length D_c and a voxel with path length
-// D = D_c + delta, the element factors as
+// D = D_c + delta, and the band centre f_c = f0 + k_c df, k_c = (K - 1)/2,
 //
-//   A_kv = p_k amp_v e^{-j 2 pi f0 D/c} e^{-j 2 pi k df D_c/c} e^{-j z_k t_v},
-//   t_v = delta_v / xi  (|t_v| <= 0.95 for every voxel slot),  z_k = 2 pi k df xi / c,
+//   f_k D = f0 D_c + f_c delta + k df D_c + (k - k_c) df delta,
+//
+// so the element factors as
+//
+//   A_kv = p_k amp_v e^{-j 2 pi (f0 D_c + f_c delta_v)/c} e^{-j 2 pi k df D_c/c} e^{-j z_k t_v},
+//   t_v = delta_v / xi  (|t_v| <= 0.95 for every voxel slot),  z_k = 2 pi (k - k_c) df xi / c,
 //
 // and the last factor has the Jacobi-Anger (Chebyshev) expansion
 //
 //   e^{-j z t} = sum_l (-j)^l b_l(z) T_l(t),   b_0 = J_0(z),  b_l = 2 J_l(z),
 //
-// truncated after L terms (L even, tail below 1e-7).  So per (pair, tile)
+// truncated after L terms (L even, tail below 1e-7 at the band edges |z| = z_max;
+// centring halves z_max and with it the number of terms).  So per (pair, tile)
 //
 //   forward:  y_k += P_k sum_l (-j)^l b_l(k) m_l,  m_l = sum_v u_v T_l(t_v),
-//             u_v = amp_v s_v e^{-j 2 pi f0 D_v/c},  P_k = e^{-j 2 pi k df D_c/c}
+//             u_v = amp_v s_v e^{-j 2 pi (f0 D_c + f_c delta_v)/c},  P_k = e^{-j 2 pi k df D_c/c}
 //   adjoint:  g_v += conj(u'_v) sum_l T_l(t_v) C_l,  C_l = j^l sum_k b_l(k) conj(p_k) r_k conj(P_k),
-//             u'_v = amp_v e^{-j 2 pi f0 D_v/c}.
+//             u'_v = amp_v e^{-j 2 pi (f0 D_c + f_c delta_v)/c}.
 //
 // The per-voxel work is L steps of the Chebyshev recurrence T_{l+1} = 2t T_l - T_{l-1}
 // (stable for |t| <= 0.95: rounding grows at most 3.2 l times) with two FMAs
