@@ -52,14 +52,16 @@ __host__ __device__ constexpr uint32_t ctc_idesc()
 }
 
 struct CtcSmem {   // byte offsets of the dynamic shared-memory regions (KS = K steps)
-    int a, b, pt, craw, scale, bar, tslot, total;
+    int a, b, pt, p8, craw, rbuf, scale, bar, tslot, total;
     __host__ __device__ CtcSmem(int KS)
     {
         a = 0;                                            // [split 2][KS][4096]
         b = a + 2 * KS * CTC_KSTEP_A;                     // [split 2][KS][1024]
         pt = b + 2 * KS * CTC_KSTEP_B;                    // [4 tiles][16 pairs] PairTile
-        craw = pt + CTC_TILES * CTC_PCH * (int)sizeof(PairTile);   // [4][16][CTC_CRS] float2 (D_re, D_im)
-        scale = craw + CTC_TILES * CTC_PCH * CTC_CRS * (int)sizeof(float2);   // [16] float
+        p8 = pt + CTC_TILES * CTC_PCH * (int)sizeof(PairTile);     // [4][16] float2 e^{+j 2 pi 8 df D_c/c}
+        craw = p8 + CTC_TILES * CTC_PCH * (int)sizeof(float2);     // [4][16][CTC_CRS] float2 (D_re, D_im)
+        rbuf = craw + CTC_TILES * CTC_PCH * CTC_CRS * (int)sizeof(float2);    // [16 pairs][16 KS] float2 r
+        scale = rbuf + CTC_PCH * 16 * KS * (int)sizeof(float2);           // [16] float
         bar = scale + CTC_PCH * (int)sizeof(float);       // one mbarrier (8-byte aligned)
         tslot = bar + 8;
         total = tslot + 16;
@@ -79,7 +81,10 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
     unsigned char* As = smem + L.a;
     unsigned char* Bs = smem + L.b;
     PairTile* pt = reinterpret_cast<PairTile*>(smem + L.pt);
+    float2* p8 = reinterpret_cast<float2*>(smem + L.p8);
     float2* craw = reinterpret_cast<float2*>(smem + L.craw);
+    float2* rbuf = reinterpret_cast<float2*>(smem + L.rbuf);
+    const int RB = 16 * KS;                  // rbuf row stride
     float* scale = reinterpret_cast<float*>(smem + L.scale);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tslot);
@@ -129,16 +134,27 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
         if (tid < CTC_TILES * CTC_PCH) {
             const int tt = tid / CTC_PCH, j = tid % CTC_PCH;
             const int til = blockIdx.x * CTC_TILES + tt;
-            if (j < nc && til < op.g.n_tiles) pt[tid] = load_pair_tile(op, a.pairs[c0 + j], til);
+            if (j < nc && til < op.g.n_tiles) {
+                pt[tid] = load_pair_tile(op, a.pairs[c0 + j], til);
+                p8[tid] = tile_step_cis_exact(pt[tid], 8);
+            }
         }
         if (c0 == 0) pdl_wait();             // r comes from the previous kernel
+        // the chunk's residual rows into shared memory (all copies in flight at once)
+        for (int e = tid; e < nc * K; e += CTC_THREADS) {
+            const int j = e / K, k = e - j * K;
+            cp_async_8(rbuf + j * RB + k, a.r + (size_t)c0 * K + e, true);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
         // FP16: per-pair power-of-two scale so that |Re r'|, |Im r'| <= |r'| < 1
         if (F16) {
             for (int j = warp; j < CTC_PCH; j += CTC_THREADS / 32) {
                 float m = 0.f;
                 if (j < nc)
                     for (int k = tid % 32; k < K; k += 32) {
-                        float2 r = a.r[(size_t)(c0 + j) * K + k];
+                        float2 r = rbuf[j * RB + k];
                         if (op.pulse) r = cmul_conj(r, op.pulse[k]);
                         m = fmaxf(m, sqrtf(r.x * r.x + r.y * r.y));   // |r'| = |conj(p) r|
                     }
@@ -153,44 +169,59 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
                     scale[j] = sc;
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
-        // A = r' rows (tile, pair, re/im), two k per 32-bit word; lanes take 8 (tile, pair) x 4 words
-        for (int e = tid; e < CTC_TILES * CTC_PCH * KS * 8; e += CTC_THREADS) {
-            const int eh = e >> 5;
-            const int tj = (eh / (KS * 2)) * 8 + ((e >> 2) & 7);
-            const int kp = (eh % (KS * 2)) * 4 + (e & 3);
+        // A = r' rows (tile, pair, re/im), two k per 32-bit word.  Thread: row tj = 8 (warp % 8) +
+        // lane / 4 and word w = lane % 4 of the k-pairs kp = 4 KS (warp / 8) + 4 m + w, m < KS; a warp
+        // stores 8 rows x 4 words at a time (distinct banks in the K-major layout), and the phasors of
+        // k and k + 1 advance by the exact 8-step phasor from one SFU start each (at most 7 steps).
+        {
+            const int w4 = tid & 3, tj = ((warp & 7) << 3) + ((tid >> 2) & 7), h = warp >> 3;
             const int tt = tj / CTC_PCH, j = tj % CTC_PCH;
-            const int k = 2 * kp;
-            float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-            if (j < nc && blockIdx.x * CTC_TILES + tt < op.g.n_tiles) {
-                const PairTile& P = pt[tt * CTC_PCH + j];
-                const float sc = F16 ? scale[j] : 1.0f;
-                if (k < K) {
-                    float2 r = a.r[(size_t)(c0 + j) * K + k];
-                    if (op.pulse) r = cmul_conj(r, op.pulse[k]);
-                    v0 = cmul(r, tile_step_cis(P, k));
-                    v0.x *= sc;
-                    v0.y *= sc;
-                }
-                if (k + 1 < K) {
-                    float2 r = a.r[(size_t)(c0 + j) * K + k + 1];
-                    if (op.pulse) r = cmul_conj(r, op.pulse[k + 1]);
-                    v1 = cmul(r, tile_step_cis(P, k + 1));
-                    v1.x *= sc;
-                    v1.y *= sc;
-                }
+            const bool valid = j < nc && blockIdx.x * CTC_TILES + tt < op.g.n_tiles;
+            const int kp0 = h * KS * 4 + w4;
+            float2 c0v = make_float2(0.f, 0.f), c1v = c0v, W8 = c0v;
+            float sc = 1.0f;
+            if (valid) {
+                const PairTile& P = pt[tj];
+                c0v = tile_step_cis(P, 2 * kp0);
+                c1v = tile_step_cis(P, 2 * kp0 + 1);
+                W8 = p8[tj];
+                sc = F16 ? scale[j] : 1.0f;
             }
-            uint32_t hre, lre, him, lim;
-            split2<F16>(v0.x, v1.x, hre, lre);
-            split2<F16>(v0.y, v1.y, him, lim);
-            const int row = (tt * CTC_PCH + j) * 2;
-            const int s = k / 16, kk = k % 16;
-            unsigned char* a0 = As + s * CTC_KSTEP_A;
-            *reinterpret_cast<uint32_t*>(a0 + kmaj_off(row, kk)) = hre;
-            *reinterpret_cast<uint32_t*>(a0 + kmaj_off(row + 1, kk)) = him;
-            *reinterpret_cast<uint32_t*>(a0 + KS * CTC_KSTEP_A + kmaj_off(row, kk)) = lre;
-            *reinterpret_cast<uint32_t*>(a0 + KS * CTC_KSTEP_A + kmaj_off(row + 1, kk)) = lim;
+            const float2* rr = rbuf + j * RB;
+            const int row = tj * 2;
+            for (int m = 0; m < KS; ++m) {
+                const int k = 2 * (kp0 + 4 * m);
+                float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+                if (valid) {
+                    if (k < K) {
+                        float2 r = rr[k];
+                        if (op.pulse) r = cmul_conj(r, op.pulse[k]);
+                        v0 = cmul(r, c0v);
+                        v0.x *= sc;
+                        v0.y *= sc;
+                    }
+                    if (k + 1 < K) {
+                        float2 r = rr[k + 1];
+                        if (op.pulse) r = cmul_conj(r, op.pulse[k + 1]);
+                        v1 = cmul(r, c1v);
+                        v1.x *= sc;
+                        v1.y *= sc;
+                    }
+                    c0v = cmul(c0v, W8);
+                    c1v = cmul(c1v, W8);
+                }
+                uint32_t hre, lre, him, lim;
+                split2<F16>(v0.x, v1.x, hre, lre);
+                split2<F16>(v0.y, v1.y, him, lim);
+                const int s = k / 16, kk = k % 16;
+                unsigned char* a0 = As + s * CTC_KSTEP_A;
+                *reinterpret_cast<uint32_t*>(a0 + kmaj_off(row, kk)) = hre;
+                *reinterpret_cast<uint32_t*>(a0 + kmaj_off(row + 1, kk)) = him;
+                *reinterpret_cast<uint32_t*>(a0 + KS * CTC_KSTEP_A + kmaj_off(row, kk)) = lre;
+                *reinterpret_cast<uint32_t*>(a0 + KS * CTC_KSTEP_A + kmaj_off(row + 1, kk)) = lim;
+            }
         }
         fence_proxy_async();
         tc_fence_before();
