@@ -102,29 +102,41 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
             }
         }
     };
-    // offset of this thread's voxel slot(s) within a tile in the scene vector (grid rows of nx,
-    // planes of nx ny); a full tile's values are then one add away from its origin
+    // offsets of this thread's voxel slots (tid, and tid + nt when nt < TILE_V) within a tile in the
+    // scene vector (grid rows of nx, planes of nx ny); a full tile's values are then one add away from
+    // its origin
     const int plane = op.g.nx * op.g.ny;
     auto slot_offset = [&](int v) {
         return (v / (TILE_X * TILE_Y)) * plane + ((v / TILE_X) % TILE_Y) * op.g.nx + v % TILE_X;
     };
     auto load_s = [&](int q) {                    // the stage's scene values (zero outside the grid)
         const int buf = q & 1;
+        const int v1 = tid + nt;                  // (computed per call: nothing stays live across stages)
+        const int off0 = slot_offset(tid), off1 = v1 < TILE_V ? slot_offset(v1) : 0;
+        int tx, ty, tz;                           // coordinates of the stage's first tile, then stepped
+        tile_coords(op.g, t_begin + q * TS, tx, ty, tz);
         for (int sl = 0; sl < TS; ++sl) {
-            const int tile = t_begin + q * TS + sl;
-            if (tile >= t_end) break;             // slots past the chunk stay idle
-            int tx, ty, tz;
-            tile_coords(op.g, tile, tx, ty, tz);
+            if (t_begin + q * TS + sl >= t_end) break;   // slots past the chunk stay idle
             const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TILE_Z;
             const bool full = x0 + TILE_X <= op.g.nx && y0 + TILE_Y <= op.g.ny && z0 + TILE_Z <= op.g.nz;
             const float2* origin = a.s + ((size_t)z0 * op.g.ny + y0) * op.g.nx + x0;
-            for (int v = tid; v < TILE_V; v += nt) {
-                bool in = full;
-                if (!full) {
+            float2* dst = s_st + (buf * TS + sl) * TILE_V;
+            if (full) {
+                cp_async_8(dst + tid, origin + off0, true);
+                if (v1 < TILE_V) cp_async_8(dst + v1, origin + off1, true);
+            } else {
+                for (int v = tid; v < TILE_V; v += nt) {
                     const int ix = x0 + v % TILE_X, iy = y0 + (v / TILE_X) % TILE_Y, iz = z0 + v / (TILE_X * TILE_Y);
-                    in = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
+                    const bool in = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
+                    cp_async_8(dst + v, in ? origin + slot_offset(v) : a.s, in);
                 }
-                cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, in ? origin + slot_offset(v) : a.s, in);
+            }
+            if (++tx == op.g.tiles_x) {           // next tile in x-fastest order
+                tx = 0;
+                if (++ty == op.g.tiles_y) {
+                    ty = 0;
+                    ++tz;
+                }
             }
         }
     };
