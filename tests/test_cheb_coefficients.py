@@ -53,3 +53,24 @@ def test_invalid_arguments(nfm):
         nfm.cheb_coefficients(float("nan"), 4, 16)
     with pytest.raises(nfm.NfmError):
         nfm.cheb_coefficients(0.1, 4, 16, float("inf"))
+
+
+def test_centred_series_reproduces_the_band_phase(nfm):
+    """The operator's table is centred on the band (k_c = (K - 1)/2): with it the truncated series
+    must reproduce exp(-j (k - k_c) z_step t) on |t| <= 0.95 for every k, and 14 terms suffice where
+    the uncentred table needs 20 (the mid workload's z_step)."""
+    K = 64
+    z_step = 3.59 / ((K - 1) / 2)                        # largest |z| of the centred table = 3.59
+    kc = (K - 1) / 2
+    t = np.linspace(-0.95, 0.95, 101)
+    T = np.cos(np.arange(32)[:, None] * np.arccos(t)[None, :])
+
+    def max_err(L, centre):
+        b = nfm.cheb_coefficients(z_step, K, L, centre)
+        series = (b * ((-1j) ** np.arange(L))[None, :]) @ T[:L]
+        exact = np.exp(-1j * ((np.arange(K) - centre) * z_step)[:, None] * t[None, :])
+        return np.max(np.abs(series - exact))
+
+    assert max_err(14, kc) <= 2e-7
+    assert max_err(14, 0.0) > 1e-5                      # uncentred: z up to 7.2 needs more terms
+    assert max_err(20, 0.0) <= 2e-7
