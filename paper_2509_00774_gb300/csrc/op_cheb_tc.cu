@@ -60,8 +60,8 @@ struct CtcSmem {   // byte offsets of the dynamic shared-memory regions (KS = K 
         pt = b + 2 * KS * CTC_KSTEP_B;                    // [4 tiles][16 pairs] PairTile
         p8 = pt + CTC_TILES * CTC_PCH * (int)sizeof(PairTile);     // [4][16] float2 e^{+j 2 pi 8 df D_c/c}
         craw = p8 + CTC_TILES * CTC_PCH * (int)sizeof(float2);     // [4][16][CTC_CRS] float2 (D_re, D_im)
-        rbuf = craw + CTC_TILES * CTC_PCH * CTC_CRS * (int)sizeof(float2);    // [16 pairs][16 KS] float2 r
-        scale = rbuf + CTC_PCH * 16 * KS * (int)sizeof(float2);           // [16] float
+        rbuf = craw + CTC_TILES * CTC_PCH * CTC_CRS * (int)sizeof(float2);    // [16 pairs][16 KS + 1] float2 r
+        scale = rbuf + CTC_PCH * (16 * KS + 1) * (int)sizeof(float2);     // [16] float
         bar = scale + CTC_PCH * (int)sizeof(float);       // one mbarrier (8-byte aligned)
         tslot = bar + 8;
         total = tslot + 16;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
     float2* p8 = reinterpret_cast<float2*>(smem + L.p8);
     float2* craw = reinterpret_cast<float2*>(smem + L.craw);
     float2* rbuf = reinterpret_cast<float2*>(smem + L.rbuf);
-    const int RB = 16 * KS;                  // rbuf row stride
+    const int RB = 16 * KS + 1;              // rbuf row stride (odd: the 8 rows a warp reads use distinct banks)
     float* scale = reinterpret_cast<float*>(smem + L.scale);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tslot);
