@@ -8,7 +8,10 @@ Operator (Sec. II, Eq. 2) in plain C (`nfm_oracle.c`); everything above it is
 plain numpy in FP64, written in the paper's order and notation:
 
   * data fidelity D(s) = ||y - A s||^2 / (2M)                    (Sec. III, Eq. 4)
-  * l1 regulariser R(s) = sum_n |s_n| (complex modulus)          (Sec. III)
+  * l1 regulariser R(s) = sum_n |s_n| (complex modulus)          (Sec. III); the extensions that
+    Sec. III allows: + (w2/2)||s||^2 (elastic net / Tikhonov) and + w3 sum_g ||s_g||_2 over
+    2 x 2 x 1 voxel blocks (sparse-group penalty; its prox is the soft threshold followed by the
+    group shrink, pinned against the definition of the prox in the tests)
   * PGM step s <- prox_{alpha R}(s - eta grad D(s)), alpha = lambda eta  (Sec. IV, Eq. 5)
   * SPGM: grad D replaced by the gradient of the mean of B component
     functions D_m(s) = |y_m - (A s)_m|^2 / 2 over a minibatch      (Sec. IV-A, Eq. 6)
@@ -102,10 +105,11 @@ def _cplx(z):
 class Oracle:
     """FP64 operator on one geometry (an `inputs.Geometry`)."""
 
-    def __init__(self, geom, w1: float = 1.0, w2: float = 0.0):
-        """w1, w2: regulariser R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 (w2 = 0: the paper's l1)."""
+    def __init__(self, geom, w1: float = 1.0, w2: float = 0.0, w3: float = 0.0):
+        """w1, w2, w3: regulariser R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 + w3 sum_g ||s_g||_2 (w2 = w3 = 0:
+        the paper's l1; the groups g are the 2 x 2 x 1 voxel blocks of `voxel_groups`)."""
         self.geom = geom
-        self.w1, self.w2 = float(w1), float(w2)
+        self.w1, self.w2, self.w3 = float(w1), float(w2), float(w3)
         self.T, self.R, self.K = geom.T, geom.R, geom.K
         self.P, self.M, self.N = geom.P, geom.M, geom.N
         self._tx = np.ascontiguousarray(geom.tx, dtype=np.float64)
@@ -179,13 +183,21 @@ class Oracle:
         return float(np.vdot(res, res).real) / (2.0 * self.M)
 
     def regulariser(self, s) -> float:
-        """R(s) = w1 sum |s_n| + (w2/2) sum |s_n|^2   (Sec. III; l1 when w2 = 0)."""
+        """R(s) = w1 sum |s_n| + (w2/2) sum |s_n|^2 + w3 sum_g ||s_g||_2   (Sec. III; l1 when w2 = w3 = 0)."""
         s = np.asarray(s)
-        return self.w1 * float(np.sum(np.abs(s))) + 0.5 * self.w2 * float(np.vdot(s, s).real)
+        r = self.w1 * float(np.sum(np.abs(s))) + 0.5 * self.w2 * float(np.vdot(s, s).real)
+        if self.w3 != 0.0:
+            r += self.w3 * float(np.sum(group_norms(s, voxel_groups(self.geom.grid))))
+        return r
 
     def prox(self, z, alpha_eta):
-        """prox of (eta lambda) R at z, alpha_eta = eta lambda."""
-        return prox_l1(z, alpha_eta * self.w1) / (1.0 + alpha_eta * self.w2)
+        """prox of (eta lambda) R at z, alpha_eta = eta lambda: the soft threshold of the l1 term, then
+        the group shrink of the group term (the prox of the sparse-group penalty is that composition),
+        then the 1/(1 + eta lambda w2) scaling of the quadratic term."""
+        u = prox_l1(z, alpha_eta * self.w1)
+        if self.w3 != 0.0:
+            u = prox_group(u, voxel_groups(self.geom.grid), alpha_eta * self.w3)
+        return u / (1.0 + alpha_eta * self.w2)
 
     def objective(self, y, s, lam) -> float:
         """D(s) + lambda R(s)   (Eq. 3, Eq. 4)."""
@@ -270,6 +282,33 @@ def prox_l1(z, alpha) -> np.ndarray:
     keep = mag > alpha
     out[keep] = z[keep] * (1.0 - alpha / mag[keep])
     return out
+
+
+def voxel_groups(grid) -> np.ndarray:
+    """Group index of every voxel (x fastest): the 2 x 2 x 1 blocks (ix // 2, iy // 2, iz); blocks at
+    an odd grid edge hold fewer voxels."""
+    ix = np.arange(grid.nx)
+    iy = np.arange(grid.ny)
+    iz = np.arange(grid.nz)
+    gx, gy = (grid.nx + 1) // 2, (grid.ny + 1) // 2
+    g = (iz[:, None, None] * gy + (iy // 2)[None, :, None]) * gx + (ix // 2)[None, None, :]
+    return g.reshape(-1)
+
+
+def group_norms(z, groups) -> np.ndarray:
+    """||z_g||_2 of every group g (index = group id)."""
+    z = np.asarray(z, dtype=np.complex128)
+    return np.sqrt(np.bincount(groups, weights=np.abs(z) ** 2))
+
+
+def prox_group(z, groups, alpha) -> np.ndarray:
+    """prox of alpha * sum_g ||z_g||_2: z_g * max(0, 1 - alpha/||z_g||), 0 if ||z_g|| <= alpha."""
+    z = np.asarray(z, dtype=np.complex128)
+    nrm = group_norms(z, groups)
+    scale = np.zeros_like(nrm)
+    keep = nrm > alpha
+    scale[keep] = 1.0 - alpha / nrm[keep]
+    return z * scale[groups]
 
 
 def nmse(a, b) -> float:

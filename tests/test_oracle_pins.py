@@ -334,3 +334,54 @@ def test_psnr_and_nmse_closed_forms():
     a = np.array([1.0, 0.5, 0.1, 0.25])          # one magnitude off by 0.1 -> mse = 0.01/4
     assert abs(oracle.psnr_magnitude(a, ref) - 10 * math.log10(400.0)) < 1e-12
     assert abs(oracle.nmse(a, ref) - 0.01 / (1 + 0.25 + 0.0625)) < 1e-15
+
+
+def test_group_prox_hand_case_and_groups():
+    """2 x 2 x 1 voxel groups on a 3 x 2 x 1 grid (an odd edge group of two voxels): the group shrink
+    scales a group by 1 - alpha/||z_g|| or zeroes it, exactly in FP64 for power-of-two factors."""
+    from oracle import group_norms, prox_group, voxel_groups
+    grid = I.Grid(0.0, 0.0, 0.3, 0.01, 0.01, 0.01, 3, 2, 1)
+    g = voxel_groups(grid)
+    assert list(g) == [0, 0, 1, 0, 0, 1]
+    z = np.array([3, 0, 1j, 4j, 0, 0], dtype=np.complex128)
+    assert np.allclose(group_norms(z, g), [5.0, 1.0])
+    out = prox_group(z, g, 2.5)
+    assert np.array_equal(out, np.array([1.5, 0, 0, 2j, 0, 0]))
+
+
+def test_sparse_group_prox_minimises_its_definition():
+    """prox(z) = argmin_p 1/2||p - z||^2 + a1 ||p||_1 + a2 sum_g ||p_g|| + (b/2)||p||^2: the oracle's
+    closed form (soft threshold, group shrink, 1/(1 + b)) must not be beaten by any perturbation,
+    including ones that zero single entries or whole groups (convex: a local minimum is global)."""
+    w = W.small_T4R4_K16_16x16x8()
+    grid = I.Grid(0.0, 0.0, 0.3, 0.01, 0.01, 0.01, 3, 4, 2)
+    geom = I.Geometry(w.geom.tx, w.geom.rx, w.geom.freq, grid)
+    from oracle import voxel_groups
+    groups = voxel_groups(grid)
+    rng = np.random.default_rng(5)
+    seen_zero = seen_nonzero = False
+    for a1, a2, b in ((0.3, 0.8, 0.0), (0.0, 1.5, 0.25), (0.7, 0.2, 0.5), (1.2, 2.5, 0.0)):
+        o = Oracle(geom, w1=a1, w2=b, w3=a2)                  # prox(z, 1) uses a1, a2, b as written
+        z = rng.standard_normal(o.N) + 1j * rng.standard_normal(o.N)
+
+        def f(p):
+            nrm = np.sqrt(np.bincount(groups, weights=np.abs(p) ** 2))
+            return (0.5 * np.sum(np.abs(p - z) ** 2) + a1 * np.sum(np.abs(p)) + a2 * np.sum(nrm)
+                    + 0.5 * b * np.sum(np.abs(p) ** 2))
+
+        p = o.prox(z, 1.0)
+        f0 = f(p)
+        for t in range(3000):
+            q = p.copy()
+            kind = t % 3
+            if kind == 0:
+                q += (rng.standard_normal(o.N) + 1j * rng.standard_normal(o.N)) * 10.0 ** rng.uniform(-6, -1)
+            elif kind == 1:
+                q[rng.integers(o.N)] = 0.0
+                q += (rng.standard_normal(o.N) + 1j * rng.standard_normal(o.N)) * 1e-4
+            else:
+                q[groups == rng.integers(groups.max() + 1)] = 0.0
+            assert f(q) >= f0 - 1e-12 * max(1.0, abs(f0))
+        seen_zero |= bool(np.any(p == 0))
+        seen_nonzero |= bool(np.any(p != 0))
+    assert seen_zero and seen_nonzero                   # both kinds of entries are exercised
