@@ -190,6 +190,18 @@ int nfm_cheb_coefficients(double z_step, double k_center, int K, int L, double* 
  * and nfm_objective adds lambda R(s).  Weights finite, >= 0, not both 0. */
 int nfm_set_regularizer(nfm_ctx* ctx, double w1, double w2);
 
+/* Group term of the regulariser (Sec. III allows other convex functionals; default
+ * w3 = 0, off): R(s) += w3 sum_g ||s_g||_2 over the 2 x 2 x 1 voxel blocks
+ * g = (ix/2, iy/2, iz) (blocks at an odd grid edge hold fewer voxels).  The prox
+ * used by every SPGM/PGM step is then the soft threshold at eta lambda w1, the
+ * block shrink u_g max(0, 1 - eta lambda w3/||u_g||), and the 1/(1 + eta lambda w2)
+ * scaling (the prox of the sparse-group penalty); nfm_objective adds lambda w3
+ * sum_g ||s_g|| (FP64).  Steps with w3 > 0 need the Chebyshev-expansion operator
+ * (equally spaced frequencies, algorithm auto or chebyshev; FP32 or tensor-core
+ * precision) and fail with NFM_ERR_ARG otherwise.  Errors: NFM_ERR_ARG for a
+ * negative or non-finite w3. */
+int nfm_set_group_weight(nfm_ctx* ctx, double w3);
+
 /* Minibatch forward operator y = A_B s (Eq. 2 rows of the listed pairs).
  *   pairs [n_pairs] int32 (device), s [N] complex64, y [n_pairs*K] complex64.
  * y must not alias s.  Uses library-owned scratch (allocated on first need). */

@@ -51,4 +51,27 @@ __device__ __forceinline__ float2 tile_step_cis_exact(const PairTile& pt, int k)
     return cis_turns(ph);
 }
 
+// Gradient step and prox of one voxel's iterate (Eq. 5 with the regulariser extended as Sec. III
+// allows): z = s - step g, the soft threshold at alpha (l1 term), the group shrink at alpha_g over the
+// 2 x 2 x 1 voxel block held by lanes lane, lane ^ 1, lane ^ 8, lane ^ 9 of the warp (thread = voxel
+// v of an 8 x 4 x 4 tile with lx = v % 8, ly = (v / 8) % 4; tile origins are even, so blocks never
+// straddle tiles), then the elastic-net scaling.  With alpha_g > 0 every lane of the warp must call
+// it; voxels outside the grid pass in = false and add nothing to their block's norm.
+__device__ __forceinline__ float2 step_prox(float2 s, float gr, float gi, float step, float alpha, float alpha_g,
+                                            float shrink, bool in)
+{
+    const float zr = fmaf(-step, gr, s.x), zi = fmaf(-step, gi, s.y);
+    const float mag = sqrtf(zr * zr + zi * zi);
+    float f = mag > alpha ? 1.0f - alpha / mag : 0.f;
+    if (alpha_g > 0.f) {
+        const float u2 = in ? f * f * (zr * zr + zi * zi) : 0.f;
+        float n2 = u2 + __shfl_xor_sync(0xffffffffu, u2, 1);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, 8);
+        const float gn = sqrtf(n2);
+        f *= gn > alpha_g ? 1.0f - alpha_g / gn : 0.f;
+    }
+    const float sc = f * shrink;
+    return make_float2(zr * sc, zi * sc);
+}
+
 }  // namespace nfm

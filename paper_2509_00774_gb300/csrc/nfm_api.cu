@@ -91,6 +91,7 @@ struct nfm_ctx {
     size_t bscale_cap = 0;
     int precision = NFM_FP32;
     double reg_w1 = 1.0, reg_w2 = 0.0;    // R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2
+    double reg_w3 = 0.0;                  //      + w3 sum over 2 x 2 x 1 voxel blocks of ||s_g||_2
     unsigned long long scratch_gen = 0;   // bumped whenever a scratch buffer is (re)allocated
     bool adj_tc_attr[2][MAX_K1 + 1] = {};
 
@@ -615,9 +616,17 @@ int enqueue_adjoint_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2
     return NFM_OK;
 }
 
+// alpha_g > 0: the fused update also shrinks 2 x 2 x 1 voxel blocks (expansion adjoints only)
 int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r, float2* g_out, float2* s,
-                    float step, float alpha, float shrink = 1.0f)
+                    float step, float alpha, float shrink = 1.0f, float alpha_g = 0.f)
 {
+    if (alpha_g > 0.f && s) {
+        bool cheb = false;
+        if (ctx->uniform) NFM_TRY(use_cheb(ctx, cheb, n_pairs));
+        if (!cheb)
+            return fail(ctx, NFM_ERR_ARG, "the group term of the regulariser needs the Chebyshev-expansion "
+                                          "operator (equally spaced frequencies, algorithm auto or chebyshev)");
+    }
     if (!ctx->uniform) {
         if (ctx->precision != NFM_FP32)
             return fail(ctx, NFM_ERR_ARG, "the tensor-core adjoint needs equally spaced frequencies");
@@ -661,6 +670,7 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         a.alpha = alpha;
         a.shrink = shrink;
         a.pchunk = 16;
+        a.alpha_g = alpha_g;
         ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
         const int e0 = prof_mark(ctx);
         NFM_CK(launch_adj_cheb_tc(op_desc(ctx), cd, a, f16, smem, ctx->stream));
@@ -685,6 +695,7 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         a.alpha = alpha;
         a.shrink = shrink;
         a.pchunk = CHEB_ADJ_PCHUNK;
+        a.alpha_g = alpha_g;
         ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
         const int e0 = prof_mark(ctx);
         NFM_CK(launch_adj_cheb(op_desc(ctx), cd, a, smem, ctx->stream));
@@ -736,7 +747,8 @@ int spgm_step_impl(nfm_ctx* ctx, const float2* y, float2* s, const int* pairs, i
     const double B = (double)n_pairs * ctx->K;
     NFM_TRY(enqueue_adjoint(ctx, pairs, n_pairs, r, nullptr, s, (float)(eta / B),
                             (float)((double)eta * lambda * ctx->reg_w1),
-                            (float)(1.0 / (1.0 + (double)eta * lambda * ctx->reg_w2))));
+                            (float)(1.0 / (1.0 + (double)eta * lambda * ctx->reg_w2)),
+                            (float)((double)eta * lambda * ctx->reg_w3)));
     return NFM_OK;
 }
 
@@ -992,6 +1004,14 @@ int nfm_set_regularizer(nfm_ctx* ctx, double w1, double w2)
         return fail(ctx, NFM_ERR_ARG, "regularizer weights must be finite, >= 0 and not both 0");
     ctx->reg_w1 = w1;
     ctx->reg_w2 = w2;
+    return NFM_OK;
+}
+
+int nfm_set_group_weight(nfm_ctx* ctx, double w3)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    if (!(w3 >= 0) || !std::isfinite(w3)) return fail(ctx, NFM_ERR_ARG, "group weight must be finite and >= 0");
+    ctx->reg_w3 = w3;
     return NFM_OK;
 }
 
@@ -1284,7 +1304,8 @@ int nfm_spgm_step_freqs(nfm_ctx* ctx, const float* y, float* s, const int* pairs
     const double B = (double)n_pairs * n_freq;
     return enqueue_adjoint(ctx, pairs, n_pairs, r, nullptr, (float2*)s, (float)(eta / B),
                            (float)((double)eta * lambda * ctx->reg_w1),
-                           (float)(1.0 / (1.0 + (double)eta * lambda * ctx->reg_w2)));
+                           (float)(1.0 / (1.0 + (double)eta * lambda * ctx->reg_w2)),
+                           (float)((double)eta * lambda * ctx->reg_w3));
 }
 
 int nfm_pgm_step(nfm_ctx* ctx, const float* y, float* s, float eta, float lambda)
@@ -1425,15 +1446,19 @@ int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, d
     NFM_CK(launch_norm2(res, ctx->M, part, sc + 4, st));
     NFM_CK(launch_abs_sum((const float2*)s, ctx->N, part, sc + 5, st));
     NFM_CK(launch_axpby(sc + 4, 1.0 / (2.0 * (double)ctx->M), sc + 5, lambda * ctx->reg_w1, sc + 6, st));
-    double F = 0, s2 = 0;
+    double F = 0, s2 = 0, gsum = 0;
     NFM_CK(cudaMemcpyAsync(&F, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (ctx->reg_w2 != 0.0) {
         NFM_CK(launch_norm2((const float2*)s, ctx->N, part, sc + 2, st));
         NFM_CK(cudaMemcpyAsync(&s2, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
+    if (ctx->reg_w3 != 0.0) {
+        NFM_CK(launch_group_norm_sum((const float2*)s, ctx->gd.nx, ctx->gd.ny, ctx->gd.nz, part, sc + 3, st));
+        NFM_CK(cudaMemcpyAsync(&gsum, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     NFM_CK(st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize());
     NFM_TRY(check_flags(ctx));
-    *F_out = F + 0.5 * lambda * ctx->reg_w2 * s2;
+    *F_out = F + 0.5 * lambda * ctx->reg_w2 * s2 + lambda * ctx->reg_w3 * gsum;
     return NFM_OK;
 }
 

@@ -36,6 +36,7 @@ struct AdjArgs {
     float step;              // eta / B
     float alpha;             // eta * lambda * w1 (soft-threshold level)
     float shrink;            // 1 / (1 + eta * lambda * w2) (elastic-net scaling; 1 for plain l1)
+    float alpha_g = 0.f;     // eta * lambda * w3: group shrink over 2 x 2 x 1 voxel blocks (expansion adjoints; 0 = off)
     int pchunk;              // pairs staged in shared memory per round
 };
 
@@ -153,6 +154,9 @@ cudaError_t launch_prox_step(const float2* s, const float2* g, float step, float
 cudaError_t launch_prox_step_backward(const float2* s, const float2* g, float step, float alpha, long long n,
                                       const float2* go, float2* grad_s, float2* grad_g, double* partial,
                                       double* out2, cudaStream_t st);
+// out = sum over the 2 x 2 x 1 voxel blocks (ix/2, iy/2, iz) of the block's l2 norm (FP64, fixed tree)
+cudaError_t launch_group_norm_sum(const float2* v, int nx, int ny, int nz, double* partial, double* out,
+                                  cudaStream_t st);
 // dst = src / sqrt(*nrm2)
 cudaError_t launch_normalize(const float2* src, float2* dst, long long n, const double* nrm2, cudaStream_t st);
 // out[0] = a[0] / (scale * b[0])

@@ -428,19 +428,10 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     }
     pdl_launch_dependents();
 
-    if (!in_grid) return;
-    if (a.s) {
-        const float2 sv = s_old;
-        const float zr = fmaf(-a.step, gr, sv.x);
-        const float zi = fmaf(-a.step, gi, sv.y);
-        const float mag = sqrtf(zr * zr + zi * zi);
-        float2 out = make_float2(0.f, 0.f);
-        if (mag > a.alpha) {
-            const float sc = (1.0f - a.alpha / mag) * a.shrink;
-            out = make_float2(zr * sc, zi * sc);
-        }
-        a.s[n] = out;
-    } else {
+    if (a.s) {                               // every lane takes part (group norms use the warp)
+        const float2 out = step_prox(s_old, gr, gi, a.step, a.alpha, a.alpha_g, a.shrink, in_grid);
+        if (in_grid) a.s[n] = out;
+    } else if (in_grid) {
         a.g_out[n] = make_float2(gr, gi);
     }
 }

@@ -299,21 +299,15 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
         tmem_dealloc(tbase, 32);
     }
 
-    if (!tile_ok) return;
+    if (!tile_ok) return;                    // uniform over a warp (a warp lies in one tile)
     const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
-    if (ix >= op.g.nx || iy >= op.g.ny || iz >= op.g.nz) return;
-    const size_t n = ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
-    if (a.s) {
-        const float2 sv = a.s[n];
-        const float zr = fmaf(-a.step, gr, sv.x), zi = fmaf(-a.step, gi, sv.y);
-        const float mag = sqrtf(zr * zr + zi * zi);
-        float2 out = make_float2(0.f, 0.f);
-        if (mag > a.alpha) {
-            const float f = (1.0f - a.alpha / mag) * a.shrink;
-            out = make_float2(zr * f, zi * f);
-        }
-        a.s[n] = out;
-    } else {
+    const bool in_grid = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
+    const size_t n = in_grid ? ((size_t)iz * op.g.ny + iy) * op.g.nx + ix : 0;
+    if (a.s) {                               // every lane of the warp takes part (group norms)
+        const float2 sv = in_grid ? a.s[n] : make_float2(0.f, 0.f);
+        const float2 out = step_prox(sv, gr, gi, a.step, a.alpha, a.alpha_g, a.shrink, in_grid);
+        if (in_grid) a.s[n] = out;
+    } else if (in_grid) {
         a.g_out[n] = make_float2(gr, gi);
     }
 }

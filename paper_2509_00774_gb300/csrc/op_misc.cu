@@ -129,6 +129,45 @@ cudaError_t launch_abs_max(const float2* v, long long n, double* partial, double
     return launch_reduce<RED_ABS_MAX>(v, n, partial, out, st);
 }
 
+__global__ void __launch_bounds__(256) group_norm_partial_kernel(const float2* v, int nx, int ny, int nz,
+                                                                 double* partial)
+{
+    __shared__ double sh[256];
+    const int gx = (nx + 1) / 2, gy = (ny + 1) / 2;
+    const long long n_groups = (long long)gx * gy * nz;
+    double acc = 0.0;
+    for (long long g = blockIdx.x * 256LL + threadIdx.x; g < n_groups; g += (long long)gridDim.x * 256) {
+        const int bx = (int)(g % gx);
+        const long long rest = g / gx;
+        const int by = (int)(rest % gy), iz = (int)(rest / gy);
+        double s2 = 0.0;
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                const int ix = 2 * bx + dx, iy = 2 * by + dy;
+                if (ix < nx && iy < ny) {
+                    const float2 x = v[((size_t)iz * ny + iy) * nx + ix];
+                    s2 += (double)x.x * x.x + (double)x.y * x.y;
+                }
+            }
+        acc += sqrt(s2);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+cudaError_t launch_group_norm_sum(const float2* v, int nx, int ny, int nz, double* partial, double* out,
+                                  cudaStream_t st)
+{
+    group_norm_partial_kernel<<<RED_BLOCKS, 256, 0, st>>>(v, nx, ny, nz, partial);
+    reduce_final_kernel<RED_ABS_SUM><<<1, 256, 0, st>>>(partial, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) mag_change_partial_kernel(const float2* a, const float2* b, long long n,
                                                                  double* partial)
 {

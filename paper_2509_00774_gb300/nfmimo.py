@@ -57,6 +57,7 @@ def load_library(path: str | None = None):
         "nfm_algorithm_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]),
         "nfm_cheb_coefficients": (i, [d, d, i, i, vp]),
         "nfm_set_forward_shape": (i, [vp, i, i, i, i, i, i]),
+        "nfm_set_group_weight": (i, [vp, d]),
         "nfm_autotune": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                              ctypes.POINTER(i)]),
         "nfm_set_regularizer": (i, [vp, d, d]),
@@ -225,6 +226,10 @@ class Context:
         self._check(self._lib.nfm_set_forward_shape(self._h, int(n_pairs), algo, int(shape["threads"]),
                                                     int(shape["lanes_per_group"]), int(shape["pairs_per_cta"]),
                                                     int(shape["chunks"])))
+
+    def set_group_weight(self, w3=0.0):
+        """Adds w3 sum_g ||s_g||_2 over 2 x 2 x 1 voxel blocks to R(s) (0 = off); needs the expansion operator."""
+        self._check(self._lib.nfm_set_group_weight(self._h, float(w3)))
 
     def set_regularizer(self, w1=1.0, w2=0.0):
         """R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2 for every SPGM/PGM step and the objective."""

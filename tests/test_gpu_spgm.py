@@ -258,3 +258,58 @@ def test_empty_minibatch_rejected():
         assert ei.value.code == -1
     g = to_host(ctx.adjoint(to_dev(np.arange(16), "int32"), to_dev(np.zeros(o.M))))
     assert np.all(g == 0)
+
+
+@pytest.mark.parametrize("grid_kind,w1,w2,w3,precision", [("small", 1.0, 0.0, 1.0, "fp32"),
+                                                          ("odd", 0.5, 0.5, 2.0, "fp32"),
+                                                          ("odd", 1.0, 0.0, 1.0, "tc_bf16x3")])
+def test_group_regulariser_spgm_matches_oracle(grid_kind, w1, w2, w3, precision):
+    """R = w1 ||s||_1 + (w2/2)||s||^2 + w3 sum_g ||s_g||_2 over 2 x 2 x 1 voxel blocks (the prox is the
+    soft threshold, the block shrink, the w2 scaling): 10 SPGM epochs against the oracle, on the small
+    grid and on a 15 x 13 x 5 grid whose edge blocks hold fewer voxels; then the FP64 objective."""
+    w = W.small_T4R4_K16_16x16x8()
+    if grid_kind == "small":
+        geom = w.geom
+    else:
+        g0 = w.geom.grid
+        grid = I.Grid(g0.x0, g0.y0, g0.z0, g0.dx, g0.dy, g0.dz, 15, 13, 5)
+        geom = I.Geometry(w.geom.tx, w.geom.rx, w.geom.freq, grid)
+    o = Oracle(geom, w1=w1, w2=w2, w3=w3)
+    y = I.add_noise(o.forward_sparse(I.point_scene(geom.grid, 12, 3)), I.complex_gaussian(o.M, 4), 25.0)
+    y = y.astype(np.complex64).astype(np.complex128)
+    ctx = make_ctx(geom, algorithm="chebyshev")
+    ctx.set_precision(precision)
+    ctx.set_regularizer(w1, w2)
+    ctx.set_group_weight(w3)
+    L = o.power_iteration(I.complex_gaussian(o.N, 5), 50)
+    eta = float(np.float32(1.0 / L))
+    lam = float(np.float32(0.2 * o.lambda_max(y)))     # strong enough that 20-35% of the blocks vanish
+    s_orc = np.zeros(o.N, dtype=np.complex128)
+    s_gpu = to_dev(np.zeros(o.N))
+    y_dev = to_dev(y)
+    for e in range(10):
+        perm = I.epoch_permutation(o.P, 6, e)
+        s_orc = o.spgm_epoch(y, s_orc, perm, 4, eta, lam)
+        ctx.spgm_epoch(y_dev, s_gpu, to_dev(perm, "int32"), 4, eta, lam)
+        assert nmse(to_host(s_gpu), s_orc) <= NMSE_TOL, e
+    from oracle import group_norms, voxel_groups
+    zero_groups = np.sum(group_norms(s_orc, voxel_groups(geom.grid)) == 0)
+    print(f"[parity] group regulariser {grid_kind} {precision}: NMSE {nmse(to_host(s_gpu), s_orc):.2e}, "
+          f"{zero_groups} zero blocks")
+    assert 0 < zero_groups < voxel_groups(geom.grid).max() + 1
+    F_gpu = ctx.objective(y_dev, s_gpu, lam)
+    F_orc = o.objective(y, to_host(s_gpu), lam)
+    assert abs(F_gpu - F_orc) <= 1e-5 * F_orc
+
+
+def test_group_regulariser_needs_the_expansion_operator():
+    from paper_2509_00774_gb300.nfmimo import NfmError
+    w = W.small_T4R4_K16_16x16x8()
+    ctx = make_ctx(w.geom, algorithm="direct")
+    ctx.set_group_weight(1.0)
+    y = to_dev(np.zeros(w.geom.M))
+    s = to_dev(np.zeros(w.geom.N))
+    with pytest.raises(NfmError):
+        ctx.spgm_epoch(y, s, to_dev(I.epoch_permutation(w.geom.P, 0, 0), "int32"), 4, 0.01, 0.01)
+    with pytest.raises(NfmError):
+        ctx.set_group_weight(-1.0)
