@@ -74,3 +74,49 @@ def test_centred_series_reproduces_the_band_phase(nfm):
     assert max_err(14, kc) <= 2e-7
     assert max_err(14, 0.0) > 1e-5                      # uncentred: z up to 7.2 needs more terms
     assert max_err(20, 0.0) <= 2e-7
+
+
+def test_band_centred_factorisation_reproduces_oracle_elements(nfm):
+    """The expansion operator's factorisation of one (pair, 8 x 4 x 4 tile) block of Eq. 2, written out in
+    FP64 with the library's centred table: with D = D_c + delta, f_c = f_0 + k_c df, t = delta/xi,
+    A_kv = amp_v e^{-j 2 pi (f_0 D_c + f_c delta_v)/c} e^{-j 2 pi k df D_c/c} sum_l (-j)^l b_l(z_k) T_l(t_v),
+    z_k = 2 pi (k - k_c) df xi / c.  It must match the oracle's elements to the series' accuracy."""
+    from oracle import Oracle
+    from paper_2509_00774_gb300 import inputs as I
+    from paper_2509_00774_gb300 import workloads as W
+    w = W.mid_T16R16_K64_64x64x32()
+    g = w.geom
+    o = Oracle(g)
+    grid = g.grid
+    f = np.asarray(g.freq, dtype=np.float64)
+    K, f0, df, c = f.size, f[0], f[1] - f[0], g.c
+    kc = (K - 1) / 2
+    fc = f0 + kc * df
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        t_ant, r_ant = int(rng.integers(g.T)), int(rng.integers(g.R))
+        pair = t_ant * g.R + r_ant
+        tx0, ty0, tz0 = (int(rng.integers(grid.nx // 8)) * 8, int(rng.integers(grid.ny // 4)) * 4,
+                         int(rng.integers(grid.nz // 4)) * 4)
+        ix, iy, iz = np.meshgrid(np.arange(8) + tx0, np.arange(4) + ty0, np.arange(4) + tz0, indexing="ij")
+        cols = ((iz * grid.ny + iy) * grid.nx + ix).reshape(-1)
+        pos = grid.positions(cols)
+        centre = np.array([grid.x0 + (tx0 + 3.5) * grid.dx, grid.y0 + (ty0 + 1.5) * grid.dy,
+                           grid.z0 + (tz0 + 1.5) * grid.dz])
+        a_t, a_r = np.asarray(g.tx)[t_ant], np.asarray(g.rx)[r_ant]
+        dT, dR = np.linalg.norm(pos - a_t, axis=1), np.linalg.norm(pos - a_r, axis=1)
+        dcT, dcR = np.linalg.norm(centre - a_t), np.linalg.norm(centre - a_r)
+        Dc, delta = dcT + dcR, (dT - dcT) + (dR - dcR)
+        xi = 2.0 * max(np.max(np.abs(dT - dcT)), np.max(np.abs(dR - dcR))) / 0.95
+        tv = delta / xi
+        L = 24
+        b = nfm.cheb_coefficients(2 * np.pi * df * xi / c, K, L, kc)
+        T = np.cos(np.arange(L)[:, None] * np.arccos(tv)[None, :])
+        series = (b * ((-1j) ** np.arange(L))[None, :]) @ T                       # [K, voxels]
+        amp = 1.0 / (4 * np.pi * dT * dR)
+        voxel = amp * np.exp(-2j * np.pi * (f0 * Dc + fc * delta) / c)
+        tile = np.exp(-2j * np.pi * np.arange(K) * df * Dc / c)
+        model = tile[:, None] * voxel[None, :] * series
+        exact = o.dense(pair * K + np.arange(K), cols)
+        err = np.max(np.abs(model - exact)) / np.max(np.abs(exact))
+        assert err <= 1e-7, err
