@@ -120,3 +120,9 @@ def test_band_centred_factorisation_reproduces_oracle_elements(nfm):
         exact = o.dense(pair * K + np.arange(K), cols)
         err = np.max(np.abs(model - exact)) / np.max(np.abs(exact))
         assert err <= 1e-7, err
+        # adjoint of the block: g_v = conj(voxel_v) sum_l T_l(t_v) C_l, C_l = j^l sum_k b_l(z_k) r_k conj(tile_k)
+        r = rng.standard_normal(K) + 1j * rng.standard_normal(K)
+        C = ((1j) ** np.arange(L)) * ((r * np.conj(tile)) @ b)
+        g_model = np.conj(voxel) * (C @ T)
+        g_exact = exact.conj().T @ r
+        assert np.max(np.abs(g_model - g_exact)) <= 1e-7 * np.max(np.abs(g_exact))
