@@ -385,3 +385,66 @@ def test_sparse_group_prox_minimises_its_definition():
         seen_zero |= bool(np.any(p == 0))
         seen_nonzero |= bool(np.any(p != 0))
     assert seen_zero and seen_nonzero                   # both kinds of entries are exercised
+
+
+# ---------------------------------------------------------------------------
+# Eq. 3 / Eq. 4: data fidelity and objective on a hand-derived operator
+# ---------------------------------------------------------------------------
+def _hand_objective_geom():
+    """TX at (0, 0.3, 0), RX at (0, -0.3, 0); two voxels at (-0.24, 0, 0.32) and (0.24, 0, 0.32) (one
+    2 x 2 x 1 block: ix = 0, 1).  Every antenna-voxel distance is sqrt(0.24^2 + 0.3^2 + 0.32^2) = 0.5, so
+    dT + dR = 1 m and dT dR = 1/4.  Frequencies c/4 and c/2 put 1/4 and 1/2 turn on that path, so by
+    Eq. 2 every column of A is (e^{-j pi/2}, e^{-j pi}) / (4 pi / 4) = (-j, -1) / pi."""
+    c = I.C_LIGHT
+    grid = I.Grid(-0.24, 0.0, 0.32, 0.48, 0.01, 0.01, 2, 1, 1)
+    return I.Geometry(np.array([[0.0, 0.3, 0.0]]), np.array([[0.0, -0.3, 0.0]]),
+                      np.array([c / 4.0, c / 2.0]), grid)
+
+
+def test_hand_operator_columns():
+    o = Oracle(_hand_objective_geom())
+    A = o.dense(np.arange(o.M), np.arange(o.N))
+    want = np.array([[-1j, -1j], [-1.0, -1.0]]) / math.pi
+    assert np.max(np.abs(A - want)) <= 1e-15
+
+
+def test_data_fidelity_and_objective_hand_values():
+    """s = pi (1, 2j): A s = (-j (1 + 2j), -(1 + 2j)) = (2 - j, -1 - 2j).  With y = A s + (3 + 4j, 0) the
+    residual norm is 25, so D = 25 / (2 M) = 25/4 (M = 2 rows).  R terms: sum |s_n| = 3 pi,
+    ||s||^2 = 5 pi^2, the one block's norm = sqrt(5) pi.  A dropped 1/2 or 1/M, or any missing or
+    mis-weighted lambda R term, changes the value."""
+    geom = _hand_objective_geom()
+    s = math.pi * np.array([1.0, 2j])
+    y = np.array([5 + 3j, -1 - 2j])
+    o = Oracle(geom)                                           # the paper's l1 (w1 = 1)
+    assert abs(o.data_fidelity(y, s) - 6.25) <= 1e-13
+    lam = 0.25
+    assert abs(o.objective(y, s, lam) - (6.25 + lam * 3 * math.pi)) <= 1e-13
+    # zero residual: D = 0 exactly (up to rounding of A s)
+    assert o.data_fidelity(np.array([2 - 1j, -1 - 2j]), s) <= 1e-28
+    w1, w2, w3 = 1.0, 0.5, 2.0
+    oe = Oracle(geom, w1=w1, w2=w2, w3=w3)
+    R = w1 * 3 * math.pi + 0.5 * w2 * 5 * math.pi ** 2 + w3 * math.sqrt(5.0) * math.pi
+    assert abs(oe.regulariser(s) - R) <= 1e-13 * R
+    assert abs(oe.objective(y, s, lam) - (6.25 + lam * R)) <= 1e-13 * (6.25 + lam * R)
+
+
+def test_data_fidelity_gradient_by_central_differences():
+    """D is quadratic, so the central difference along e_n (and j e_n) is exact up to rounding and
+    equals Re (and Im) of the gradient A^H (A s - y) / M.  This ties the scale of D to the gradient
+    that the KKT pins check."""
+    o = Oracle(_tiny_random_geom(7, T=2, R=3, K=4, grid=(3, 2, 2)))
+    rng = np.random.default_rng(11)
+    s = rng.standard_normal(o.N) + 1j * rng.standard_normal(o.N)
+    y = (rng.standard_normal(o.M) + 1j * rng.standard_normal(o.M)) * 0.01
+    g = o.full_gradient(y, s)
+    eps = 1e-3
+    fd = np.zeros(o.N, dtype=np.complex128)
+    for n in range(o.N):
+        for unit, part in ((1.0, "re"), (1j, "im")):
+            sp, sm = s.copy(), s.copy()
+            sp[n] += eps * unit
+            sm[n] -= eps * unit
+            d = (o.data_fidelity(y, sp) - o.data_fidelity(y, sm)) / (2 * eps)
+            fd[n] += d if part == "re" else 1j * d
+    assert np.max(np.abs(fd - g)) <= 1e-7 * np.max(np.abs(g))
