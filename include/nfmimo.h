@@ -218,13 +218,17 @@ int nfm_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* r, flo
 int nfm_spgm_step(nfm_ctx* ctx, const float* y, float* s, const int* pairs, int n_pairs,
                   float eta, float lambda);
 
-/* One SPGM epoch: the P pair indices in perm [P] (device) are taken in
- * consecutive chunks of pairs_per_batch (the last chunk may be shorter and
- * uses its own B) and nfm_spgm_step runs on each chunk in order. */
+/* One SPGM epoch (Sec. IV-A, Eq. 6, iterated by Eq. 5): the P pair indices in
+ * perm [P] (device) are taken in consecutive chunks of pairs_per_batch (the
+ * last chunk may be shorter and uses its own B) and nfm_spgm_step runs on each
+ * chunk in order, so every pair's rows enter one minibatch gradient per epoch
+ * (the paper draws the minibatch index uniformly; the caller supplies the
+ * draws as the permutation).  y [P*K], s [N] (in place), perm [P]: device.
+ * Errors: NFM_ERR_ARG (pairs_per_batch outside [1, P], bad pointers). */
 int nfm_spgm_epoch(nfm_ctx* ctx, const float* y, float* s, const int* perm, int pairs_per_batch,
                    float eta, float lambda);
 
-/* Same as nfm_spgm_epoch for n_epochs epochs, but y_host [P*K], s_host [N]
+/* Same as nfm_spgm_epoch (Sec. IV-A, Eq. 6) for n_epochs epochs, but y_host [P*K], s_host [N]
  * (in/out) and perms_host [n_epochs][P] are HOST buffers: the call copies
  * them to library-owned device buffers, runs, copies s back and synchronises.
  * Pinned host memory makes the copies asynchronous-capable and faster. */
@@ -267,7 +271,8 @@ int nfm_prox_step(nfm_ctx* ctx, const float* s, const float* g, float step, floa
 int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n,
                            const float* grad_out, float* grad_s, float* grad_g, double* grad_scalars);
 
-/* Batched solves of many independent scenes (uneven grids, arrays and K).
+/* Batched solves of many independent scenes (uneven grids, arrays and K):
+ * Sec. IV-A, Eq. 6 with Eq. 5, applied to every scene independently.
  * A batch holds n_scenes contexts (each with its own geometry, set by
  * nfm_set_geometry; the batch does not own them) and enqueues on cuda_stream
  * (caller-owned; NULL = legacy default stream).  nfm_batch_spgm_epoch runs one
@@ -287,7 +292,11 @@ int nfm_batch_spgm_epoch(nfm_batch* batch, const float* const* y, float* const* 
 const char* nfm_batch_last_error(const nfm_batch* batch);
 
 /* Largest eigenvalue L of A^H A / M by `iters` power iterations from
- * v0 [N] (device, complex64, not modified), with FP64 norms:
+ * v0 [N] (device, complex64, not modified), with FP64 norms.  L is the
+ * Lipschitz constant of the gradient of D(s) = ||y - A s||^2/(2M) (Eq. 4); the
+ * paper states its step eta without saying how it was found, and the step
+ * eta = 1/L used here is not in the paper (a standard choice for Eq. 5).
+ * The iteration:
  *   v <- A^H A v / ||A^H A v||, then L = ||A v||^2 / (M ||v||^2).
  * Writes *L_out (host) and synchronises.  The SPGM step is eta = 1/L. */
 int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out);
@@ -298,7 +307,8 @@ int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out)
 int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, double* F_out);
 
 /* lambda_max = max_n |(A^H y)_n| / M (FP64 result on the host; synchronises):
- * for lambda >= lambda_max the l1 problem has s = 0 as a solution. */
+ * for lambda >= lambda_max the l1 problem of Eq. 3 has s = 0 as a solution
+ * (its optimality condition at s = 0; the paper does not state it). */
 int nfm_lambda_max(nfm_ctx* ctx, const float* y, double* out);
 
 /* Wait for the context's stream and report device-side flags. */
@@ -315,9 +325,11 @@ int nfm_synchronize(nfm_ctx* ctx);
  * loaded library (4 MiB, held on every GPU that loads the library until the
  * process exits), and it allocates nothing.
  *   Arguments, layout and result are those of nfm_forward (y = A_B s).
- *   Limit: n_pairs * K <= 524288 (the scratch holds 524288 complex64 partial
- *   sums; fewer voxel chunks are used when the usual plan does not fit).  A
- *   larger request returns NFM_ERR_ARG and enqueues nothing.
+ *   Limit: ceil(n_pairs / 8) * 8 * K <= 524288 (the scratch holds 524288
+ *   complex64 partial sums and one voxel chunk needs that many, the pairs
+ *   padded to whole groups of 8; fewer voxel chunks are used when the usual
+ *   plan does not fit).  A larger request returns NFM_ERR_ARG and enqueues
+ *   nothing.
  *   The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.

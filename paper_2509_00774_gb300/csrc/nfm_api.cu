@@ -357,7 +357,9 @@ int use_cheb(nfm_ctx* ctx, bool& on, int n_pairs = -1)
     return NFM_OK;
 }
 
-int plan_forward(nfm_ctx* ctx, int n_pairs, FwdPlan* pl)
+// max_chunks > 0 caps the number of voxel-tile chunks (the allocation-free forward holds every
+// chunk's partial sums in a fixed array); the tile split below is the same for every count
+int plan_forward(nfm_ctx* ctx, int n_pairs, FwdPlan* pl, long long max_chunks = 0)
 {
     const int K1 = ctx->K1;
     pl->VS = 32 / K1;            // voxel subsets per warp; one warp per pair
@@ -381,6 +383,7 @@ int plan_forward(nfm_ctx* ctx, int n_pairs, FwdPlan* pl)
     if (nch < 1) nch = 1;
     if (nch > ctx->gd.n_tiles) nch = ctx->gd.n_tiles;
     if (nch > 65535) nch = 65535;
+    if (max_chunks > 0 && nch > max_chunks) nch = max_chunks;
     pl->n_chunks = (int)nch;
     pl->base = ctx->gd.n_tiles / pl->n_chunks;
     pl->rem = ctx->gd.n_tiles % pl->n_chunks;
@@ -1568,21 +1571,13 @@ extern "C" int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, 
     NFM_TRY(check_ptr(ctx, y, "y", 8));
     if (!ctx->uniform)
         return fail(ctx, NFM_ERR_ARG, "the allocation-free forward needs equally spaced frequencies");
-    if ((size_t)n_pairs * ctx->K > NOALLOC_SCRATCH_ELEMS)
-        return fail(ctx, NFM_ERR_ARG, "n_pairs * K = %lld exceeds the allocation-free limit %zu",
-                    (long long)n_pairs * ctx->K, NOALLOC_SCRATCH_ELEMS);
-    FwdPlan pl;
-    NFM_TRY(plan_forward(ctx, n_pairs, &pl));
-    const size_t per_chunk = (size_t)pl.n_slots * ctx->K;
+    // one voxel chunk holds ceil(n_pairs / 8) * 8 * K partial sums (pairs padded to whole CTAs)
+    const size_t per_chunk = (size_t)((n_pairs + FWD_PC - 1) / FWD_PC) * FWD_PC * ctx->K;
     if (per_chunk > NOALLOC_SCRATCH_ELEMS)
-        return fail(ctx, NFM_ERR_ARG, "%zu partial sums per voxel chunk exceed the allocation-free limit %zu",
+        return fail(ctx, NFM_ERR_ARG, "ceil(n_pairs / 8) * 8 * K = %zu exceeds the allocation-free limit %zu",
                     per_chunk, NOALLOC_SCRATCH_ELEMS);
-    const size_t max_chunks = NOALLOC_SCRATCH_ELEMS / per_chunk;
-    if ((size_t)pl.n_chunks > max_chunks) {
-        pl.n_chunks = (int)max_chunks;
-        pl.base = ctx->gd.n_tiles / pl.n_chunks;
-        pl.rem = ctx->gd.n_tiles % pl.n_chunks;
-    }
+    FwdPlan pl;
+    NFM_TRY(plan_forward(ctx, n_pairs, &pl, (long long)(NOALLOC_SCRATCH_ELEMS / per_chunk)));
     float2* scratch = nullptr;
     NFM_TRY(noalloc_scratch(ctx, &scratch));
     OpDesc op = op_desc(ctx);

@@ -250,6 +250,15 @@ class Context:
         import torch
         return _ptr(t, torch.int32, name, self.device)
 
+    def _sizes(self, **want):
+        """Raise NfmError(-1) unless every named tensor has the given element count (checked before any
+        raw pointer reaches the library, which cannot see the extents of what it is given)."""
+        if self.K is None:
+            raise NfmError(-4, "no geometry: call set_geometry first")
+        for name, (t, n) in want.items():
+            if t.numel() != n:
+                raise NfmError(-1, f"{name} has {t.numel()} elements, expected {n}")
+
     def forward(self, pairs, s, y=None):
         """y = A_B s for the pair list `pairs` (int32, device); returns y [n_pairs*K]."""
         import torch
@@ -258,11 +267,13 @@ class Context:
             if self.K is None:
                 raise NfmError(-4, "no geometry: call set_geometry first")
             y = torch.empty(n * self.K, dtype=torch.complex64, device=s.device)
+        self._sizes(s=(s, self.N), y=(y, n * self.K))
         self._check(self._lib.nfm_forward(self._h, self._i(pairs, "pairs"), n, self._c(s, "s"), self._c(y, "y")))
         return y
 
     def forward_noalloc(self, pairs, s, y):
         """y = A_B s through the allocation-free entry point (y must be given; nothing is allocated)."""
+        self._sizes(s=(s, self.N), y=(y, pairs.numel() * self.K))
         self._check(self._lib.nfm_forward_noalloc(self._h, self._i(pairs, "pairs"), pairs.numel(),
                                                   self._c(s, "s"), self._c(y, "y")))
         return y
@@ -275,15 +286,18 @@ class Context:
             if self.N is None:
                 raise NfmError(-4, "no geometry: call set_geometry first")
             g = torch.empty(self.N, dtype=torch.complex64, device=r.device)
+        self._sizes(r=(r, n * self.K), g=(g, self.N))
         self._check(self._lib.nfm_adjoint(self._h, self._i(pairs, "pairs"), n, self._c(r, "r"), self._c(g, "g")))
         return g
 
     def spgm_step(self, y, s, pairs, eta, lam):
+        self._sizes(y=(y, self.P * self.K), s=(s, self.N))
         self._check(self._lib.nfm_spgm_step(self._h, self._c(y, "y"), self._c(s, "s"), self._i(pairs, "pairs"),
                                             pairs.numel(), float(eta), float(lam)))
         return s
 
     def spgm_epoch(self, y, s, perm, pairs_per_batch, eta, lam):
+        self._sizes(y=(y, self.P * self.K), s=(s, self.N), perm=(perm, self.P))
         self._check(self._lib.nfm_spgm_epoch(self._h, self._c(y, "y"), self._c(s, "s"), self._i(perm, "perm"),
                                              int(pairs_per_batch), float(eta), float(lam)))
         return s
