@@ -301,6 +301,18 @@ const char* nfm_batch_last_error(const nfm_batch* batch);
  * Writes *L_out (host) and synchronises.  The SPGM step is eta = 1/L. */
 int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out);
 
+/* The same for the minibatch of the listed pairs (Sec. IV-A, Eq. 6): the
+ * largest eigenvalue L_B of A_B^H A_B / B, B = n_pairs * K, the Lipschitz
+ * constant of the minibatch gradient (1/B) A_B^H (A_B s - y_B).  An SPGM step
+ * is stable only where eta < 2 / L_B for every minibatch it takes, and L_B can
+ * exceed the full-batch L several times (a few pairs see the scene from one
+ * viewpoint), so a step of 1/L that suits PGM can make SPGM diverge.
+ * pairs [n_pairs] int32 (device), v0 [N] (device, not modified).  Writes
+ * *L_out (host) and synchronises.  Errors: NFM_ERR_ARG (n_pairs < 1, bad
+ * pointers), NFM_ERR_NUMERIC. */
+int nfm_power_iteration_pairs(nfm_ctx* ctx, const int* pairs, int n_pairs, int iters, const float* v0,
+                              double* L_out);
+
 /* Objective of Eq. 3 with Eq. 4 and the regulariser, accumulated in FP64:
  *   F(s) = ||y - A s||^2 / (2M) + lambda R(s)   (R = sum_n |s_n| by default).
  * y [P*K], s [N] device.  Writes *F_out (host) and synchronises. */
@@ -313,6 +325,21 @@ int nfm_lambda_max(nfm_ctx* ctx, const float* y, double* out);
 
 /* Wait for the context's stream and report device-side flags. */
 int nfm_synchronize(nfm_ctx* ctx);
+
+/* Test hooks for the error paths (no counterpart in the paper).  Every wait of
+ * the tensor-core kernels on their MMA completion barrier is bounded by
+ * wait_ms milliseconds of the GPU's global timer (0 = the default, 1000 ms).
+ * When one runs out the kernel stops issuing MMAs, reads no tensor memory,
+ * waits once more (bounded) for the MMAs it had committed, releases its tensor
+ * memory, raises a device flag and leaves its output (the iterate s, or g)
+ * unwritten; the next synchronising call returns NFM_ERR_TIMEOUT and the
+ * context stays usable.  flags = NFM_HOOK_TC_SKIP_ISSUE makes those kernels
+ * issue no MMA and no commit, so that their first wait runs out on purpose
+ * (nothing is left in flight); flags = 0 is normal operation.  Applies to
+ * calls enqueued afterwards.  Errors: NFM_ERR_ARG for unknown flags or
+ * wait_ms outside [0, 60000]. */
+enum { NFM_HOOK_TC_SKIP_ISSUE = 1 };
+int nfm_set_test_hooks(nfm_ctx* ctx, int flags, int wait_ms);
 
 /* Allocation-free variant of nfm_forward.  The paper has no counterpart; this
  * entry point exists for callers that cannot call cudaMalloc once they are

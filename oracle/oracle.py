@@ -238,19 +238,28 @@ class Oracle:
             s = self.spgm_step(y, s, perm[c0:c0 + pairs_per_batch], eta, lam)
         return s
 
-    def power_iteration(self, v0, iters: int) -> float:
-        """Largest eigenvalue L of A^H A / M by power iteration from v0.
+    def power_iteration(self, v0, iters: int, pairs=None) -> float:
+        """Largest eigenvalue L of A^H A / M by power iteration from v0; with `pairs`, L_B of the minibatch
+        A_B^H A_B / B (B = len(pairs) K rows), the Lipschitz constant of the Eq. 6 minibatch gradient.
 
-        v <- A^H A v / M, v <- v / ||v|| for `iters` steps, then the Rayleigh
-        quotient L = ||A v||^2 / (M ||v||^2).
+        v <- A_B^H A_B v / B, v <- v / ||v|| for `iters` steps, then the Rayleigh
+        quotient L = ||A_B v||^2 / (B ||v||^2).
         """
+        rows = None if pairs is None else self.rows_of_pairs(pairs)
+        B = self.M if rows is None else rows.size
         v = _cplx(v0).copy()
         v /= np.linalg.norm(v)
         for _ in range(iters):
-            v = self.adjoint(self.forward(v)) / self.M
+            v = self.adjoint(self.forward(v, rows=rows), rows=rows) / B
             v /= np.linalg.norm(v)
-        Av = self.forward(v)
-        return float(np.vdot(Av, Av).real) / (self.M * float(np.vdot(v, v).real))
+        Av = self.forward(v, rows=rows)
+        return float(np.vdot(Av, Av).real) / (B * float(np.vdot(v, v).real))
+
+    def spgm_lipschitz(self, perm, pairs_per_batch, v0, iters: int) -> float:
+        """Largest minibatch constant L_B over the minibatches of one epoch with permutation perm."""
+        perm = np.asarray(perm)
+        return max(self.power_iteration(v0, iters, pairs=perm[c:c + pairs_per_batch])
+                   for c in range(0, perm.size, pairs_per_batch))
 
     def frobenius_bound(self) -> float:
         """||A||_F^2 / M, an upper bound on L = lambda_max(A^H A)/M (the trace bounds the largest
@@ -268,6 +277,32 @@ class Oracle:
             inv_r += 1.0 / np.sum((pos - a) ** 2, axis=1)
         pk = float(self.K) if self._p is None else float(np.sum(self._p ** 2))
         return pk * float(np.sum(inv_t * inv_r)) / ((4.0 * math.pi) ** 2 * self.M)
+
+    def minimiser_dense(self, y, lam, L, iters: int = 10000):
+        """A minimiser of Eq. 3 (D + lambda R) for a problem small enough to hold A as a dense matrix:
+        accelerated proximal gradient (FISTA: the Eq. 5 step from an extrapolated point, momentum
+        (t_k - 1)/t_{k+1}, t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2) with step 1/L for `iters` iterations.
+        Not the paper's method: a reference solution that the tests certify by its optimality
+        conditions.  Returns (s, kkt) with kkt the largest violation of the l1 optimality conditions
+        divided by lambda (w1 = 1, w2 = w3 = 0 only)."""
+        assert self.w1 == 1.0 and self.w2 == 0.0 and self.w3 == 0.0
+        A = self.dense(np.arange(self.M), self.all_cols())
+        AH = A.conj().T
+        y = np.asarray(y, dtype=np.complex128)
+        eta = 1.0 / L
+        s = np.zeros(self.N, dtype=np.complex128)
+        z = s.copy()
+        t = 1.0
+        for _ in range(iters):
+            s_new = prox_l1(z - eta * (AH @ (A @ z - y)) / self.M, eta * lam)
+            t_new = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
+            z = s_new + ((t - 1.0) / t_new) * (s_new - s)
+            s, t = s_new, t_new
+        g = AH @ (A @ s - y) / self.M
+        nz = np.abs(s) > 0
+        v_nz = float(np.max(np.abs(g[nz] + lam * s[nz] / np.abs(s[nz])))) if nz.any() else 0.0
+        v_z = float(np.max(np.maximum(np.abs(g[~nz]) - lam, 0.0))) if (~nz).any() else 0.0
+        return s, max(v_nz, v_z) / lam
 
     def lambda_max(self, y) -> float:
         """max_n |(A^H y)_n| / M: the smallest lambda for which s = 0 is a minimiser."""

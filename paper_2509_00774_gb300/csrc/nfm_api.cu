@@ -90,6 +90,8 @@ struct nfm_ctx {
     void* d_bscale = nullptr;
     size_t bscale_cap = 0;
     int precision = NFM_FP32;
+    int hooks = 0;                        // test hooks (nfm_set_test_hooks)
+    unsigned long long tc_wait_ns = 1000000000ull;   // limit of one bounded wait on the tensor core
     double reg_w1 = 1.0, reg_w2 = 0.0;    // R(s) = w1 ||s||_1 + (w2/2) ||s||_2^2
     double reg_w3 = 0.0;                  //      + w3 sum over 2 x 2 x 1 voxel blocks of ||s_g||_2
     unsigned long long scratch_gen = 0;   // bumped whenever a scratch buffer is (re)allocated
@@ -194,6 +196,8 @@ OpDesc op_desc(const nfm_ctx* ctx)
     op.K1 = ctx->K1;
     op.P = ctx->P;
     op.err = ctx->d_err;
+    op.wait_ns = ctx->tc_wait_ns;
+    op.hooks = ctx->hooks;
     return op;
 }
 
@@ -1392,14 +1396,20 @@ int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float s
     return NFM_OK;
 }
 
-int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out)
+}  // extern "C"
+
+namespace {
+// lambda_max(A_B^H A_B) / B for the rows of the listed pairs (B = n_pairs K) by `iters` power
+// iterations from v0, FP64 norms (the full operator is the list of every pair)
+int power_iteration_impl(nfm_ctx* ctx, const int* pairs, int n_pairs, int iters, const float* v0, double* L_out)
 {
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (iters < 0) return fail(ctx, NFM_ERR_ARG, "iters must be >= 0");
     NFM_TRY(check_ptr(ctx, v0, "v0", 8));
     if (!L_out) return fail(ctx, NFM_ERR_ARG, "L_out is NULL");
-    const size_t nb = (size_t)ctx->N * sizeof(float2), mb = (size_t)ctx->M * sizeof(float2);
+    const long long rows = (long long)n_pairs * ctx->K;
+    const size_t nb = (size_t)ctx->N * sizeof(float2), mb = (size_t)rows * sizeof(float2);
     NFM_TRY(ensure(ctx, &ctx->d_v, &ctx->v_cap, nb));
     NFM_TRY(ensure(ctx, &ctx->d_g, &ctx->g_cap, nb));
     NFM_TRY(ensure(ctx, &ctx->d_y, &ctx->y_cap, mb));
@@ -1412,17 +1422,17 @@ int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out)
     NFM_CK(launch_norm2((const float2*)v0, ctx->N, part, sc + 0, st));
     NFM_CK(launch_normalize((const float2*)v0, v, ctx->N, sc + 0, st));
     for (int it = 0; it < iters; ++it) {
-        NFM_TRY(enqueue_forward(ctx, ctx->d_pairs_all, ctx->P, v, nullptr, y));
-        NFM_TRY(enqueue_adjoint(ctx, ctx->d_pairs_all, ctx->P, y, g, nullptr, 0.f, 0.f));
+        NFM_TRY(enqueue_forward(ctx, pairs, n_pairs, v, nullptr, y));
+        NFM_TRY(enqueue_adjoint(ctx, pairs, n_pairs, y, g, nullptr, 0.f, 0.f));
         const int e0 = prof_mark(ctx);
         NFM_CK(launch_norm2(g, ctx->N, part, sc + 0, st));
         NFM_CK(launch_normalize(g, v, ctx->N, sc + 0, st));
         prof_pair(ctx, 3, e0, prof_mark(ctx));
     }
-    NFM_TRY(enqueue_forward(ctx, ctx->d_pairs_all, ctx->P, v, nullptr, y));
-    NFM_CK(launch_norm2(y, ctx->M, part, sc + 1, st));
+    NFM_TRY(enqueue_forward(ctx, pairs, n_pairs, v, nullptr, y));
+    NFM_CK(launch_norm2(y, rows, part, sc + 1, st));
     NFM_CK(launch_norm2(v, ctx->N, part, sc + 2, st));
-    NFM_CK(launch_ratio(sc + 1, sc + 2, (double)ctx->M, sc + 3, st));
+    NFM_CK(launch_ratio(sc + 1, sc + 2, (double)rows, sc + 3, st));
     double L = 0;
     NFM_CK(cudaMemcpyAsync(&L, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
     NFM_CK(st ? cudaStreamSynchronize(st) : cudaDeviceSynchronize());
@@ -1430,6 +1440,24 @@ int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out)
     if (!std::isfinite(L)) return fail(ctx, NFM_ERR_NUMERIC, "power iteration gave a non-finite L");
     *L_out = L;
     return NFM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out)
+{
+    NFM_TRY(require_geom(ctx));
+    return power_iteration_impl(ctx, ctx->d_pairs_all, ctx->P, iters, v0, L_out);
+}
+
+int nfm_power_iteration_pairs(nfm_ctx* ctx, const int* pairs, int n_pairs, int iters, const float* v0,
+                              double* L_out)
+{
+    NFM_TRY(require_geom(ctx));
+    if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
+    NFM_TRY(check_ptr(ctx, pairs, "pairs", 4));
+    return power_iteration_impl(ctx, pairs, n_pairs, iters, v0, L_out);
 }
 
 int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, double* F_out)
@@ -1492,6 +1520,18 @@ int nfm_synchronize(nfm_ctx* ctx)
     DevGuard guard(ctx->device);
     NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
     return check_flags(ctx);
+}
+
+static_assert((int)NFM_HOOK_TC_SKIP_ISSUE == (int)HOOK_TC_SKIP_ISSUE, "hook flags of the header and the kernels");
+
+int nfm_set_test_hooks(nfm_ctx* ctx, int flags, int wait_ms)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    if (flags & ~NFM_HOOK_TC_SKIP_ISSUE) return fail(ctx, NFM_ERR_ARG, "unknown test hook flags 0x%x", flags);
+    if (wait_ms < 0 || wait_ms > 60000) return fail(ctx, NFM_ERR_ARG, "wait_ms must lie in [0, 60000]");
+    ctx->hooks = flags;
+    ctx->tc_wait_ns = wait_ms > 0 ? (unsigned long long)wait_ms * 1000000ull : 1000000000ull;
+    return NFM_OK;
 }
 
 int nfm_profile_enable(nfm_ctx* ctx, int enable)

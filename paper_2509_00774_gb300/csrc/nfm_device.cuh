@@ -72,9 +72,14 @@ struct OpDesc {
     const float2* pulse;   // [K] or nullptr (p = 1)
     int T, R, K, K1, P;
     int* err;              // device error flags
+    unsigned long long wait_ns = 1000000000ull;   // limit of one bounded wait on the tensor core
+    int hooks = 0;         // test hooks (HOOK_*), 0 in normal operation
 };
 
 enum : int { ERRF_PAIR = 1, ERRF_TIMEOUT = 2 };
+// HOOK_TC_SKIP_ISSUE: the tensor-core kernels issue no MMA and no commit, so their bounded waits run
+// out and the timeout path runs (no outstanding tensor-core work, nothing faults or hangs)
+enum : int { HOOK_TC_SKIP_ISSUE = 1 };
 
 __device__ __forceinline__ float frac_turns(float x) { return x - rintf(x); }
 

@@ -136,13 +136,21 @@ __global__ void __launch_bounds__(128) adj_tc_kernel(OpDesc op, AdjArgs a, const
     // pending pairs (ring of two, slot = pair & 1): phasor a, block step Z and 1/scale
     float2 pa0 = make_float2(0.f, 0.f), pa1 = pa0, pZ0 = pa0, pZ1 = pa0;
     float pinv0 = 0.f, pinv1 = 0.f;
-    int issued = 0;                        // pairs whose MMAs are committed
+    int issued = 0;                        // pairs whose MMAs are issued (chunk granularity)
     int done = 0;                          // pairs whose result has been read back
+    int committed = 0;                     // pairs whose MMAs were actually committed (same in every thread)
+    const bool issue = !(op.hooks & HOOK_TC_SKIP_ISSUE);
 
     auto finish = [&](int q) {             // read TMEM of pair q and add its contribution
+        if (!ok) return;                   // after a timeout: no TMEM reads (ok is uniform over the CTA)
         const int buf = q & 1;
-        const bool done = mbar_wait(&bar[buf], (uint32_t)((q >> 1) & 1));
-        if (!done) ok = false;
+        // uniform outcome; on a timeout every committed pair from q on gets one more bounded wait so that
+        // no MMA is in flight when TMEM is released, no further MMA is issued, and the output is left unwritten
+        if (!__syncthreads_and(mbar_wait(&bar[buf], (uint32_t)((q >> 1) & 1), op.wait_ns))) {
+            for (int qq = q; qq < committed; ++qq) mbar_wait(&bar[qq & 1], (uint32_t)((qq >> 1) & 1), op.wait_ns);
+            ok = false;
+            return;
+        }
         tc_fence_after();
         float h[16];
         tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * TC_N), h);
@@ -218,7 +226,9 @@ __global__ void __launch_bounds__(128) adj_tc_kernel(OpDesc op, AdjArgs a, const
             fence_proxy_async();
             tc_fence_before();
             __syncthreads();
-            if (v == 0) {
+            const bool go = ok && issue;    // uniform
+            if (go) ++committed;
+            if (v == 0 && go) {
                 tc_fence_after();
                 const uint32_t d = tbase + (uint32_t)(buf * TC_N);
                 const uint32_t a0 = smem_u32(Ab);
@@ -250,7 +260,7 @@ __global__ void __launch_bounds__(128) adj_tc_kernel(OpDesc op, AdjArgs a, const
     }
 
     const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
-    if (ix >= op.g.nx || iy >= op.g.ny || iz >= op.g.nz) return;
+    if (!ok || ix >= op.g.nx || iy >= op.g.ny || iz >= op.g.nz) return;
     const size_t n = ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
     if (a.s) {
         const float2 sv = a.s[n];

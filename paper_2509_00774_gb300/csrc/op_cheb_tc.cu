@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
         fence_proxy_async();
         tc_fence_before();
         __syncthreads();
-        if (tid == 0) {
+        const bool issue = !(op.hooks & HOOK_TC_SKIP_ISSUE);
+        if (tid == 0 && issue) {
             tc_fence_after();
             const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
             for (int s = 0; s < KS; ++s) {
@@ -240,7 +241,14 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
             }
             tc_commit(bar);
         }
-        if (!mbar_wait(bar, (uint32_t)(chunk & 1))) ok = false;
+        // the wait's outcome is made uniform over the CTA: on a timeout no thread reads TMEM, no further
+        // MMA is issued and the iterate (or g) is left unwritten; the MMAs already committed get one more
+        // bounded wait so that none is in flight when TMEM is released
+        if (!__syncthreads_and(mbar_wait(bar, (uint32_t)(chunk & 1), op.wait_ns))) {
+            if (issue) mbar_wait(bar, (uint32_t)(chunk & 1), op.wait_ns);
+            ok = false;
+            break;
+        }
         tc_fence_after();
         if (warp < 4) {                      // lanes 32 warp .. : rows (tile, pair, re/im)
             float d[32];
@@ -299,7 +307,7 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
         tmem_dealloc(tbase, 32);
     }
 
-    if (!tile_ok) return;                    // uniform over a warp (a warp lies in one tile)
+    if (!tile_ok || !ok) return;             // uniform over a warp (a warp lies in one tile; ok per CTA)
     const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
     const bool in_grid = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
     const size_t n = in_grid ? ((size_t)iz * op.g.ny + iy) * op.g.nx + ix : 0;

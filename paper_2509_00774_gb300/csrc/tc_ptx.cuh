@@ -10,7 +10,7 @@
 namespace nfm {
 namespace tc {
 
-constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;      // bounded mbarrier spin
+constexpr uint32_t TC_WAIT_SPIN_LIMIT = 1u << 28;  // backstop on the number of polls of one wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -40,11 +40,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait for phase `parity` of bar; false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ uint64_t globaltimer_ns()
 {
-    for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for phase `parity` of bar: false if it did not complete within limit_ns nanoseconds
+// of the global timer (or TC_WAIT_SPIN_LIMIT polls, whichever comes first).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0; i < TC_WAIT_SPIN_LIMIT; i += 32) {
+        for (int j = 0; j < 32; ++j)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

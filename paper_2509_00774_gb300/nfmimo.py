@@ -75,9 +75,11 @@ def load_library(path: str | None = None):
         "nfm_prox_step": (i, [vp, vp, vp, f, f, ctypes.c_longlong, vp]),
         "nfm_prox_step_backward": (i, [vp, vp, vp, f, f, ctypes.c_longlong, vp, vp, vp, vp]),
         "nfm_power_iteration": (i, [vp, i, vp, ctypes.POINTER(d)]),
+        "nfm_power_iteration_pairs": (i, [vp, vp, i, i, vp, ctypes.POINTER(d)]),
         "nfm_objective": (i, [vp, vp, vp, d, ctypes.POINTER(d)]),
         "nfm_lambda_max": (i, [vp, vp, ctypes.POINTER(d)]),
         "nfm_synchronize": (i, [vp]),
+        "nfm_set_test_hooks": (i, [vp, i, i]),
         "nfm_profile_enable": (i, [vp, i]),
         "nfm_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]),
         "nfm_batch_destroy": (None, [vp]),
@@ -250,11 +252,13 @@ class Context:
         import torch
         return _ptr(t, torch.int32, name, self.device)
 
+    def _need_geom(self):
+        if self.K is None:
+            raise NfmError(-4, "no geometry: call set_geometry first")
+
     def _sizes(self, **want):
         """Raise NfmError(-1) unless every named tensor has the given element count (checked before any
         raw pointer reaches the library, which cannot see the extents of what it is given)."""
-        if self.K is None:
-            raise NfmError(-4, "no geometry: call set_geometry first")
         for name, (t, n) in want.items():
             if t.numel() != n:
                 raise NfmError(-1, f"{name} has {t.numel()} elements, expected {n}")
@@ -262,10 +266,9 @@ class Context:
     def forward(self, pairs, s, y=None):
         """y = A_B s for the pair list `pairs` (int32, device); returns y [n_pairs*K]."""
         import torch
+        self._need_geom()
         n = pairs.numel()
         if y is None:
-            if self.K is None:
-                raise NfmError(-4, "no geometry: call set_geometry first")
             y = torch.empty(n * self.K, dtype=torch.complex64, device=s.device)
         self._sizes(s=(s, self.N), y=(y, n * self.K))
         self._check(self._lib.nfm_forward(self._h, self._i(pairs, "pairs"), n, self._c(s, "s"), self._c(y, "y")))
@@ -273,6 +276,7 @@ class Context:
 
     def forward_noalloc(self, pairs, s, y):
         """y = A_B s through the allocation-free entry point (y must be given; nothing is allocated)."""
+        self._need_geom()
         self._sizes(s=(s, self.N), y=(y, pairs.numel() * self.K))
         self._check(self._lib.nfm_forward_noalloc(self._h, self._i(pairs, "pairs"), pairs.numel(),
                                                   self._c(s, "s"), self._c(y, "y")))
@@ -281,22 +285,23 @@ class Context:
     def adjoint(self, pairs, r, g=None):
         """g = A_B^H r; returns g [N]."""
         import torch
+        self._need_geom()
         n = pairs.numel()
         if g is None:
-            if self.N is None:
-                raise NfmError(-4, "no geometry: call set_geometry first")
             g = torch.empty(self.N, dtype=torch.complex64, device=r.device)
         self._sizes(r=(r, n * self.K), g=(g, self.N))
         self._check(self._lib.nfm_adjoint(self._h, self._i(pairs, "pairs"), n, self._c(r, "r"), self._c(g, "g")))
         return g
 
     def spgm_step(self, y, s, pairs, eta, lam):
+        self._need_geom()
         self._sizes(y=(y, self.P * self.K), s=(s, self.N))
         self._check(self._lib.nfm_spgm_step(self._h, self._c(y, "y"), self._c(s, "s"), self._i(pairs, "pairs"),
                                             pairs.numel(), float(eta), float(lam)))
         return s
 
     def spgm_epoch(self, y, s, perm, pairs_per_batch, eta, lam):
+        self._need_geom()
         self._sizes(y=(y, self.P * self.K), s=(s, self.N), perm=(perm, self.P))
         self._check(self._lib.nfm_spgm_epoch(self._h, self._c(y, "y"), self._c(s, "s"), self._i(perm, "perm"),
                                              int(pairs_per_batch), float(eta), float(lam)))
@@ -368,6 +373,21 @@ class Context:
         self._check(self._lib.nfm_power_iteration(self._h, int(iters), self._c(v0, "v0"), ctypes.byref(L)))
         return L.value
 
+    def power_iteration_pairs(self, pairs, v0, iters: int = 50) -> float:
+        """L_B = lambda_max(A_B^H A_B) / B for the minibatch of the listed pairs (int32, device)."""
+        self._need_geom()
+        self._sizes(v0=(v0, self.N))
+        L = ctypes.c_double()
+        self._check(self._lib.nfm_power_iteration_pairs(self._h, self._i(pairs, "pairs"), pairs.numel(), int(iters),
+                                                        self._c(v0, "v0"), ctypes.byref(L)))
+        return L.value
+
+    def spgm_lipschitz(self, perm, pairs_per_batch, v0, iters: int = 50) -> float:
+        """Largest L_B over the minibatches that one epoch with permutation `perm` (int32, device) takes."""
+        P = perm.numel()
+        return max(self.power_iteration_pairs(perm[c:c + pairs_per_batch], v0, iters)
+                   for c in range(0, P, int(pairs_per_batch)))
+
     def objective(self, y, s, lam) -> float:
         F = ctypes.c_double()
         self._check(self._lib.nfm_objective(self._h, self._c(y, "y"), self._c(s, "s"), float(lam), ctypes.byref(F)))
@@ -380,6 +400,14 @@ class Context:
 
     def synchronize(self):
         self._check(self._lib.nfm_synchronize(self._h))
+
+    HOOK_TC_SKIP_ISSUE = 1
+
+    def set_test_hooks(self, flags=0, wait_ms=0):
+        """Error-path hooks for tests: flags = HOOK_TC_SKIP_ISSUE makes the tensor-core kernels issue no
+        MMA, so their bounded waits (wait_ms; 0 = 1000 ms) run out and the next synchronising call raises
+        NfmError(-5) with the output left unwritten.  flags = 0 restores normal operation."""
+        self._check(self._lib.nfm_set_test_hooks(self._h, int(flags), int(wait_ms)))
 
     PROFILE_KINDS = ("forward_partial", "forward_reduce", "adjoint", "reductions")
 

@@ -76,3 +76,24 @@ def make_ctx(geom, algorithm=None):
 def term_scale(dense_block, x):
     """sqrt(sum_j |B_ij x_j|^2) for every row i of an FP64 dense block."""
     return np.sqrt((np.abs(dense_block) ** 2) @ (np.abs(x) ** 2))
+
+
+def spgm_eta(o, row_sets):
+    """SPGM step for a small problem: 1 / max over the minibatches of L_B = lambda_max(A_B A_B^H) / B from
+    the oracle's dense rows (FP64 eigensolver), rounded to FP32.  A step of 1/L (full batch) makes SPGM
+    diverge on these geometries: a few pairs' L_B is several times L."""
+    cols = np.arange(o.N)
+    LB = max(float(np.linalg.eigvalsh((lambda A: A @ A.conj().T / A.shape[0])(o.dense(np.asarray(r), cols)))[-1])
+             for r in row_sets)
+    return float(np.float32(1.0 / LB))
+
+
+def spgm_eta_epochs(o, seed, bp, epochs):
+    """spgm_eta over every minibatch of `epochs` epochs of seeded permutations in chunks of bp pairs."""
+    from paper_2509_00774_gb300 import inputs as I
+    sets = []
+    for e in range(epochs):
+        perm = I.epoch_permutation(o.P, seed, e)
+        sets += [o.rows_of_pairs(perm[c:c + bp]) for c in range(0, o.P, bp)]
+    uniq = {tuple(sorted(r)) for r in sets}
+    return spgm_eta(o, [np.array(r) for r in uniq])

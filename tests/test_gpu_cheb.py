@@ -7,7 +7,7 @@ import pytest
 from oracle import Oracle, nmse
 from paper_2509_00774_gb300 import inputs as I
 from paper_2509_00774_gb300 import workloads as W
-from tests.gpu_helpers import NMSE_TOL, REL_L2, make_ctx, to_dev, to_host
+from tests.gpu_helpers import NMSE_TOL, REL_L2, make_ctx, spgm_eta_epochs, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -47,8 +47,7 @@ def test_spgm_small_both_algorithms(algo):
     o = Oracle(w.geom)
     y = I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db)
     y = y.astype(np.complex64).astype(np.complex128)
-    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
-    eta = float(np.float32(1.0 / L))
+    eta = spgm_eta_epochs(o, w.seeds["perm"], w.pairs_per_batch, w.epochs)
     lam = float(np.float32(0.05 * o.lambda_max(y)))
     ctx = make_ctx(w.geom, algorithm=algo)
     s_orc = np.zeros(o.N, dtype=np.complex128)
@@ -92,8 +91,7 @@ def test_autotuned_small_spgm_matches_oracle():
     o = Oracle(w.geom)
     y = I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db)
     y = y.astype(np.complex64).astype(np.complex128)
-    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
-    eta = float(np.float32(1.0 / L))
+    eta = spgm_eta_epochs(o, w.seeds["perm"], w.pairs_per_batch, w.epochs)
     lam = float(np.float32(0.05 * o.lambda_max(y)))
     ctx = make_ctx(w.geom)
     choice = ctx.autotune(w.pairs_per_batch)

@@ -6,7 +6,7 @@ import pytest
 from oracle import Oracle, nmse
 from paper_2509_00774_gb300 import inputs as I
 from paper_2509_00774_gb300 import workloads as W
-from tests.gpu_helpers import NMSE_TOL, assert_close_operator, make_ctx, term_scale, to_dev, to_host
+from tests.gpu_helpers import NMSE_TOL, assert_close_operator, make_ctx, spgm_eta_epochs, term_scale, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -59,7 +59,7 @@ def test_general_spgm_and_power_iteration():
     v0 = _c64(I.complex_gaussian(o.N, 8))
     L_gpu, L_orc = ctx.power_iteration(to_dev(v0), 30), o.power_iteration(v0, 30)
     assert abs(L_gpu - L_orc) <= 1e-4 * L_orc
-    eta = float(np.float32(1.0 / L_orc))
+    eta = spgm_eta_epochs(o, 9, 4, 5)
     lam = float(np.float32(0.05 * o.lambda_max(y)))
     s_o = np.zeros(o.N, dtype=np.complex128)
     s_g = to_dev(np.zeros(o.N))

@@ -7,7 +7,7 @@ from oracle import Oracle, nmse
 from paper_2509_00774_gb300 import inputs as I
 from paper_2509_00774_gb300 import workloads as W
 from paper_2509_00774_gb300.nfmimo import NfmError
-from tests.gpu_helpers import NMSE_TOL, OBJ_TOL, make_ctx, to_dev, to_host
+from tests.gpu_helpers import NMSE_TOL, OBJ_TOL, make_ctx, spgm_eta, spgm_eta_epochs, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -50,8 +50,7 @@ def test_spgm_small_matches_oracle(bp):
     """All 30 epochs of the small workload; bp = 5 leaves a 1-pair last chunk."""
     w, o, y = _small_problem()
     ctx = make_ctx(w.geom)
-    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
-    eta = float(np.float32(1.0 / L))
+    eta = spgm_eta_epochs(o, w.seeds["perm"], bp, w.epochs)
     lam = float(np.float32(0.05 * o.lambda_max(y)))
     s_orc = np.zeros(o.N, dtype=np.complex128)
     s_gpu = to_dev(np.zeros(o.N))
@@ -92,8 +91,7 @@ def test_solve_termination_rule():
     """Sec. V: epochs run until the change in reflectivity magnitudes drops below tol."""
     w, o, y = _small_problem()
     ctx = make_ctx(w.geom)
-    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
-    eta = float(np.float32(1.0 / L))
+    eta = spgm_eta_epochs(o, w.seeds["perm"], 4, 60)
     lam = float(np.float32(0.05 * o.lambda_max(y)))
     tol, E = 2e-3, 60
     perms = np.stack([I.epoch_permutation(o.P, w.seeds["perm"], e) for e in range(E)]).astype(np.int32)
@@ -124,8 +122,8 @@ def test_cartesian_minibatch_steps_match_oracle(comp):
     n_f, n_t, n_r = comp
     w, o, y = _small_problem()
     ctx = make_ctx(w.geom)
-    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
-    eta = float(np.float32(0.5 / L))
+    draws = [I.cartesian_minibatch(o.T, o.R, o.K, n_t, n_r, n_f, seed=4, it=it) for it in range(12)]
+    eta = spgm_eta(o, [np.array([p * o.K + k for p in pairs for k in np.flatnonzero(mask)]) for pairs, mask in draws])
     lam = float(np.float32(0.05 * o.lambda_max(y)))
     s_orc = np.zeros(o.N, dtype=np.complex128)
     s_gpu = to_dev(np.zeros(o.N))
@@ -146,8 +144,7 @@ def test_elastic_net_and_tikhonov_spgm_match_oracle(w1, w2):
     o = Oracle(w.geom, w1=w1, w2=w2)
     ctx = make_ctx(w.geom)
     ctx.set_regularizer(w1, w2)
-    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
-    eta = float(np.float32(1.0 / L))
+    eta = spgm_eta_epochs(o, w.seeds["perm"], 4, 10)
     lam = float(np.float32(0.05 * o.lambda_max(y)))
     s_orc = np.zeros(o.N, dtype=np.complex128)
     s_gpu = to_dev(np.zeros(o.N))
@@ -281,8 +278,7 @@ def test_group_regulariser_spgm_matches_oracle(grid_kind, w1, w2, w3, precision)
     ctx.set_precision(precision)
     ctx.set_regularizer(w1, w2)
     ctx.set_group_weight(w3)
-    L = o.power_iteration(I.complex_gaussian(o.N, 5), 50)
-    eta = float(np.float32(1.0 / L))
+    eta = spgm_eta_epochs(o, 6, 4, 10)
     lam = float(np.float32(0.2 * o.lambda_max(y)))     # strong enough that 20-35% of the blocks vanish
     s_orc = np.zeros(o.N, dtype=np.complex128)
     s_gpu = to_dev(np.zeros(o.N))

@@ -12,7 +12,7 @@ import pytest
 from oracle import Oracle, nmse
 from paper_2509_00774_gb300 import inputs as I
 from paper_2509_00774_gb300 import workloads as W
-from tests.gpu_helpers import NMSE_TOL, OBJ_TOL, make_ctx, term_scale, to_dev, to_host
+from tests.gpu_helpers import NMSE_TOL, OBJ_TOL, make_ctx, spgm_eta_epochs, term_scale, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -82,8 +82,7 @@ def test_tc_spgm_small_matches_oracle(mode):
     y = _c64(I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, 1), w.snr_db))
     ctx = make_ctx(w.geom)
     ctx.set_precision(mode)
-    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
-    eta = float(np.float32(1.0 / L))
+    eta = spgm_eta_epochs(o, w.seeds["perm"], 4, w.epochs)
     lam = float(np.float32(0.05 * o.lambda_max(y)))
     s_orc = np.zeros(o.N, dtype=np.complex128)
     s_gpu = to_dev(np.zeros(o.N))
@@ -95,3 +94,41 @@ def test_tc_spgm_small_matches_oracle(mode):
         assert nmse(to_host(s_gpu), s_orc) <= NMSE_TOL, e
     F_gpu, F_orc = o.objective(y, to_host(s_gpu), lam), o.objective(y, s_orc, lam)
     assert abs(F_gpu - F_orc) <= OBJ_TOL * F_orc
+
+
+@pytest.mark.parametrize("algorithm", ["chebyshev", "direct"])
+def test_tc_wait_timeout_is_reported_and_leaves_the_iterate(algorithm):
+    """The tensor-core kernels' bounded wait on their MMA barrier runs out (the test hook makes them
+    issue no MMA, so nothing is in flight): the step must leave s bit for bit unchanged, the next
+    synchronise must report NFM_ERR_TIMEOUT (-5), and the context must stay usable afterwards."""
+    from paper_2509_00774_gb300.nfmimo import NfmError
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    y = _c64(I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, 1), 30.0))
+    ctx = make_ctx(w.geom, algorithm)
+    ctx.set_precision("tc_bf16x3")
+    pairs = to_dev(I.epoch_permutation(o.P, 3, 0)[:4], "int32")
+    s0 = _c64(I.complex_gaussian(o.N, 8)) * 0.1
+    s = to_dev(s0)
+    y_d = to_dev(y)
+    ctx.set_test_hooks(ctx.HOOK_TC_SKIP_ISSUE, wait_ms=2)
+    ctx.spgm_step(y_d, s, pairs, 0.05, 1e-3)
+    with pytest.raises(NfmError) as ei:
+        ctx.synchronize()
+    assert ei.value.code == -5
+    assert np.array_equal(to_host(s), s0.astype(np.complex64).astype(np.complex128))
+    # plain adjoint: the output is left unwritten as well
+    g = to_dev(np.full(o.N, 7.0 + 7.0j))
+    ctx.adjoint(pairs, to_dev(np.ones(4 * o.K)), g)
+    with pytest.raises(NfmError) as ei:
+        ctx.synchronize()
+    assert ei.value.code == -5
+    assert np.all(to_host(g) == 7.0 + 7.0j)
+    # normal operation again: the same step matches the oracle
+    ctx.set_test_hooks(0)
+    ctx.spgm_step(y_d, s, pairs, 0.05, 1e-3)
+    ctx.synchronize()
+    want = o.spgm_step(y, s0.astype(np.complex64).astype(np.complex128), I.epoch_permutation(o.P, 3, 0)[:4],
+                       0.05, 1e-3)
+    assert nmse(to_host(s), want) <= NMSE_TOL
+    ctx.close()

@@ -448,3 +448,59 @@ def test_data_fidelity_gradient_by_central_differences():
             d = (o.data_fidelity(y, sp) - o.data_fidelity(y, sm)) / (2 * eps)
             fd[n] += d if part == "re" else 1j * d
     assert np.max(np.abs(fd - g)) <= 1e-7 * np.max(np.abs(g))
+
+
+# ---------------------------------------------------------------------------
+# Sec. IV-A: the step of the minibatch gradient
+# ---------------------------------------------------------------------------
+def test_minibatch_power_iteration_matches_eigvalsh():
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    v0 = I.complex_gaussian(o.N, 3)
+    for pairs in ([5], [3, 12, 0, 7]):
+        A = o.dense(o.rows_of_pairs(pairs), np.arange(o.N))
+        top = float(np.linalg.eigvalsh(A @ A.conj().T / A.shape[0])[-1])
+        assert abs(o.power_iteration(v0, 300, pairs=pairs) - top) <= 1e-8 * top
+    # the full list of pairs is the full-batch L
+    assert abs(o.power_iteration(v0, 20, pairs=np.arange(o.P)) - o.power_iteration(v0, 20)) <= 1e-12 * o.M
+
+
+def test_spgm_step_needs_the_minibatch_constant():
+    """On the small workload a 4-pair minibatch has L_B up to several times the full-batch L, so
+    SPGM with eta = 1/L diverges (the iterate grows without bound), while eta = 1/max L_B over the
+    epoch's minibatches keeps it bounded: the reading of the step used for SPGM."""
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    y = I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db)
+    v0 = I.complex_gaussian(o.N, w.seeds["power"])
+    L = o.power_iteration(v0, 50)
+    LB = o.spgm_lipschitz(I.epoch_permutation(o.P, w.seeds["perm"], 0), 4, v0, 50)
+    assert LB > 2.0 * L
+    lam = 0.05 * o.lambda_max(y)
+    norms = {}
+    for name, eta in (("1/L", 1.0 / L), ("1/L_B", 1.0 / LB)):
+        s = np.zeros(o.N, dtype=np.complex128)
+        for e in range(20):
+            s = o.spgm_epoch(y, s, I.epoch_permutation(o.P, w.seeds["perm"], e), 4, eta, lam)
+        norms[name] = np.linalg.norm(s)
+    ref = np.linalg.norm(w.scene_vector())        # the scene that made y
+    assert norms["1/L"] > 1e4 * ref            # diverged
+    assert norms["1/L_B"] < 10.0 * ref         # bounded
+
+
+def test_dense_minimiser_is_optimal():
+    """The reference minimiser of Eq. 3 used to time convergence: KKT conditions hold (from the dense
+    gradient, checked independently here) and no PGM iterate started from it lowers the objective."""
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    y = I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]), w.snr_db)
+    L = o.power_iteration(I.complex_gaussian(o.N, w.seeds["power"]), 50)
+    lam = 0.05 * o.lambda_max(y)
+    s, kkt = o.minimiser_dense(y, lam, L, iters=6000)
+    A = o.dense(np.arange(o.M), np.arange(o.N))
+    assert kkt < 1e-4 and _kkt_violation(A, o.M, y, s, lam) < 1e-4
+    F = o.objective(y, s, lam)
+    t = s
+    for _ in range(50):
+        t = o.pgm_step(y, t, 1.0 / L, lam)
+        assert o.objective(y, t, lam) >= F - 1e-9 * F
