@@ -17,11 +17,11 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnfmimo.so")
 SOURCES = ["nfm_api.cu", "op_forward.cu", "op_adjoint.cu", "op_adjoint_tc.cu", "op_misc.cu", "op_prox.cu", "op_general.cu",
-           "op_cheb.cu", "op_cheb_tc.cu"]
+           "op_cheb.cu", "op_cheb_tc.cu", "op_cheb_tc_fwd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # per-file extra flags: the expansion kernels handle no subnormal values (distances, unit phasors,
 # Chebyshev values in [-1, 1]); flushing them lets rsqrt / reciprocal skip their subnormal paths
-FILE_FLAGS = {"op_cheb.cu": ["-ftz=true"], "op_cheb_tc.cu": ["-ftz=true"]}
+FILE_FLAGS = {"op_cheb.cu": ["-ftz=true"], "op_cheb_tc.cu": ["-ftz=true"], "op_cheb_tc_fwd.cu": ["-ftz=true"]}
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 

@@ -118,6 +118,7 @@ struct nfm_ctx {
     bool fwd_cheb_attr[CHEB_MAX_L + 1][2] = {};
     bool adj_cheb_attr[CHEB_MAX_L + 1] = {};
     bool adj_cheb_tc_attr[2][CHEB_MAX_L + 1] = {};
+    bool fwd_cheb_tc_attr[2][CHEB_MAX_L + 1] = {};
     // launch shapes of the expansion forward chosen by nfm_autotune, per minibatch size
     struct FwdShape { int n_pairs, threads, group, pch, chunks; bool direct; };
     std::vector<FwdShape> fwd_tuned;
@@ -522,9 +523,64 @@ int launch_cheb_forward_shape(nfm_ctx* ctx, const ChebShape& sh, const int* pair
     return NFM_OK;
 }
 
+// Tensor-core expansion forward (precision modes): 256-thread CTAs, 16, 32 or 64 pairs per CTA, one
+// wave of two CTAs per SM over the voxel-tile chunks.
+int enqueue_forward_cheb_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
+                            float2* out, const unsigned char* fmask)
+{
+    const int LT = ctx->cheb_L;
+    const bool f16 = ctx->precision == NFM_TC_FP16X3;
+    const int pch = n_pairs <= 16 ? 16 : n_pairs <= 32 ? 32 : 64;
+    const int TS = 64 / pch;
+    const size_t smem = fwd_cheb_tc_smem_bytes(LT, ctx->K, pch);
+    if (smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "tensor-core expansion forward needs %zu B shared memory", smem);
+    if (!ctx->fwd_cheb_tc_attr[f16][LT]) {
+        NFM_CK(cudaFuncSetAttribute(fwd_cheb_tc_kernel_ptr(LT, f16), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ctx->smem_optin));
+        ctx->fwd_cheb_tc_attr[f16][LT] = true;
+    }
+    const int n_groups = (n_pairs + pch - 1) / pch;
+    const int n_slots = n_groups * pch;
+    long long nch = (2LL * ctx->num_sms + n_groups - 1) / n_groups;
+    const long long max_ch = (ctx->gd.n_tiles + TS - 1) / TS;
+    if (nch > max_ch) nch = max_ch;
+    if (nch > 65535) nch = 65535;
+    if (nch < 1) nch = 1;
+    NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, (size_t)nch * n_slots * ctx->K * sizeof(float2)));
+    ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
+    FwdArgs a;
+    a.pairs = pairs;
+    a.n_pairs = n_pairs;
+    a.s = s;
+    a.partial = (float2*)ctx->d_partial;
+    a.n_slots = n_slots;
+    a.VS = pch;
+    a.tiles_base = (int)(ctx->gd.n_tiles / nch);
+    a.tiles_rem = (int)(ctx->gd.n_tiles % nch);
+    OpDesc op = op_desc(ctx);
+    const int e0 = prof_mark(ctx);
+    NFM_CK(launch_fwd_cheb_tc(op, cd, a, dim3(n_groups, (unsigned)nch), f16, smem, ctx->stream));
+    const int e1 = prof_mark(ctx);
+    ReduceArgs ra;
+    ra.partial = (const float2*)ctx->d_partial;
+    ra.n_chunks = (int)nch;
+    ra.n_slots = n_slots;
+    ra.n_out = n_pairs * ctx->K;
+    ra.pairs = pairs;
+    ra.y_obs = y_obs;
+    ra.fmask = fmask;
+    ra.out = out;
+    NFM_CK(launch_fwd_reduce(op, ra, ctx->stream));
+    const int e2 = prof_mark(ctx);
+    prof_pair(ctx, 0, e0, e1);
+    prof_pair(ctx, 1, e1, e2);
+    return NFM_OK;
+}
+
 int enqueue_forward_cheb(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
                          float2* out, const unsigned char* fmask)
 {
+    if (ctx->precision != NFM_FP32) return enqueue_forward_cheb_tc(ctx, pairs, n_pairs, s, y_obs, out, fmask);
     ChebShape sh;
     bool tuned = false;
     for (const auto& t : ctx->fwd_tuned)

@@ -91,6 +91,12 @@ const void* adj_cheb_kernel_ptr(int LT);
 cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
                             int group, size_t smem, cudaStream_t st);
 cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, size_t smem, cudaStream_t st);
+// tensor-core (tcgen05) expansion stage of the forward (op_cheb_tc_fwd.cu): 256 threads, a.VS = pairs per
+// CTA in {16, 32, 64}, K <= 128
+size_t fwd_cheb_tc_smem_bytes(int LT, int K, int pch);
+const void* fwd_cheb_tc_kernel_ptr(int LT, bool f16);
+cudaError_t launch_fwd_cheb_tc(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, bool f16,
+                               size_t smem, cudaStream_t st);
 // tensor-core (tcgen05) coefficient stage of the expansion adjoint (op_cheb_tc.cu), K <= 128, L <= 32
 size_t adj_cheb_tc_smem_bytes(int K);
 const void* adj_cheb_tc_kernel_ptr(int LT, bool f16);

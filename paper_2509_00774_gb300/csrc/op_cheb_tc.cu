@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    bool ok = true;
+    bool ok = true, hold = false;
     float gr = 0.f, gi = 0.f;
 
     for (int c0 = 0, chunk = 0; c0 < a.n_pairs; c0 += CTC_PCH, ++chunk) {
@@ -139,7 +139,11 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
                 p8[tid] = tile_step_cis_exact(pt[tid], 8);
             }
         }
-        if (c0 == 0) pdl_wait();             // r comes from the previous kernel
+        if (c0 == 0) {
+            pdl_wait();                      // r comes from the previous kernel
+            // a tensor-core forward of the same step whose wait ran out left r stale: keep the iterate
+            hold = (*reinterpret_cast<volatile int*>(op.err) & ERRF_TIMEOUT) != 0;
+        }
         // the chunk's residual rows into shared memory (all copies in flight at once)
         for (int e = tid; e < nc * K; e += CTC_THREADS) {
             const int j = e / K, k = e - j * K;
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
         tmem_dealloc(tbase, 32);
     }
 
-    if (!tile_ok || !ok) return;             // uniform over a warp (a warp lies in one tile; ok per CTA)
+    if (!tile_ok || !ok || (hold && a.s)) return;   // uniform over a warp (a warp lies in one tile; ok per CTA)
     const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
     const bool in_grid = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
     const size_t n = in_grid ? ((size_t)iz * op.g.ny + iy) * op.g.nx + ix : 0;

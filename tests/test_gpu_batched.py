@@ -95,3 +95,74 @@ def test_batch_of_uneven_scenes_from_the_48_scene_set():
     for i in range(3):
         assert torch.equal(ss[i], sq[i]), ws[i].name
     batch.close()
+
+
+def test_batched48_sampled_operator_matches_oracle():
+    """Every scene of the 48-scene uneven set (grids 32..96, 8..24 TX/RX, 32..96 freqs): the forward of a
+    16-pair minibatch on 64 sampled rows (scene = the workload's reflectivity, so the oracle's forward is
+    a sparse sum) and the adjoint of a random residual on 64 sampled voxels, against the oracle."""
+    from tests.gpu_helpers import REL_L2, ELEM_FACTOR
+    worst = 0.0
+    for i in range(48):
+        w = W.batched_scene(i)
+        g = w.geom
+        o = Oracle(g)
+        ctx = make_ctx(g)
+        rng = np.random.default_rng(500 + i)
+        pairs = I.epoch_permutation(g.P, 3, i)[:16]
+        rows = o.rows_of_pairs(pairs)
+        s = w.scene_vector()
+        y = to_host(ctx.forward(to_dev(pairs, "int32"), to_dev(s)))
+        sel = np.sort(rng.choice(rows.size, 64, replace=False))
+        want = o.forward_sparse(_c64(s), rows=rows[sel])
+        err = y[sel] - want
+        rel = np.linalg.norm(err) / np.linalg.norm(want)
+        rms = np.linalg.norm(want) / np.sqrt(want.size)
+        assert rel <= REL_L2 and np.max(np.abs(err)) <= ELEM_FACTOR * REL_L2 * rms, (w.name, "forward", rel)
+        r = _c64(I.complex_gaussian(rows.size, 600 + i))
+        gad = to_host(ctx.adjoint(to_dev(pairs, "int32"), to_dev(r)))
+        cols = np.sort(rng.choice(g.N, 64, replace=False))
+        want = o.adjoint(r, rows=rows, cols=cols)
+        err = gad[cols] - want
+        rel2 = np.linalg.norm(err) / np.linalg.norm(want)
+        rms = np.linalg.norm(want) / np.sqrt(want.size)
+        assert rel2 <= REL_L2 and np.max(np.abs(err)) <= ELEM_FACTOR * REL_L2 * rms, (w.name, "adjoint", rel2)
+        worst = max(worst, rel, rel2)
+        ctx.close()
+    print(f"[parity] 48 uneven scenes, sampled rows and voxels: worst rel l2 {worst:.2e}")
+
+
+def test_batched48_smallest_scenes_spgm_match_oracle():
+    """The 4 smallest scenes of the 48-scene set (by M N) solved together by one batched graph per epoch:
+    3 SPGM epochs against the oracle's epochs with the same permutations (step 1/L_F, L_F = ||A||_F^2/M,
+    which bounds every minibatch constant)."""
+    import torch
+    from paper_2509_00774_gb300.nfmimo import Batch
+    ws = sorted((W.batched_scene(i) for i in range(48)), key=lambda w: w.geom.M * w.geom.N)[:4]
+    ctxs, ys, y_d, s_b, s_o, perm_d, etas, lams = [], [], [], [], [], [], [], []
+    for i, w in enumerate(ws):
+        g = w.geom
+        o = Oracle(g)
+        y = _c64(I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, w.seeds["noise"]),
+                             w.snr_db))
+        ctxs.append(make_ctx(g))
+        ys.append(y)
+        y_d.append(to_dev(y))
+        s_b.append(torch.zeros(g.N, dtype=torch.complex64, device="cuda"))
+        s_o.append(np.zeros(g.N, dtype=np.complex128))
+        perm_d.append(torch.zeros(g.P, dtype=torch.int32, device="cuda"))
+        etas.append(float(np.float32(1.0 / o.frobenius_bound())))
+        lams.append(float(np.float32(0.05 * o.lambda_max(y))))
+    bps = [w.pairs_per_batch for w in ws]
+    batch = Batch(ctxs)
+    for e in range(3):
+        for i, w in enumerate(ws):
+            p = I.epoch_permutation(w.geom.P, w.seeds["perm"], e)
+            perm_d[i].copy_(torch.from_numpy(p.astype(np.int32)))
+            s_o[i] = Oracle(w.geom).spgm_epoch(ys[i], s_o[i], p, bps[i], etas[i], lams[i])
+        batch.spgm_epoch(y_d, s_b, perm_d, bps, etas, lams)
+        torch.cuda.synchronize()
+        for i, w in enumerate(ws):
+            err = nmse(to_host(s_b[i]), s_o[i])
+            assert err <= NMSE_TOL, (w.name, e, err)
+    batch.close()

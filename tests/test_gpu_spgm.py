@@ -35,6 +35,20 @@ def test_power_iteration_and_lambda_small():
     assert abs(lm_gpu - lm_orc) <= 1e-5 * lm_orc, (lm_gpu, lm_orc)
 
 
+def test_minibatch_power_iteration_small():
+    """L_B = lambda_max(A_B^H A_B)/B of a minibatch (the SPGM step bound) against the oracle."""
+    w, o, y = _small_problem()
+    ctx = make_ctx(w.geom)
+    v0 = _c64(I.complex_gaussian(o.N, w.seeds["power"]))
+    for pairs in ([5], [3, 12, 0, 7], list(range(16))):
+        L_gpu = ctx.power_iteration_pairs(to_dev(np.array(pairs), "int32"), to_dev(v0), 50)
+        L_orc = o.power_iteration(v0, 50, pairs=pairs)
+        assert abs(L_gpu - L_orc) <= 1e-4 * L_orc, (pairs, L_gpu, L_orc)
+    perm = I.epoch_permutation(o.P, w.seeds["perm"], 0)
+    LB_gpu = ctx.spgm_lipschitz(to_dev(perm, "int32"), 4, to_dev(v0), 50)
+    assert abs(LB_gpu - o.spgm_lipschitz(perm, 4, v0, 50)) <= 1e-4 * LB_gpu
+
+
 def test_objective_small():
     w, o, y = _small_problem()
     ctx = make_ctx(w.geom)

@@ -75,6 +75,56 @@ def test_tc_adjoint_mid_and_large_sampled(mode):
                   dense_scale=False)
 
 
+def _forward_case(geom, pairs, mode, seed, rows_sample=None, dense_scale=True):
+    """The tensor-core expansion forward (algorithm chebyshev, precision `mode`) against the oracle's rows."""
+    o = Oracle(geom)
+    ctx = make_ctx(geom, "chebyshev")
+    ctx.set_precision(mode)
+    s = _c64(I.complex_gaussian(geom.N, seed))
+    y = to_host(ctx.forward(to_dev(pairs, "int32"), to_dev(s)))
+    rows = o.rows_of_pairs(pairs)
+    idx = np.arange(rows.size) if rows_sample is None else rows_sample
+    want = o.forward(s, rows=rows[idx])
+    scale = term_scale(o.dense(rows[idx], np.arange(geom.N)), s) if dense_scale else None
+    _check(y[idx], want, TOL[mode], scale, f"{mode} forward")
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["tc_bf16x3", "tc_fp16x3"])
+@pytest.mark.parametrize("pairs", [[5], [3, 12, 0, 7], list(range(16)), [15, 14, 13, 2, 2, 9, 1, 8, 4, 6, 11]])
+def test_tc_forward_small(mode, pairs):
+    _forward_case(W.small_T4R4_K16_16x16x8().geom, np.array(pairs), mode, seed=70)
+
+
+@pytest.mark.parametrize("mode", ["tc_bf16x3", "tc_fp16x3"])
+@pytest.mark.parametrize("case", [0, 1, 3, 4])
+def test_tc_forward_ragged(mode, case):
+    """Ragged grids (tiles cut by the grid edge), K = 11, 37, 128, 96 (N not a multiple of 16 for 11 and
+    37), complex pulse spectra, pair counts 1, 9 and all (16, 32 or 64 pairs per CTA)."""
+    from tests.test_gpu_operator import RAGGED, _ragged_geom
+    T, R, K, dims = RAGGED[case]
+    geom = _ragged_geom(T, R, K, dims, pulse=True, seed=case)
+    rng = np.random.default_rng(400 + case)
+    for n in sorted({1, min(T * R, 9), T * R}):
+        _forward_case(geom, rng.choice(T * R, size=n, replace=False), mode, seed=71 + case)
+
+
+@pytest.mark.parametrize("mode", ["tc_bf16x3", "tc_fp16x3"])
+def test_tc_forward_mid_and_large_sampled(mode):
+    """The bench minibatches: 16 pairs of the mid workload (512 sampled rows), 64 pairs of the large one
+    (256 sampled rows), and 40 pairs (two CTAs of 32 pairs, the second partly empty)."""
+    rng = np.random.default_rng(72)
+    w = W.mid_T16R16_K64_64x64x32()
+    pairs = I.epoch_permutation(w.geom.P, 2, 0)[:16]
+    _forward_case(w.geom, pairs, mode, seed=73, rows_sample=np.sort(rng.choice(16 * 64, 512, replace=False)),
+                  dense_scale=False)
+    w = W.large_T32R32_K128_128x128x64()
+    for n in (64, 40):
+        pairs = I.epoch_permutation(w.geom.P, 2, 0)[:n]
+        _forward_case(w.geom, pairs, mode, seed=74, rows_sample=np.sort(rng.choice(n * 128, 256, replace=False)),
+                      dense_scale=False)
+
+
 @pytest.mark.parametrize("mode", ["tc_bf16x3", "tc_fp16x3"])
 def test_tc_spgm_small_matches_oracle(mode):
     w = W.small_T4R4_K16_16x16x8()
