@@ -41,11 +41,13 @@ CHEB_GEOM_OPS = 42             # expansion: FP32/SFU ops of geometry and base ph
 
 
 def cheb_flops_per_pair_voxel(L, K):
-    """Algorithmic FP32 work of the expansion operator per (pair, voxel): L Chebyshev recurrence
-    steps with a complex-by-real accumulation (3L FMAs), the per-(pair, tile) expansion over the
-    128 voxels of a tile (2KL FMAs / 128) and the geometry (two distances, amplitude, base phase:
-    CHEB_GEOM_OPS ops), counted as 2 flops per FMA-pipe operation."""
-    return 2.0 * (3 * L + 2.0 * K * L / 128.0 + CHEB_GEOM_OPS)
+    """Algorithmic FP32 work of the expansion operator per (pair, voxel), each FMA-pipe operation counted as
+    2 flops: L Chebyshev recurrence steps with a complex-by-real accumulation (3L FMAs); per (pair, tile),
+    spread over the tile's 128 voxels, the expansion over half the band with its mirror (K L FMAs: the
+    band-centred table has b_l(K-1-k) = (-1)^l b_l(k)), the even/odd fold (2K adds) and the tile phasor
+    (a complex multiply and a recurrence step per frequency, 8K); and the geometry (two distances,
+    amplitude, base phase: CHEB_GEOM_OPS ops)."""
+    return 2.0 * (3 * L + (K * L + 10.0 * K) / 128.0 + CHEB_GEOM_OPS)
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -204,6 +206,8 @@ KERNEL_SOURCES = {"fwd_cheb_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "cheb
                   "adj_cheb_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "cheb_device.cuh", "op_cheb.cu"),
                   "adj_cheb_tc_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "cheb_device.cuh", "tc_ptx.cuh",
                                          "op_cheb_tc.cu"),
+                  "fwd_cheb_tc_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "cheb_device.cuh", "tc_ptx.cuh",
+                                         "op_cheb_tc_fwd.cu"),
                   "fwd_partial_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_forward.cu"),
                   "adj_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "op_adjoint.cu"),
                   "adj_tc_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "tc_ptx.cuh", "op_adjoint_tc.cu")}
@@ -669,15 +673,17 @@ def run_ours(args):
         kernels[kind] = entry
     dom = max(("forward_partial", "adjoint"), key=lambda k: kernels.get(k, {}).get("total_ms", 0.0))
     dk = kernels[dom]
-    kname = {"forward_partial": "fwd_cheb_kernel" if cheb else "fwd_partial_kernel",
+    kname = {"forward_partial": ("fwd_cheb_kernel" if args.precision == "fp32" else "fwd_cheb_tc_kernel") if cheb
+             else "fwd_partial_kernel",
              "adjoint": ("adj_cheb_kernel" if cheb else "adj_kernel") if args.precision == "fp32"
              else ("adj_cheb_tc_kernel" if cheb else "adj_tc_kernel")}[dom]
     if cheb:
         work = (f"{cheb_flops_per_pair_voxel(cheb_L, geom.K):.0f} flops per (pair, voxel) = 2 x (3L recurrence/accumulate "
-                f"FMAs + 2KL/128 expansion FMAs + {CHEB_GEOM_OPS} geometry ops), L = {cheb_L}, K = {geom.K}; "
+                f"FMAs + (KL + 10K)/128 mirror-folded expansion and tile-phasor ops + {CHEB_GEOM_OPS} geometry ops), "
+                f"L = {cheb_L}, K = {geom.K}; "
                 f"{bp * geom.N} (pair, voxel) = {elems} (row, voxel) per launch" +
-                ("" if args.precision == "fp32" or dom != "adjoint" else
-                 "; the 2KL/128 coefficient FMAs run on tcgen05, the rest on the FP32 lanes"))
+                ("" if args.precision == "fp32" else
+                 "; the expansion contraction runs on tcgen05, the rest on the FP32 lanes"))
     else:
         work = (f"{FLOPS_PER_PAIR:.0f} flops = 8 FP32 FMA-pipe lane-instructions (complex MAC + phasor step) "
                 f"per (row, voxel) pair, {elems} pairs per launch")
@@ -699,7 +705,8 @@ def run_ours(args):
                    "operator": (f"fp32 cuda-core tile-local Chebyshev expansion, L = {cheb_L}" if cheb else
                                 "forward: fp32 cuda-core three-term phasor recurrence; adjoint: fp32 cuda-core Horner") +
                                ("" if args.precision == "fp32" else
-                                f"; adjoint: tcgen05 {args.precision[3:]} split, FP32 accumulate in TMEM"),
+                                f"; expansion contractions of the forward{' and the adjoint' if cheb else ''} on "
+                                f"tcgen05, {args.precision[3:]} split, FP32 accumulate in TMEM"),
                    "forward_launch_shape": shape,
                    "l2": "256 MiB buffer written between timed steps, outside the timed events",
                    "eta": eta, "lambda": lam, "L": L_full, "L_B_max_epoch0": L_B,

@@ -90,6 +90,29 @@ int nfm_set_geometry(nfm_ctx* ctx,
                      const nfm_grid* grid,
                      double c);
 
+/* Geometry with explicit voxel positions (Sec. II, Eq. 2: the r_n are any set
+ * of points), otherwise as nfm_set_geometry.
+ *   vox_xyz [n_vox][3]: HOST FP64 voxel positions r_n; voxel n is entry n of
+ *     the reflectivity vector s (and of g).  1 <= n_vox <= 2^31 - 129.
+ * The operator groups the voxels in runs of 128 consecutive entries (n / 128)
+ * and expands the frequency dependence about each run's bounding-box centre,
+ * so the voxels should be ordered so that each run of 128 is spatially compact
+ * (for example 8 x 4 x 4 blocks of a jittered grid); a run whose path-length
+ * spread needs more than 32 expansion terms makes this call fail with
+ * NFM_ERR_ARG.  Every antenna must lie at least 1e-6 m from every voxel.
+ * Supported by the FP32 expansion operator: frequencies must be equally
+ * spaced; the direct recurrence, the tensor-core precision modes, the
+ * allocation-free forward and the group term of the regulariser need a
+ * regular grid and return NFM_ERR_ARG.  Copies what it needs, synchronises.
+ * Errors: NFM_ERR_ARG, NFM_ERR_NOMEM, NFM_ERR_CUDA. */
+int nfm_set_geometry_points(nfm_ctx* ctx,
+                            const double* tx_xyz, int T,
+                            const double* rx_xyz, int R,
+                            const double* freq_hz, int K,
+                            const double* pulse_re_im,
+                            const double* vox_xyz, long long n_vox,
+                            double c);
+
 /* Sizes of the current geometry (any pointer may be NULL). */
 int nfm_dims(const nfm_ctx* ctx, int* T, int* R, int* K, long long* N);
 

@@ -10,7 +10,8 @@
  *             / (4 pi |r_Tm - r_n| |r_Rm - r_n|)
  * with row m = pair * K + k, pair = t * R + r (TX index t, RX index r,
  * frequency index k) and voxel n = (iz * ny + iy) * nx + ix on a regular grid
- * r_n = (x0 + ix dx, y0 + iy dy, z0 + iz dz).
+ * r_n = (x0 + ix dx, y0 + iy dy, z0 + iz dz), or voxel n at the explicit
+ * position pos[3n .. 3n + 2] when a point list is given.
  *
  * Every element is evaluated directly from the formula: two FP64 distances, the
  * phase f (dT + dR) / c in cycles with its nearest integer removed (exp of
@@ -36,12 +37,19 @@ typedef struct {
     double x0, y0, z0, dx, dy, dz;
     long nx, ny, nz;
     double c;
+    const double* pos;    /* [N][3] explicit voxel positions, or NULL for the grid */
 } orc_geom;
 
 static const double ORC_PI = 3.14159265358979323846;
 
 static void voxel_position(const orc_geom* g, long n, double* px, double* py, double* pz)
 {
+    if (g->pos) {
+        *px = g->pos[3 * n];
+        *py = g->pos[3 * n + 1];
+        *pz = g->pos[3 * n + 2];
+        return;
+    }
     long ix = n % g->nx;
     long iy = (n / g->nx) % g->ny;
     long iz = n / (g->nx * g->ny);

@@ -49,6 +49,7 @@ class _Geom(ctypes.Structure):
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
         ("nx", ctypes.c_long), ("ny", ctypes.c_long), ("nz", ctypes.c_long),
         ("c", ctypes.c_double),
+        ("pos", ctypes.c_void_p),
     ]
 
 
@@ -121,9 +122,17 @@ class Oracle:
             p = np.asarray(geom.pulse, dtype=np.complex128)
             self._p = np.ascontiguousarray(np.stack([p.real, p.imag], 1))
         g = geom.grid
-        self._g = _Geom(self.T, self.R, self.K, _ptr(self._tx).value, _ptr(self._rx).value,
-                        _ptr(self._f).value, None if self._p is None else _ptr(self._p).value,
-                        g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, g.nx, g.ny, g.nz, geom.c)
+        pp = None if self._p is None else _ptr(self._p).value
+        if hasattr(g, "xyz"):                 # explicit voxel positions (Sec. II: any set of points r_n)
+            self._pos = np.ascontiguousarray(g.xyz, dtype=np.float64)
+            self._g = _Geom(self.T, self.R, self.K, _ptr(self._tx).value, _ptr(self._rx).value,
+                            _ptr(self._f).value, pp, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, g.N, 1, 1, geom.c,
+                            _ptr(self._pos).value)
+        else:
+            self._pos = None
+            self._g = _Geom(self.T, self.R, self.K, _ptr(self._tx).value, _ptr(self._rx).value,
+                            _ptr(self._f).value, pp, g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, g.nx, g.ny, g.nz,
+                            geom.c, None)
 
     # ---- index helpers --------------------------------------------------
     def rows_of_pairs(self, pairs) -> np.ndarray:

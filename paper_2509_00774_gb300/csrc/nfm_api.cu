@@ -59,6 +59,10 @@ struct nfm_ctx {
 
     AntTile* d_ant = nullptr;
     double* d_ant_xyz = nullptr;
+    bool points = false;          // explicit voxel positions (nfm_set_geometry_points)
+    float4* d_pts = nullptr;      // points: per-voxel offsets from the tile centre [n_tiles * 128]
+    double* d_tile_c = nullptr;   // points: tile centres [n_tiles][3]
+    double* d_vox_xyz = nullptr;  // points: voxel positions [N][3]
     bool uniform = true;          // equally spaced frequencies (recurrence / tensor-core paths)
     float* d_antk = nullptr;      // general frequencies: [(T+R) * n_tiles * K] reduced phases
     float2* d_fkc = nullptr;      // general frequencies: f_k / c as hi + lo
@@ -470,12 +474,13 @@ int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int group, int pch, doubl
         pch = 4;
         while (pch < ng && pch < n_pairs) pch *= 2;
     }
+    if (ctx->points && pch < ng / 2) pch = ng / 2;     // explicit positions: at most two tiles per stage
     if (ng % pch != 0) return fail(ctx, NFM_ERR_ARG, "pairs per CTA %d does not divide %d groups", pch, ng);
     const int TS = ng / pch;
     sh->threads = threads;
     sh->group = group;
     sh->pch = pch;
-    sh->smem = fwd_cheb_smem_bytes(LT, KP, pch, threads, group);
+    sh->smem = fwd_cheb_smem_bytes(LT, KP, pch, threads, group, ctx->points);
     if (sh->smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "expansion forward needs %zu B shared memory", sh->smem);
     const void* fn = fwd_cheb_kernel_ptr(LT, group);
     if (!fn) return fail(ctx, NFM_ERR_ARG, "no expansion forward for L = %d, group %d", LT, group);
@@ -610,12 +615,23 @@ int enqueue_forward_cheb(nfm_ctx* ctx, const int* pairs, int n_pairs, const floa
     return NFM_OK;
 }
 
+// Geometries with explicit voxel positions run the FP32 expansion kernels only.
+int points_check(nfm_ctx* ctx, bool cheb)
+{
+    if (!ctx->points) return NFM_OK;
+    if (!cheb) return fail(ctx, NFM_ERR_ARG, "explicit voxel positions need the Chebyshev-expansion operator");
+    if (ctx->precision != NFM_FP32)
+        return fail(ctx, NFM_ERR_ARG, "explicit voxel positions run the FP32 operator only (precision FP32)");
+    return NFM_OK;
+}
+
 int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
                     float2* out, const unsigned char* fmask = nullptr)
 {
     if (!ctx->uniform) return enqueue_forward_general(ctx, pairs, n_pairs, s, y_obs, out, fmask);
     bool cheb = false;
     NFM_TRY(use_cheb(ctx, cheb, n_pairs));
+    NFM_TRY(points_check(ctx, cheb));
     if (cheb) return enqueue_forward_cheb(ctx, pairs, n_pairs, s, y_obs, out, fmask);
     FwdPlan pl;
     NFM_TRY(plan_forward(ctx, n_pairs, &pl));
@@ -711,6 +727,9 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
     }
     bool cheb = false;
     NFM_TRY(use_cheb(ctx, cheb, n_pairs));
+    NFM_TRY(points_check(ctx, cheb));
+    if (ctx->points && alpha_g > 0.f && s)
+        return fail(ctx, NFM_ERR_ARG, "the group term of the regulariser needs a regular voxel grid");
     if (ctx->precision != NFM_FP32) {
         if (!cheb) return enqueue_adjoint_tc(ctx, pairs, n_pairs, r, g_out, s, step, alpha, shrink);
         // expansion adjoint with its coefficient stage on the tensor cores
@@ -869,7 +888,8 @@ void nfm_destroy(nfm_ctx* ctx)
     else cudaDeviceSynchronize();
     void* ps[] = {ctx->d_ant, ctx->d_ant_xyz, ctx->d_pulse, ctx->d_antk, ctx->d_fkc, ctx->d_pairs_all, ctx->d_err, ctx->d_red,
                   ctx->d_partial, ctx->d_resid, ctx->d_v, ctx->d_g, ctx->d_y, ctx->d_hy, ctx->d_hs, ctx->d_hperm,
-                  ctx->d_prox_partial, ctx->d_bmat, ctx->d_bscale, ctx->d_cheb};
+                  ctx->d_prox_partial, ctx->d_bmat, ctx->d_bscale, ctx->d_cheb, ctx->d_pts, ctx->d_tile_c,
+                  ctx->d_vox_xyz};
     for (void* p : ps) free_ptr(p);
     for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
     delete ctx;
@@ -887,23 +907,42 @@ int nfm_set_stream(nfm_ctx* ctx, void* cuda_stream)
     return NFM_OK;
 }
 
-int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx_xyz, int R,
-                     const double* freq_hz, int K, const double* pulse_re_im, const nfm_grid* grid, double c)
+}  // extern "C"
+
+namespace {
+// Geometry set-up shared by the regular grid (grid != NULL) and explicit voxel positions (vox_xyz [n_vox][3],
+// host FP64; voxel n in slot n % 128 of tile n / 128).
+int set_geometry_impl(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx_xyz, int R, const double* freq_hz,
+                      int K, const double* pulse_re_im, const nfm_grid* grid, const double* vox_xyz, long long n_vox,
+                      double c)
 {
     if (!ctx) return NFM_ERR_ARG;
     DevGuard guard(ctx->device);
-    if (!tx_xyz || !rx_xyz || !freq_hz || !grid) return fail(ctx, NFM_ERR_ARG, "NULL geometry array");
+    const bool pts = grid == nullptr;
+    if (!tx_xyz || !rx_xyz || !freq_hz || (!grid && !vox_xyz)) return fail(ctx, NFM_ERR_ARG, "NULL geometry array");
     if (T < 1 || R < 1) return fail(ctx, NFM_ERR_ARG, "need T >= 1 and R >= 1 (got %d, %d)", T, R);
     if (K < 1 || K > K2 * MAX_K1) return fail(ctx, NFM_ERR_ARG, "K = %d outside [1, %d]", K, K2 * MAX_K1);
     if ((long long)T * R > (1LL << 30)) return fail(ctx, NFM_ERR_ARG, "too many pairs");
-    const nfm_grid g = *grid;
-    if (g.nx < 1 || g.ny < 1 || g.nz < 1) return fail(ctx, NFM_ERR_ARG, "grid dimensions must be >= 1");
-    const long long N = (long long)g.nx * g.ny * g.nz;
-    if (N >= (1LL << 31)) return fail(ctx, NFM_ERR_ARG, "N = %lld voxels exceeds 2^31 - 1", N);
-    const double gv[6] = {g.x0, g.y0, g.z0, g.dx, g.dy, g.dz};
-    for (double x : gv)
-        if (!std::isfinite(x)) return fail(ctx, NFM_ERR_ARG, "non-finite grid parameter");
-    if (!(g.dx > 0 && g.dy > 0 && g.dz > 0)) return fail(ctx, NFM_ERR_ARG, "grid steps must be > 0");
+    nfm_grid g{};
+    long long N = 0;
+    if (pts) {
+        if (n_vox < 1 || n_vox >= (1LL << 31) - TILE_V)
+            return fail(ctx, NFM_ERR_ARG, "N = %lld voxels outside [1, 2^31 - 129]", n_vox);
+        for (long long i = 0; i < 3 * n_vox; ++i)
+            if (!std::isfinite(vox_xyz[i])) return fail(ctx, NFM_ERR_ARG, "non-finite voxel coordinate");
+        N = n_vox;
+        g.nx = (int)N;
+        g.ny = g.nz = 1;
+    } else {
+        g = *grid;
+        if (g.nx < 1 || g.ny < 1 || g.nz < 1) return fail(ctx, NFM_ERR_ARG, "grid dimensions must be >= 1");
+        N = (long long)g.nx * g.ny * g.nz;
+        if (N >= (1LL << 31)) return fail(ctx, NFM_ERR_ARG, "N = %lld voxels exceeds 2^31 - 1", N);
+        const double gv[6] = {g.x0, g.y0, g.z0, g.dx, g.dy, g.dz};
+        for (double x : gv)
+            if (!std::isfinite(x)) return fail(ctx, NFM_ERR_ARG, "non-finite grid parameter");
+        if (!(g.dx > 0 && g.dy > 0 && g.dz > 0)) return fail(ctx, NFM_ERR_ARG, "grid steps must be > 0");
+    }
     if (!(c > 0) || !std::isfinite(c)) return fail(ctx, NFM_ERR_ARG, "c must be finite and > 0");
     for (int i = 0; i < 3 * T; ++i)
         if (!std::isfinite(tx_xyz[i])) return fail(ctx, NFM_ERR_ARG, "non-finite TX coordinate");
@@ -921,10 +960,23 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
         double want = f0 + k * df;
         if (std::fabs(freq_hz[k] - want) > 1e-9 * std::fabs(freq_hz[K - 1])) uniform = false;
     }
+    if (pts && !uniform)
+        return fail(ctx, NFM_ERR_ARG, "explicit voxel positions need equally spaced frequencies");
+    if (pts) {                               // every antenna at least 1e-6 m from every voxel
+        for (int a = 0; a < T + R; ++a) {
+            const double* p = a < T ? tx_xyz + 3 * a : rx_xyz + 3 * (a - T);
+            for (long long n = 0; n < N; ++n) {
+                const double* v = vox_xyz + 3 * n;
+                const double d2 = (p[0] - v[0]) * (p[0] - v[0]) + (p[1] - v[1]) * (p[1] - v[1]) +
+                                  (p[2] - v[2]) * (p[2] - v[2]);
+                if (d2 < 1e-12) return fail(ctx, NFM_ERR_ARG, "antenna %d lies within 1e-6 m of voxel %lld", a, n);
+            }
+        }
+    }
     // smallest antenna-voxel distance (distance to the grid's bounding box)
     const double lo[3] = {g.x0, g.y0, g.z0};
     const double hi[3] = {g.x0 + (g.nx - 1) * g.dx, g.y0 + (g.ny - 1) * g.dy, g.z0 + (g.nz - 1) * g.dz};
-    for (int a = 0; a < T + R; ++a) {
+    for (int a = 0; a < T + R && !pts; ++a) {
         const double* p = a < T ? tx_xyz + 3 * a : rx_xyz + 3 * (a - T);
         bool inside = true;
         double d2 = 0;
@@ -954,15 +1006,27 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     ctx->d_ant_xyz = nullptr;
     ctx->d_pulse = nullptr;
     ctx->d_pairs_all = nullptr;
+    free_ptr(ctx->d_pts);
+    free_ptr(ctx->d_tile_c);
+    free_ptr(ctx->d_vox_xyz);
+    ctx->d_pts = nullptr;
+    ctx->d_tile_c = nullptr;
+    ctx->d_vox_xyz = nullptr;
+    ctx->points = false;
     ctx->has_geom = false;
 
     GridDesc gd;
     gd.nx = g.nx;
     gd.ny = g.ny;
     gd.nz = g.nz;
-    gd.tiles_x = (g.nx + TILE_X - 1) / TILE_X;
-    gd.tiles_y = (g.ny + TILE_Y - 1) / TILE_Y;
-    gd.tiles_z = (g.nz + TILE_Z - 1) / TILE_Z;
+    if (pts) {                               // tiles of 128 consecutive voxels
+        gd.tiles_x = (int)((N + TILE_V - 1) / TILE_V);
+        gd.tiles_y = gd.tiles_z = 1;
+    } else {
+        gd.tiles_x = (g.nx + TILE_X - 1) / TILE_X;
+        gd.tiles_y = (g.ny + TILE_Y - 1) / TILE_Y;
+        gd.tiles_z = (g.nz + TILE_Z - 1) / TILE_Z;
+    }
     gd.n_tiles = gd.tiles_x * gd.tiles_y * gd.tiles_z;
     gd.mx = tile_div_magic(gd.n_tiles, gd.tiles_x);
     gd.my = tile_div_magic(gd.n_tiles, gd.tiles_y);
@@ -1016,6 +1080,43 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     as.dfc = df / c;
     as.dfc2 = K2 * df / c;
     as.out = ctx->d_ant;
+    if (pts) {
+        // per tile: the centre of its voxels' bounding box (FP64) and every voxel's offset from it (FP32,
+        // with |u|^2 from the FP64 offset); slots past N stay at the centre
+        const long long nt = gd.n_tiles;
+        std::vector<double> hc((size_t)nt * 3);
+        std::vector<float4> hu((size_t)nt * TILE_V, make_float4(0.f, 0.f, 0.f, 0.f));
+        for (long long t = 0; t < nt; ++t) {
+            const long long n0 = t * TILE_V, n1 = std::min(N, n0 + TILE_V);
+            for (int j = 0; j < 3; ++j) {
+                double mn = vox_xyz[3 * n0 + j], mx = mn;
+                for (long long n = n0; n < n1; ++n) {
+                    mn = std::min(mn, vox_xyz[3 * n + j]);
+                    mx = std::max(mx, vox_xyz[3 * n + j]);
+                }
+                hc[3 * t + j] = 0.5 * (mn + mx);
+            }
+            for (long long n = n0; n < n1; ++n) {
+                const double ux = vox_xyz[3 * n] - hc[3 * t], uy = vox_xyz[3 * n + 1] - hc[3 * t + 1],
+                             uz = vox_xyz[3 * n + 2] - hc[3 * t + 2];
+                hu[n] = make_float4((float)ux, (float)uy, (float)uz, (float)(ux * ux + uy * uy + uz * uz));
+            }
+        }
+        e = cudaMalloc((void**)&ctx->d_pts, hu.size() * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_tile_c, hc.size() * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_vox_xyz, (size_t)N * 3 * sizeof(double));
+        if (e != cudaSuccess) return fail(ctx, NFM_ERR_NOMEM, "voxel position tables: %s", cudaGetErrorString(e));
+        e = cudaMemcpy(ctx->d_pts, hu.data(), hu.size() * sizeof(float4), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ctx->d_tile_c, hc.data(), hc.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ctx->d_vox_xyz, vox_xyz, (size_t)N * 3 * sizeof(double), cudaMemcpyHostToDevice);
+        NFM_CK(e);
+        gd.pts = ctx->d_pts;
+        as.tile_c = ctx->d_tile_c;
+        as.vox_xyz = ctx->d_vox_xyz;
+        as.n_vox = N;
+        ctx->points = true;
+    }
     NFM_CK(launch_ant_setup(gd, as, ctx->stream));
     if (!uniform) {
         // general frequencies: FP64 reduced phases per (antenna, tile, k) and f_k / c split hi + lo
@@ -1041,6 +1142,10 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     }
     if (uniform) NFM_TRY(setup_cheb(ctx, gd, as, K, f0, df, c));
     NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
+    if (pts && ctx->cheb_L == 0)
+        return fail(ctx, NFM_ERR_ARG, "explicit voxel positions: the path-length spread of a run of 128 voxels needs "
+                                      "more than %d expansion terms; order the voxels so that each run of 128 is compact",
+                    CHEB_MAX_L);
 
     ctx->T = T;
     ctx->R = R;
@@ -1058,6 +1163,24 @@ int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx
     ctx->uniform = uniform;
     ctx->has_geom = true;
     return NFM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx_xyz, int R,
+                     const double* freq_hz, int K, const double* pulse_re_im, const nfm_grid* grid, double c)
+{
+    if (!grid) return ctx ? fail(ctx, NFM_ERR_ARG, "NULL grid") : NFM_ERR_ARG;
+    return set_geometry_impl(ctx, tx_xyz, T, rx_xyz, R, freq_hz, K, pulse_re_im, grid, nullptr, 0, c);
+}
+
+int nfm_set_geometry_points(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx_xyz, int R,
+                            const double* freq_hz, int K, const double* pulse_re_im, const double* vox_xyz,
+                            long long n_vox, double c)
+{
+    if (!vox_xyz) return ctx ? fail(ctx, NFM_ERR_ARG, "NULL voxel positions") : NFM_ERR_ARG;
+    return set_geometry_impl(ctx, tx_xyz, T, rx_xyz, R, freq_hz, K, pulse_re_im, nullptr, vox_xyz, n_vox, c);
 }
 
 int nfm_set_regularizer(nfm_ctx* ctx, double w1, double w2)
@@ -1207,7 +1330,7 @@ int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out
         ctx->fwd_tuned.push_back({n_pairs, best_sh.threads, best_sh.group, best_sh.pch, (int)best_sh.nch, false});
     // With NFM_ALGO_AUTO, the same step with the direct recurrence; the faster algorithm is kept.
     bool direct = false;
-    if (rc == NFM_OK && algorithm == NFM_ALGO_AUTO) {
+    if (rc == NFM_OK && algorithm == NFM_ALGO_AUTO && !ctx->points) {
         float t_direct = 0.f;
         ctx->algorithm = NFM_ALGO_DIRECT;
         rc = time_step(t_direct, 12);
@@ -1540,6 +1663,7 @@ int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, d
         NFM_CK(cudaMemcpyAsync(&s2, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
     if (ctx->reg_w3 != 0.0) {
+        if (ctx->points) return fail(ctx, NFM_ERR_ARG, "the group term of the regulariser needs a regular voxel grid");
         NFM_CK(launch_group_norm_sum((const float2*)s, ctx->gd.nx, ctx->gd.ny, ctx->gd.nz, part, sc + 3, st));
         NFM_CK(cudaMemcpyAsync(&gsum, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
@@ -1667,6 +1791,7 @@ extern "C" int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, 
     NFM_TRY(check_ptr(ctx, y, "y", 8));
     if (!ctx->uniform)
         return fail(ctx, NFM_ERR_ARG, "the allocation-free forward needs equally spaced frequencies");
+    if (ctx->points) return fail(ctx, NFM_ERR_ARG, "the allocation-free forward needs a regular voxel grid");
     // one voxel chunk holds ceil(n_pairs / 8) * 8 * K partial sums (pairs padded to whole CTAs)
     const size_t per_chunk = (size_t)((n_pairs + FWD_PC - 1) / FWD_PC) * FWD_PC * ctx->K;
     if (per_chunk > NOALLOC_SCRATCH_ELEMS)

@@ -56,6 +56,10 @@ struct GridDesc {
     // n / tiles_x = umulhi(n, mx) and n / tiles_y = umulhi(n, my) for 0 <= n < n_tiles (division by an
     // invariant integer with a rounded-up reciprocal: exact while n * divisor < 2^32); 0 = divide
     unsigned mx, my;
+    // Explicit voxel positions: voxel n sits in slot n % 128 of tile n / 128 (tiles_x = n_tiles, nx = N,
+    // ny = nz = 1) and pts[n] (padded to whole tiles) holds its offset from the tile centre as
+    // (ux, uy, uz, |u|^2) in FP32; nullptr for a regular grid.
+    const float4* pts = nullptr;
 };
 
 struct PhaseConsts {

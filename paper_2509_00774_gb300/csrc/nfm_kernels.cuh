@@ -47,6 +47,9 @@ struct AntSetup {
     double x0, y0, z0, dx, dy, dz;
     double f0c, dfc, dfc2;   // f0/c, df/c, K2 df/c
     AntTile* out;            // [n_ant * n_tiles]
+    const double* tile_c = nullptr;    // explicit voxel positions: tile centres [n_tiles][3] (FP64)
+    const double* vox_xyz = nullptr;   //                           voxel positions [n_vox][3] (FP64)
+    long long n_vox = 0;
 };
 
 constexpr int GEN_MAX_K = 128;    // frequencies of the general-frequency path
@@ -82,7 +85,8 @@ __host__ __device__ constexpr int fwd_coef_stride(int LT)
 {
     return ((LT + 3) & ~3) % 16 == 0 ? ((LT + 3) & ~3) + 4 : ((LT + 3) & ~3);
 }
-size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group);
+// points: the geometry has explicit voxel positions (per-stage voxel offsets are staged too)
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, bool points = false);
 size_t adj_cheb_smem_bytes(int LT, int k_pad);
 const void* fwd_cheb_kernel_ptr(int LT, int group);
 const void* adj_cheb_kernel_ptr(int LT);

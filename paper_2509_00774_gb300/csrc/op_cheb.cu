@@ -56,6 +56,8 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     float2* s_st = reinterpret_cast<float2*>(voff + TILE_V);                 // [2][TS][TILE_V]
     AntTile* ant_st = reinterpret_cast<AntTile*>(s_st + 2 * TS * TILE_V);    // [2][ng][2]
     int* pair_s = reinterpret_cast<int*>(ant_st + 2 * ng * 2);               // [PCH] pair or -1
+    // explicit voxel positions: the stage's voxel offsets [2][TS][TILE_V] (16-byte aligned after pair_s)
+    VoxelOffset* vox_st = reinterpret_cast<VoxelOffset*>(pair_s + ((PCH + 3) & ~3));
 
     const int tid = threadIdx.x;
     const int nt = blockDim.x;
@@ -74,8 +76,9 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     for (int i = tid; i < KP * LS / 4; i += nt)
         reinterpret_cast<float4*>(coef)[(i / (LS / 4)) * (LSS / 4) + i % (LS / 4)] =
             reinterpret_cast<const float4*>(cd.coef)[i];
-    for (int v = tid; v < TILE_V; v += nt)
-        voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
+    if (!op.g.pts)
+        for (int v = tid; v < TILE_V; v += nt)
+            voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
     if (tid < PCH) {
         const int sp = pair_base + tid;
         int pair = sp < a.n_pairs ? a.pairs[sp] : -1;
@@ -111,6 +114,19 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     };
     auto load_s = [&](int q) {                    // the stage's scene values (zero outside the grid)
         const int buf = q & 1;
+        if (op.g.pts) {                           // explicit positions: voxel n = tile * 128 + slot, and its offset
+            for (int sl = 0; sl < TS; ++sl) {
+                const int tile = t_begin + q * TS + sl;
+                if (tile >= t_end) break;
+                for (int v = tid; v < TILE_V; v += nt) {
+                    const long long n = (long long)tile * TILE_V + v;
+                    const bool in = n < op.g.nx;
+                    cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, in ? a.s + n : a.s, in);
+                    cp_async_16(vox_st + (buf * TS + sl) * TILE_V + v, op.g.pts + n);   // padded to whole tiles
+                }
+            }
+            return;
+        }
         const int v1 = tid + nt;                  // (computed per call: nothing stays live across stages)
         const int off0 = slot_offset(tid), off1 = v1 < TILE_V ? slot_offset(v1) : 0;
         int tx, ty, tz;                           // coordinates of the stage's first tile, then stepped
@@ -161,6 +177,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
             const AntTile* ap = ant_st + (buf * ng + g) * 2;
             const PairTile P = fold_pair_tile(ap[0], ap[1]);
             const float2* sb = s_st + (buf * TS + slot) * TILE_V;
+            const VoxelOffset* vsrc = op.g.pts ? vox_st + (buf * TS + slot) * TILE_V : voff;
             float mr[LT], mi[LT];
 #pragma unroll
             for (int l = 0; l < LT; ++l) mr[l] = mi[l] = 0.f;
@@ -168,7 +185,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
             for (int i = 0; i < TILE_V / G; ++i) {
                 const int v = ln + G * i;
                 const float2 sv = sb[v];
-                const ChebVoxel cv = cheb_voxel(P, voff[v], cd.fc_hi, cd.fc_lo);
+                const ChebVoxel cv = cheb_voxel(P, vsrc[v], cd.fc_hi, cd.fc_lo);
                 const float2 c0 = cis_turns_sfu(cv.th0);
                 const float2 u = cmul_conj(make_float2(cv.amp * sv.x, cv.amp * sv.y), c0);
                 const float t = cv.delta * cd.tau;
@@ -196,58 +213,65 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
                     mi[l] += __shfl_xor_sync(gmask, mi[l], w);
                 }
             }
-            // expansion: lane ln owns k = ln + G j; (-j)^l applied by permuting re/im.  The tile
-            // phasors P_k = e^{-j 2 pi k df D_c/c} of the lane's k advance by W = P_{2G} (Taylor
-            // phasor, error ~1e-7, at most K/(2G) steps) from directly evaluated starts.
+            // expansion over half the band: the band-centred table is mirror-symmetric,
+            // b_l(K-1-k) = (-1)^l b_l(k), so with E = sum over even l and O = sum over odd l of
+            // (-j)^l b_l(k) m_l, S_k = E + O and S_{K-1-k} = E - O.  Lane ln owns k = ln + G j < K/2 and the
+            // mirrors; (-j)^l is applied by permuting re/im.  The tile phasors P_k = e^{-j 2 pi k df D_c/c}
+            // of k and K-1-k advance by W = P_G and its conjugate (Taylor phasor, error ~1e-7, at most K/(2G)
+            // steps) from directly evaluated starts; for odd K one lane adds the centre row.
             float2* accg = acc + g * AS;
-            float2 c0 = tile_step_cis(P, ln), c1 = tile_step_cis(P, ln + G);
-            const float2 W = tile_step_cis_exact(P, 2 * G);
-            for (int k0 = ln; k0 < K; k0 += 2 * G) {
-                const int k1 = k0 + G;                   // may be >= K: zero table row, not stored
-                const float* b0 = coef + k0 * LSS;
-                const float* b1 = coef + min(k1, KP - 1) * LSS;
-                float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
+            const int KH = K / 2;
+            float2 cu = tile_step_cis(P, ln), cdn = tile_step_cis(P, K - 1 - ln);
+            const float2 W = tile_step_cis_exact(P, G);
+            const float2 Wc = make_float2(W.x, -W.y);
+            auto accumulate = [&](int k, float2 c, float sr, float si) {   // y_k (+)= P_k S_k, P_k = (c.x, -c.y)
+                float2 av = make_float2(fmaf(c.x, sr, c.y * si), fmaf(c.x, si, -c.y * sr));
+                if (q > 0) {                                 // the first stage writes, later stages add
+                    av.x += accg[k].x;
+                    av.y += accg[k].y;
+                }
+                accg[k] = av;
+            };
+            for (int k = ln; k < KH; k += G) {
+                const float* b0 = coef + k * LSS;
+                float er = 0.f, ei = 0.f, orr = 0.f, oi = 0.f;
 #pragma unroll
                 for (int l = 0; l < LT; l += 4) {
                     const float4 x = *reinterpret_cast<const float4*>(b0 + l);
-                    const float4 y = *reinterpret_cast<const float4*>(b1 + l);
-                    sr0 = fmaf(x.x, mr[l], sr0);
-                    si0 = fmaf(x.x, mi[l], si0);
-                    sr1 = fmaf(y.x, mr[l], sr1);
-                    si1 = fmaf(y.x, mi[l], si1);
-                    sr0 = fmaf(x.y, mi[l + 1], sr0);
-                    si0 = fmaf(-x.y, mr[l + 1], si0);
-                    sr1 = fmaf(y.y, mi[l + 1], sr1);
-                    si1 = fmaf(-y.y, mr[l + 1], si1);
+                    er = fmaf(x.x, mr[l], er);
+                    ei = fmaf(x.x, mi[l], ei);
+                    orr = fmaf(x.y, mi[l + 1], orr);
+                    oi = fmaf(-x.y, mr[l + 1], oi);
                     if (l + 2 < LT) {                    // LT is even: l + 2 < LT covers l + 3
-                        sr0 = fmaf(-x.z, mr[l + 2], sr0);
-                        si0 = fmaf(-x.z, mi[l + 2], si0);
-                        sr1 = fmaf(-y.z, mr[l + 2], sr1);
-                        si1 = fmaf(-y.z, mi[l + 2], si1);
-                        sr0 = fmaf(-x.w, mi[l + 3], sr0);
-                        si0 = fmaf(x.w, mr[l + 3], si0);
-                        sr1 = fmaf(-y.w, mi[l + 3], sr1);
-                        si1 = fmaf(y.w, mr[l + 3], si1);
+                        er = fmaf(-x.z, mr[l + 2], er);
+                        ei = fmaf(-x.z, mi[l + 2], ei);
+                        orr = fmaf(-x.w, mi[l + 3], orr);
+                        oi = fmaf(x.w, mr[l + 3], oi);
                     }
                 }
-                {                                        // y_k (+)= P_k S_k, P_k = (c.x, -c.y)
-                    float2 av = make_float2(fmaf(c0.x, sr0, c0.y * si0), fmaf(c0.x, si0, -c0.y * sr0));
-                    if (q > 0) {                         // the first stage writes, later stages add
-                        av.x += accg[k0].x;
-                        av.y += accg[k0].y;
+                accumulate(k, cu, er + orr, ei + oi);
+                accumulate(K - 1 - k, cdn, er - orr, ei - oi);
+                cu = cmul(cu, W);
+                cdn = cmul(cdn, Wc);
+            }
+            if ((K & 1) && ln == KH % G) {               // centre row k_c = K/2 (its own mirror)
+                const float* b0 = coef + KH * LSS;
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int l = 0; l < LT; l += 4) {
+                    const float4 x = *reinterpret_cast<const float4*>(b0 + l);
+                    sr = fmaf(x.x, mr[l], sr);
+                    si = fmaf(x.x, mi[l], si);
+                    sr = fmaf(x.y, mi[l + 1], sr);
+                    si = fmaf(-x.y, mr[l + 1], si);
+                    if (l + 2 < LT) {
+                        sr = fmaf(-x.z, mr[l + 2], sr);
+                        si = fmaf(-x.z, mi[l + 2], si);
+                        sr = fmaf(-x.w, mi[l + 3], sr);
+                        si = fmaf(x.w, mr[l + 3], si);
                     }
-                    accg[k0] = av;
                 }
-                if (k1 < K) {
-                    float2 av = make_float2(fmaf(c1.x, sr1, c1.y * si1), fmaf(c1.x, si1, -c1.y * sr1));
-                    if (q > 0) {
-                        av.x += accg[k1].x;
-                        av.y += accg[k1].y;
-                    }
-                    accg[k1] = av;
-                }
-                c0 = cmul(c0, W);
-                c1 = cmul(c1, W);
+                accumulate(KH, tile_step_cis(P, KH), sr, si);
             }
         }
         cp_async_wait_all();
@@ -303,7 +327,16 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     int tx, ty, tz;
     tile_coords(op.g, tile, tx, ty, tz);
     const int lx = tid % TILE_X, ly = (tid / TILE_X) % TILE_Y, lz = tid / (TILE_X * TILE_Y);
-    const VoxelOffset o = voxel_offset(op.g, lx, ly, lz);
+    VoxelOffset o;
+    if (op.g.pts) {                          // explicit positions: voxel n = tile * 128 + thread
+        const float4 u = op.g.pts[(size_t)tile * TILE_V + tid];
+        o.ux = u.x;
+        o.uy = u.y;
+        o.uz = u.z;
+        o.uu = u.w;
+    } else {
+        o = voxel_offset(op.g, lx, ly, lz);
+    }
     for (int i = tid; i < KP * LS / 4; i += CHEB_THREADS)
         reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
     constexpr int LQ = LS / 4;
@@ -317,8 +350,9 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     pdl_wait();                              // r comes from the previous kernel
     // the voxel's iterate for the fused update, loaded now so that its latency overlaps the r copies
     const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
-    const bool in_grid = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
-    const size_t n = in_grid ? ((size_t)iz * op.g.ny + iy) * op.g.nx + ix : 0;
+    const size_t np = (size_t)tile * TILE_V + tid;
+    const bool in_grid = op.g.pts ? np < (size_t)op.g.nx : (ix < op.g.nx && iy < op.g.ny && iz < op.g.nz);
+    const size_t n = !in_grid ? 0 : op.g.pts ? np : ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
     const float2 s_old = (a.s && in_grid) ? a.s[n] : make_float2(0.f, 0.f);
 
     for (int c0 = 0; c0 < a.n_pairs; c0 += CHEB_ADJ_PCHUNK) {
@@ -341,40 +375,69 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();                     // pt and w16 of this chunk
-        // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c}: the phasor starts from the SFU and advances by the
-        // pair's exact 16-step phasor, restarted from the SFU every 8 steps (at most 7 rounded products)
+        // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c} for k and its mirror K-1-k, folded in place into
+        // u_k = r'_k + r'_{K-1-k} (stored at k) and v_k = r'_k - r'_{K-1-k} (stored at K-1-k), k < K/2; for odd K
+        // the centre row k_c = K/2 keeps r'.  The band-centred table is mirror-symmetric,
+        // b_l(K-1-k) = (-1)^l b_l(k), so C_l needs only b_l(k) u_k (even l) and b_l(k) v_k (odd l) over half the
+        // band.  A thread owns both slots of its k, so no barrier separates the transform from the fold.
+        // Phasors: an SFU start each for k0 and K-1-k0, then the pair's exact 16-step phasor up and its
+        // conjugate down (at most 4 steps).
+        const int KH = K / 2;
         for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16) {
             const PairTile& P = pt[j];
             const float2 W = w16[j];
+            const float2 Wc = make_float2(W.x, -W.y);
             float2* row = rp + j * RS;
-            for (int kb = k0; kb < K; kb += 16 * 8) {
-                float2 c = tile_step_cis(P, kb);
-                const int kend = min(K, kb + 16 * 8);
-                for (int k = kb; k < kend; k += 16) {
-                    float2 v = row[k];
-                    if (op.pulse) v = cmul_conj(v, op.pulse[k]);
-                    row[k] = cmul(v, c);
-                    c = cmul(c, W);
+            float2 cu = tile_step_cis(P, k0), cd = tile_step_cis(P, K - 1 - k0);
+            for (int k = k0; k < KH; k += 16) {
+                const int km = K - 1 - k;
+                float2 x = row[k], y = row[km];
+                if (op.pulse) {
+                    x = cmul_conj(x, op.pulse[k]);
+                    y = cmul_conj(y, op.pulse[km]);
                 }
+                x = cmul(x, cu);
+                y = cmul(y, cd);
+                row[k] = make_float2(x.x + y.x, x.y + y.y);
+                row[km] = make_float2(x.x - y.x, x.y - y.y);
+                cu = cmul(cu, W);
+                cd = cmul(cd, Wc);
+            }
+            if ((K & 1) && k0 == KH % 16) {  // centre row (its own mirror)
+                float2 x = row[KH];
+                if (op.pulse) x = cmul_conj(x, op.pulse[KH]);
+                row[KH] = cmul(x, tile_step_cis(P, KH));
             }
         }
         __syncthreads();
-        // C_l = j^l sum_k b_l(k) r'_k, four l per task
+        // C_l = j^l sum_k b_l(k) r'_k = j^l [sum_{k < K/2} b_l(k) (u_k or v_k) + b_l(k_c) r'_{k_c}], four l per task
         for (int e = tid; e < nc * LQ; e += CHEB_THREADS) {
             const int j = e / LQ, l = 4 * (e - (e / LQ) * LQ);
             const float2* rj = rp + j * RS;
             float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f, cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
-            for (int k = 0; k < K; ++k) {
-                const float2 rv = rj[k];
+            for (int k = 0; k < KH; ++k) {
+                const float2 u = rj[k], v = rj[K - 1 - k];
                 const float4 b = *reinterpret_cast<const float4*>(coef + k * LS + l);
-                cr0 = fmaf(b.x, rv.x, cr0);
-                ci0 = fmaf(b.x, rv.y, ci0);
-                cr1 = fmaf(b.y, rv.x, cr1);
-                ci1 = fmaf(b.y, rv.y, ci1);
-                cr2 = fmaf(b.z, rv.x, cr2);
-                ci2 = fmaf(b.z, rv.y, ci2);
-                cr3 = fmaf(b.w, rv.x, cr3);
-                ci3 = fmaf(b.w, rv.y, ci3);
+                cr0 = fmaf(b.x, u.x, cr0);
+                ci0 = fmaf(b.x, u.y, ci0);
+                cr1 = fmaf(b.y, v.x, cr1);
+                ci1 = fmaf(b.y, v.y, ci1);
+                cr2 = fmaf(b.z, u.x, cr2);
+                ci2 = fmaf(b.z, u.y, ci2);
+                cr3 = fmaf(b.w, v.x, cr3);
+                ci3 = fmaf(b.w, v.y, ci3);
+            }
+            if (K & 1) {                     // the centre row (b_l(k_c), l >= 1, is zero up to rounding)
+                const float2 w = rj[KH];
+                const float4 b = *reinterpret_cast<const float4*>(coef + KH * LS + l);
+                cr0 = fmaf(b.x, w.x, cr0);
+                ci0 = fmaf(b.x, w.y, ci0);
+                cr1 = fmaf(b.y, w.x, cr1);
+                ci1 = fmaf(b.y, w.y, ci1);
+                cr2 = fmaf(b.z, w.x, cr2);
+                ci2 = fmaf(b.z, w.y, ci2);
+                cr3 = fmaf(b.w, w.x, cr3);
+                ci3 = fmaf(b.w, w.y, ci3);
             }
             float2* Cj = Cs + j * LS + l;      // l % 4 == 0: factors 1, j, -1, -j
             Cj[0] = make_float2(cr0, ci0);
@@ -449,9 +512,22 @@ __global__ void __launch_bounds__(256) cheb_range_kernel(GridDesc g, AntSetup a,
          i += (long long)gridDim.x * blockDim.x) {
         const int ant = (int)(i / g.n_tiles);
         const int tile = (int)(i - (long long)ant * g.n_tiles);
+        const double ax = a.ant_xyz[3 * ant], ay = a.ant_xyz[3 * ant + 1], az = a.ant_xyz[3 * ant + 2];
+        if (a.tile_c) {                      // explicit voxel positions: the tile's voxels about its centre
+            const double cx = a.tile_c[3 * (size_t)tile], cy = a.tile_c[3 * (size_t)tile + 1],
+                         cz = a.tile_c[3 * (size_t)tile + 2];
+            const double dc = sqrt((ax - cx) * (ax - cx) + (ay - cy) * (ay - cy) + (az - cz) * (az - cz));
+            for (int v = 0; v < TILE_V; ++v) {
+                const long long n = (long long)tile * TILE_V + v;
+                if (n >= a.n_vox) break;
+                const double* p = a.vox_xyz + 3 * n;
+                const double d = sqrt((ax - p[0]) * (ax - p[0]) + (ay - p[1]) * (ay - p[1]) + (az - p[2]) * (az - p[2]));
+                mx = fmax(mx, fabs(d - dc));
+            }
+            continue;
+        }
         int tx, ty, tz;
         tile_coords(g, tile, tx, ty, tz);
-        const double ax = a.ant_xyz[3 * ant], ay = a.ant_xyz[3 * ant + 1], az = a.ant_xyz[3 * ant + 2];
         const double cx = a.x0 + (tx * TILE_X + 0.5 * (TILE_X - 1)) * a.dx;
         const double cy = a.y0 + (ty * TILE_Y + 0.5 * (TILE_Y - 1)) * a.dy;
         const double cz = a.z0 + (tz * TILE_Z + 0.5 * (TILE_Z - 1)) * a.dz;
@@ -477,13 +553,14 @@ __global__ void __launch_bounds__(256) cheb_range_kernel(GridDesc g, AntSetup a,
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group)
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, bool points)
 {
     const int ng = threads / group;
     const int TS = ng / pch;
     return (size_t)k_pad * fwd_coef_stride(LT) * sizeof(float) + (size_t)ng * (k_pad + 4) * sizeof(float2) +
            TILE_V * sizeof(VoxelOffset) + (size_t)2 * TS * TILE_V * sizeof(float2) +
-           (size_t)2 * ng * 2 * sizeof(AntTile) + (size_t)pch * sizeof(int);
+           (size_t)2 * ng * 2 * sizeof(AntTile) + (size_t)((pch + 3) & ~3) * sizeof(int) +
+           (points ? (size_t)2 * TS * TILE_V * sizeof(VoxelOffset) : 0);
 }
 
 size_t adj_cheb_smem_bytes(int LT, int k_pad)

@@ -16,11 +16,18 @@ __global__ void ant_setup_kernel(GridDesc g, AntSetup a)
          i += (long long)gridDim.x * blockDim.x) {
         int ant = (int)(i / g.n_tiles);
         int tile = (int)(i - (long long)ant * g.n_tiles);
-        int tx, ty, tz;
-        tile_coords(g, tile, tx, ty, tz);
-        double cx = a.x0 + (tx * TILE_X + 0.5 * (TILE_X - 1)) * a.dx;
-        double cy = a.y0 + (ty * TILE_Y + 0.5 * (TILE_Y - 1)) * a.dy;
-        double cz = a.z0 + (tz * TILE_Z + 0.5 * (TILE_Z - 1)) * a.dz;
+        double cx, cy, cz;
+        if (a.tile_c) {                      // explicit voxel positions: the tile's own centre
+            cx = a.tile_c[3 * (size_t)tile];
+            cy = a.tile_c[3 * (size_t)tile + 1];
+            cz = a.tile_c[3 * (size_t)tile + 2];
+        } else {
+            int tx, ty, tz;
+            tile_coords(g, tile, tx, ty, tz);
+            cx = a.x0 + (tx * TILE_X + 0.5 * (TILE_X - 1)) * a.dx;
+            cy = a.y0 + (ty * TILE_Y + 0.5 * (TILE_Y - 1)) * a.dy;
+            cz = a.z0 + (tz * TILE_Z + 0.5 * (TILE_Z - 1)) * a.dz;
+        }
         double vx = a.ant_xyz[3 * ant + 0] - cx;
         double vy = a.ant_xyz[3 * ant + 1] - cy;
         double vz = a.ant_xyz[3 * ant + 2] - cz;

@@ -60,13 +60,49 @@ class Grid:
                          self.z0 + iz * self.dz], axis=1)
 
 
+@dataclass(frozen=True, eq=False)
+class PointSet:
+    """Explicit voxel positions r_n (Sec. II: the voxels are any set of points), FP64 [N, 3], in the
+    order of the reflectivity vector."""
+    xyz: np.ndarray
+
+    @property
+    def N(self) -> int:
+        return int(self.xyz.shape[0])
+
+    def positions(self, idx=None) -> np.ndarray:
+        """FP64 positions [len(idx), 3] of voxel indices (all voxels if None)."""
+        return self.xyz if idx is None else self.xyz[np.asarray(idx, dtype=np.int64)]
+
+
+def block_order(grid: Grid, bx: int = 8, by: int = 4, bz: int = 4) -> np.ndarray:
+    """Voxel indices of the grid listed block by block (bx x by x bz blocks in x-fastest block order, the
+    voxels of a block x-fastest; blocks cut by the grid edge hold fewer voxels): a spatially compact order."""
+    n = np.arange(grid.N, dtype=np.int64)
+    ix, iy, iz = n % grid.nx, (n // grid.nx) % grid.ny, n // (grid.nx * grid.ny)
+    tbx, tby = -(-grid.nx // bx), -(-grid.ny // by)
+    block = ((iz // bz) * tby + iy // by) * tbx + ix // bx
+    within = ((iz % bz) * by + iy % by) * bx + ix % bx
+    return np.lexsort((within, block))
+
+
+def jittered_points(grid: Grid, frac: float, seed: int, order=None) -> PointSet:
+    """The grid's voxels moved by independent uniform offsets of up to +-frac of the step along each axis:
+    a voxel set that is no regular grid.  order: voxel indices giving the listed order (default x-fastest)."""
+    rng = np.random.default_rng(seed)
+    d = np.array([grid.dx, grid.dy, grid.dz])
+    pos = grid.positions() + rng.uniform(-frac, frac, (grid.N, 3)) * d
+    return PointSet(pos if order is None else pos[np.asarray(order)])
+
+
 @dataclass
 class Geometry:
-    """Antennas (FP64, z = 0), frequencies (FP64, Hz), pulse spectrum, grid."""
+    """Antennas (FP64, z = 0), frequencies (FP64, Hz), pulse spectrum, voxels (a regular grid or an
+    explicit point set)."""
     tx: np.ndarray            # [T, 3]
     rx: np.ndarray            # [R, 3]
     freq: np.ndarray          # [K]
-    grid: Grid
+    grid: "Grid | PointSet"
     pulse: np.ndarray | None = None   # complex [K] or None (p = 1)
     c: float = C_LIGHT
 

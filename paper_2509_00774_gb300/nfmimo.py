@@ -52,6 +52,7 @@ def load_library(path: str | None = None):
         "nfm_last_error": (ctypes.c_char_p, [vp]),
         "nfm_set_stream": (i, [vp, vp]),
         "nfm_set_geometry": (i, [vp, vp, i, vp, i, vp, i, vp, ctypes.POINTER(_Grid), d]),
+        "nfm_set_geometry_points": (i, [vp, vp, i, vp, i, vp, i, vp, vp, ctypes.c_longlong, d]),
         "nfm_set_precision": (i, [vp, i]),
         "nfm_set_algorithm": (i, [vp, i]),
         "nfm_algorithm_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]),
@@ -180,16 +181,27 @@ class Context:
             p = np.asarray(geom.pulse, dtype=np.complex128)
             pulse = np.ascontiguousarray(np.stack([p.real, p.imag], 1))
         g = geom.grid
-        grid = _Grid(g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, g.nx, g.ny, g.nz)
-        self._check(self._lib.nfm_set_geometry(
-            self._h, tx.ctypes.data_as(ctypes.c_void_p), tx.shape[0],
-            rx.ctypes.data_as(ctypes.c_void_p), rx.shape[0],
-            fr.ctypes.data_as(ctypes.c_void_p), fr.shape[0],
-            None if pulse is None else pulse.ctypes.data_as(ctypes.c_void_p),
-            ctypes.byref(grid), float(geom.c)))
+        vp = ctypes.c_void_p
+        pp = None if pulse is None else pulse.ctypes.data_as(vp)
+        if hasattr(g, "xyz"):                 # explicit voxel positions (an inputs.PointSet)
+            xyz = np.ascontiguousarray(g.xyz, dtype=np.float64)
+            self._check(self._lib.nfm_set_geometry_points(
+                self._h, tx.ctypes.data_as(vp), tx.shape[0], rx.ctypes.data_as(vp), rx.shape[0],
+                fr.ctypes.data_as(vp), fr.shape[0], pp, xyz.ctypes.data_as(vp), xyz.shape[0], float(geom.c)))
+        else:
+            grid = _Grid(g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, g.nx, g.ny, g.nz)
+            self._check(self._lib.nfm_set_geometry(
+                self._h, tx.ctypes.data_as(vp), tx.shape[0], rx.ctypes.data_as(vp), rx.shape[0],
+                fr.ctypes.data_as(vp), fr.shape[0], pp, ctypes.byref(grid), float(geom.c)))
         self.T, self.R, self.K, self.N = tx.shape[0], rx.shape[0], fr.shape[0], g.N
         self.P = self.T * self.R
         self.M = self.P * self.K
+
+    def set_geometry_points(self, geom):
+        """set_geometry for a geometry whose voxels are an explicit point set (inputs.PointSet)."""
+        if not hasattr(geom.grid, "xyz"):
+            raise ValueError("set_geometry_points needs a geometry whose grid is an inputs.PointSet")
+        self.set_geometry(geom)
 
     PRECISION = {"fp32": 0, "tc_bf16x3": 1, "tc_fp16x3": 2}
 

@@ -504,3 +504,30 @@ def test_dense_minimiser_is_optimal():
     for _ in range(50):
         t = o.pgm_step(y, t, 1.0 / L, lam)
         assert o.objective(y, t, lam) >= F - 1e-9 * F
+
+
+# ---------------------------------------------------------------------------
+# Sec. II: explicit voxel positions
+# ---------------------------------------------------------------------------
+def test_point_set_hand_cases_and_grid_equivalence():
+    """A one-point set reproduces the hand-derived Eq. 2 values, and a point set holding a grid's
+    positions reproduces the grid's dense matrix exactly."""
+    with open(os.path.join(GOLDEN, "eq2_hand_cases.json")) as f:
+        gold = json.load(f)
+    c = gold["c"]
+    for case in gold["cases"]:
+        geom = I.Geometry(np.atleast_2d(np.asarray(case["tx"], float)), np.atleast_2d(np.asarray(case["rx"], float)),
+                          np.array([case["f_over_c"] * c]), I.PointSet(np.array([gold["voxel"]], float)))
+        a = Oracle(geom).element(0, 0)
+        want = complex(case["expected_re"], case["expected_im"]) / case["expected_scale_inv"]
+        assert abs(a - want) <= 1e-12 * abs(want), case["why"]
+    g = _tiny_random_geom(3, T=2, R=3, K=4, grid=(4, 3, 2))
+    pts = I.Geometry(g.tx, g.rx, g.freq, I.PointSet(g.grid.positions()))
+    A = Oracle(g).dense(np.arange(g.M), np.arange(g.N))
+    B = Oracle(pts).dense(np.arange(g.M), np.arange(g.N))
+    assert np.array_equal(A, B)
+    # a permuted point set permutes the columns
+    perm = np.random.default_rng(1).permutation(g.N)
+    C = Oracle(I.Geometry(g.tx, g.rx, g.freq, I.PointSet(g.grid.positions()[perm]))).dense(np.arange(g.M),
+                                                                                           np.arange(g.N))
+    assert np.array_equal(C, A[:, perm])
