@@ -230,6 +230,13 @@ int nfm_set_group_weight(nfm_ctx* ctx, double w3);
  * y must not alias s.  Uses library-owned scratch (allocated on first need). */
 int nfm_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, float* y);
 
+/* Minibatch residual r = A_B s - y_B (the residual inside Eq. 4 and the gradient
+ * of Eq. 6): the forward of nfm_forward with the listed pairs' rows of the FULL
+ * measurement vector y [P*K] subtracted in the same kernel (no gather pass).
+ *   pairs [n_pairs] int32, s [N], y [P*K], r [n_pairs*K] complex64 (device);
+ *   r must not alias s or y. */
+int nfm_residual(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, const float* y, float* r);
+
 /* Minibatch adjoint g = A_B^H r, the operator inside the gradient of Eq. 4/6.
  *   pairs [n_pairs] int32 (device), r [n_pairs*K] complex64, g [N] complex64. */
 int nfm_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* r, float* g);
@@ -358,10 +365,15 @@ int nfm_synchronize(nfm_ctx* ctx);
  * unwritten; the next synchronising call returns NFM_ERR_TIMEOUT and the
  * context stays usable.  flags = NFM_HOOK_TC_SKIP_ISSUE makes those kernels
  * issue no MMA and no commit, so that their first wait runs out on purpose
- * (nothing is left in flight); flags = 0 is normal operation.  Applies to
- * calls enqueued afterwards.  Errors: NFM_ERR_ARG for unknown flags or
+ * (nothing is left in flight); flags = NFM_HOOK_SHRINK_EXTENTS halves the
+ * buffer extents the kernels of the default operator path receive, which only
+ * the bounds-checked build (libnfmimo_check.so, compiled with
+ * -DNFM_BOUNDS_CHECK) reads: there a checked index past the declared extent
+ * raises a device flag and is replaced by 0 (an element inside the real
+ * buffer), and the next synchronising call returns NFM_ERR_STATE;
+ * flags = 0 is normal operation.  Applies to calls enqueued afterwards.  Errors: NFM_ERR_ARG for unknown flags or
  * wait_ms outside [0, 60000]. */
-enum { NFM_HOOK_TC_SKIP_ISSUE = 1 };
+enum { NFM_HOOK_TC_SKIP_ISSUE = 1, NFM_HOOK_SHRINK_EXTENTS = 2 };
 int nfm_set_test_hooks(nfm_ctx* ctx, int flags, int wait_ms);
 
 /* Allocation-free variant of nfm_forward.  The paper has no counterpart; this

@@ -33,6 +33,20 @@ class _ForwardFn(torch.autograd.Function):
         return ctx.op.adjoint(ctx.pairs, gy.contiguous()), None, None
 
 
+class _ResidualFn(torch.autograd.Function):
+    """r = A_B s - y_B in one fused launch (the residual of Eq. 4 / Eq. 6); y is data (no gradient)."""
+
+    @staticmethod
+    def forward(ctx, s, op, pairs, y):
+        ctx.op = op
+        ctx.pairs = pairs
+        return op.residual(pairs, s.contiguous(), y)
+
+    @staticmethod
+    def backward(ctx, gr):
+        return ctx.op.adjoint(ctx.pairs, gr.contiguous()), None, None, None
+
+
 class _AdjointFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, r, op, pairs):
@@ -76,6 +90,12 @@ def forward_op(op, pairs, s):
     return _ForwardFn.apply(s, op, pairs)
 
 
+def residual_op(op, pairs, s, y):
+    """r = A_B s - y_B with y the full measurement vector [P*K] (fused into the forward kernel),
+    differentiable in s."""
+    return _ResidualFn.apply(s, op, pairs, y)
+
+
 def adjoint_op(op, pairs, r):
     """g = A_B^H r, differentiable in r."""
     return _AdjointFn.apply(r, op, pairs)
@@ -97,9 +117,9 @@ class UnrolledSPGM(torch.nn.Module):
         self.lam = torch.nn.Parameter(torch.full((self.n_iter,), float(lam), dtype=torch.float64))
         self.checkpoint = checkpoint
 
-    def _iteration(self, s, y_b, pairs, eta, lam):
+    def _iteration(self, s, y, pairs, eta, lam):
         B = pairs.numel() * self.op.K
-        r = forward_op(self.op, pairs, s) - y_b
+        r = residual_op(self.op, pairs, s, y)       # A_B s - y_B fused in the forward kernel
         g = adjoint_op(self.op, pairs, r)
         return prox_step(self.op, s, g, eta / B, eta * lam)
 
@@ -108,20 +128,18 @@ class UnrolledSPGM(torch.nn.Module):
         Returns the final iterate(s), [N] or [n_scenes, N]."""
         single = y.dim() == 1
         ys = y.unsqueeze(0) if single else y
-        K = self.op.K
         outs = []
         for j in range(ys.shape[0]):
-            yj = ys[j].view(-1, K)
+            yj = ys[j].contiguous()
             if s0 is None:
                 s = torch.zeros(self.op.N, dtype=torch.complex64, device=y.device)
             else:
                 s = (s0 if single else s0[j]).contiguous()
             for i in range(self.n_iter):
                 pairs = batches[i % len(batches)]
-                y_b = yj[pairs.long()].reshape(-1).contiguous()
                 if self.checkpoint and torch.is_grad_enabled():
-                    s = _checkpoint(self._iteration, s, y_b, pairs, self.eta[i], self.lam[i], use_reentrant=False)
+                    s = _checkpoint(self._iteration, s, yj, pairs, self.eta[i], self.lam[i], use_reentrant=False)
                 else:
-                    s = self._iteration(s, y_b, pairs, self.eta[i], self.lam[i])
+                    s = self._iteration(s, yj, pairs, self.eta[i], self.lam[i])
             outs.append(s)
         return outs[0] if single else torch.stack(outs)

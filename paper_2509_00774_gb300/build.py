@@ -47,14 +47,20 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    flags = NVCC_FLAGS + list(extra_flags or [])
+LIB_CHECK = os.path.join(HERE, "libnfmimo_check.so")
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=None, check: bool = False) -> str:
+    """Build libnfmimo.so, or with check=True the bounds-checked libnfmimo_check.so (-DNFM_BOUNDS_CHECK:
+    checked kernel indices raise a device flag instead of leaving their buffer)."""
+    lib, bdir = (LIB_CHECK, BUILD + "_check") if check else (LIB, BUILD)
+    if not force and os.path.exists(lib) and all(os.path.getmtime(f) <= os.path.getmtime(lib) for f in _deps()):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
+    flags = NVCC_FLAGS + list(extra_flags or []) + (["-DNFM_BOUNDS_CHECK"] if check else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         cmd = [nvcc()] + ARCH + flags + FILE_FLAGS.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -67,13 +73,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -4,6 +4,7 @@
 // the host only validates, plans and enqueues.
 #include "nfmimo.h"
 #include "nfm_kernels.cuh"
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -19,6 +20,13 @@ using namespace nfm;
 namespace {
 
 thread_local std::string g_create_error;
+
+// NVTX range around an entry point (tracing aid: a profiler shows the library's calls on its timeline;
+// without one attached the push and pop cost a branch each)
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+};
 
 struct DevGuard {
     int prev = -1;
@@ -203,6 +211,11 @@ OpDesc op_desc(const nfm_ctx* ctx)
     op.err = ctx->d_err;
     op.wait_ns = ctx->tc_wait_ns;
     op.hooks = ctx->hooks;
+    // extents for the bounds-checked build; the test hook halves them so that a check trips on an access
+    // that is in fact inside its buffer
+    const long long shrink = (ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1;
+    op.n_vox = ctx->N / shrink;
+    op.m_rows = ctx->M / shrink;
     return op;
 }
 
@@ -430,6 +443,7 @@ int enqueue_forward_general(nfm_ctx* ctx, const int* pairs, int n_pairs, const f
     a.n_pairs = n_pairs;
     a.s = s;
     a.partial = (float2*)ctx->d_partial;
+    a.partial_elems = (long long)(ctx->partial_cap / sizeof(float2)) / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     a.n_slots = pl.n_slots;
     a.VS = 1;
     a.tiles_base = pl.base;
@@ -439,6 +453,7 @@ int enqueue_forward_general(nfm_ctx* ctx, const int* pairs, int n_pairs, const f
     const int e1 = prof_mark(ctx);
     ReduceArgs ra;
     ra.partial = (const float2*)ctx->d_partial;
+    ra.partial_elems = (long long)(ctx->partial_cap / sizeof(float2)) / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     ra.n_chunks = pl.n_chunks;
     ra.n_slots = pl.n_slots;
     ra.n_out = n_pairs * ctx->K;
@@ -519,6 +534,7 @@ int launch_cheb_forward_shape(nfm_ctx* ctx, const ChebShape& sh, const int* pair
     a.n_pairs = n_pairs;
     a.s = s;
     a.partial = (float2*)ctx->d_partial;
+    a.partial_elems = (long long)(ctx->partial_cap / sizeof(float2)) / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     a.n_slots = sh.n_slots;
     a.VS = sh.pch;
     a.tiles_base = (int)(ctx->gd.n_tiles / sh.nch);
@@ -558,6 +574,7 @@ int enqueue_forward_cheb_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const f
     a.n_pairs = n_pairs;
     a.s = s;
     a.partial = (float2*)ctx->d_partial;
+    a.partial_elems = (long long)(ctx->partial_cap / sizeof(float2)) / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     a.n_slots = n_slots;
     a.VS = pch;
     a.tiles_base = (int)(ctx->gd.n_tiles / nch);
@@ -568,6 +585,7 @@ int enqueue_forward_cheb_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const f
     const int e1 = prof_mark(ctx);
     ReduceArgs ra;
     ra.partial = (const float2*)ctx->d_partial;
+    ra.partial_elems = (long long)(ctx->partial_cap / sizeof(float2)) / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     ra.n_chunks = (int)nch;
     ra.n_slots = n_slots;
     ra.n_out = n_pairs * ctx->K;
@@ -601,6 +619,7 @@ int enqueue_forward_cheb(nfm_ctx* ctx, const int* pairs, int n_pairs, const floa
     OpDesc op = op_desc(ctx);
     ReduceArgs ra;
     ra.partial = (const float2*)ctx->d_partial;
+    ra.partial_elems = (long long)(ctx->partial_cap / sizeof(float2)) / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     ra.n_chunks = (int)sh.nch;
     ra.n_slots = sh.n_slots;
     ra.n_out = n_pairs * ctx->K;
@@ -642,6 +661,7 @@ int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s
     a.n_pairs = n_pairs;
     a.s = s;
     a.partial = (float2*)ctx->d_partial;
+    a.partial_elems = (long long)(ctx->partial_cap / sizeof(float2)) / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     a.n_slots = pl.n_slots;
     a.VS = pl.VS;
     a.tiles_base = pl.base;
@@ -651,6 +671,7 @@ int enqueue_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s
     const int e1 = prof_mark(ctx);
     ReduceArgs ra;
     ra.partial = (const float2*)ctx->d_partial;
+    ra.partial_elems = (long long)(ctx->partial_cap / sizeof(float2)) / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     ra.n_chunks = pl.n_chunks;
     ra.n_slots = pl.n_slots;
     ra.n_out = n_pairs * ctx->K;
@@ -682,6 +703,7 @@ int enqueue_adjoint_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2
     a.pairs = pairs;
     a.n_pairs = n_pairs;
     a.r = r;
+    a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     a.g_out = g_out;
     a.s = s;
     a.step = step;
@@ -713,6 +735,8 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         a.pairs = pairs;
         a.n_pairs = n_pairs;
         a.r = r;
+        a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
+    a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
         a.g_out = g_out;
         a.s = s;
         a.step = step;
@@ -746,6 +770,8 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         a.pairs = pairs;
         a.n_pairs = n_pairs;
         a.r = r;
+        a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
+    a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
         a.g_out = g_out;
         a.s = s;
         a.step = step;
@@ -771,6 +797,8 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         a.pairs = pairs;
         a.n_pairs = n_pairs;
         a.r = r;
+        a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
+    a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
         a.g_out = g_out;
         a.s = s;
         a.step = step;
@@ -795,6 +823,7 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
     a.pairs = pairs;
     a.n_pairs = n_pairs;
     a.r = r;
+    a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     a.g_out = g_out;
     a.s = s;
     a.step = step;
@@ -815,6 +844,8 @@ int check_flags(nfm_ctx* ctx)
         NFM_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
         if (flags & ERRF_PAIR) return fail(ctx, NFM_ERR_ARG, "a pair index was outside [0, P)");
         if (flags & ERRF_TIMEOUT) return fail(ctx, NFM_ERR_TIMEOUT, "a bounded wait on the tensor core gave up");
+        if (flags & ERRF_BOUNDS)
+            return fail(ctx, NFM_ERR_STATE, "a kernel index fell outside its buffer (bounds-checked build)");
         return fail(ctx, NFM_ERR_NUMERIC, "device flag 0x%x", flags);
     }
     return NFM_OK;
@@ -1171,6 +1202,7 @@ extern "C" {
 int nfm_set_geometry(nfm_ctx* ctx, const double* tx_xyz, int T, const double* rx_xyz, int R,
                      const double* freq_hz, int K, const double* pulse_re_im, const nfm_grid* grid, double c)
 {
+    TraceRange trace_("nfm_set_geometry");
     if (!grid) return ctx ? fail(ctx, NFM_ERR_ARG, "NULL grid") : NFM_ERR_ARG;
     return set_geometry_impl(ctx, tx_xyz, T, rx_xyz, R, freq_hz, K, pulse_re_im, grid, nullptr, 0, c);
 }
@@ -1179,6 +1211,7 @@ int nfm_set_geometry_points(nfm_ctx* ctx, const double* tx_xyz, int T, const dou
                             const double* freq_hz, int K, const double* pulse_re_im, const double* vox_xyz,
                             long long n_vox, double c)
 {
+    TraceRange trace_("nfm_set_geometry_points");
     if (!vox_xyz) return ctx ? fail(ctx, NFM_ERR_ARG, "NULL voxel positions") : NFM_ERR_ARG;
     return set_geometry_impl(ctx, tx_xyz, T, rx_xyz, R, freq_hz, K, pulse_re_im, nullptr, vox_xyz, n_vox, c);
 }
@@ -1233,6 +1266,7 @@ int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_m
 int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out, int* group_out,
                  int* pairs_per_cta_out, int* chunks_out)
 {
+    TraceRange trace_("nfm_autotune");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (n_pairs < 1 || n_pairs > ctx->P) return fail(ctx, NFM_ERR_ARG, "n_pairs = %d outside [1, P]", n_pairs);
@@ -1399,6 +1433,7 @@ int nfm_dims(const nfm_ctx* ctx, int* T, int* R, int* K, long long* N)
 
 int nfm_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, float* y)
 {
+    TraceRange trace_("nfm_forward");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
@@ -1408,8 +1443,22 @@ int nfm_forward(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, flo
     return enqueue_forward(ctx, pairs, n_pairs, (const float2*)s, nullptr, (float2*)y);
 }
 
+int nfm_residual(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, const float* y, float* r)
+{
+    TraceRange trace_("nfm_residual");
+    NFM_TRY(require_geom(ctx));
+    DevGuard guard(ctx->device);
+    if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
+    NFM_TRY(check_ptr(ctx, pairs, "pairs", 4));
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, y, "y", 8));
+    NFM_TRY(check_ptr(ctx, r, "r", 8));
+    return enqueue_forward(ctx, pairs, n_pairs, (const float2*)s, (const float2*)y, (float2*)r);
+}
+
 int nfm_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* r, float* g)
 {
+    TraceRange trace_("nfm_adjoint");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
@@ -1421,6 +1470,7 @@ int nfm_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* r, flo
 
 int nfm_spgm_step(nfm_ctx* ctx, const float* y, float* s, const int* pairs, int n_pairs, float eta, float lambda)
 {
+    TraceRange trace_("nfm_spgm_step");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
@@ -1435,6 +1485,7 @@ int nfm_spgm_step(nfm_ctx* ctx, const float* y, float* s, const int* pairs, int 
 int nfm_spgm_epoch(nfm_ctx* ctx, const float* y, float* s, const int* perm, int pairs_per_batch, float eta,
                    float lambda)
 {
+    TraceRange trace_("nfm_spgm_epoch");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (pairs_per_batch < 1) return fail(ctx, NFM_ERR_ARG, "pairs_per_batch must be >= 1");
@@ -1449,6 +1500,7 @@ int nfm_spgm_epoch(nfm_ctx* ctx, const float* y, float* s, const int* perm, int 
 int nfm_spgm_epochs_host(nfm_ctx* ctx, const float* y_host, float* s_host, const int* perms_host, int n_epochs,
                          int pairs_per_batch, float eta, float lambda)
 {
+    TraceRange trace_("nfm_spgm_epochs_host");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (n_epochs < 1 || pairs_per_batch < 1) return fail(ctx, NFM_ERR_ARG, "n_epochs and pairs_per_batch must be >= 1");
@@ -1474,6 +1526,7 @@ int nfm_spgm_epochs_host(nfm_ctx* ctx, const float* y_host, float* s_host, const
 int nfm_spgm_step_freqs(nfm_ctx* ctx, const float* y, float* s, const int* pairs, int n_pairs,
                         const unsigned char* freq_mask, int n_freq, float eta, float lambda)
 {
+    TraceRange trace_("nfm_spgm_step_freqs");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
@@ -1496,6 +1549,7 @@ int nfm_spgm_step_freqs(nfm_ctx* ctx, const float* y, float* s, const int* pairs
 
 int nfm_pgm_step(nfm_ctx* ctx, const float* y, float* s, float eta, float lambda)
 {
+    TraceRange trace_("nfm_pgm_step");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (!(eta > 0) || !std::isfinite(eta)) return fail(ctx, NFM_ERR_ARG, "eta must be finite and > 0");
@@ -1508,6 +1562,7 @@ int nfm_pgm_step(nfm_ctx* ctx, const float* y, float* s, float eta, float lambda
 int nfm_solve(nfm_ctx* ctx, const float* y, float* s, const int* perms, int max_epochs, int pairs_per_batch,
               float eta, float lambda, double tol, int* epochs_out, double* change_out)
 {
+    TraceRange trace_("nfm_solve");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (max_epochs < 1 || pairs_per_batch < 1) return fail(ctx, NFM_ERR_ARG, "max_epochs and pairs_per_batch must be >= 1");
@@ -1626,6 +1681,7 @@ extern "C" {
 
 int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out)
 {
+    TraceRange trace_("nfm_power_iteration");
     NFM_TRY(require_geom(ctx));
     return power_iteration_impl(ctx, ctx->d_pairs_all, ctx->P, iters, v0, L_out);
 }
@@ -1633,6 +1689,7 @@ int nfm_power_iteration(nfm_ctx* ctx, int iters, const float* v0, double* L_out)
 int nfm_power_iteration_pairs(nfm_ctx* ctx, const int* pairs, int n_pairs, int iters, const float* v0,
                               double* L_out)
 {
+    TraceRange trace_("nfm_power_iteration_pairs");
     NFM_TRY(require_geom(ctx));
     if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
     NFM_TRY(check_ptr(ctx, pairs, "pairs", 4));
@@ -1641,6 +1698,7 @@ int nfm_power_iteration_pairs(nfm_ctx* ctx, const int* pairs, int n_pairs, int i
 
 int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, double* F_out)
 {
+    TraceRange trace_("nfm_objective");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     NFM_TRY(check_ptr(ctx, y, "y", 8));
@@ -1675,6 +1733,7 @@ int nfm_objective(nfm_ctx* ctx, const float* y, const float* s, double lambda, d
 
 int nfm_lambda_max(nfm_ctx* ctx, const float* y, double* out)
 {
+    TraceRange trace_("nfm_lambda_max");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     NFM_TRY(check_ptr(ctx, y, "y", 8));
@@ -1703,11 +1762,13 @@ int nfm_synchronize(nfm_ctx* ctx)
 }
 
 static_assert((int)NFM_HOOK_TC_SKIP_ISSUE == (int)HOOK_TC_SKIP_ISSUE, "hook flags of the header and the kernels");
+static_assert((int)NFM_HOOK_SHRINK_EXTENTS == (int)HOOK_SHRINK_EXTENTS, "hook flags of the header and the kernels");
 
 int nfm_set_test_hooks(nfm_ctx* ctx, int flags, int wait_ms)
 {
     if (!ctx) return NFM_ERR_ARG;
-    if (flags & ~NFM_HOOK_TC_SKIP_ISSUE) return fail(ctx, NFM_ERR_ARG, "unknown test hook flags 0x%x", flags);
+    if (flags & ~(NFM_HOOK_TC_SKIP_ISSUE | NFM_HOOK_SHRINK_EXTENTS))
+        return fail(ctx, NFM_ERR_ARG, "unknown test hook flags 0x%x", flags);
     if (wait_ms < 0 || wait_ms > 60000) return fail(ctx, NFM_ERR_ARG, "wait_ms must lie in [0, 60000]");
     ctx->hooks = flags;
     ctx->tc_wait_ns = wait_ms > 0 ? (unsigned long long)wait_ms * 1000000ull : 1000000000ull;
@@ -1783,6 +1844,7 @@ int noalloc_scratch(nfm_ctx* ctx, float2** out)
 
 extern "C" int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float* s, float* y)
 {
+    TraceRange trace_("nfm_forward_noalloc");
     NFM_TRY(require_geom(ctx));
     DevGuard guard(ctx->device);
     if (n_pairs < 1) return fail(ctx, NFM_ERR_ARG, "n_pairs must be >= 1");
@@ -1807,6 +1869,7 @@ extern "C" int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, 
     a.n_pairs = n_pairs;
     a.s = (const float2*)s;
     a.partial = scratch;
+    a.partial_elems = (long long)NOALLOC_SCRATCH_ELEMS;
     a.n_slots = pl.n_slots;
     a.VS = pl.VS;
     a.tiles_base = pl.base;
@@ -1814,6 +1877,7 @@ extern "C" int nfm_forward_noalloc(nfm_ctx* ctx, const int* pairs, int n_pairs, 
     NFM_CK(launch_fwd_partial(op, a, dim3(pl.n_groups, pl.n_chunks), pl.nt, pl.smem, ctx->stream));
     ReduceArgs ra;
     ra.partial = scratch;
+    ra.partial_elems = (long long)NOALLOC_SCRATCH_ELEMS / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     ra.n_chunks = pl.n_chunks;
     ra.n_slots = pl.n_slots;
     ra.n_out = n_pairs * ctx->K;
@@ -1951,6 +2015,7 @@ const char* nfm_batch_last_error(const nfm_batch* b) { return b ? b->err.c_str()
 int nfm_batch_spgm_epoch(nfm_batch* b, const float* const* y, float* const* s, const int* const* perm,
                          const int* pairs_per_batch, const float* eta, const float* lambda)
 {
+    TraceRange trace_("nfm_batch_spgm_epoch");
     if (!b) return NFM_ERR_ARG;
     const int n = (int)b->scenes.size();
     if (!y || !s || !perm || !pairs_per_batch || !eta || !lambda) return bfail(b, NFM_ERR_ARG, "NULL argument array");

@@ -78,12 +78,31 @@ struct OpDesc {
     int* err;              // device error flags
     unsigned long long wait_ns = 1000000000ull;   // limit of one bounded wait on the tensor core
     int hooks = 0;         // test hooks (HOOK_*), 0 in normal operation
+    long long n_vox = 0;   // N: extent of s and g (checked in the bounds-checked build)
+    long long m_rows = 0;  // P K: extent of the full measurement vector (checked in the bounds-checked build)
 };
 
-enum : int { ERRF_PAIR = 1, ERRF_TIMEOUT = 2 };
+enum : int { ERRF_PAIR = 1, ERRF_TIMEOUT = 2, ERRF_BOUNDS = 4 };
 // HOOK_TC_SKIP_ISSUE: the tensor-core kernels issue no MMA and no commit, so their bounded waits run
 // out and the timeout path runs (no outstanding tensor-core work, nothing faults or hangs)
-enum : int { HOOK_TC_SKIP_ISSUE = 1 };
+enum : int { HOOK_TC_SKIP_ISSUE = 1, HOOK_SHRINK_EXTENTS = 2 };
+
+// Bounds-checked build (-DNFM_BOUNDS_CHECK): a checked global index is compared with the extent the host
+// passed for that buffer; an index outside it raises ERRF_BOUNDS and is replaced by 0, an element that
+// exists, so the access stays inside the buffer.  In the normal build the check compiles away.
+#ifdef NFM_BOUNDS_CHECK
+__device__ __forceinline__ long long nfm_checked(long long i, long long n, int* err)
+{
+    if (i < 0 || i >= n) {
+        atomicOr(err, ERRF_BOUNDS);
+        return 0;
+    }
+    return i;
+}
+#define NFM_IDX(i, n, err) nfm_checked((long long)(i), (long long)(n), (err))
+#else
+#define NFM_IDX(i, n, err) (i)
+#endif
 
 __device__ __forceinline__ float frac_turns(float x) { return x - rintf(x); }
 

@@ -14,6 +14,7 @@ struct FwdArgs {
     int VS;                  // voxel subsets per CTA
     int tiles_base;          // chunk c owns tiles_base (+1 for c < tiles_rem) tiles
     int tiles_rem;
+    long long partial_elems = 0;   // extent of partial (checked in the bounds-checked build)
 };
 
 struct ReduceArgs {
@@ -25,6 +26,7 @@ struct ReduceArgs {
     const float2* y_obs;     // full measurement vector [P*K] or nullptr
     const unsigned char* fmask;  // [K]: rows with fmask[k] == 0 get a zero residual (nullptr = all rows)
     float2* out;             // [n_pairs * K]
+    long long partial_elems = 0;   // extent of partial (checked in the bounds-checked build)
 };
 
 struct AdjArgs {
@@ -38,6 +40,7 @@ struct AdjArgs {
     float shrink;            // 1 / (1 + eta * lambda * w2) (elastic-net scaling; 1 for plain l1)
     float alpha_g = 0.f;     // eta * lambda * w3: group shrink over 2 x 2 x 1 voxel blocks (expansion adjoints; 0 = off)
     int pchunk;              // pairs staged in shared memory per round
+    long long r_elems = 0;   // extent of r (checked in the bounds-checked build)
 };
 
 // per (antenna, tile) FP64 set-up

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
                 for (int v = tid; v < TILE_V; v += nt) {
                     const long long n = (long long)tile * TILE_V + v;
                     const bool in = n < op.g.nx;
-                    cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, in ? a.s + n : a.s, in);
+                    cp_async_8(s_st + (buf * TS + sl) * TILE_V + v, in ? a.s + NFM_IDX(n, op.n_vox, op.err) : a.s, in);
                     cp_async_16(vox_st + (buf * TS + sl) * TILE_V + v, op.g.pts + n);   // padded to whole tiles
                 }
             }
@@ -135,16 +135,16 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
             if (t_begin + q * TS + sl >= t_end) break;   // slots past the chunk stay idle
             const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TILE_Z;
             const bool full = x0 + TILE_X <= op.g.nx && y0 + TILE_Y <= op.g.ny && z0 + TILE_Z <= op.g.nz;
-            const float2* origin = a.s + ((size_t)z0 * op.g.ny + y0) * op.g.nx + x0;
             float2* dst = s_st + (buf * TS + sl) * TILE_V;
+            const long long obase = ((long long)z0 * op.g.ny + y0) * op.g.nx + x0;   // index of origin in s
             if (full) {
-                cp_async_8(dst + tid, origin + off0, true);
-                if (v1 < TILE_V) cp_async_8(dst + v1, origin + off1, true);
+                cp_async_8(dst + tid, a.s + NFM_IDX(obase + off0, op.n_vox, op.err), true);
+                if (v1 < TILE_V) cp_async_8(dst + v1, a.s + NFM_IDX(obase + off1, op.n_vox, op.err), true);
             } else {
                 for (int v = tid; v < TILE_V; v += nt) {
                     const int ix = x0 + v % TILE_X, iy = y0 + (v / TILE_X) % TILE_Y, iz = z0 + v / (TILE_X * TILE_Y);
                     const bool in = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
-                    cp_async_8(dst + v, in ? origin + slot_offset(v) : a.s, in);
+                    cp_async_8(dst + v, in ? a.s + NFM_IDX(obase + slot_offset(v), op.n_vox, op.err) : a.s, in);
                 }
             }
             if (++tx == op.g.tiles_x) {           // next tile in x-fastest order
@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     for (int p = p_first; p < PCH; p += p_step) {
         const int sp = pair_base + p;
         if (sp >= a.n_pairs) break;
-        float2* out = a.partial + ((size_t)chunk * a.n_slots + sp) * K;
+        const long long out0 = ((long long)chunk * a.n_slots + sp) * K;
+        float2* out = a.partial + out0;
         for (int k = k_first; k < K; k += k_step) {
             const float2* col = acc + p * AS + k;
             float2 sum = col[0];
@@ -300,7 +301,11 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
                 sum.x += x.x;
                 sum.y += x.y;
             }
+#ifdef NFM_BOUNDS_CHECK
+            a.partial[NFM_IDX(out0 + k, a.partial_elems, op.err)] = sum;
+#else
             out[k] = sum;
+#endif
         }
     }
 }
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     const size_t np = (size_t)tile * TILE_V + tid;
     const bool in_grid = op.g.pts ? np < (size_t)op.g.nx : (ix < op.g.nx && iy < op.g.ny && iz < op.g.nz);
     const size_t n = !in_grid ? 0 : op.g.pts ? np : ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
-    const float2 s_old = (a.s && in_grid) ? a.s[n] : make_float2(0.f, 0.f);
+    const float2 s_old = (a.s && in_grid) ? a.s[NFM_IDX(n, op.n_vox, op.err)] : make_float2(0.f, 0.f);
 
     for (int c0 = 0; c0 < a.n_pairs; c0 += CHEB_ADJ_PCHUNK) {
         const int nc = min(CHEB_ADJ_PCHUNK, a.n_pairs - c0);
@@ -369,8 +374,8 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
         // the same elements.
         const int k0 = tid % 16;
         for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16) {
-            const float2* src = a.r + (size_t)(c0 + j) * K;
-            for (int k = k0; k < K; k += 16) cp_async_8(rp + j * RS + k, src + k, true);
+            for (int k = k0; k < K; k += 16)
+                cp_async_8(rp + j * RS + k, a.r + NFM_IDX((long long)(c0 + j) * K + k, a.r_elems, op.err), true);
         }
         cp_async_commit();
         cp_async_wait_all();
@@ -410,40 +415,59 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
             }
         }
         __syncthreads();
-        // C_l = j^l sum_k b_l(k) r'_k = j^l [sum_{k < K/2} b_l(k) (u_k or v_k) + b_l(k_c) r'_{k_c}], four l per task
-        for (int e = tid; e < nc * LQ; e += CHEB_THREADS) {
-            const int j = e / LQ, l = 4 * (e - (e / LQ) * LQ);
-            const float2* rj = rp + j * RS;
-            float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f, cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
-            for (int k = 0; k < KH; ++k) {
-                const float2 u = rj[k], v = rj[K - 1 - k];
-                const float4 b = *reinterpret_cast<const float4*>(coef + k * LS + l);
-                cr0 = fmaf(b.x, u.x, cr0);
-                ci0 = fmaf(b.x, u.y, ci0);
-                cr1 = fmaf(b.y, v.x, cr1);
-                ci1 = fmaf(b.y, v.y, ci1);
-                cr2 = fmaf(b.z, u.x, cr2);
-                ci2 = fmaf(b.z, u.y, ci2);
-                cr3 = fmaf(b.w, v.x, cr3);
-                ci3 = fmaf(b.w, v.y, ci3);
+        // C_l = j^l sum_k b_l(k) r'_k = j^l [sum_{k < K/2} b_l(k) (u_k or v_k) + b_l(k_c) r'_{k_c}], four l per task,
+        // each task split over the parity of k between lanes e and e ^ 1 (combined by one shuffle; the pair's
+        // rows and table rows of the two parities sit in different banks); the centre row goes to parity 0
+        {
+            const int n_task = 2 * nc * LQ;  // even, so lane pairs never straddle a round or the end
+            for (int e0 = 0; e0 < n_task; e0 += CHEB_THREADS) {
+                const int e = e0 + tid;
+                const bool active = e < n_task;
+                if (!__any_sync(0xffffffffu, active)) continue;   // whole warp past the end
+                const int h = e & 1, et = (active ? e : 0) >> 1;
+                const int j = et / LQ, l = 4 * (et - (et / LQ) * LQ);
+                const float2* rj = rp + j * RS;
+                float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f, cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
+                for (int k = active ? h : KH; k < KH; k += 2) {
+                    const float2 u = rj[k], v = rj[K - 1 - k];
+                    const float4 b = *reinterpret_cast<const float4*>(coef + k * LS + l);
+                    cr0 = fmaf(b.x, u.x, cr0);
+                    ci0 = fmaf(b.x, u.y, ci0);
+                    cr1 = fmaf(b.y, v.x, cr1);
+                    ci1 = fmaf(b.y, v.y, ci1);
+                    cr2 = fmaf(b.z, u.x, cr2);
+                    ci2 = fmaf(b.z, u.y, ci2);
+                    cr3 = fmaf(b.w, v.x, cr3);
+                    ci3 = fmaf(b.w, v.y, ci3);
+                }
+                if ((K & 1) && active && h == 0) {   // the centre row (b_l(k_c), l >= 1, is zero up to rounding)
+                    const float2 w = rj[KH];
+                    const float4 b = *reinterpret_cast<const float4*>(coef + KH * LS + l);
+                    cr0 = fmaf(b.x, w.x, cr0);
+                    ci0 = fmaf(b.x, w.y, ci0);
+                    cr1 = fmaf(b.y, w.x, cr1);
+                    ci1 = fmaf(b.y, w.y, ci1);
+                    cr2 = fmaf(b.z, w.x, cr2);
+                    ci2 = fmaf(b.z, w.y, ci2);
+                    cr3 = fmaf(b.w, w.x, cr3);
+                    ci3 = fmaf(b.w, w.y, ci3);
+                }
+                cr0 += __shfl_xor_sync(0xffffffffu, cr0, 1);
+                ci0 += __shfl_xor_sync(0xffffffffu, ci0, 1);
+                cr1 += __shfl_xor_sync(0xffffffffu, cr1, 1);
+                ci1 += __shfl_xor_sync(0xffffffffu, ci1, 1);
+                cr2 += __shfl_xor_sync(0xffffffffu, cr2, 1);
+                ci2 += __shfl_xor_sync(0xffffffffu, ci2, 1);
+                cr3 += __shfl_xor_sync(0xffffffffu, cr3, 1);
+                ci3 += __shfl_xor_sync(0xffffffffu, ci3, 1);
+                if (active && h == 0) {
+                    float2* Cj = Cs + j * LS + l;  // l % 4 == 0: factors 1, j, -1, -j
+                    Cj[0] = make_float2(cr0, ci0);
+                    Cj[1] = make_float2(-ci1, cr1);
+                    Cj[2] = make_float2(-cr2, -ci2);
+                    Cj[3] = make_float2(ci3, -cr3);
+                }
             }
-            if (K & 1) {                     // the centre row (b_l(k_c), l >= 1, is zero up to rounding)
-                const float2 w = rj[KH];
-                const float4 b = *reinterpret_cast<const float4*>(coef + KH * LS + l);
-                cr0 = fmaf(b.x, w.x, cr0);
-                ci0 = fmaf(b.x, w.y, ci0);
-                cr1 = fmaf(b.y, w.x, cr1);
-                ci1 = fmaf(b.y, w.y, ci1);
-                cr2 = fmaf(b.z, w.x, cr2);
-                ci2 = fmaf(b.z, w.y, ci2);
-                cr3 = fmaf(b.w, w.x, cr3);
-                ci3 = fmaf(b.w, w.y, ci3);
-            }
-            float2* Cj = Cs + j * LS + l;      // l % 4 == 0: factors 1, j, -1, -j
-            Cj[0] = make_float2(cr0, ci0);
-            Cj[1] = make_float2(-ci1, cr1);
-            Cj[2] = make_float2(-cr2, -ci2);
-            Cj[3] = make_float2(ci3, -cr3);
         }
         __syncthreads();
         // per voxel: sum over the chunk's pairs of conj(u') sum_l T_l(t) C_l; the geometry of pair
@@ -493,9 +517,9 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
 
     if (a.s) {                               // every lane takes part (group norms use the warp)
         const float2 out = step_prox(s_old, gr, gi, a.step, a.alpha, a.alpha_g, a.shrink, in_grid);
-        if (in_grid) a.s[n] = out;
+        if (in_grid) a.s[NFM_IDX(n, op.n_vox, op.err)] = out;
     } else if (in_grid) {
-        a.g_out[n] = make_float2(gr, gi);
+        a.g_out[NFM_IDX(n, op.n_vox, op.err)] = make_float2(gr, gi);
     }
 }
 

@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(RED_OUT * 32) fwd_reduce_kernel(OpDesc op, Red
 #pragma unroll
             for (int u = 0; u < UN; ++u) {
                 const int c = c0 + 32 * u;
-                x[u] = c < a.n_chunks ? a.partial[(size_t)c * stride + o] : make_float2(0.f, 0.f);
+                x[u] = c < a.n_chunks ? a.partial[NFM_IDX((size_t)c * stride + o, a.partial_elems, op.err)]
+                                      : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < UN; ++u) {
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(RED_OUT * 32) fwd_reduce_kernel(OpDesc op, Red
                 atomicOr(op.err, ERRF_PAIR);
                 pair = 0;
             }
-            const float2 yo = a.y_obs[(size_t)pair * op.K + k];
+            const float2 yo = a.y_obs[NFM_IDX((size_t)pair * op.K + k, op.m_rows, op.err)];
             t.x -= yo.x;
             t.y -= yo.y;
             if (a.fmask && !a.fmask[k]) t = make_float2(0.f, 0.f);

@@ -22,6 +22,7 @@ _STATUS = {-1: "NFM_ERR_ARG", -2: "NFM_ERR_CUDA", -3: "NFM_ERR_NOMEM", -4: "NFM_
            -5: "NFM_ERR_TIMEOUT", -6: "NFM_ERR_NUMERIC"}
 
 _lib = None
+_libs = {}
 
 
 class NfmError(RuntimeError):
@@ -37,11 +38,12 @@ class _Grid(ctypes.Structure):
 
 
 def load_library(path: str | None = None):
-    """Load libnfmimo.so (raises if it has not been built)."""
+    """Load libnfmimo.so, or the library at `path` (e.g. the bounds-checked libnfmimo_check.so); raises if it
+    has not been built.  Each path is loaded once."""
     global _lib
-    if _lib is not None:
-        return _lib
     path = path or LIB_PATH
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with paper_2509_00774_gb300.build.build()")
     L = ctypes.CDLL(path)
@@ -67,6 +69,7 @@ def load_library(path: str | None = None):
         "nfm_forward": (i, [vp, vp, i, vp, vp]),
         "nfm_forward_noalloc": (i, [vp, vp, i, vp, vp]),
         "nfm_adjoint": (i, [vp, vp, i, vp, vp]),
+        "nfm_residual": (i, [vp, vp, i, vp, vp, vp]),
         "nfm_spgm_step": (i, [vp, vp, vp, vp, i, f, f]),
         "nfm_spgm_epoch": (i, [vp, vp, vp, vp, i, f, f]),
         "nfm_spgm_epochs_host": (i, [vp, vp, vp, vp, i, i, f, f]),
@@ -93,7 +96,9 @@ def load_library(path: str | None = None):
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = L
+    _libs[path] = L
+    if path == LIB_PATH:
+        _lib = L
     return L
 
 
@@ -127,9 +132,10 @@ def _ptr(t, dtype, name, device=None):
 class Context:
     """One nfm_ctx: a geometry on one GPU and a stream."""
 
-    def __init__(self, device: int = 0, stream=None):
+    def __init__(self, device: int = 0, stream=None, library: str | None = None):
+        """library: path of an alternative build of the library (the bounds-checked one); default libnfmimo.so."""
         import torch
-        self._lib = load_library()
+        self._lib = load_library(library)
         self.device = int(device)
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
@@ -294,6 +300,19 @@ class Context:
                                                   self._c(s, "s"), self._c(y, "y")))
         return y
 
+    def residual(self, pairs, s, y, r=None):
+        """r = A_B s - y_B for the pair list `pairs` (int32, device), y the full measurement vector [P*K];
+        returns r [n_pairs*K]."""
+        import torch
+        self._need_geom()
+        n = pairs.numel()
+        if r is None:
+            r = torch.empty(n * self.K, dtype=torch.complex64, device=s.device)
+        self._sizes(s=(s, self.N), y=(y, self.P * self.K), r=(r, n * self.K))
+        self._check(self._lib.nfm_residual(self._h, self._i(pairs, "pairs"), n, self._c(s, "s"), self._c(y, "y"),
+                                           self._c(r, "r")))
+        return r
+
     def adjoint(self, pairs, r, g=None):
         """g = A_B^H r; returns g [N]."""
         import torch
@@ -414,6 +433,7 @@ class Context:
         self._check(self._lib.nfm_synchronize(self._h))
 
     HOOK_TC_SKIP_ISSUE = 1
+    HOOK_SHRINK_EXTENTS = 2
 
     def set_test_hooks(self, flags=0, wait_ms=0):
         """Error-path hooks for tests: flags = HOOK_TC_SKIP_ISSUE makes the tensor-core kernels issue no

@@ -43,6 +43,26 @@ def test_forward_op_gradient_matches_oracle_and_fd():
         assert abs(got[j] - (d_re + 1j * d_im)) <= 1e-4 * abs(d_re + 1j * d_im) + 1e-6
 
 
+def test_residual_op_value_and_gradient_match_oracle():
+    """r = A_B s - y_B fused in one launch (y the full measurement vector): value against the oracle's rows,
+    and the gradient of ||r||^2, 2 A_B^H (A_B s - y_B)."""
+    from paper_2509_00774_gb300.autograd import residual_op
+    w = W.small_T4R4_K16_16x16x8()
+    o = Oracle(w.geom)
+    ctx = make_ctx(w.geom)
+    pairs = np.array([9, 2, 15, 4, 4])
+    rows = o.rows_of_pairs(pairs)
+    s = _c64(I.complex_gaussian(o.N, 44)) * 0.3
+    y = _c64(I.complex_gaussian(o.M, 45))
+    s_d = to_dev(s).requires_grad_(True)
+    r = residual_op(ctx, to_dev(pairs, "int32"), s_d, to_dev(y))
+    want_r = o.forward(s, rows=rows) - y[rows]
+    assert np.linalg.norm(to_host(r) - want_r) <= 1e-5 * np.linalg.norm(want_r)
+    r.abs().pow(2).sum().backward()
+    want = 2.0 * o.adjoint(want_r, rows=rows)
+    assert np.linalg.norm(to_host(s_d.grad) - want) <= 1e-5 * np.linalg.norm(want)
+
+
 def test_adjoint_op_gradient_matches_oracle():
     """L(r) = ||A_B^H r - t||^2: grad = 2 A_B (A_B^H r - t)."""
     from paper_2509_00774_gb300.autograd import adjoint_op

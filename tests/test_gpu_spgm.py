@@ -323,3 +323,43 @@ def test_group_regulariser_needs_the_expansion_operator():
         ctx.spgm_epoch(y, s, to_dev(I.epoch_permutation(w.geom.P, 0, 0), "int32"), 4, 0.01, 0.01)
     with pytest.raises(NfmError):
         ctx.set_group_weight(-1.0)
+
+
+def test_bounds_checked_build_matches_and_reports():
+    """The bounds-checked build (-DNFM_BOUNDS_CHECK) gives the normal build's results on the default
+    operator path, and when the test hook halves the extents its kernels receive, a checked access past the
+    declared extent (still inside the real buffer) raises the device flag and the next synchronise reports
+    NFM_ERR_STATE; the context stays usable."""
+    from paper_2509_00774_gb300 import build as nb
+    from paper_2509_00774_gb300.nfmimo import Context
+    w, o, y = _small_problem()
+    path = nb.build(check=True)
+    ref = make_ctx(w.geom, "chebyshev")
+    chk = Context(0, library=path)
+    chk.set_geometry(w.geom)
+    chk.set_algorithm("chebyshev")
+    pairs = to_dev(I.epoch_permutation(o.P, 4, 0)[:5], "int32")
+    s0 = _c64(I.complex_gaussian(o.N, 12)) * 0.1
+    y_d = to_dev(y)
+    outs = []
+    for ctx in (ref, chk):
+        s = to_dev(s0)
+        for _ in range(3):
+            ctx.spgm_step(y_d, s, pairs, 0.003, 1e-3)
+        ctx.synchronize()
+        outs.append(to_host(s))
+    assert np.array_equal(outs[0], outs[1])
+    chk.set_test_hooks(chk.HOOK_SHRINK_EXTENTS)
+    s = to_dev(s0)
+    chk.spgm_step(y_d, s, pairs, 0.003, 1e-3)
+    with pytest.raises(NfmError) as ei:
+        chk.synchronize()
+    assert ei.value.code == -4 and "bounds" in str(ei.value)
+    chk.set_test_hooks(0)
+    chk.spgm_step(y_d, s, pairs, 0.003, 1e-3)
+    chk.synchronize()
+    ref.set_test_hooks(ref.HOOK_SHRINK_EXTENTS)    # the normal build ignores the extents
+    ref.spgm_step(y_d, to_dev(s0), pairs, 0.003, 1e-3)
+    ref.synchronize()
+    ref.close()
+    chk.close()
