@@ -296,7 +296,7 @@ def cpu_baseline(w, y_np, eta, lam, seconds):
                       f"{dt:.1f} s"}
 
 
-def time_to_oracle_nmse(include_mid=False, tols=(1e-1, 3e-2, 1e-2, 1e-3, 1e-4), max_epochs=4000, block=50):
+def time_to_oracle_nmse(include_mid=False, tols=(1e-1, 3e-2, 1e-2, 1e-3, 1e-4), max_epochs=12000, block=100):
     """Time for each GPU form to bring its iterate within NMSE tol of the FP64 oracle's minimiser of Eq. 3.
 
     Small workload (4 TX x 4 RX, 16 freqs, 16x16x8 voxels, 4 pairs per minibatch): y, L (50 power

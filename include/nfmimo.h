@@ -289,17 +289,21 @@ int nfm_solve(nfm_ctx* ctx, const float* y, float* s, const int* perms, int max_
               float eta, float lambda, double tol, int* epochs_out, double* change_out);
 
 /* Gradient step and prox of Eq. 5 as a separate op (used by unrolled SPGM):
- *   out = prox_alpha(s - step g),  prox(z) = z max(0, 1 - alpha/|z|).
- * s, g, out: device complex64 [n] (out may alias s). */
-int nfm_prox_step(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n, float* out);
+ *   out = shrink prox_alpha(s - step g),  prox(z) = z max(0, 1 - alpha/|z|),
+ * shrink = 1 for the paper's l1 and 1/(1 + eta lambda w2) for the elastic net
+ * R = w1 ||s||_1 + (w2/2) ||s||^2 (alpha = eta lambda w1).
+ * s, g, out: device complex64 [n] (out may alias s).  Errors: NFM_ERR_ARG for
+ * alpha < 0, shrink <= 0 or non-finite scalars. */
+int nfm_prox_step(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, float shrink, long long n,
+                  float* out);
 
 /* Backward of nfm_prox_step for a real loss, with complex gradients as real
  * pairs (d/dRe + j d/dIm, the PyTorch convention).  grad_out [n] is the
  * gradient of the output; writes grad_s [n] and grad_g [n] (either may be
- * NULL) and, to the device buffer grad_scalars [2] (FP64), dL/dstep and
- * dL/dalpha.  All pointers device. */
-int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n,
-                           const float* grad_out, float* grad_s, float* grad_g, double* grad_scalars);
+ * NULL) and, to the device buffer grad_scalars [3] (FP64), dL/dstep,
+ * dL/dalpha and dL/dshrink.  All pointers device. */
+int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, float shrink,
+                           long long n, const float* grad_out, float* grad_s, float* grad_g, double* grad_scalars);
 
 /* Batched solves of many independent scenes (uneven grids, arrays and K):
  * Sec. IV-A, Eq. 6 with Eq. 5, applied to every scene independently.

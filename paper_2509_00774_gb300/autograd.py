@@ -61,28 +61,30 @@ class _AdjointFn(torch.autograd.Function):
 
 class _ProxStepFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, s, g, step, alpha, op):
+    def forward(ctx, s, g, step, alpha, shrink, op):
         s = s.contiguous()
         g = g.contiguous()
-        st, al = float(step), float(alpha)
+        st, al, sh = float(step), float(alpha), float(shrink)
         out = torch.empty_like(s)
-        op.prox_step(s, g, st, al, out)
+        op.prox_step(s, g, st, al, out, sh)
         ctx.save_for_backward(s, g)
-        ctx.op, ctx.st, ctx.al = op, st, al
-        ctx.scalar_meta = (step.dtype, step.device) if torch.is_tensor(step) else (torch.float64, torch.device("cpu"))
+        ctx.op, ctx.st, ctx.al, ctx.sh = op, st, al, sh
+        ref = step if torch.is_tensor(step) else alpha
+        ctx.scalar_meta = (ref.dtype, ref.device) if torch.is_tensor(ref) else (torch.float64, torch.device("cpu"))
         return out
 
     @staticmethod
     def backward(ctx, go):
         s, g = ctx.saved_tensors
-        need_s, need_g, need_step, need_alpha = ctx.needs_input_grad[:4]
+        need_s, need_g, need_step, need_alpha, need_shrink = ctx.needs_input_grad[:5]
         grad_s = torch.empty_like(s) if need_s else None
         grad_g = torch.empty_like(g) if need_g else None
-        scalars = torch.empty(2, dtype=torch.float64, device=s.device)
-        ctx.op.prox_step_backward(s, g, ctx.st, ctx.al, go.contiguous(), grad_s, grad_g, scalars)
+        scalars = torch.empty(3, dtype=torch.float64, device=s.device)
+        ctx.op.prox_step_backward(s, g, ctx.st, ctx.al, go.contiguous(), grad_s, grad_g, scalars, ctx.sh)
         dt, dev = ctx.scalar_meta
         sc = scalars.to(device=dev, dtype=dt)
-        return grad_s, grad_g, (sc[0] if need_step else None), (sc[1] if need_alpha else None), None
+        return (grad_s, grad_g, (sc[0] if need_step else None), (sc[1] if need_alpha else None),
+                (sc[2] if need_shrink else None), None)
 
 
 def forward_op(op, pairs, s):
@@ -101,27 +103,33 @@ def adjoint_op(op, pairs, r):
     return _AdjointFn.apply(r, op, pairs)
 
 
-def prox_step(op, s, g, step, alpha):
-    """prox_alpha(s - step g), differentiable in s, g, step and alpha (0-dim tensors or floats)."""
-    return _ProxStepFn.apply(s, g, step, alpha, op)
+def prox_step(op, s, g, step, alpha, shrink=1.0):
+    """shrink * prox_alpha(s - step g), differentiable in s, g, step, alpha and shrink (0-dim tensors or floats);
+    shrink = 1/(1 + eta lambda w2) gives the prox of the elastic net w1 ||s||_1 + (w2/2) ||s||^2 with
+    alpha = eta lambda w1."""
+    return _ProxStepFn.apply(s, g, step, alpha, shrink, op)
 
 
 class UnrolledSPGM(torch.nn.Module):
     """n_iter SPGM iterations with learnable per-iteration eta_i and lambda_i (FP64 CPU parameters)."""
 
-    def __init__(self, op, n_iter: int, eta: float, lam: float, checkpoint: bool = True):
+    def __init__(self, op, n_iter: int, eta: float, lam: float, checkpoint: bool = True, w1: float = 1.0,
+                 w2: float = 0.0):
+        """w1, w2: regulariser w1 ||s||_1 + (w2/2) ||s||^2 (w2 = 0: the paper's l1)."""
         super().__init__()
         self.op = op
         self.n_iter = int(n_iter)
         self.eta = torch.nn.Parameter(torch.full((self.n_iter,), float(eta), dtype=torch.float64))
         self.lam = torch.nn.Parameter(torch.full((self.n_iter,), float(lam), dtype=torch.float64))
         self.checkpoint = checkpoint
+        self.w1, self.w2 = float(w1), float(w2)
 
     def _iteration(self, s, y, pairs, eta, lam):
         B = pairs.numel() * self.op.K
         r = residual_op(self.op, pairs, s, y)       # A_B s - y_B fused in the forward kernel
         g = adjoint_op(self.op, pairs, r)
-        return prox_step(self.op, s, g, eta / B, eta * lam)
+        shrink = 1.0 / (1.0 + eta * lam * self.w2) if self.w2 != 0.0 else 1.0
+        return prox_step(self.op, s, g, eta / B, eta * lam * self.w1, shrink)
 
     def forward(self, y, batches, s0=None):
         """y: [M] or [n_scenes, M] complex64 device; batches: n_iter int32 pair lists.

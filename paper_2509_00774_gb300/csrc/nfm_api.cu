@@ -1597,34 +1597,37 @@ int nfm_solve(nfm_ctx* ctx, const float* y, float* s, const int* perms, int max_
     return NFM_OK;
 }
 
-int nfm_prox_step(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n, float* out)
+int nfm_prox_step(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, float shrink, long long n,
+                  float* out)
 {
     if (!ctx) return NFM_ERR_ARG;
     DevGuard guard(ctx->device);
     if (n < 1) return fail(ctx, NFM_ERR_ARG, "n must be >= 1");
-    if (!std::isfinite(step) || !(alpha >= 0) || !std::isfinite(alpha)) return fail(ctx, NFM_ERR_ARG, "bad step/alpha");
+    if (!std::isfinite(step) || !(alpha >= 0) || !std::isfinite(alpha) || !(shrink > 0) || !std::isfinite(shrink))
+        return fail(ctx, NFM_ERR_ARG, "bad step/alpha/shrink");
     NFM_TRY(check_ptr(ctx, s, "s", 8));
     NFM_TRY(check_ptr(ctx, g, "g", 8));
     NFM_TRY(check_ptr(ctx, out, "out", 8));
-    NFM_CK(launch_prox_step((const float2*)s, (const float2*)g, step, alpha, n, (float2*)out, ctx->stream));
+    NFM_CK(launch_prox_step((const float2*)s, (const float2*)g, step, alpha, shrink, n, (float2*)out, ctx->stream));
     return NFM_OK;
 }
 
-int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, long long n,
-                           const float* grad_out, float* grad_s, float* grad_g, double* grad_scalars)
+int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, float shrink,
+                           long long n, const float* grad_out, float* grad_s, float* grad_g, double* grad_scalars)
 {
     if (!ctx) return NFM_ERR_ARG;
     DevGuard guard(ctx->device);
     if (n < 1) return fail(ctx, NFM_ERR_ARG, "n must be >= 1");
-    if (!std::isfinite(step) || !(alpha >= 0) || !std::isfinite(alpha)) return fail(ctx, NFM_ERR_ARG, "bad step/alpha");
+    if (!std::isfinite(step) || !(alpha >= 0) || !std::isfinite(alpha) || !(shrink > 0) || !std::isfinite(shrink))
+        return fail(ctx, NFM_ERR_ARG, "bad step/alpha/shrink");
     NFM_TRY(check_ptr(ctx, s, "s", 8));
     NFM_TRY(check_ptr(ctx, g, "g", 8));
     NFM_TRY(check_ptr(ctx, grad_out, "grad_out", 8));
     NFM_TRY(check_ptr(ctx, grad_scalars, "grad_scalars", 8));
     if (grad_s) NFM_TRY(check_ptr(ctx, grad_s, "grad_s", 8));
     if (grad_g) NFM_TRY(check_ptr(ctx, grad_g, "grad_g", 8));
-    NFM_TRY(ensure(ctx, &ctx->d_prox_partial, &ctx->prox_partial_cap, 2 * RED_BLOCKS * sizeof(double)));
-    NFM_CK(launch_prox_step_backward((const float2*)s, (const float2*)g, step, alpha, n, (const float2*)grad_out,
+    NFM_TRY(ensure(ctx, &ctx->d_prox_partial, &ctx->prox_partial_cap, 3 * RED_BLOCKS * sizeof(double)));
+    NFM_CK(launch_prox_step_backward((const float2*)s, (const float2*)g, step, alpha, shrink, n, (const float2*)grad_out,
                                      (float2*)grad_s, (float2*)grad_g, (double*)ctx->d_prox_partial, grad_scalars,
                                      ctx->stream));
     return NFM_OK;

@@ -160,13 +160,13 @@ cudaError_t launch_abs_max(const float2* v, long long n, double* partial, double
 // out = max_n | |a_n| - |b_n| |  (FP64)
 cudaError_t launch_mag_change(const float2* a, const float2* b, long long n, double* partial, double* out,
                               cudaStream_t st);
-// out = prox_alpha(s - step g)  and its backward (grad_s, grad_g may be null;
-// out2[0] = dL/dstep, out2[1] = dL/dalpha in FP64; partial holds 2*RED_BLOCKS doubles)
-cudaError_t launch_prox_step(const float2* s, const float2* g, float step, float alpha, long long n, float2* out,
-                             cudaStream_t st);
-cudaError_t launch_prox_step_backward(const float2* s, const float2* g, float step, float alpha, long long n,
-                                      const float2* go, float2* grad_s, float2* grad_g, double* partial,
-                                      double* out2, cudaStream_t st);
+// out = shrink prox_alpha(s - step g)  and its backward (grad_s, grad_g may be null; out3[0] = dL/dstep,
+// out3[1] = dL/dalpha, out3[2] = dL/dshrink in FP64; partial holds 3*RED_BLOCKS doubles)
+cudaError_t launch_prox_step(const float2* s, const float2* g, float step, float alpha, float shrink, long long n,
+                             float2* out, cudaStream_t st);
+cudaError_t launch_prox_step_backward(const float2* s, const float2* g, float step, float alpha, float shrink,
+                                      long long n, const float2* go, float2* grad_s, float2* grad_g, double* partial,
+                                      double* out3, cudaStream_t st);
 // out = sum over the 2 x 2 x 1 voxel blocks (ix/2, iy/2, iz) of the block's l2 norm (FP64, fixed tree)
 cudaError_t launch_group_norm_sum(const float2* v, int nx, int ny, int nz, double* partial, double* out,
                                   cudaStream_t st);

@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
                 const int j = et / LQ, l = 4 * (et - (et / LQ) * LQ);
                 const float2* rj = rp + j * RS;
                 float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f, cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
+#pragma unroll 4
                 for (int k = active ? h : KH; k < KH; k += 2) {
                     const float2 u = rj[k], v = rj[K - 1 - k];
                     const float4 b = *reinterpret_cast<const float4*>(coef + k * LS + l);

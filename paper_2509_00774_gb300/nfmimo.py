@@ -76,8 +76,8 @@ def load_library(path: str | None = None):
         "nfm_pgm_step": (i, [vp, vp, vp, f, f]),
         "nfm_spgm_step_freqs": (i, [vp, vp, vp, vp, i, vp, i, f, f]),
         "nfm_solve": (i, [vp, vp, vp, vp, i, i, f, f, d, ctypes.POINTER(i), ctypes.POINTER(d)]),
-        "nfm_prox_step": (i, [vp, vp, vp, f, f, ctypes.c_longlong, vp]),
-        "nfm_prox_step_backward": (i, [vp, vp, vp, f, f, ctypes.c_longlong, vp, vp, vp, vp]),
+        "nfm_prox_step": (i, [vp, vp, vp, f, f, f, ctypes.c_longlong, vp]),
+        "nfm_prox_step_backward": (i, [vp, vp, vp, f, f, f, ctypes.c_longlong, vp, vp, vp, vp]),
         "nfm_power_iteration": (i, [vp, i, vp, ctypes.POINTER(d)]),
         "nfm_power_iteration_pairs": (i, [vp, vp, i, i, vp, ctypes.POINTER(d)]),
         "nfm_objective": (i, [vp, vp, vp, d, ctypes.POINTER(d)]),
@@ -384,19 +384,22 @@ class Context:
                                         ctypes.byref(ep), ctypes.byref(ch)))
         return ep.value, ch.value
 
-    def prox_step(self, s, g, step, alpha, out):
-        """out = prox_alpha(s - step g) (Eq. 5); out may be s."""
+    def prox_step(self, s, g, step, alpha, out, shrink=1.0):
+        """out = shrink prox_alpha(s - step g) (Eq. 5; shrink = 1/(1 + eta lambda w2) for the elastic net);
+        out may be s."""
         self._check(self._lib.nfm_prox_step(self._h, self._c(s, "s"), self._c(g, "g"), float(step), float(alpha),
-                                            s.numel(), self._c(out, "out")))
+                                            float(shrink), s.numel(), self._c(out, "out")))
         return out
 
-    def prox_step_backward(self, s, g, step, alpha, grad_out, grad_s, grad_g, scalars):
-        """Backward of prox_step; scalars: float64 device tensor [2] <- (dL/dstep, dL/dalpha)."""
+    def prox_step_backward(self, s, g, step, alpha, grad_out, grad_s, grad_g, scalars, shrink=1.0):
+        """Backward of prox_step; scalars: float64 device tensor [3] <- (dL/dstep, dL/dalpha, dL/dshrink)."""
         import torch
         ps = self._c(grad_s, "grad_s") if grad_s is not None else None
         pg = self._c(grad_g, "grad_g") if grad_g is not None else None
+        if scalars.numel() < 3:
+            raise NfmError(-1, "scalars needs 3 float64 entries")
         self._check(self._lib.nfm_prox_step_backward(
-            self._h, self._c(s, "s"), self._c(g, "g"), float(step), float(alpha), s.numel(),
+            self._h, self._c(s, "s"), self._c(g, "g"), float(step), float(alpha), float(shrink), s.numel(),
             self._c(grad_out, "grad_out"), ps, pg, _ptr(scalars, torch.float64, "scalars", self.device)))
 
     def power_iteration(self, v0, iters: int = 50) -> float:

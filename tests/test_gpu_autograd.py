@@ -131,6 +131,50 @@ def test_prox_step_backward_matches_fd():
     assert abs(float(al2.grad) - fd_alpha) <= 1e-4 * abs(fd_alpha) + 1e-3
 
 
+def test_elastic_net_prox_step_backward_matches_fd():
+    """out = shrink prox_alpha(s - step g) (the elastic-net prox, shrink = 1/(1 + eta lambda w2)):
+    value against the oracle's prox of w1 ||s||_1 + (w2/2)||s||^2, and dL/dshrink, dL/dalpha and grad_s
+    against FP64 central differences (entries near |z| = alpha excluded)."""
+    import torch
+    from oracle import Oracle
+    from paper_2509_00774_gb300.autograd import prox_step
+    w = W.small_T4R4_K16_16x16x8()
+    ctx = make_ctx(w.geom)
+    n = 3000
+    s = _c64(I.complex_gaussian(n, 48))
+    g = _c64(I.complex_gaussian(n, 49))
+    c = _c64(I.complex_gaussian(n, 50))
+    step, eta_lam, w1, w2 = 0.3, 0.5, 1.2, 0.5          # alpha = eta lambda w1, shrink = 1/(1 + eta lambda w2)
+    alpha, shrink = eta_lam * w1, 1.0 / (1.0 + eta_lam * w2)
+    z = s - step * g
+    keep = np.abs(np.abs(z) - alpha) > 1e-2
+    o = Oracle(w.geom, w1=w1, w2=w2)
+    want = o.prox(z, eta_lam)
+    sh = torch.tensor(shrink, dtype=torch.float64, requires_grad=True)
+    al = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+    s_d = to_dev(s).requires_grad_(True)
+    out = prox_step(ctx, s_d, to_dev(g), step, al, sh)
+    assert np.max(np.abs(to_host(out) - want)) <= 1e-5 * np.max(np.abs(want))
+    mask = torch.from_numpy(keep).cuda()
+    ((torch.conj(to_dev(c)) * out).real * mask).sum().backward()
+
+    def loss(s_, al_, sh_):
+        return float(np.sum((np.conj(c) * sh_ * prox_l1(s_ - step * g, al_)).real[keep]))
+
+    h = 1e-6
+    fd_sh = (loss(s, alpha, shrink + h) - loss(s, alpha, shrink - h)) / (2 * h)
+    fd_al = (loss(s, alpha + h, shrink) - loss(s, alpha - h, shrink)) / (2 * h)
+    assert abs(float(sh.grad) - fd_sh) <= 1e-4 * abs(fd_sh) + 1e-3
+    assert abs(float(al.grad) - fd_al) <= 1e-4 * abs(fd_al) + 1e-3
+    gs = to_host(s_d.grad)
+    for j in np.flatnonzero(keep)[:: max(1, keep.sum() // 30)]:
+        e = np.zeros(n, dtype=np.complex128)
+        e[j] = h
+        fd = (loss(s + e, alpha, shrink) - loss(s - e, alpha, shrink)) / (2 * h) + \
+            1j * (loss(s + 1j * e, alpha, shrink) - loss(s - 1j * e, alpha, shrink)) / (2 * h)
+        assert abs(gs[j] - fd) <= 1e-4 * max(1.0, abs(fd)), (j, gs[j], fd)
+
+
 def _oracle_unrolled(o, y, batches, eta, lam, s_ref):
     s = np.zeros(o.N, dtype=np.complex128)
     for i, b in enumerate(batches):
