@@ -325,6 +325,23 @@ int nfm_batch_spgm_epoch(nfm_batch* batch, const float* const* y, float* const* 
                          const int* pairs_per_batch, const float* eta, const float* lambda);
 const char* nfm_batch_last_error(const nfm_batch* batch);
 
+/* How nfm_batch_spgm_epoch runs the scenes (the next call re-captures):
+ *   NFM_BATCH_BRANCHES (default): the graph holds one concurrent branch per
+ *     scene, each the scene's own launches (any operator, precision or
+ *     algorithm the scene is set to);
+ *   NFM_BATCH_FUSED: for each step index t of the epoch, one launch of the
+ *     expansion forward, one of the chunk reduction and one of the expansion
+ *     adjoint cover every scene that still has a minibatch at t (each CTA
+ *     finds its scene in a table), so an epoch is 3 max_i ceil(P_i/B_i)
+ *     launches whatever the number of scenes.  Needs every scene on the FP32
+ *     expansion operator with L <= 20; the scenes share the largest L (the
+ *     others' coefficient tables are padded with zero columns, which leaves
+ *     their results unchanged).
+ * Errors: NFM_ERR_ARG for another mode (and, at the next epoch, for scenes the
+ * fused mode cannot run). */
+enum { NFM_BATCH_BRANCHES = 0, NFM_BATCH_FUSED = 1 };
+int nfm_batch_set_mode(nfm_batch* batch, int mode);
+
 /* Largest eigenvalue L of A^H A / M by `iters` power iterations from
  * v0 [N] (device, complex64, not modified), with FP64 norms.  L is the
  * Lipschitz constant of the gradient of D(s) = ||y - A s||^2/(2M) (Eq. 4); the

@@ -546,13 +546,30 @@ int launch_cheb_forward_shape(nfm_ctx* ctx, const ChebShape& sh, const int* pair
 
 // Tensor-core expansion forward (precision modes): 256-thread CTAs, 16, 32 or 64 pairs per CTA, one
 // wave of two CTAs per SM over the voxel-tile chunks.
+// launch shape of the tensor-core forward for n_pairs pairs: pairs per CTA, pair groups, voxel-tile chunks
+void tc_fwd_shape(const nfm_ctx* ctx, int n_pairs, int* pch_out, int* groups_out, long long* nch_out)
+{
+    const int pch = n_pairs <= 16 ? 16 : n_pairs <= 32 ? 32 : 64;
+    const int TS = 64 / pch;
+    const int n_groups = (n_pairs + pch - 1) / pch;
+    long long nch = (2LL * ctx->num_sms + n_groups - 1) / n_groups;
+    const long long max_ch = (ctx->gd.n_tiles + TS - 1) / TS;
+    if (nch > max_ch) nch = max_ch;
+    if (nch > 65535) nch = 65535;
+    if (nch < 1) nch = 1;
+    *pch_out = pch;
+    *groups_out = n_groups;
+    *nch_out = nch;
+}
+
 int enqueue_forward_cheb_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* s, const float2* y_obs,
                             float2* out, const unsigned char* fmask)
 {
     const int LT = ctx->cheb_L;
     const bool f16 = ctx->precision == NFM_TC_FP16X3;
-    const int pch = n_pairs <= 16 ? 16 : n_pairs <= 32 ? 32 : 64;
-    const int TS = 64 / pch;
+    int pch = 0, n_groups = 0;
+    long long nch = 0;
+    tc_fwd_shape(ctx, n_pairs, &pch, &n_groups, &nch);
     const size_t smem = fwd_cheb_tc_smem_bytes(LT, ctx->K, pch);
     if (smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "tensor-core expansion forward needs %zu B shared memory", smem);
     if (!ctx->fwd_cheb_tc_attr[f16][LT]) {
@@ -560,13 +577,7 @@ int enqueue_forward_cheb_tc(nfm_ctx* ctx, const int* pairs, int n_pairs, const f
                                     (int)ctx->smem_optin));
         ctx->fwd_cheb_tc_attr[f16][LT] = true;
     }
-    const int n_groups = (n_pairs + pch - 1) / pch;
     const int n_slots = n_groups * pch;
-    long long nch = (2LL * ctx->num_sms + n_groups - 1) / n_groups;
-    const long long max_ch = (ctx->gd.n_tiles + TS - 1) / TS;
-    if (nch > max_ch) nch = max_ch;
-    if (nch > 65535) nch = 65535;
-    if (nch < 1) nch = 1;
     NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, (size_t)nch * n_slots * ctx->K * sizeof(float2)));
     ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
     FwdArgs a;
@@ -1908,6 +1919,11 @@ struct nfm_batch {
     std::vector<float> eta, lam;
     std::vector<unsigned long long> gen;   // scene scratch generations the graph was captured with
     std::string err;
+    int mode = NFM_BATCH_BRANCHES;
+    int captured_mode = -1;
+    // fused mode: scene items of every launch and the coefficient tables padded to the launch's L
+    void* d_items = nullptr;
+    std::vector<float*> d_coef;
 };
 
 namespace {
@@ -1938,11 +1954,32 @@ int prepare_epoch(nfm_ctx* ctx, int bp)
     for (int nb : {bp, ctx->P % bp}) {
         if (nb <= 0) continue;
         FwdPlan pl;
-        if (ctx->uniform)
-            NFM_TRY(plan_forward(ctx, nb, &pl));
-        else
+        size_t pbytes = 0;
+        bool cheb = false;
+        if (ctx->uniform) NFM_TRY(use_cheb(ctx, cheb, nb));
+        if (!ctx->uniform) {
             plan_forward_general(ctx, nb, &pl);
-        NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, pl.partial_bytes));
+            pbytes = pl.partial_bytes;
+        } else if (cheb && ctx->precision != NFM_FP32) {       // the tensor-core forward's shape
+            int pch = 0, ng = 0;
+            long long nch = 0;
+            tc_fwd_shape(ctx, nb, &pch, &ng, &nch);
+            pbytes = (size_t)nch * ng * pch * ctx->K * sizeof(float2);
+        } else if (cheb) {                                      // the expansion forward's (tuned or default) shape
+            ChebShape sh;
+            bool tuned = false;
+            for (const auto& t : ctx->fwd_tuned)
+                if (t.n_pairs == nb && !t.direct) {
+                    NFM_TRY(cheb_shape(ctx, nb, t.threads, t.group, t.pch, 0.0, t.chunks, &sh));
+                    tuned = true;
+                }
+            if (!tuned) NFM_TRY(cheb_shape(ctx, nb, CHEB_THREADS, CHEB_GROUP, 0, 2.0, 0, &sh));
+            pbytes = (size_t)sh.nch * sh.n_slots * ctx->K * sizeof(float2);
+        } else {
+            NFM_TRY(plan_forward(ctx, nb, &pl));
+            pbytes = pl.partial_bytes;
+        }
+        NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, pbytes));
         if (ctx->precision != NFM_FP32) {
             NFM_TRY(ensure(ctx, &ctx->d_bmat, &ctx->bmat_cap, adj_tc_bmat_bytes(nb)));
             NFM_TRY(ensure(ctx, &ctx->d_bscale, &ctx->bscale_cap, (size_t)nb * sizeof(float)));
@@ -2010,10 +2047,183 @@ void nfm_batch_destroy(nfm_batch* b)
         if (ev) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
+    free_ptr(b->d_items);
+    for (float* p : b->d_coef) free_ptr(p);
     delete b;
 }
 
 const char* nfm_batch_last_error(const nfm_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+int nfm_batch_set_mode(nfm_batch* b, int mode)
+{
+    if (!b) return NFM_ERR_ARG;
+    if (mode != NFM_BATCH_BRANCHES && mode != NFM_BATCH_FUSED) return bfail(b, NFM_ERR_ARG, "unknown batch mode %d", mode);
+    b->mode = mode;
+    return NFM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Fused epoch: for step t of the epoch, one launch each of the expansion forward, the chunk reduction and
+// the expansion adjoint over every scene that still has a minibatch at t (scene i takes pairs
+// perm_i[t bp_i ...]), enqueued on `st` (the capture stream).
+int batch_fused_enqueue(nfm_batch* b, const float* const* y, float* const* s, const int* const* perm,
+                        const int* bp, const float* eta, const float* lambda, cudaStream_t st)
+{
+    const int n = (int)b->scenes.size();
+    int LT = 0, steps = 0;
+    for (int i = 0; i < n; ++i) {
+        nfm_ctx* c = b->scenes[i];
+        if (!c->uniform || c->cheb_L == 0 || c->algorithm == NFM_ALGO_DIRECT || c->precision != NFM_FP32)
+            return bfail(b, NFM_ERR_ARG, "scene %d: the fused batch needs the FP32 expansion operator", i);
+        LT = std::max(LT, c->cheb_L);
+        steps = std::max(steps, (c->P + bp[i] - 1) / bp[i]);
+    }
+    if (!fwd_cheb_multi_ptr(LT))
+        return bfail(b, NFM_ERR_ARG, "the fused batch covers expansion lengths up to 20 (here %d)", LT);
+    const int LS = (LT + 3) & ~3;
+    // coefficient tables with the row stride of LT (zero columns beyond each scene's L)
+    for (float* p : b->d_coef) free_ptr(p);
+    b->d_coef.assign(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        nfm_ctx* c = b->scenes[i];
+        const size_t bytes = (size_t)c->cheb_kpad * LS * sizeof(float);
+        cudaError_t e = cudaMalloc((void**)&b->d_coef[i], bytes);
+        if (e == cudaSuccess) e = cudaMemset(b->d_coef[i], 0, bytes);
+        const int ls_i = (c->cheb_L + 3) & ~3;
+        if (e == cudaSuccess)
+            e = cudaMemcpy2D(b->d_coef[i], LS * sizeof(float), c->d_cheb, ls_i * sizeof(float), ls_i * sizeof(float),
+                             c->cheb_kpad, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) return bfail(b, NFM_ERR_CUDA, "fused coefficient tables: %s", cudaGetErrorString(e));
+    }
+    std::vector<MultiFwdItem> fwd;
+    std::vector<MultiRedItem> red;
+    std::vector<MultiAdjItem> adj;
+    struct Launch { size_t f0, nf, r0, nr, a0, na; int cf, cr, ca; };
+    std::vector<Launch> launches;
+    size_t smem_f = 0, smem_a = 0;
+    for (int t = 0; t < steps; ++t) {
+        Launch L{fwd.size(), 0, red.size(), 0, adj.size(), 0, 0, 0, 0};
+        for (int i = 0; i < n; ++i) {
+            nfm_ctx* c = b->scenes[i];
+            if (t * bp[i] >= c->P) continue;
+            const int np = std::min(bp[i], c->P - t * bp[i]);
+            const int* pairs = perm[i] + (size_t)t * bp[i];
+            ChebShape sh;
+            bool tuned = false;
+            for (const auto& tu : c->fwd_tuned)
+                if (tu.n_pairs == np && tu.threads == CHEB_THREADS && tu.group == CHEB_GROUP) {
+                    NFM_TRY(cheb_shape(c, np, tu.threads, tu.group, tu.pch, 0.0, tu.chunks, &sh));
+                    tuned = true;
+                }
+            if (!tuned) NFM_TRY(cheb_shape(c, np, CHEB_THREADS, CHEB_GROUP, 0, 2.0, 0, &sh));
+            const size_t pbytes = (size_t)sh.nch * sh.n_slots * c->K * sizeof(float2);
+            NFM_TRY(ensure(c, &c->d_partial, &c->partial_cap, pbytes));
+            NFM_TRY(ensure(c, &c->d_resid, &c->resid_cap, (size_t)bp[i] * c->K * sizeof(float2)));
+            smem_f = std::max(smem_f, fwd_cheb_smem_bytes(LT, c->cheb_kpad, sh.pch, CHEB_THREADS, CHEB_GROUP, c->points));
+            smem_a = std::max(smem_a, adj_cheb_smem_bytes(LT, c->cheb_kpad));
+            const OpDesc op = op_desc(c);
+            ChebDesc cd{b->d_coef[i], c->cheb_tau, LT, c->cheb_kpad, c->cheb_fc_hi, c->cheb_fc_lo};
+            MultiFwdItem fi;
+            fi.op = op;
+            fi.cd = cd;
+            fi.a.pairs = pairs;
+            fi.a.n_pairs = np;
+            fi.a.s = (const float2*)s[i];
+            fi.a.partial = (float2*)c->d_partial;
+            fi.a.partial_elems = (long long)(c->partial_cap / sizeof(float2));
+            fi.a.n_slots = sh.n_slots;
+            fi.a.VS = sh.pch;
+            fi.a.tiles_base = (int)(c->gd.n_tiles / sh.nch);
+            fi.a.tiles_rem = (int)(c->gd.n_tiles % sh.nch);
+            fi.n_groups = sh.n_groups;
+            fi.cta0 = L.cf;
+            L.cf += (int)(sh.n_groups * sh.nch);
+            fwd.push_back(fi);
+            MultiRedItem ri;
+            ri.op = op;
+            ri.a.partial = (const float2*)c->d_partial;
+            ri.a.partial_elems = fi.a.partial_elems;
+            ri.a.n_chunks = (int)sh.nch;
+            ri.a.n_slots = sh.n_slots;
+            ri.a.n_out = np * c->K;
+            ri.a.pairs = pairs;
+            ri.a.y_obs = (const float2*)y[i];
+            ri.a.fmask = nullptr;
+            ri.a.out = (float2*)c->d_resid;
+            ri.cta0 = L.cr;
+            L.cr += fwd_reduce_blocks(ri.a.n_out);
+            red.push_back(ri);
+            const double B = (double)np * c->K;
+            MultiAdjItem ai;
+            ai.op = op;
+            ai.cd = cd;
+            ai.a.pairs = pairs;
+            ai.a.n_pairs = np;
+            ai.a.r = (const float2*)c->d_resid;
+            ai.a.r_elems = (long long)np * c->K;
+            ai.a.g_out = nullptr;
+            ai.a.s = (float2*)s[i];
+            ai.a.step = (float)(eta[i] / B);
+            ai.a.alpha = (float)((double)eta[i] * lambda[i] * c->reg_w1);
+            ai.a.shrink = (float)(1.0 / (1.0 + (double)eta[i] * lambda[i] * c->reg_w2));
+            ai.a.alpha_g = (float)((double)eta[i] * lambda[i] * c->reg_w3);
+            ai.a.pchunk = CHEB_ADJ_PCHUNK;
+            ai.cta0 = L.ca;
+            L.ca += c->gd.n_tiles;
+            adj.push_back(ai);
+        }
+        L.nf = fwd.size() - L.f0;
+        L.nr = red.size() - L.r0;
+        L.na = adj.size() - L.a0;
+        launches.push_back(L);
+    }
+    for (nfm_ctx* c : b->scenes)
+        if (c->points && c->reg_w3 != 0.0) return bfail(b, NFM_ERR_ARG, "the group term needs a regular voxel grid");
+    // every item of every launch in one device buffer
+    const size_t bf = fwd.size() * sizeof(MultiFwdItem), br = red.size() * sizeof(MultiRedItem),
+                 ba = adj.size() * sizeof(MultiAdjItem);
+    free_ptr(b->d_items);
+    b->d_items = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_items, bf + br + ba);
+    unsigned char* base = (unsigned char*)b->d_items;
+    if (e == cudaSuccess) e = cudaMemcpy(base, fwd.data(), bf, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + bf, red.data(), br, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + bf + br, adj.data(), ba, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fwd_cheb_multi_ptr(LT), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(adj_cheb_multi_ptr(LT), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
+    if (e != cudaSuccess) return bfail(b, NFM_ERR_CUDA, "fused batch items: %s", cudaGetErrorString(e));
+    const MultiFwdItem* df = (const MultiFwdItem*)base;
+    const MultiRedItem* dr = (const MultiRedItem*)(base + bf);
+    const MultiAdjItem* da = (const MultiAdjItem*)(base + bf + br);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    for (const Launch& L : launches) {
+        if (e == cudaSuccess) e = launch_fwd_cheb_multi(LT, df + L.f0, (int)L.nf, L.cf, smem_f, st);
+        if (e == cudaSuccess) e = launch_fwd_reduce_multi(dr + L.r0, (int)L.nr, L.cr, st);
+        if (e == cudaSuccess) e = launch_adj_cheb_multi(LT, da + L.a0, (int)L.na, L.ca, smem_a, st);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return bfail(b, NFM_ERR_CUDA, "fused capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return bfail(b, NFM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    return NFM_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int nfm_batch_spgm_epoch(nfm_batch* b, const float* const* y, float* const* s, const int* const* perm,
                          const int* pairs_per_batch, const float* eta, const float* lambda)
@@ -2023,7 +2233,7 @@ int nfm_batch_spgm_epoch(nfm_batch* b, const float* const* y, float* const* s, c
     const int n = (int)b->scenes.size();
     if (!y || !s || !perm || !pairs_per_batch || !eta || !lambda) return bfail(b, NFM_ERR_ARG, "NULL argument array");
     DevGuard guard(b->scenes[0]->device);
-    bool same = b->exec != nullptr;
+    bool same = b->exec != nullptr && b->captured_mode == b->mode;
     for (int i = 0; i < n; ++i) {
         nfm_ctx* c = b->scenes[i];
         if (!c->has_geom) return bfail(b, NFM_ERR_STATE, "scene %d has no geometry", i);
@@ -2045,6 +2255,12 @@ int nfm_batch_spgm_epoch(nfm_batch* b, const float* const* y, float* const* s, c
             int r = prepare_epoch(b->scenes[i], pairs_per_batch[i]);
             if (r != NFM_OK) return bfail(b, r, "scene %d: %s", i, b->scenes[i]->err.c_str());
         }
+        if (b->mode == NFM_BATCH_FUSED) {
+            int r = batch_fused_enqueue(b, y, s, perm, pairs_per_batch, eta, lambda, b->cap);
+            if (r != NFM_OK) return r;
+        }
+    }
+    if (!same && b->mode == NFM_BATCH_BRANCHES) {
         NFM_BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
         int rc = NFM_OK;
         cudaError_t e = cudaEventRecord(b->fork, b->cap);
@@ -2076,6 +2292,8 @@ int nfm_batch_spgm_epoch(nfm_batch* b, const float* const* y, float* const* s, c
             b->exec = nullptr;
             return bfail(b, NFM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
         }
+    }
+    if (!same) {
         b->y.assign(y, y + n);
         b->s.assign((const void* const*)s, (const void* const*)s + n);
         b->perm.assign((const void* const*)perm, (const void* const*)perm + n);
@@ -2084,6 +2302,7 @@ int nfm_batch_spgm_epoch(nfm_batch* b, const float* const* y, float* const* s, c
         b->lam.assign(lambda, lambda + n);
         b->gen.resize(n);
         for (int i = 0; i < n; ++i) b->gen[i] = b->scenes[i]->scratch_gen;
+        b->captured_mode = b->mode;
     }
     NFM_BCK(cudaGraphLaunch(b->exec, b->stream));
     return NFM_OK;

@@ -110,6 +110,35 @@ const void* adj_cheb_tc_kernel_ptr(int LT, bool f16);
 cudaError_t launch_adj_cheb_tc(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, bool f16, size_t smem,
                                cudaStream_t st);
 
+// One launch over the same phase of several scenes (batched SPGM): item i covers the CTAs
+// [cta0_i, cta0_{i+1}) of the launch; the items of a launch are sorted by cta0, the first at 0.
+struct MultiFwdItem {
+    OpDesc op;
+    ChebDesc cd;             // coefficient table padded to the launch's expansion length (zero rows beyond L)
+    FwdArgs a;
+    int n_groups;            // pair groups of the scene (CTA = pair group + n_groups * chunk)
+    int cta0;
+};
+struct MultiRedItem {
+    OpDesc op;
+    ReduceArgs a;
+    int cta0;
+};
+struct MultiAdjItem {
+    OpDesc op;
+    ChebDesc cd;
+    AdjArgs a;
+    int cta0;                // CTA = voxel tile of the scene
+};
+cudaError_t launch_fwd_cheb_multi(int LT, const MultiFwdItem* items, int n_items, int n_ctas, size_t smem,
+                                  cudaStream_t st);
+cudaError_t launch_adj_cheb_multi(int LT, const MultiAdjItem* items, int n_items, int n_ctas, size_t smem,
+                                  cudaStream_t st);
+cudaError_t launch_fwd_reduce_multi(const MultiRedItem* items, int n_items, int n_ctas, cudaStream_t st);
+const void* fwd_cheb_multi_ptr(int LT);
+const void* adj_cheb_multi_ptr(int LT);
+int fwd_reduce_blocks(int n_out);
+
 constexpr int FWD_PC = 8;         // pairs per forward CTA
 constexpr int ADJ_TC_PCHUNK = 8;  // pairs whose tensor-core B operands a CTA holds at once
 constexpr int ADJ_THREADS = 128;  // one 8x4x4 tile: two voxels per thread, pairs split in two halves

@@ -38,12 +38,14 @@ namespace nfm {
 // ---------------------------------------------------------------------------
 // 4-lane groups: 96 registers (5 CTAs of 128 threads per SM); 8-lane groups hold half the voxels
 // per lane and are capped at 72 registers (7 CTAs per SM) so nearly twice the warps stay resident.
+// The CTA body for pair group pg and voxel-tile chunk `chunk` (the single-scene kernel passes blockIdx.x
+// and blockIdx.y; the multi-scene kernel its CTA's position within its scene).
 template <int LT, int G>
-__global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
+__device__ __forceinline__ void fwd_cheb_body(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, int pg,
+                                              int chunk, unsigned char* smem)
 {
     constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
     constexpr int LSS = fwd_coef_stride(LT); // its row stride in shared memory
-    extern __shared__ __align__(16) unsigned char smem[];
     const int ng = blockDim.x / G;           // groups per CTA
     const int PCH = a.VS;                    // pairs per CTA (power of two dividing ng)
     const int TS = ng / PCH;                 // tiles per stage
@@ -64,8 +66,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     const int g = tid / G, ln = tid % G;
     const int pl = g % PCH, slot = g / PCH;
     const unsigned gmask = ((1u << G) - 1u) << ((tid % 32) & ~(G - 1));
-    const int pair_base = blockIdx.x * PCH;
-    const int chunk = blockIdx.y;
+    const int pair_base = pg * PCH;
     const int t_begin = chunk * a.tiles_base + min(chunk, a.tiles_rem);
     const int t_end = t_begin + a.tiles_base + (chunk < a.tiles_rem ? 1 : 0);
     const int n_stages = (t_end - t_begin + TS - 1) / TS;
@@ -310,14 +311,21 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
     }
 }
 
+template <int LT, int G>
+__global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    fwd_cheb_body<LT, G>(op, cd, a, blockIdx.x, blockIdx.y, smem);
+}
+
 // ---------------------------------------------------------------------------
 // adjoint: CTA = one voxel tile, thread = voxel; pairs in chunks of CHEB_ADJ_PCHUNK
 // ---------------------------------------------------------------------------
 template <int LT>
-__global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
+__device__ __forceinline__ void adj_cheb_body(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, int tile,
+                                              unsigned char* smem)
 {
     constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
-    extern __shared__ __align__(16) unsigned char smem[];
     const int K = op.K;
     const int KP = cd.k_pad;
     float* coef = reinterpret_cast<float*>(smem);                          // [KP][LS]
@@ -327,7 +335,6 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     PairTile* pt = reinterpret_cast<PairTile*>(Cs + CHEB_ADJ_PCHUNK * LS);  // [PCH]
     float2* w16 = reinterpret_cast<float2*>(pt + CHEB_ADJ_PCHUNK);          // [PCH] e^{+j 2 pi 16 df D_c/c}
 
-    const int tile = blockIdx.x;
     const int tid = threadIdx.x;
     int tx, ty, tz;
     tile_coords(op.g, tile, tx, ty, tz);
@@ -428,7 +435,6 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
                 const int j = et / LQ, l = 4 * (et - (et / LQ) * LQ);
                 const float2* rj = rp + j * RS;
                 float cr0 = 0.f, ci0 = 0.f, cr1 = 0.f, ci1 = 0.f, cr2 = 0.f, ci2 = 0.f, cr3 = 0.f, ci3 = 0.f;
-#pragma unroll 4
                 for (int k = active ? h : KH; k < KH; k += 2) {
                     const float2 u = rj[k], v = rj[K - 1 - k];
                     const float4 b = *reinterpret_cast<const float4*>(coef + k * LS + l);
@@ -522,6 +528,53 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, Ch
     } else if (in_grid) {
         a.g_out[NFM_IDX(n, op.n_vox, op.err)] = make_float2(gr, gi);
     }
+}
+
+template <int LT>
+__global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    adj_cheb_body<LT>(op, cd, a, blockIdx.x, smem);
+}
+
+// ---------------------------------------------------------------------------
+// the same bodies over several scenes in one launch (batched SPGM): the CTA finds its scene item
+// ---------------------------------------------------------------------------
+template <typename Item>
+__device__ __forceinline__ int multi_item(const Item* __restrict__ items, int n_items)
+{
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].cta0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int LT>
+__global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_multi_kernel(const MultiFwdItem* __restrict__ items,
+                                                                         int n_items)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int i = multi_item(items, n_items);
+    const OpDesc op = items[i].op;
+    const ChebDesc cd = items[i].cd;
+    const FwdArgs a = items[i].a;
+    const int local = (int)blockIdx.x - items[i].cta0, ng = items[i].n_groups;
+    fwd_cheb_body<LT, CHEB_GROUP>(op, cd, a, local % ng, local / ng, smem);
+}
+
+template <int LT>
+__global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_multi_kernel(const MultiAdjItem* __restrict__ items,
+                                                                         int n_items)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int i = multi_item(items, n_items);
+    const OpDesc op = items[i].op;
+    const ChebDesc cd = items[i].cd;
+    const AdjArgs a = items[i].a;
+    adj_cheb_body<LT>(op, cd, a, (int)blockIdx.x - items[i].cta0, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -658,6 +711,50 @@ cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs&
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&op, (void*)&cd, (void*)&a};
     return launch_pdl(fn, dim3(op.g.n_tiles), dim3(CHEB_THREADS), smem, st, args);
+}
+
+const void* fwd_cheb_multi_ptr(int LT)
+{
+    switch (LT) {
+    case 10: return (const void*)fwd_cheb_multi_kernel<10>;
+    case 12: return (const void*)fwd_cheb_multi_kernel<12>;
+    case 14: return (const void*)fwd_cheb_multi_kernel<14>;
+    case 16: return (const void*)fwd_cheb_multi_kernel<16>;
+    case 18: return (const void*)fwd_cheb_multi_kernel<18>;
+    case 20: return (const void*)fwd_cheb_multi_kernel<20>;
+    default: return nullptr;   // the batched launch covers expansion lengths up to 20
+    }
+}
+
+const void* adj_cheb_multi_ptr(int LT)
+{
+    switch (LT) {
+    case 10: return (const void*)adj_cheb_multi_kernel<10>;
+    case 12: return (const void*)adj_cheb_multi_kernel<12>;
+    case 14: return (const void*)adj_cheb_multi_kernel<14>;
+    case 16: return (const void*)adj_cheb_multi_kernel<16>;
+    case 18: return (const void*)adj_cheb_multi_kernel<18>;
+    case 20: return (const void*)adj_cheb_multi_kernel<20>;
+    default: return nullptr;
+    }
+}
+
+cudaError_t launch_fwd_cheb_multi(int LT, const MultiFwdItem* items, int n_items, int n_ctas, size_t smem,
+                                  cudaStream_t st)
+{
+    const void* fn = fwd_cheb_multi_ptr(LT);
+    if (!fn || n_items < 1 || n_ctas < 1) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&items, (void*)&n_items};
+    return launch_pdl(fn, dim3(n_ctas), dim3(CHEB_THREADS), smem, st, args);
+}
+
+cudaError_t launch_adj_cheb_multi(int LT, const MultiAdjItem* items, int n_items, int n_ctas, size_t smem,
+                                  cudaStream_t st)
+{
+    const void* fn = adj_cheb_multi_ptr(LT);
+    if (!fn || n_items < 1 || n_ctas < 1) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&items, (void*)&n_items};
+    return launch_pdl(fn, dim3(n_ctas), dim3(CHEB_THREADS), smem, st, args);
 }
 
 cudaError_t launch_cheb_range(const GridDesc& g, const AntSetup& a, unsigned long long* out, cudaStream_t st)

@@ -292,12 +292,12 @@ cudaError_t launch_fwd_partial(const OpDesc& op, const FwdArgs& a, dim3 grid, in
 // CTA = RED_OUT outputs x 32 chunk lanes; lane y sums chunks y, y+32, ... in that
 // order, then the 32 lane sums are added in lane order.
 constexpr int RED_OUT = 4;
-__global__ void __launch_bounds__(RED_OUT * 32) fwd_reduce_kernel(OpDesc op, ReduceArgs a)
+__device__ __forceinline__ void fwd_reduce_body(const OpDesc& op, const ReduceArgs& a, int block)
 {
     constexpr int UN = 8;                 // loads in flight per thread
     __shared__ float2 red[32][RED_OUT + 1];
     const int ox = threadIdx.x % RED_OUT, cy = threadIdx.x / RED_OUT;
-    const int o = blockIdx.x * RED_OUT + ox;
+    const int o = block * RED_OUT + ox;
     const size_t stride = (size_t)a.n_slots * op.K;
     pdl_wait();
     float2 s = make_float2(0.f, 0.f);
@@ -343,6 +343,35 @@ __global__ void __launch_bounds__(RED_OUT * 32) fwd_reduce_kernel(OpDesc op, Red
     }
     pdl_launch_dependents();
 }
+
+__global__ void __launch_bounds__(RED_OUT * 32) fwd_reduce_kernel(OpDesc op, ReduceArgs a)
+{
+    fwd_reduce_body(op, a, blockIdx.x);
+}
+
+// One launch over the chunk reductions of several scenes: CTA b belongs to the item with the largest
+// cta0 <= b (items sorted by cta0, the first at 0).
+__global__ void __launch_bounds__(RED_OUT * 32) fwd_reduce_multi_kernel(const MultiRedItem* __restrict__ items,
+                                                                        int n_items)
+{
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].cta0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const OpDesc op = items[lo].op;
+    const ReduceArgs a = items[lo].a;
+    fwd_reduce_body(op, a, (int)blockIdx.x - items[lo].cta0);
+}
+
+cudaError_t launch_fwd_reduce_multi(const MultiRedItem* items, int n_items, int n_ctas, cudaStream_t st)
+{
+    void* args[] = {(void*)&items, (void*)&n_items};
+    return launch_pdl((const void*)fwd_reduce_multi_kernel, dim3(n_ctas), dim3(RED_OUT * 32), 0, st, args);
+}
+
+int fwd_reduce_blocks(int n_out) { return (n_out + RED_OUT - 1) / RED_OUT; }
 
 cudaError_t launch_fwd_reduce(const OpDesc& op, const ReduceArgs& a, cudaStream_t st)
 {

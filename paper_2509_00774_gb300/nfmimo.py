@@ -90,6 +90,7 @@ def load_library(path: str | None = None):
         "nfm_batch_spgm_epoch": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(i), ctypes.POINTER(f), ctypes.POINTER(f)]),
         "nfm_batch_last_error": (ctypes.c_char_p, [vp]),
+        "nfm_batch_set_mode": (i, [vp, i]),
         "nfm_profile_report": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
     }
     for name, (res, args) in sig.items():
@@ -486,6 +487,15 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    MODES = {"branches": 0, "fused": 1}
+
+    def set_mode(self, mode):
+        """"branches": a graph branch per scene (default); "fused": one launch per phase and step over all
+        scenes (FP32 expansion operator, L <= 20)."""
+        rc = self._lib.nfm_batch_set_mode(self._h, self.MODES[mode] if isinstance(mode, str) else int(mode))
+        if rc != NFM_OK:
+            raise NfmError(rc, self._lib.nfm_batch_last_error(self._h).decode())
 
     def spgm_epoch(self, ys, ss, perms, pairs_per_batch, etas, lams):
         """ys, ss, perms: per-scene device tensors (complex64, complex64 in/out, int32)."""

@@ -166,3 +166,65 @@ def test_batched48_smallest_scenes_spgm_match_oracle():
             err = nmse(to_host(s_b[i]), s_o[i])
             assert err <= NMSE_TOL, (w.name, e, err)
     batch.close()
+
+
+def test_fused_batch_matches_branch_batch_and_oracle():
+    """The fused batch (one forward, one reduction and one adjoint launch per step index over every scene)
+    against the graph of per-scene branches on uneven scenes (grids 8..16, K 16..37, 4 to 36 pairs, ragged
+    minibatches), and against the oracle's epochs; then three scenes of the 48-scene set."""
+    import torch
+    from paper_2509_00774_gb300.nfmimo import Batch
+    geoms = [_tiny_scene(4, 4, 16, 12, 0), _tiny_scene(6, 4, 37, 8, 1), _tiny_scene(4, 6, 24, 10, 2),
+             W.small_T4R4_K16_16x16x8().geom, _tiny_scene(6, 6, 20, 16, 3)]
+    ctxs_f, ys = _setup(geoms, [10, 20, 30, 40, 50])
+    ctxs_b = [make_ctx(g) for g in geoms]
+    bps = [4, 5, 16, 3, 7]
+    etas = [0.02, 0.03, 0.025, 0.02, 0.01]
+    lams = [1e-3, 2e-3, 1e-3, 5e-4, 1e-3]
+    y_d = [to_dev(y) for y in ys]
+    s_f = [torch.zeros(g.N, dtype=torch.complex64, device="cuda") for g in geoms]
+    s_b = [torch.zeros(g.N, dtype=torch.complex64, device="cuda") for g in geoms]
+    s_o = [np.zeros(g.N, dtype=np.complex128) for g in geoms]
+    perm_d = [torch.zeros(g.P, dtype=torch.int32, device="cuda") for g in geoms]
+    fused, branches = Batch(ctxs_f), Batch(ctxs_b)
+    fused.set_mode("fused")
+    for c in ctxs_b:                                 # the same operator in both
+        c.set_algorithm("chebyshev")
+    for c in ctxs_f:
+        c.set_algorithm("chebyshev")
+    for e in range(3):
+        for i, g in enumerate(geoms):
+            p = I.epoch_permutation(g.P, 5 + i, e)
+            perm_d[i].copy_(torch.from_numpy(p))
+            s_o[i] = Oracle(g).spgm_epoch(ys[i], s_o[i], p, bps[i], etas[i], lams[i])
+        fused.spgm_epoch(y_d, s_f, perm_d, bps, etas, lams)
+        branches.spgm_epoch(y_d, s_b, perm_d, bps, etas, lams)
+        torch.cuda.synchronize()
+        for i in range(len(geoms)):
+            a, b = to_host(s_f[i]), to_host(s_b[i])
+            assert np.linalg.norm(a - b) <= 1e-6 * max(np.linalg.norm(b), 1e-30), (e, i)
+            assert nmse(a, s_o[i]) <= NMSE_TOL, (e, i)
+    fused.close()
+    branches.close()
+    # three scenes of the uneven set, fused against branches over one epoch
+    ws = [W.batched_scene(i) for i in (0, 1, 2)]
+    cf, cb = [make_ctx(w.geom) for w in ws], [make_ctx(w.geom) for w in ws]
+    yy, sf, sb, pp = [], [], [], []
+    for w, c in zip(ws, cf):
+        g = w.geom
+        yy.append(c.forward(to_dev(np.arange(g.P), "int32"), to_dev(w.scene_vector())))
+        sf.append(torch.zeros(g.N, dtype=torch.complex64, device="cuda"))
+        sb.append(torch.zeros(g.N, dtype=torch.complex64, device="cuda"))
+        pp.append(to_dev(I.epoch_permutation(g.P, 9, 0), "int32"))
+    for c in cf + cb:
+        c.set_algorithm("chebyshev")
+    bf, bb = Batch(cf), Batch(cb)
+    bf.set_mode("fused")
+    bf.spgm_epoch(yy, sf, pp, [16] * 3, [0.005] * 3, [1e-3] * 3)
+    bb.spgm_epoch(yy, sb, pp, [16] * 3, [0.005] * 3, [1e-3] * 3)
+    torch.cuda.synchronize()
+    for i in range(3):
+        a, b = to_host(sf[i]), to_host(sb[i])
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), ws[i].name
+    bf.close()
+    bb.close()
