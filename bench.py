@@ -726,7 +726,7 @@ def run_ours(args):
     if world == 1 and not args.no_extras and not args.nonuniform:
         ctx.close()
         line["batched48"] = batched48_leg(args, min(args.steps, 10), 3)
-        line["time_to_oracle_nmse"] = time_to_oracle_nmse()
+        line["time_to_oracle_nmse"] = time_to_oracle_nmse(include_mid=True)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -802,6 +802,8 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         if (!ctx->adj_cheb_attr[LT]) {
             NFM_CK(cudaFuncSetAttribute(adj_cheb_kernel_ptr(LT), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)ctx->smem_optin));
+            // all of the unified L1 / shared memory as shared memory, so that eight CTAs fit per SM
+            NFM_CK(cudaFuncSetAttribute(adj_cheb_kernel_ptr(LT), cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             ctx->adj_cheb_attr[LT] = true;
         }
         AdjArgs a;

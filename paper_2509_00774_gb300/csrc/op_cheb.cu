@@ -41,7 +41,7 @@ namespace nfm {
 // The CTA body for pair group pg and voxel-tile chunk `chunk` (the single-scene kernel passes blockIdx.x
 // and blockIdx.y; the multi-scene kernel its CTA's position within its scene).
 template <int LT, int G>
-__device__ __forceinline__ void fwd_cheb_body(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, int pg,
+__device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd, const FwdArgs a, int pg,
                                               int chunk, unsigned char* smem)
 {
     constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
 // adjoint: CTA = one voxel tile, thread = voxel; pairs in chunks of CHEB_ADJ_PCHUNK
 // ---------------------------------------------------------------------------
 template <int LT>
-__device__ __forceinline__ void adj_cheb_body(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, int tile,
+__device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd, const AdjArgs a, int tile,
                                               unsigned char* smem)
 {
     constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
@@ -531,7 +531,7 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc& op, const ChebDesc& 
 }
 
 template <int LT>
-__global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
+__global__ void __launch_bounds__(CHEB_THREADS, 8) adj_cheb_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     adj_cheb_body<LT>(op, cd, a, blockIdx.x, smem);
