@@ -213,16 +213,18 @@ KERNEL_SOURCES = {"fwd_cheb_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "cheb
                   "adj_tc_kernel": ("nfm_device.cuh", "nfm_kernels.cuh", "tc_ptx.cuh", "op_adjoint_tc.cu")}
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's sources are unchanged."""
+def traffic_for(kernel, workload, pairs_per_batch):
+    """DRAM bytes per launch from the committed ncu summary of this workload and minibatch size, if the
+    kernel's sources are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f).get("kernels", {}).get(kernel, {})
-    if not d or d.get("sources_sha256") != sources_digest(kernel):
+        d = json.load(f).get("workloads", {}).get(workload, {})
+    k = d.get("kernels", {}).get(kernel, {})
+    if not k or d.get("pairs_per_batch") != pairs_per_batch or k.get("sources_sha256") != sources_digest(kernel):
         return None
-    return d.get("dram_bytes_per_launch")
+    return k.get("dram_bytes_per_launch")
 
 
 def sources_digest(kernel):
@@ -689,7 +691,7 @@ def run_ours(args):
                 f"per (row, voxel) pair, {elems} pairs per launch")
     roofline = {"bound": "alu", "kernel": kname, "achieved": dk["tflops"], "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": dk["tflops"] / fp32_peak_tflops,
-                "traffic": traffic_for(kname),
+                "traffic": None if args.nonuniform else traffic_for(kname, w.name, bp),
                 "peak_source": f"FP32 FMA lanes: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} x 2 flops x "
                                f"{sm_mhz:.0f} MHz (sm_max_mhz, {peak_src})",
                 "work": work,
