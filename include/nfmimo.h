@@ -305,6 +305,30 @@ int nfm_prox_step(nfm_ctx* ctx, const float* s, const float* g, float step, floa
 int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, float shrink,
                            long long n, const float* grad_out, float* grad_s, float* grad_g, double* grad_scalars);
 
+/* The same op with the group term of the sparse-group regulariser (Sec. III
+ * allows any convex regulariser with a cheap prox; Eq. 5 with
+ * R = w1 ||s||_1 + (w2/2) ||s||^2 + w3 sum_b ||s_b||_2):
+ *   u = prox_alpha(s - step g),
+ *   out_v = shrink u_v max(0, 1 - alpha_g / ||u_b||_2),
+ * where b is the 2 x 2 x 1 voxel block (ix/2, iy/2, iz) of the context's grid that holds voxel v.
+ * Blocks at an odd grid edge hold fewer voxels.  alpha = eta lambda w1, alpha_g = eta lambda w3,
+ * shrink = 1/(1 + eta lambda w2).  The prox of the whole penalty is the soft threshold, then the
+ * block shrink, then the scaling.
+ * s, g, out: device complex64 [N] in the grid's x-fastest order (out may alias s).
+ * Errors: NFM_ERR_STATE without geometry or with explicit voxel positions (no grid blocks);
+ * NFM_ERR_ARG for alpha < 0, alpha_g < 0, shrink <= 0 or non-finite scalars. */
+int nfm_prox_group_step(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, float alpha_g,
+                        float shrink, float* out);
+
+/* Backward of nfm_prox_group_step for a real loss (complex gradients as real
+ * pairs, as nfm_prox_step_backward).  grad_out [N] is the gradient of the output;
+ * writes grad_s [N] and grad_g [N] (either may be NULL) and, to the device
+ * buffer grad_scalars [4] (FP64), dL/dstep, dL/dalpha, dL/dalpha_g and
+ * dL/dshrink.  All pointers device; errors as nfm_prox_group_step. */
+int nfm_prox_group_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, float alpha_g,
+                                 float shrink, const float* grad_out, float* grad_s, float* grad_g,
+                                 double* grad_scalars);
+
 /* Batched solves of many independent scenes (uneven grids, arrays and K):
  * Sec. IV-A, Eq. 6 with Eq. 5, applied to every scene independently.
  * A batch holds n_scenes contexts (each with its own geometry, set by

@@ -87,6 +87,36 @@ class _ProxStepFn(torch.autograd.Function):
                 (sc[2] if need_shrink else None), None)
 
 
+class _ProxGroupStepFn(torch.autograd.Function):
+    """shrink G_{alpha_g}(prox_alpha(s - step g)) over the grid's 2 x 2 x 1 voxel blocks."""
+
+    @staticmethod
+    def forward(ctx, s, g, step, alpha, alpha_g, shrink, op):
+        s = s.contiguous()
+        g = g.contiguous()
+        st, al, ag, sh = float(step), float(alpha), float(alpha_g), float(shrink)
+        out = torch.empty_like(s)
+        op.prox_group_step(s, g, st, al, ag, out, sh)
+        ctx.save_for_backward(s, g)
+        ctx.op, ctx.st, ctx.al, ctx.ag, ctx.sh = op, st, al, ag, sh
+        ref = next((x for x in (step, alpha, alpha_g, shrink) if torch.is_tensor(x)), None)
+        ctx.scalar_meta = (ref.dtype, ref.device) if ref is not None else (torch.float64, torch.device("cpu"))
+        return out
+
+    @staticmethod
+    def backward(ctx, go):
+        s, g = ctx.saved_tensors
+        need = ctx.needs_input_grad[:6]
+        grad_s = torch.empty_like(s) if need[0] else None
+        grad_g = torch.empty_like(g) if need[1] else None
+        scalars = torch.empty(4, dtype=torch.float64, device=s.device)
+        ctx.op.prox_group_step_backward(s, g, ctx.st, ctx.al, ctx.ag, go.contiguous(), grad_s, grad_g, scalars, ctx.sh)
+        dt, dev = ctx.scalar_meta
+        sc = scalars.to(device=dev, dtype=dt)
+        return (grad_s, grad_g, (sc[0] if need[2] else None), (sc[1] if need[3] else None),
+                (sc[2] if need[4] else None), (sc[3] if need[5] else None), None)
+
+
 def forward_op(op, pairs, s):
     """y = A_B s, differentiable in s (op: nfmimo.Context, pairs: int32 device tensor)."""
     return _ForwardFn.apply(s, op, pairs)
@@ -103,33 +133,39 @@ def adjoint_op(op, pairs, r):
     return _AdjointFn.apply(r, op, pairs)
 
 
-def prox_step(op, s, g, step, alpha, shrink=1.0):
+def prox_step(op, s, g, step, alpha, shrink=1.0, alpha_g=None):
     """shrink * prox_alpha(s - step g), differentiable in s, g, step, alpha and shrink (0-dim tensors or floats);
     shrink = 1/(1 + eta lambda w2) gives the prox of the elastic net w1 ||s||_1 + (w2/2) ||s||^2 with
-    alpha = eta lambda w1."""
-    return _ProxStepFn.apply(s, g, step, alpha, shrink, op)
+    alpha = eta lambda w1.  With alpha_g (= eta lambda w3) the block shrink of the group term
+    w3 sum_b ||s_b||_2 over the grid's 2 x 2 x 1 voxel blocks follows the soft threshold (the prox of the
+    sparse-group penalty), differentiable in alpha_g as well."""
+    if alpha_g is None:
+        return _ProxStepFn.apply(s, g, step, alpha, shrink, op)
+    return _ProxGroupStepFn.apply(s, g, step, alpha, alpha_g, shrink, op)
 
 
 class UnrolledSPGM(torch.nn.Module):
     """n_iter SPGM iterations with learnable per-iteration eta_i and lambda_i (FP64 CPU parameters)."""
 
     def __init__(self, op, n_iter: int, eta: float, lam: float, checkpoint: bool = True, w1: float = 1.0,
-                 w2: float = 0.0):
-        """w1, w2: regulariser w1 ||s||_1 + (w2/2) ||s||^2 (w2 = 0: the paper's l1)."""
+                 w2: float = 0.0, w3: float = 0.0):
+        """w1, w2, w3: regulariser w1 ||s||_1 + (w2/2) ||s||^2 + w3 sum_b ||s_b||_2 over the grid's 2 x 2 x 1
+        voxel blocks (w2 = w3 = 0: the paper's l1)."""
         super().__init__()
         self.op = op
         self.n_iter = int(n_iter)
         self.eta = torch.nn.Parameter(torch.full((self.n_iter,), float(eta), dtype=torch.float64))
         self.lam = torch.nn.Parameter(torch.full((self.n_iter,), float(lam), dtype=torch.float64))
         self.checkpoint = checkpoint
-        self.w1, self.w2 = float(w1), float(w2)
+        self.w1, self.w2, self.w3 = float(w1), float(w2), float(w3)
 
     def _iteration(self, s, y, pairs, eta, lam):
         B = pairs.numel() * self.op.K
         r = residual_op(self.op, pairs, s, y)       # A_B s - y_B fused in the forward kernel
         g = adjoint_op(self.op, pairs, r)
         shrink = 1.0 / (1.0 + eta * lam * self.w2) if self.w2 != 0.0 else 1.0
-        return prox_step(self.op, s, g, eta / B, eta * lam * self.w1, shrink)
+        alpha_g = eta * lam * self.w3 if self.w3 != 0.0 else None
+        return prox_step(self.op, s, g, eta / B, eta * lam * self.w1, shrink, alpha_g)
 
     def forward(self, y, batches, s0=None):
         """y: [M] or [n_scenes, M] complex64 device; batches: n_iter int32 pair lists.

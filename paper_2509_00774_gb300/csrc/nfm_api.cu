@@ -747,7 +747,6 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         a.n_pairs = n_pairs;
         a.r = r;
         a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
-    a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
         a.g_out = g_out;
         a.s = s;
         a.step = step;
@@ -775,6 +774,9 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         if (!ctx->adj_cheb_tc_attr[f16][LT]) {
             NFM_CK(cudaFuncSetAttribute(adj_cheb_tc_kernel_ptr(LT, f16), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)ctx->smem_optin));
+            // all of the unified L1 / shared memory as shared memory, so that two CTAs fit per SM
+            NFM_CK(cudaFuncSetAttribute(adj_cheb_tc_kernel_ptr(LT, f16), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        100));
             ctx->adj_cheb_tc_attr[f16][LT] = true;
         }
         AdjArgs a;
@@ -1643,6 +1645,51 @@ int nfm_prox_step_backward(nfm_ctx* ctx, const float* s, const float* g, float s
     NFM_CK(launch_prox_step_backward((const float2*)s, (const float2*)g, step, alpha, shrink, n, (const float2*)grad_out,
                                      (float2*)grad_s, (float2*)grad_g, (double*)ctx->d_prox_partial, grad_scalars,
                                      ctx->stream));
+    return NFM_OK;
+}
+
+int nfm_prox_group_step(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, float alpha_g,
+                        float shrink, float* out)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    TraceRange trace_("nfm_prox_group_step");
+    DevGuard guard(ctx->device);
+    NFM_TRY(require_geom(ctx));
+    if (ctx->points) return fail(ctx, NFM_ERR_STATE, "the group term of the regulariser needs a regular voxel grid");
+    if (!std::isfinite(step) || !(alpha >= 0) || !std::isfinite(alpha) || !(alpha_g >= 0) || !std::isfinite(alpha_g) ||
+        !(shrink > 0) || !std::isfinite(shrink))
+        return fail(ctx, NFM_ERR_ARG, "bad step/alpha/alpha_g/shrink");
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, g, "g", 8));
+    NFM_TRY(check_ptr(ctx, out, "out", 8));
+    NFM_CK(launch_prox_group_step((const float2*)s, (const float2*)g, step, alpha, alpha_g, shrink, ctx->gd.nx,
+                                  ctx->gd.ny, ctx->gd.nz, (float2*)out, ctx->stream));
+    return NFM_OK;
+}
+
+int nfm_prox_group_step_backward(nfm_ctx* ctx, const float* s, const float* g, float step, float alpha, float alpha_g,
+                                 float shrink, const float* grad_out, float* grad_s, float* grad_g,
+                                 double* grad_scalars)
+{
+    if (!ctx) return NFM_ERR_ARG;
+    TraceRange trace_("nfm_prox_group_step_backward");
+    DevGuard guard(ctx->device);
+    NFM_TRY(require_geom(ctx));
+    if (ctx->points) return fail(ctx, NFM_ERR_STATE, "the group term of the regulariser needs a regular voxel grid");
+    if (!std::isfinite(step) || !(alpha >= 0) || !std::isfinite(alpha) || !(alpha_g >= 0) || !std::isfinite(alpha_g) ||
+        !(shrink > 0) || !std::isfinite(shrink))
+        return fail(ctx, NFM_ERR_ARG, "bad step/alpha/alpha_g/shrink");
+    NFM_TRY(check_ptr(ctx, s, "s", 8));
+    NFM_TRY(check_ptr(ctx, g, "g", 8));
+    NFM_TRY(check_ptr(ctx, grad_out, "grad_out", 8));
+    NFM_TRY(check_ptr(ctx, grad_scalars, "grad_scalars", 8));
+    if (grad_s) NFM_TRY(check_ptr(ctx, grad_s, "grad_s", 8));
+    if (grad_g) NFM_TRY(check_ptr(ctx, grad_g, "grad_g", 8));
+    NFM_TRY(ensure(ctx, &ctx->d_prox_partial, &ctx->prox_partial_cap, 4 * RED_BLOCKS * sizeof(double)));
+    NFM_CK(launch_prox_group_step_backward((const float2*)s, (const float2*)g, step, alpha, alpha_g, shrink,
+                                           ctx->gd.nx, ctx->gd.ny, ctx->gd.nz, (const float2*)grad_out,
+                                           (float2*)grad_s, (float2*)grad_g, (double*)ctx->d_prox_partial,
+                                           grad_scalars, ctx->stream));
     return NFM_OK;
 }
 

@@ -196,6 +196,14 @@ cudaError_t launch_prox_step(const float2* s, const float2* g, float step, float
 cudaError_t launch_prox_step_backward(const float2* s, const float2* g, float step, float alpha, float shrink,
                                       long long n, const float2* go, float2* grad_s, float2* grad_g, double* partial,
                                       double* out3, cudaStream_t st);
+// out = shrink G_alpha_g(prox_alpha(s - step g)) with the block shrink G over the 2 x 2 x 1 voxel blocks of an
+// nx x ny x nz grid, and its backward (out4 = dL/dstep, dL/dalpha, dL/dalpha_g, dL/dshrink in FP64; partial
+// holds 4*RED_BLOCKS doubles)
+cudaError_t launch_prox_group_step(const float2* s, const float2* g, float step, float alpha, float alpha_g,
+                                   float shrink, int nx, int ny, int nz, float2* out, cudaStream_t st);
+cudaError_t launch_prox_group_step_backward(const float2* s, const float2* g, float step, float alpha, float alpha_g,
+                                            float shrink, int nx, int ny, int nz, const float2* go, float2* grad_s,
+                                            float2* grad_g, double* partial, double* out4, cudaStream_t st);
 // out = sum over the 2 x 2 x 1 voxel blocks (ix/2, iy/2, iz) of the block's l2 norm (FP64, fixed tree)
 cudaError_t launch_group_norm_sum(const float2* v, int nx, int ny, int nz, double* partial, double* out,
                                   cudaStream_t st);

@@ -16,7 +16,10 @@
 // Both operands are split x = hi + lo in BF16 (or FP16, r' scaled per pair by a
 // power of two) and D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in FP32 in
 // tensor memory (3 tcgen05.mma of M128 N32 K16 per K step, one thread issues,
-// completion through tcgen05.commit -> mbarrier with a bounded wait).  Warps 0-3
+// completion through tcgen05.commit -> mbarrier with a bounded wait).  A is built
+// and multiplied in two parts of the K range through one buffer, so that the
+// shared memory of two CTAs fits on an SM (the other CTA's per-voxel work covers
+// each part's wait).  Warps 0-3
 // read D back (lane = row) into shared memory; the per-voxel part, sum_l T_l(t)
 // C_l with the Chebyshev recurrence and the fused step/prox epilogue, stays on
 // the CUDA cores exactly as in the FP32 expansion adjoint.
@@ -40,7 +43,6 @@ constexpr int CTC_M = CTC_TILES * CTC_PCH * 2;     // 128 rows (tile, pair, re/i
 constexpr int CTC_N = 32;                          // l, L <= 32
 constexpr int CTC_KSTEP_A = CTC_M * 16 * 2;        // 4096 bytes: one K step of A
 constexpr int CTC_KSTEP_B = CTC_N * 16 * 2;        // 1024 bytes: one K step of B
-constexpr int CTC_MAX_KS = GEN_MAX_K / 16;         // 8 K steps (K <= 128)
 constexpr int CTC_CRS = CTC_N + 2;                 // float2 row stride of the read-back D (16-byte rows,
                                                    // two rows per bank group: 2-way stores, not 16-way)
 
@@ -51,12 +53,18 @@ __host__ __device__ constexpr uint32_t ctc_idesc()
            ((uint32_t)(CTC_M >> 4) << 24);
 }
 
-struct CtcSmem {   // byte offsets of the dynamic shared-memory regions (KS = K steps)
+struct CtcSmem {   // K-step counts and byte offsets of the dynamic shared-memory regions
+    int ks, nh, ksp;   // K steps (zero-padded to whole parts), parts of the K range, K steps per part
     int a, b, pt, p8, craw, rbuf, scale, bar, tslot, total;
-    __host__ __device__ CtcSmem(int KS)
+    __host__ __device__ explicit CtcSmem(int K)
     {
-        a = 0;                                            // [split 2][KS][4096]
-        b = a + 2 * KS * CTC_KSTEP_A;                     // [split 2][KS][1024]
+        const int ks0 = (K + 15) / 16;
+        nh = ks0 >= 2 ? 2 : 1;
+        ksp = (ks0 + nh - 1) / nh;
+        ks = nh * ksp;
+        const int KS = ks;
+        a = 0;                                            // [split 2][ksp][4096]: one part of A
+        b = a + 2 * ksp * CTC_KSTEP_A;                    // [split 2][KS][1024]
         pt = b + 2 * KS * CTC_KSTEP_B;                    // [4 tiles][16 pairs] PairTile
         p8 = pt + CTC_TILES * CTC_PCH * (int)sizeof(PairTile);     // [4][16] float2 e^{+j 2 pi 8 df D_c/c}
         craw = p8 + CTC_TILES * CTC_PCH * (int)sizeof(float2);     // [4][16][CTC_CRS] float2 (D_re, D_im)
@@ -76,8 +84,8 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
     constexpr int LS = (LT + 3) & ~3;        // table row stride of the coefficient table
     extern __shared__ __align__(1024) unsigned char smem[];
     const int K = op.K;
-    const int KS = (K + 15) / 16;
-    const CtcSmem L(KS);
+    const CtcSmem L(K);
+    const int KS = L.ks, KSP = L.ksp, NH = L.nh;
     unsigned char* As = smem + L.a;
     unsigned char* Bs = smem + L.b;
     PairTile* pt = reinterpret_cast<PairTile*>(smem + L.pt);
@@ -126,9 +134,10 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
     tc_fence_after();
     const uint32_t tbase = *tslot;
     bool ok = true, hold = false;
+    uint32_t n_waits = 0;                    // completed commit -> mbarrier phases
     float gr = 0.f, gi = 0.f;
 
-    for (int c0 = 0, chunk = 0; c0 < a.n_pairs; c0 += CTC_PCH, ++chunk) {
+    for (int c0 = 0; c0 < a.n_pairs; c0 += CTC_PCH) {
         const int nc = min(CTC_PCH, a.n_pairs - c0);
         // pair tiles of the chunk (geometry only: no kernel of this library writes it)
         if (tid < CTC_TILES * CTC_PCH) {
@@ -175,15 +184,17 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
             }
             __syncthreads();
         }
-        // A = r' rows (tile, pair, re/im), two k per 32-bit word.  Thread: row tj = 8 (warp % 8) +
-        // lane / 4 and word w = lane % 4 of the k-pairs kp = 4 KS (warp / 8) + 4 m + w, m < KS; a warp
-        // stores 8 rows x 4 words at a time (distinct banks in the K-major layout), and the phasors of
-        // k and k + 1 advance by the exact 8-step phasor from one SFU start each (at most 7 steps).
-        {
+        // A = r' rows (tile, pair, re/im), two k per 32-bit word, one part of the K range (KSP K steps) at a
+        // time.  Thread: row tj = 8 (warp % 8) + lane / 4 and word w4 = lane % 4 of the part's k-pairs
+        // kp = 4 KSP (warp / 8) + 4 m + w4, m < KSP; a warp stores 8 rows x 4 words at a time (distinct banks
+        // in the K-major layout), and the phasors of k and k + 1 advance by the exact 8-step phasor from one
+        // SFU start each.  The part's MMAs are committed and waited for before the next part is written.
+        const bool issue = !(op.hooks & HOOK_TC_SKIP_ISSUE);
+        for (int part = 0; part < NH; ++part) {
             const int w4 = tid & 3, tj = ((warp & 7) << 3) + ((tid >> 2) & 7), h = warp >> 3;
             const int tt = tj / CTC_PCH, j = tj % CTC_PCH;
             const bool valid = j < nc && blockIdx.x * CTC_TILES + tt < op.g.n_tiles;
-            const int kp0 = h * KS * 4 + w4;
+            const int kp0 = part * 8 * KSP + h * 4 * KSP + w4;       // global k-pair index of m = 0
             float2 c0v = make_float2(0.f, 0.f), c1v = c0v, W8 = c0v;
             float sc = 1.0f;
             if (valid) {
@@ -191,11 +202,14 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
                 c0v = tile_step_cis(P, 2 * kp0);
                 c1v = tile_step_cis(P, 2 * kp0 + 1);
                 W8 = p8[tj];
-                sc = F16 ? scale[j] : 1.0f;
+                if (F16) sc = scale[j];
             }
             const float2* rr = rbuf + j * RB;
-            const int row = tj * 2;
-            for (int m = 0; m < KS; ++m) {
+            // byte offsets of the re / im rows' words at m = 0 within the part's A buffer: the word of
+            // local k = 8 q + 2 w4 sits in K step q / 2, 8-column half q % 2 (q = (k_local >> 3))
+            const uint32_t row_re = kmaj_off(2 * tj, 2 * w4), row_im = kmaj_off(2 * tj + 1, 2 * w4);
+            const int q0 = h * KSP;                                   // (2 kp0 - part * 16 KSP) >> 3
+            for (int m = 0; m < KSP; ++m) {
                 const int k = 2 * (kp0 + 4 * m);
                 float2 v0 = make_float2(0.f, 0.f), v1 = v0;
                 if (valid) {
@@ -203,15 +217,19 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
                         float2 r = rr[k];
                         if (op.pulse) r = cmul_conj(r, op.pulse[k]);
                         v0 = cmul(r, c0v);
-                        v0.x *= sc;
-                        v0.y *= sc;
+                        if (F16) {
+                            v0.x *= sc;
+                            v0.y *= sc;
+                        }
                     }
                     if (k + 1 < K) {
                         float2 r = rr[k + 1];
                         if (op.pulse) r = cmul_conj(r, op.pulse[k + 1]);
                         v1 = cmul(r, c1v);
-                        v1.x *= sc;
-                        v1.y *= sc;
+                        if (F16) {
+                            v1.x *= sc;
+                            v1.y *= sc;
+                        }
                     }
                     c0v = cmul(c0v, W8);
                     c1v = cmul(c1v, W8);
@@ -219,40 +237,42 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
                 uint32_t hre, lre, him, lim;
                 split2<F16>(v0.x, v1.x, hre, lre);
                 split2<F16>(v0.y, v1.y, him, lim);
-                const int s = k / 16, kk = k % 16;
-                unsigned char* a0 = As + s * CTC_KSTEP_A;
-                *reinterpret_cast<uint32_t*>(a0 + kmaj_off(row, kk)) = hre;
-                *reinterpret_cast<uint32_t*>(a0 + kmaj_off(row + 1, kk)) = him;
-                *reinterpret_cast<uint32_t*>(a0 + KS * CTC_KSTEP_A + kmaj_off(row, kk)) = lre;
-                *reinterpret_cast<uint32_t*>(a0 + KS * CTC_KSTEP_A + kmaj_off(row + 1, kk)) = lim;
+                const int q = q0 + m;
+                unsigned char* a0 = As + (q >> 1) * CTC_KSTEP_A + (q & 1) * 128;
+                *reinterpret_cast<uint32_t*>(a0 + row_re) = hre;
+                *reinterpret_cast<uint32_t*>(a0 + row_im) = him;
+                *reinterpret_cast<uint32_t*>(a0 + KSP * CTC_KSTEP_A + row_re) = lre;
+                *reinterpret_cast<uint32_t*>(a0 + KSP * CTC_KSTEP_A + row_im) = lim;
             }
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        const bool issue = !(op.hooks & HOOK_TC_SKIP_ISSUE);
-        if (tid == 0 && issue) {
-            tc_fence_after();
-            const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
-            for (int s = 0; s < KS; ++s) {
-                const uint64_t ahi = smem_desc(a_base + s * CTC_KSTEP_A);
-                const uint64_t alo = smem_desc(a_base + (KS + s) * CTC_KSTEP_A);
-                const uint64_t bhi = smem_desc(b_base + s * CTC_KSTEP_B);
-                const uint64_t blo = smem_desc(b_base + (KS + s) * CTC_KSTEP_B);
-                tc_mma(tbase, ahi, bhi, IDESC, s > 0 ? 1u : 0u);
-                tc_mma(tbase, ahi, blo, IDESC, 1u);
-                tc_mma(tbase, alo, bhi, IDESC, 1u);
+            fence_proxy_async();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0 && issue) {
+                tc_fence_after();
+                const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
+                for (int sl = 0; sl < KSP; ++sl) {
+                    const int sg = part * KSP + sl;                    // K step of B
+                    const uint64_t ahi = smem_desc(a_base + sl * CTC_KSTEP_A);
+                    const uint64_t alo = smem_desc(a_base + (KSP + sl) * CTC_KSTEP_A);
+                    const uint64_t bhi = smem_desc(b_base + sg * CTC_KSTEP_B);
+                    const uint64_t blo = smem_desc(b_base + (KS + sg) * CTC_KSTEP_B);
+                    tc_mma(tbase, ahi, bhi, IDESC, (part > 0 || sl > 0) ? 1u : 0u);
+                    tc_mma(tbase, ahi, blo, IDESC, 1u);
+                    tc_mma(tbase, alo, bhi, IDESC, 1u);
+                }
+                tc_commit(bar);
             }
-            tc_commit(bar);
+            // the wait's outcome is made uniform over the CTA: on a timeout no thread reads TMEM, no further
+            // MMA is issued and the iterate (or g) is left unwritten; the MMAs already committed get one more
+            // bounded wait so that none is in flight when TMEM is released
+            if (!__syncthreads_and(mbar_wait(bar, n_waits & 1u, op.wait_ns))) {
+                if (issue) mbar_wait(bar, n_waits & 1u, op.wait_ns);
+                ok = false;
+                break;
+            }
+            ++n_waits;
         }
-        // the wait's outcome is made uniform over the CTA: on a timeout no thread reads TMEM, no further
-        // MMA is issued and the iterate (or g) is left unwritten; the MMAs already committed get one more
-        // bounded wait so that none is in flight when TMEM is released
-        if (!__syncthreads_and(mbar_wait(bar, (uint32_t)(chunk & 1), op.wait_ns))) {
-            if (issue) mbar_wait(bar, (uint32_t)(chunk & 1), op.wait_ns);
-            ok = false;
-            break;
-        }
+        if (!ok) break;
         tc_fence_after();
         if (warp < 4) {                      // lanes 32 warp .. : rows (tile, pair, re/im)
             float d[32];
@@ -326,7 +346,7 @@ __global__ void __launch_bounds__(CTC_THREADS, 2) adj_cheb_tc_kernel(OpDesc op, 
 
 size_t adj_cheb_tc_smem_bytes(int K)
 {
-    return (size_t)CtcSmem((K + 15) / 16).total;
+    return (size_t)CtcSmem(K).total;
 }
 
 template <bool F16>

@@ -78,6 +78,8 @@ def load_library(path: str | None = None):
         "nfm_solve": (i, [vp, vp, vp, vp, i, i, f, f, d, ctypes.POINTER(i), ctypes.POINTER(d)]),
         "nfm_prox_step": (i, [vp, vp, vp, f, f, f, ctypes.c_longlong, vp]),
         "nfm_prox_step_backward": (i, [vp, vp, vp, f, f, f, ctypes.c_longlong, vp, vp, vp, vp]),
+        "nfm_prox_group_step": (i, [vp, vp, vp, f, f, f, f, vp]),
+        "nfm_prox_group_step_backward": (i, [vp, vp, vp, f, f, f, f, vp, vp, vp, vp]),
         "nfm_power_iteration": (i, [vp, i, vp, ctypes.POINTER(d)]),
         "nfm_power_iteration_pairs": (i, [vp, vp, i, i, vp, ctypes.POINTER(d)]),
         "nfm_objective": (i, [vp, vp, vp, d, ctypes.POINTER(d)]),
@@ -401,6 +403,32 @@ class Context:
             raise NfmError(-1, "scalars needs 3 float64 entries")
         self._check(self._lib.nfm_prox_step_backward(
             self._h, self._c(s, "s"), self._c(g, "g"), float(step), float(alpha), float(shrink), s.numel(),
+            self._c(grad_out, "grad_out"), ps, pg, _ptr(scalars, torch.float64, "scalars", self.device)))
+
+    def prox_group_step(self, s, g, step, alpha, alpha_g, out, shrink=1.0):
+        """out = shrink G_{alpha_g}(prox_alpha(s - step g)), G the block shrink over the grid's 2 x 2 x 1 voxel
+        blocks (the prox of the sparse-group regulariser, Eq. 5); s, g, out: [N]; out may be s."""
+        self._need_geom()
+        self._sizes(s=(s, self.N), g=(g, self.N), out=(out, self.N))
+        self._check(self._lib.nfm_prox_group_step(self._h, self._c(s, "s"), self._c(g, "g"), float(step),
+                                                  float(alpha), float(alpha_g), float(shrink), self._c(out, "out")))
+        return out
+
+    def prox_group_step_backward(self, s, g, step, alpha, alpha_g, grad_out, grad_s, grad_g, scalars, shrink=1.0):
+        """Backward of prox_group_step; scalars: float64 device tensor [4] <- (dL/dstep, dL/dalpha,
+        dL/dalpha_g, dL/dshrink)."""
+        import torch
+        self._need_geom()
+        self._sizes(s=(s, self.N), g=(g, self.N), grad_out=(grad_out, self.N))
+        for name, t in (("grad_s", grad_s), ("grad_g", grad_g)):
+            if t is not None:
+                self._sizes(**{name: (t, self.N)})
+        ps = self._c(grad_s, "grad_s") if grad_s is not None else None
+        pg = self._c(grad_g, "grad_g") if grad_g is not None else None
+        if scalars.numel() < 4:
+            raise NfmError(-1, "scalars needs 4 float64 entries")
+        self._check(self._lib.nfm_prox_group_step_backward(
+            self._h, self._c(s, "s"), self._c(g, "g"), float(step), float(alpha), float(alpha_g), float(shrink),
             self._c(grad_out, "grad_out"), ps, pg, _ptr(scalars, torch.float64, "scalars", self.device)))
 
     def power_iteration(self, v0, iters: int = 50) -> float:

@@ -290,3 +290,94 @@ def test_prox_step_forward_matches_oracle_prox(n, offset):
     want = prox_l1(z, 0.8)
     got = out.cpu().numpy().astype(np.complex128)
     assert np.max(np.abs(got - want)) <= 1e-5 * max(1.0, np.max(np.abs(want)))
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 8), (15, 13, 5)])
+def test_group_prox_step_matches_oracle_and_fd(dims):
+    """out = shrink G_{alpha_g}(prox_alpha(s - step g)) over the 2 x 2 x 1 voxel blocks (the prox of the
+    sparse-group penalty): value against the oracle's prox, and grad_s, grad_g, dL/dstep, dL/dalpha,
+    dL/dalpha_g and dL/dshrink against FP64 central differences of the oracle's prox (voxels near
+    |z| = alpha and blocks near ||u_b|| = alpha_g excluded).  The 15 x 13 x 5 grid has edge blocks of
+    one and two voxels."""
+    import torch
+    from oracle import group_norms, prox_group, voxel_groups
+    from paper_2509_00774_gb300.autograd import prox_step
+    w = W.small_T4R4_K16_16x16x8()
+    g0 = w.geom.grid
+    grid = I.Grid(g0.x0, g0.y0, g0.z0, g0.dx, g0.dy, g0.dz, *dims)
+    geom = I.Geometry(w.geom.tx, w.geom.rx, w.geom.freq, grid)
+    ctx = make_ctx(geom)
+    n = geom.N
+    s = _c64(I.complex_gaussian(n, 61))
+    g = _c64(I.complex_gaussian(n, 62))
+    c = _c64(I.complex_gaussian(n, 63))
+    step, alpha, alpha_g, shrink = 0.3, 0.4, 0.9, 0.8
+    groups = voxel_groups(grid)
+
+    def prox(s_, g_, st, al, ag, sh):
+        return sh * prox_group(prox_l1(s_ - st * g_, al), groups, ag)
+
+    z = s - step * g
+    u = prox_l1(z, alpha)
+    nb = group_norms(u, groups)
+    keep = (np.abs(np.abs(z) - alpha) > 1e-2) & (np.abs(nb[groups] - alpha_g) > 1e-2)
+    want = prox(s, g, step, alpha, alpha_g, shrink)
+    zero_blocks = int(np.sum(nb <= alpha_g))
+    assert 0 < zero_blocks < nb.size                       # both branches of the block shrink are taken
+    pars = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in (step, alpha, alpha_g, shrink)]
+    s_d = to_dev(s).requires_grad_(True)
+    g_d = to_dev(g).requires_grad_(True)
+    out = prox_step(ctx, s_d, g_d, pars[0], pars[1], pars[3], alpha_g=pars[2])
+    assert np.max(np.abs(to_host(out) - want)) <= 1e-5 * np.max(np.abs(want))
+    # keep whole blocks: a voxel's gradient depends on its block's other voxels
+    keep_blocks = np.bincount(groups, weights=(~keep).astype(float), minlength=nb.size) == 0
+    keep = keep_blocks[groups]
+    mask = torch.from_numpy(keep).cuda()
+    ((torch.conj(to_dev(c)) * out).real * mask).sum().backward()
+
+    def loss(s_=s, g_=g, st=step, al=alpha, ag=alpha_g, sh=shrink):
+        return float(np.sum((np.conj(c) * prox(s_, g_, st, al, ag, sh)).real[keep]))
+
+    h = 1e-6
+    for i, name in enumerate(("st", "al", "ag", "sh")):
+        base = {"st": step, "al": alpha, "ag": alpha_g, "sh": shrink}
+        up, dn = dict(base), dict(base)
+        up[name] += h
+        dn[name] -= h
+        fd = (loss(**up) - loss(**dn)) / (2 * h)
+        assert abs(float(pars[i].grad) - fd) <= 1e-4 * abs(fd) + 1e-3, (name, float(pars[i].grad), fd)
+    gs, gg = to_host(s_d.grad), to_host(g_d.grad)
+    for j in np.flatnonzero(keep)[:: max(1, keep.sum() // 25)]:
+        e = np.zeros(n, dtype=np.complex128)
+        e[j] = h
+        fd_s = (loss(s_=s + e) - loss(s_=s - e)) / (2 * h) + 1j * (loss(s_=s + 1j * e) - loss(s_=s - 1j * e)) / (2 * h)
+        fd_g = (loss(g_=g + e) - loss(g_=g - e)) / (2 * h) + 1j * (loss(g_=g + 1j * e) - loss(g_=g - 1j * e)) / (2 * h)
+        assert abs(gs[j] - fd_s) <= 1e-4 * max(1.0, abs(fd_s)), (j, gs[j], fd_s)
+        assert abs(gg[j] - fd_g) <= 1e-4 * max(1.0, abs(fd_g)), (j, gg[j], fd_g)
+    print(f"[parity] group prox step {dims}: {zero_blocks} of {nb.size} blocks zero")
+
+
+def test_unrolled_spgm_with_group_term_matches_oracle_iterations():
+    """Unrolled SPGM with R = w1 ||s||_1 + w3 sum_b ||s_b||_2: the iterate after 6 iterations against the
+    oracle's SPGM steps with the same regulariser, and finite eta / lambda gradients."""
+    import torch
+    from paper_2509_00774_gb300.autograd import UnrolledSPGM
+    w = W.small_T4R4_K16_16x16x8()
+    w1, w3 = 1.0, 0.7
+    o = Oracle(w.geom, w1=w1, w3=w3)
+    y = _c64(I.add_noise(o.forward_sparse(w.scene_vector()), I.complex_gaussian(o.M, 1), 30.0))
+    L = o.power_iteration(I.complex_gaussian(o.N, 3), 50)
+    eta, lam = 0.25 / L, float(np.float32(0.3 * o.lambda_max(y)))    # 64 of the 512 blocks vanish
+    batches = [I.epoch_permutation(o.P, 7, 0)[4 * i:4 * i + 4] for i in range(4)]
+    ctx = make_ctx(w.geom)
+    model = UnrolledSPGM(ctx, 6, eta, lam, w1=w1, w3=w3)
+    out = model(to_dev(y), [to_dev(b, "int32") for b in batches])
+    s = np.zeros(o.N, dtype=np.complex128)
+    for i in range(6):
+        s = o.spgm_step(y, s, batches[i % 4], eta, lam)
+    from oracle import nmse
+    assert nmse(to_host(out), s) <= 1e-4
+    from oracle import group_norms, voxel_groups
+    assert np.sum(group_norms(s, voxel_groups(w.geom.grid)) == 0) > 0     # the group shrink zeroes blocks
+    (out.abs() ** 2).sum().backward()
+    assert torch.isfinite(model.eta.grad).all() and torch.isfinite(model.lam.grad).all()

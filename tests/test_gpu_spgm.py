@@ -220,6 +220,34 @@ def test_spgm_mid_three_epochs():
     assert np.count_nonzero(s_orc) > 0
 
 
+def test_power_iteration_mid_matches_oracle_rayleigh_quotient():
+    """Mid workload: L from nfm_power_iteration (50 iterations) against the oracle's FP64 Rayleigh
+    quotient ||A v||^2 / (M ||v||^2) at the iterate v_50 of the same iteration run through the GPU
+    forward and adjoint (one full oracle application instead of 50), and the Rayleigh quotient at
+    v_50 bounds the one at v_0 from above (the iteration climbs towards the top eigenvalue)."""
+    import torch
+    w = W.mid_T16R16_K64_64x64x32()
+    o = Oracle(w.geom)
+    ctx = make_ctx(w.geom)
+    v0 = _c64(I.complex_gaussian(o.N, w.seeds["power"]))
+    L_gpu = ctx.power_iteration(to_dev(v0), 50)
+    pairs = to_dev(np.arange(o.P), "int32")
+    v = to_dev(v0)
+    for _ in range(50):
+        u = ctx.adjoint(pairs, ctx.forward(pairs, v))
+        v = u / torch.linalg.vector_norm(u)
+    v50 = to_host(v)
+
+    def rayleigh(x):
+        ax = o.forward(x)
+        return float(np.vdot(ax, ax).real) / (o.M * float(np.vdot(x, x).real))
+
+    rq50 = rayleigh(v50)
+    print(f"[parity] mid power iteration: L_gpu {L_gpu:.6f}, oracle Rayleigh quotient at v_50 {rq50:.6f}")
+    assert abs(L_gpu - rq50) <= 1e-4 * rq50, (L_gpu, rq50)
+    assert rq50 >= rayleigh(v0)
+
+
 # ---------------------------------------------------------------------------
 # errors
 # ---------------------------------------------------------------------------
