@@ -769,7 +769,7 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         // expansion adjoint with its coefficient stage on the tensor cores
         const bool f16 = ctx->precision == NFM_TC_FP16X3;
         const int LT = ctx->cheb_L;
-        const size_t smem = adj_cheb_tc_smem_bytes(ctx->K);
+        const size_t smem = adj_cheb_tc_smem_bytes(ctx->K, LT);
         if (smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "tensor-core expansion needs %zu B shared memory", smem);
         if (!ctx->adj_cheb_tc_attr[f16][LT]) {
             NFM_CK(cudaFuncSetAttribute(adj_cheb_tc_kernel_ptr(LT, f16), cudaFuncAttributeMaxDynamicSharedMemorySize,

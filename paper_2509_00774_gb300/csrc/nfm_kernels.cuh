@@ -105,7 +105,7 @@ const void* fwd_cheb_tc_kernel_ptr(int LT, bool f16);
 cudaError_t launch_fwd_cheb_tc(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, bool f16,
                                size_t smem, cudaStream_t st);
 // tensor-core (tcgen05) coefficient stage of the expansion adjoint (op_cheb_tc.cu), K <= 128, L <= 32
-size_t adj_cheb_tc_smem_bytes(int K);
+size_t adj_cheb_tc_smem_bytes(int K, int L);
 const void* adj_cheb_tc_kernel_ptr(int LT, bool f16);
 cudaError_t launch_adj_cheb_tc(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, bool f16, size_t smem,
                                cudaStream_t st);

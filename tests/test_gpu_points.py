@@ -97,6 +97,10 @@ def test_points_reject_grid_only_paths():
         ctx.spgm_step(to_dev(np.zeros(geom.M)), s, pairs, 1e-3, 1e-3)
     assert ei.value.code == -1
     ctx.set_group_weight(0.0)
+    out = to_dev(np.zeros(geom.N))
+    with pytest.raises(NfmError) as ei:        # the stand-alone group prox needs grid blocks too
+        ctx.prox_group_step(s, s, 0.1, 0.1, 0.1, out)
+    assert ei.value.code == -4
     ctx.forward(pairs, s, y)                   # usable again
     ctx.synchronize()
     ctx.close()
