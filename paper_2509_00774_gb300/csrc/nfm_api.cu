@@ -501,6 +501,8 @@ int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int group, int pch, doubl
     if (!fn) return fail(ctx, NFM_ERR_ARG, "no expansion forward for L = %d, group %d", LT, group);
     if (!ctx->fwd_cheb_attr[LT][group == 8]) {
         NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin));
+        // all of the unified L1 / shared memory as shared memory: the CTA count per SM is set by shared memory
+        NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
         ctx->fwd_cheb_attr[LT][group == 8] = true;
     }
     sh->n_groups = (n_pairs + pch - 1) / pch;

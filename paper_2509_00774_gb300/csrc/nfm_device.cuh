@@ -38,6 +38,13 @@ struct __align__(16) AntTile {
     float pad0, pad1;
 };
 
+// The leading 32 bytes of an AntTile: what the expansion operator reads (no K2 step).
+struct __align__(16) AntHead {
+    float vx, vy, vz, dc;
+    float dc2, b, s_hi, s_lo;
+};
+static_assert(sizeof(AntHead) == 32, "AntHead is the first two 16-byte words of an AntTile");
+
 // Per (pair, tile) constants: the TX and RX AntTile folded together.
 struct __align__(16) PairTile {
     float vTx, vTy, vTz, dcT, dcT2;
@@ -177,6 +184,23 @@ __device__ __forceinline__ PairTile fold_pair_tile(const AntTile& t, const AntTi
     two_sum(t.s2_hi, r.s2_hi, h, e);
     p.S2_hi = frac_turns(h);
     p.S2_lo = e + (t.s2_lo + r.s2_lo);
+    return p;
+}
+
+// The same from the leading words only (S2 left zero; the expansion operator does not use it).
+__device__ __forceinline__ PairTile fold_pair_head(const AntHead& t, const AntHead& r)
+{
+    PairTile p;
+    p.pad = 0.f;
+    p.vTx = t.vx; p.vTy = t.vy; p.vTz = t.vz; p.dcT = t.dc; p.dcT2 = t.dc2;
+    p.vRx = r.vx; p.vRy = r.vy; p.vRz = r.vz; p.dcR = r.dc; p.dcR2 = r.dc2;
+    p.B = frac_turns(t.b + r.b);
+    float h, e;
+    two_sum(t.s_hi, r.s_hi, h, e);
+    p.S_hi = frac_turns(h);
+    p.S_lo = e + (t.s_lo + r.s_lo);
+    p.S2_hi = 0.f;
+    p.S2_lo = 0.f;
     return p;
 }
 

@@ -88,6 +88,9 @@ __host__ __device__ constexpr int fwd_coef_stride(int LT)
 {
     return ((LT + 3) & ~3) % 16 == 0 ? ((LT + 3) & ~3) + 4 : ((LT + 3) & ~3);
 }
+// Rows of the coefficient table the forward holds in shared memory: k <= K/2 (k_pad = K rounded up to 4), the
+// rows the mirror-folded expansion reads (k < K/2 and, for odd K, the centre row).
+__host__ __device__ constexpr int fwd_coef_rows(int k_pad) { return k_pad / 2 + 1; }
 // points: the geometry has explicit voxel positions (per-stage voxel offsets are staged too)
 size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, bool points = false);
 size_t adj_cheb_smem_bytes(int LT, int k_pad);

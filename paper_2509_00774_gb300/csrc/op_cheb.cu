@@ -52,11 +52,12 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     const int K = op.K;
     const int KP = cd.k_pad;                 // table rows (multiple of 4, zero rows beyond K)
     const int AS = KP + 4;                   // accumulator row stride (float2), staggers the banks
-    float* coef = reinterpret_cast<float*>(smem);                            // [KP][LSS]
-    float2* acc = reinterpret_cast<float2*>(coef + KP * LSS);                // [ng][AS]
+    const int CR = fwd_coef_rows(KP);        // table rows held: k <= K/2 (the rest follow by the mirror fold)
+    float* coef = reinterpret_cast<float*>(smem);                            // [CR][LSS]
+    float2* acc = reinterpret_cast<float2*>(coef + CR * LSS);                // [ng][AS]
     VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + ng * AS);       // [TILE_V]
     float2* s_st = reinterpret_cast<float2*>(voff + TILE_V);                 // [2][TS][TILE_V]
-    AntTile* ant_st = reinterpret_cast<AntTile*>(s_st + 2 * TS * TILE_V);    // [2][ng][2]
+    AntHead* ant_st = reinterpret_cast<AntHead*>(s_st + 2 * TS * TILE_V);    // [2][ng][2]
     int* pair_s = reinterpret_cast<int*>(ant_st + 2 * ng * 2);               // [PCH] pair or -1
     // explicit voxel positions: the stage's voxel offsets [2][TS][TILE_V] (16-byte aligned after pair_s)
     VoxelOffset* vox_st = reinterpret_cast<VoxelOffset*>(pair_s + ((PCH + 3) & ~3));
@@ -74,7 +75,7 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     // Constants and the pair list: no kernel of this library writes them, so they are read
     // before the wait on the previous kernel (which may still be running its tail).  (Plain loads:
     // asynchronous copies of the table measured slower here.)
-    for (int i = tid; i < KP * LS / 4; i += nt)
+    for (int i = tid; i < CR * LS / 4; i += nt)
         reinterpret_cast<float4*>(coef)[(i / (LS / 4)) * (LSS / 4) + i % (LS / 4)] =
             reinterpret_cast<const float4*>(cd.coef)[i];
     if (!op.g.pts)
@@ -91,18 +92,18 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     }
     __syncthreads();
 
-    auto load_geom = [&](int q) {                 // the two antenna-tile rows of every group
+    auto load_geom = [&](int q) {                 // the leading 32 B of the two antenna-tile rows of every group
         const int buf = q & 1;
-        for (int i = tid; i < ng * 6; i += nt) {  // 2 rows x 48 B per group
-            const int gi = i / 6, part = i % 6;
+        for (int i = tid; i < ng * 4; i += nt) {
+            const int gi = i / 4, part = i % 4;
             const int tile = t_begin + q * TS + gi / PCH;
             const int pair = pair_s[gi % PCH];
             if (tile < t_end && pair >= 0) {
                 const AntTile *at, *ar;
                 pair_rows(op, pair, tile, at, ar);
-                AntTile* dst = ant_st + (buf * ng + gi) * 2 + (part < 3 ? 0 : 1);
-                cp_async_16(reinterpret_cast<float4*>(dst) + part % 3,
-                            reinterpret_cast<const float4*>(part < 3 ? at : ar) + part % 3);
+                AntHead* dst = ant_st + (buf * ng + gi) * 2 + (part < 2 ? 0 : 1);
+                cp_async_16(reinterpret_cast<float4*>(dst) + part % 2,
+                            reinterpret_cast<const float4*>(part < 2 ? at : ar) + part % 2);
             }
         }
     };
@@ -175,8 +176,8 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
         const int buf = q & 1;
         const int tile = t_begin + q * TS + slot;
         if (tile < t_end && pair_s[pl] >= 0) {      // uniform over the group's lanes
-            const AntTile* ap = ant_st + (buf * ng + g) * 2;
-            const PairTile P = fold_pair_tile(ap[0], ap[1]);
+            const AntHead* ap = ant_st + (buf * ng + g) * 2;
+            const PairTile P = fold_pair_head(ap[0], ap[1]);
             const float2* sb = s_st + (buf * TS + slot) * TILE_V;
             const VoxelOffset* vsrc = op.g.pts ? vox_st + (buf * TS + slot) * TILE_V : voff;
             float mr[LT], mi[LT];
@@ -635,9 +636,10 @@ size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, b
 {
     const int ng = threads / group;
     const int TS = ng / pch;
-    return (size_t)k_pad * fwd_coef_stride(LT) * sizeof(float) + (size_t)ng * (k_pad + 4) * sizeof(float2) +
-           TILE_V * sizeof(VoxelOffset) + (size_t)2 * TS * TILE_V * sizeof(float2) +
-           (size_t)2 * ng * 2 * sizeof(AntTile) + (size_t)((pch + 3) & ~3) * sizeof(int) +
+    return (size_t)fwd_coef_rows(k_pad) * fwd_coef_stride(LT) * sizeof(float) +
+           (size_t)ng * (k_pad + 4) * sizeof(float2) + TILE_V * sizeof(VoxelOffset) +
+           (size_t)2 * TS * TILE_V * sizeof(float2) + (size_t)2 * ng * 2 * sizeof(AntHead) +
+           (size_t)((pch + 3) & ~3) * sizeof(int) +
            (points ? (size_t)2 * TS * TILE_V * sizeof(VoxelOffset) : 0);
 }
 
