@@ -368,6 +368,8 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
     const size_t n = !in_grid ? 0 : op.g.pts ? np : ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
     const float2 s_old = (a.s && in_grid) ? a.s[NFM_IDX(n, op.n_vox, op.err)] : make_float2(0.f, 0.f);
 
+    // rows of r start on 16-byte boundaries in shared memory (RS even) and, for even K, in r
+    const bool r_vec = !(K & 1) && !(reinterpret_cast<uintptr_t>(a.r) & 15);
     for (int c0 = 0; c0 < a.n_pairs; c0 += CHEB_ADJ_PCHUNK) {
         const int nc = min(CHEB_ADJ_PCHUNK, a.n_pairs - c0);
         if (c0 > 0) {
@@ -381,9 +383,14 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
         // all its copies before it waits, so the loads overlap (one L2 round trip), and later transforms
         // the same elements.
         const int k0 = tid % 16;
-        for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16) {
-            for (int k = k0; k < K; k += 16)
-                cp_async_8(rp + j * RS + k, a.r + NFM_IDX((long long)(c0 + j) * K + k, a.r_elems, op.err), true);
+        if (r_vec) {                         // 16-byte copies of (r_k, r_k+1), k even (K even, r 16-byte aligned)
+            for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16)
+                for (int k = 2 * k0; k < K; k += 32)
+                    cp_async_16_ca(rp + j * RS + k, a.r + NFM_IDX((long long)(c0 + j) * K + k, a.r_elems, op.err));
+        } else {
+            for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16)
+                for (int k = k0; k < K; k += 16)
+                    cp_async_8(rp + j * RS + k, a.r + NFM_IDX((long long)(c0 + j) * K + k, a.r_elems, op.err), true);
         }
         cp_async_commit();
         cp_async_wait_all();
