@@ -81,6 +81,8 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     if (!op.g.pts)
         for (int v = tid; v < TILE_V; v += nt)
             voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
+    for (int i = tid; i < ng * AS / 2; i += nt)   // the per-slot spectra start at zero (AS even)
+        reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid < PCH) {
         const int sp = pair_base + tid;
         int pair = sp < a.n_pairs ? a.pairs[sp] : -1;
@@ -226,12 +228,10 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
             float2 cu = tile_step_cis(P, ln), cdn = tile_step_cis(P, K - 1 - ln);
             const float2 W = tile_step_cis_exact(P, G);
             const float2 Wc = make_float2(W.x, -W.y);
-            auto accumulate = [&](int k, float2 c, float sr, float si) {   // y_k (+)= P_k S_k, P_k = (c.x, -c.y)
-                float2 av = make_float2(fmaf(c.x, sr, c.y * si), fmaf(c.x, si, -c.y * sr));
-                if (q > 0) {                                 // the first stage writes, later stages add
-                    av.x += accg[k].x;
-                    av.y += accg[k].y;
-                }
+            auto accumulate = [&](int k, float2 c, float sr, float si) {   // y_k += P_k S_k, P_k = (c.x, -c.y)
+                float2 av = accg[k];
+                av.x = fmaf(c.x, sr, fmaf(c.y, si, av.x));
+                av.y = fmaf(c.x, si, fmaf(-c.y, sr, av.y));
                 accg[k] = av;
             };
             for (int k = ln; k < KH; k += G) {
@@ -281,9 +281,9 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     }
     pdl_launch_dependents();
 
-    // sum the live stage slots of each pair in slot order and write the chunk partial (every pair
-    // and tile of the chunk wrote its row in the first stage); the threads split as (nt / K) pairs
-    // x K frequencies when K <= nt
+    // sum the live stage slots of each pair in slot order and write the chunk partial (the rows start
+    // at zero and every live slot added its tiles); the threads split as (nt / K) pairs x K
+    // frequencies when K <= nt
     const int live_slots = min(TS, t_end - t_begin);
     const bool kfit = K <= nt;
     const int p_step = kfit ? nt / K : 1;
