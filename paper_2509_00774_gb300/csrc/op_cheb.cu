@@ -495,21 +495,17 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
         };
         float2 w;
         float t;
-        stage_pair(0, w, t);
-        for (int j = 0; j < nc; ++j) {
-            float2 wn;
-            float tn;
-            stage_pair(min(j + 1, nc - 1), wn, tn);
-            const float t2 = t + t;
-            // the pair's coefficients are read into registers first, so the recurrence below
-            // does not wait on shared-memory latency term by term
+        // pair j's coefficient sum and its contribution to g (the coefficients are read into registers
+        // first, so the recurrence does not wait on shared-memory latency term by term)
+        auto add_pair = [&](int j, float2 wj, float tj) {
+            const float t2 = tj + tj;
             const float4* C = reinterpret_cast<const float4*>(Cs + j * LS);
             float4 cr[LT / 2];
 #pragma unroll
             for (int i = 0; i < LT / 2; ++i) cr[i] = C[i];
             float4 q = cr[0];
-            float ar = fmaf(t, q.z, q.x), ai = fmaf(t, q.w, q.y);
-            float Tp = 1.f, Tc = t;
+            float ar = fmaf(tj, q.z, q.x), ai = fmaf(tj, q.w, q.y);
+            float Tp = 1.f, Tc = tj;
 #pragma unroll
             for (int l = 2; l < LT; l += 2) {
                 q = cr[l / 2];
@@ -522,11 +518,19 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
                 Tp = Ta;
                 Tc = Tb;
             }
-            gr = fmaf(w.x, ar, fmaf(-w.y, ai, gr));
-            gi = fmaf(w.x, ai, fmaf(w.y, ar, gi));
+            gr = fmaf(wj.x, ar, fmaf(-wj.y, ai, gr));
+            gi = fmaf(wj.x, ai, fmaf(wj.y, ar, gi));
+        };
+        stage_pair(0, w, t);
+        for (int j = 0; j + 1 < nc; ++j) {   // the last pair is peeled: nothing left to stage
+            float2 wn;
+            float tn;
+            stage_pair(j + 1, wn, tn);
+            add_pair(j, w, t);
             w = wn;
             t = tn;
         }
+        add_pair(nc - 1, w, t);
     }
     pdl_launch_dependents();
 
