@@ -379,9 +379,8 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
                 w16[tid] = tile_step_cis_exact(pt[tid], 16);
             }
         }
-        // The chunk's residual rows into rp, 16 threads per pair taking k = k0 + 16 m: every thread issues
-        // all its copies before it waits, so the loads overlap (one L2 round trip), and later transforms
-        // the same elements.
+        // The chunk's residual rows into rp, 16 threads per pair: every thread issues all its copies before
+        // it waits, so the loads overlap (one L2 round trip).
         const int k0 = tid % 16;
         if (r_vec) {                         // 16-byte copies of (r_k, r_k+1), k even (K even, r 16-byte aligned)
             for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16)
