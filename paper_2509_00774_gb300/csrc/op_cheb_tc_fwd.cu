@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(FTC_THREADS, 2) fwd_cheb_tc_kernel(OpDesc op, 
     }
     for (int v = tid; v < TILE_V; v += FTC_THREADS)
         voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
+    for (int i = tid; i < FTC_NG * AS; i += FTC_THREADS)   // the accumulator rows start at zero
+        acc[i] = make_float2(0.f, 0.f);
     if (tid < PCH) {
         const int sp = pair_base + tid;
         int pair = sp < a.n_pairs ? a.pairs[sp] : -1;
@@ -341,19 +343,18 @@ __global__ void __launch_bounds__(FTC_THREADS, 2) fwd_cheb_tc_kernel(OpDesc op, 
 #pragma unroll
             for (int i = 0; i < 4; ++i) o[i] = __shfl_xor_sync(0xffffffffu, c ? d[i] : d[4 + i], 1);
             const int k0 = half * NH + cb + 4 * c;
-            float2 ph = slot_cis(so.S_hi, so.S_lo, k0);
+            float2 ph = slot_cis(so.S_hi, so.S_lo, k0);   // scaled by the item's 1/scale (w has unit modulus)
+            ph.x *= so.inv_scale;
+            ph.y *= so.inv_scale;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float sr = (c ? o[i] : d[i]) * so.inv_scale;
-                const float si = (c ? d[4 + i] : o[i]) * so.inv_scale;
+                const float sr = c ? o[i] : d[i];
+                const float si = c ? d[4 + i] : o[i];
                 const int k = k0 + i;
-                if (k < K) {                 // y_k += P_k S_k, P_k = (ph.x, -ph.y)
-                    float2 y = make_float2(fmaf(ph.x, sr, ph.y * si), fmaf(ph.x, si, -ph.y * sr));
-                    if (qe > 0) {            // the first stage writes, later stages add
-                        const float2 prev = accg[k];
-                        y.x += prev.x;
-                        y.y += prev.y;
-                    }
+                if (k < K) {                 // y_k += P_k S_k, P_k = (ph.x, -ph.y); the rows start at zero
+                    float2 y = accg[k];
+                    y.x = fmaf(ph.x, sr, fmaf(ph.y, si, y.x));
+                    y.y = fmaf(ph.x, si, fmaf(-ph.y, sr, y.y));
                     accg[k] = y;
                 }
                 ph = cmul(ph, w);
@@ -412,8 +413,7 @@ __global__ void __launch_bounds__(FTC_THREADS, 2) fwd_cheb_tc_kernel(OpDesc op, 
         tmem_dealloc(tbase, (uint32_t)ftc_tmem_cols(N));
     }
     if (!ok) return;
-    // sum the TS slots of each pair in slot order (every slot row was written by the first stage) and
-    // write the chunk partial
+    // sum the TS slots of each pair in slot order (the rows start at zero) and write the chunk partial
     for (int e = tid; e < PCH * K; e += FTC_THREADS) {
         const int p = e / K, k = e - (e / K) * K;
         const int sp = pair_base + p;
