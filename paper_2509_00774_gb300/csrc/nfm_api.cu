@@ -131,6 +131,14 @@ struct nfm_ctx {
     bool adj_cheb_attr[CHEB_MAX_L + 1] = {};
     bool adj_cheb_tc_attr[2][CHEB_MAX_L + 1] = {};
     bool fwd_cheb_tc_attr[2][CHEB_MAX_L + 1] = {};
+    // the FP32 expansion adjoint's blocks of two tiles along z (regular grids): their grid descriptor,
+    // antenna-block table and expansion table (cheb_L2 = 0: not set up, the adjoint runs over the tiles)
+    GridDesc gd2{};
+    AntTile* d_ant2 = nullptr;
+    float* d_cheb2 = nullptr;
+    int cheb_L2 = 0;
+    float cheb_tau2 = 0.f;
+    bool adj_cheb2_attr[CHEB_MAX_L + 1] = {};
     // launch shapes of the expansion forward chosen by nfm_autotune, per minibatch size
     struct FwdShape { int n_pairs, threads, group, pch, chunks; bool direct; };
     std::vector<FwdShape> fwd_tuned;
@@ -359,6 +367,77 @@ int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, doub
     const double fcc = (f0 + k_center * df) / c;
     ctx->cheb_fc_hi = (float)fcc;
     ctx->cheb_fc_lo = (float)(fcc - (double)ctx->cheb_fc_hi);
+    return NFM_OK;
+}
+
+// The FP32 expansion adjoint's blocks of two tiles along z (8 x 4 x 8 voxels, regular grids): a grid
+// descriptor over the blocks, the FP64 antenna-block rows (centres given explicitly to ant_setup_kernel)
+// and an expansion table for the larger span.  |d - d_c| <= |u| (triangle inequality), so the block's
+// corner offset bounds delta.  Leaves cheb_L2 = 0 (the adjoint stays on the tiles) where the span needs
+// more terms than the block kernels are built for.
+int setup_blocks2(nfm_ctx* ctx, const nfm_grid& g, const GridDesc& gd, const AntSetup& as, int K, double df, double c)
+{
+    constexpr int TZ2 = 2 * TILE_Z;
+    GridDesc g2 = gd;
+    g2.tiles_z = (g.nz + TZ2 - 1) / TZ2;
+    g2.n_tiles = g2.tiles_x * g2.tiles_y * g2.tiles_z;
+    g2.mx = tile_div_magic(g2.n_tiles, g2.tiles_x);
+    g2.my = tile_div_magic(g2.n_tiles, g2.tiles_y);
+    const double hx = 0.5 * (TILE_X - 1) * g.dx, hy = 0.5 * (TILE_Y - 1) * g.dy, hz = 0.5 * (TZ2 - 1) * g.dz;
+    const double span = 2.0 * std::sqrt(hx * hx + hy * hy + hz * hz);
+    const double margin = 0.95;
+    const double z_step = 2.0 * 3.14159265358979323846 * df * span / (c * margin);
+    const double k_center = 0.5 * (K - 1);
+    const int LP = 80;
+    std::vector<double> probe(2 * LP);
+    cheb_coefficients(z_step * k_center, 0.0, 2, LP, probe.data());   // rows z = 0 and the band edge
+    int L = 0;
+    for (int cand = CHEB_MIN_L; cand <= CHEB_MAX_L; cand += 2) {
+        double tail = 0.0;
+        for (int l = cand; l < LP; ++l) tail += std::fabs(probe[LP + l]);
+        if (tail < 1e-7) {
+            L = cand;
+            break;
+        }
+    }
+    if (L == 0 || !adj_cheb_kernel_ptr(L, TZ2)) return NFM_OK;
+    const int kpad = ctx->cheb_kpad, ls = (L + 3) & ~3;
+    std::vector<double> b((size_t)K * L);
+    cheb_coefficients(z_step, k_center, K, L, b.data());
+    std::vector<float> hb((size_t)kpad * ls, 0.f);
+    for (int k = 0; k < K; ++k)
+        for (int l = 0; l < L; ++l) hb[(size_t)k * ls + l] = (float)b[(size_t)k * L + l];
+    std::vector<double> hc((size_t)g2.n_tiles * 3);
+    for (int t = 0; t < g2.n_tiles; ++t) {   // block order: x fastest, then y, then z (as tile_coords)
+        const int bx = t % g2.tiles_x, by = (t / g2.tiles_x) % g2.tiles_y, bz = t / (g2.tiles_x * g2.tiles_y);
+        hc[3 * (size_t)t] = g.x0 + (bx * TILE_X + 0.5 * (TILE_X - 1)) * g.dx;
+        hc[3 * (size_t)t + 1] = g.y0 + (by * TILE_Y + 0.5 * (TILE_Y - 1)) * g.dy;
+        hc[3 * (size_t)t + 2] = g.z0 + (bz * TZ2 + 0.5 * (TZ2 - 1)) * g.dz;
+    }
+    double* d_c = nullptr;
+    cudaError_t e = cudaMalloc((void**)&ctx->d_ant2, (size_t)as.n_ant * g2.n_tiles * sizeof(AntTile));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_cheb2, hb.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_c, hc.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_cheb2, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_c, hc.data(), hc.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        AntSetup a2 = as;
+        a2.tile_c = d_c;
+        a2.out = ctx->d_ant2;
+        e = launch_ant_setup(g2, a2, ctx->stream);
+    }
+    if (e == cudaSuccess) e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
+    free_ptr(d_c);
+    if (e != cudaSuccess) {
+        free_ptr(ctx->d_ant2);
+        free_ptr(ctx->d_cheb2);
+        ctx->d_ant2 = nullptr;
+        ctx->d_cheb2 = nullptr;
+        return fail(ctx, NFM_ERR_NOMEM, "adjoint block tables: %s", cudaGetErrorString(e));
+    }
+    ctx->gd2 = g2;
+    ctx->cheb_L2 = L;
+    ctx->cheb_tau2 = (float)(margin / span);
     return NFM_OK;
 }
 
@@ -801,31 +880,41 @@ int enqueue_adjoint(nfm_ctx* ctx, const int* pairs, int n_pairs, const float2* r
         return NFM_OK;
     }
     if (cheb) {
-        const int LT = ctx->cheb_L;
-        const size_t smem = adj_cheb_smem_bytes(LT, ctx->cheb_kpad);
-        if (!ctx->adj_cheb_attr[LT]) {
-            NFM_CK(cudaFuncSetAttribute(adj_cheb_kernel_ptr(LT), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)ctx->smem_optin));
-            // all of the unified L1 / shared memory as shared memory, so that eight CTAs fit per SM
-            NFM_CK(cudaFuncSetAttribute(adj_cheb_kernel_ptr(LT), cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-            ctx->adj_cheb_attr[LT] = true;
+        // on a regular grid the adjoint runs over blocks of two tiles along z (their own tables)
+        const bool blk2 = ctx->cheb_L2 > 0 && !ctx->points;
+        const int LT = blk2 ? ctx->cheb_L2 : ctx->cheb_L;
+        const int tz = blk2 ? 2 * TILE_Z : TILE_Z;
+        const size_t smem = adj_cheb_smem_bytes(LT, ctx->cheb_kpad, tz);
+        const void* fn = adj_cheb_kernel_ptr(LT, tz);
+        if (!fn) return fail(ctx, NFM_ERR_ARG, "no expansion adjoint for L = %d", LT);
+        bool& attr = blk2 ? ctx->adj_cheb2_attr[LT] : ctx->adj_cheb_attr[LT];
+        if (!attr) {
+            NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin));
+            // all of the unified L1 / shared memory as shared memory, so that eight (four) CTAs fit per SM
+            NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            attr = true;
         }
         AdjArgs a;
         a.pairs = pairs;
         a.n_pairs = n_pairs;
         a.r = r;
         a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
-    a.r_elems = (long long)n_pairs * ctx->K / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
         a.g_out = g_out;
         a.s = s;
         a.step = step;
         a.alpha = alpha;
         a.shrink = shrink;
-        a.pchunk = CHEB_ADJ_PCHUNK;
+        a.pchunk = adj_cheb_pchunk(tz);
         a.alpha_g = alpha_g;
-        ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, LT, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
+        ChebDesc cd{blk2 ? ctx->d_cheb2 : ctx->d_cheb, blk2 ? ctx->cheb_tau2 : ctx->cheb_tau, LT, ctx->cheb_kpad,
+                    ctx->cheb_fc_hi, ctx->cheb_fc_lo};
+        OpDesc op = op_desc(ctx);
+        if (blk2) {
+            op.g = ctx->gd2;
+            op.ant = ctx->d_ant2;
+        }
         const int e0 = prof_mark(ctx);
-        NFM_CK(launch_adj_cheb(op_desc(ctx), cd, a, smem, ctx->stream));
+        NFM_CK(launch_adj_cheb(op, cd, a, tz, smem, ctx->stream));
         prof_pair(ctx, 2, e0, prof_mark(ctx));
         return NFM_OK;
     }
@@ -936,7 +1025,8 @@ void nfm_destroy(nfm_ctx* ctx)
     else cudaDeviceSynchronize();
     void* ps[] = {ctx->d_ant, ctx->d_ant_xyz, ctx->d_pulse, ctx->d_antk, ctx->d_fkc, ctx->d_pairs_all, ctx->d_err, ctx->d_red,
                   ctx->d_partial, ctx->d_resid, ctx->d_v, ctx->d_g, ctx->d_y, ctx->d_hy, ctx->d_hs, ctx->d_hperm,
-                  ctx->d_prox_partial, ctx->d_bmat, ctx->d_bscale, ctx->d_cheb, ctx->d_pts, ctx->d_tile_c,
+                  ctx->d_prox_partial, ctx->d_bmat, ctx->d_bscale, ctx->d_cheb, ctx->d_ant2, ctx->d_cheb2,
+                  ctx->d_pts, ctx->d_tile_c,
                   ctx->d_vox_xyz};
     for (void* p : ps) free_ptr(p);
     for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
@@ -1047,6 +1137,11 @@ int set_geometry_impl(nfm_ctx* ctx, const double* tx_xyz, int T, const double* r
     free_ptr(ctx->d_cheb);
     ctx->d_cheb = nullptr;
     ctx->cheb_L = 0;
+    free_ptr(ctx->d_ant2);
+    free_ptr(ctx->d_cheb2);
+    ctx->d_ant2 = nullptr;
+    ctx->d_cheb2 = nullptr;
+    ctx->cheb_L2 = 0;
     ctx->fwd_tuned.clear();
     ctx->d_antk = nullptr;
     ctx->d_fkc = nullptr;
@@ -1189,6 +1284,7 @@ int set_geometry_impl(nfm_ctx* ctx, const double* tx_xyz, int T, const double* r
         if (e != cudaSuccess) return fail(ctx, NFM_ERR_CUDA, "general-frequency tables: %s", cudaGetErrorString(e));
     }
     if (uniform) NFM_TRY(setup_cheb(ctx, gd, as, K, f0, df, c));
+    if (uniform && !pts && ctx->cheb_L > 0) NFM_TRY(setup_blocks2(ctx, g, gd, as, K, df, c));
     NFM_CK(ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize());
     if (pts && ctx->cheb_L == 0)
         return fail(ctx, NFM_ERR_ARG, "explicit voxel positions: the path-length spread of a run of 128 voxels needs "

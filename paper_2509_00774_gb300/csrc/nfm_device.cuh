@@ -209,11 +209,12 @@ struct __align__(16) VoxelOffset {
     float ux, uy, uz, uu;
 };
 
-__device__ __forceinline__ VoxelOffset voxel_offset(const GridDesc& g, int lx, int ly, int lz)
+// (tz: the z extent of the block the offset is taken in; TILE_Z for the tiles)
+__device__ __forceinline__ VoxelOffset voxel_offset(const GridDesc& g, int lx, int ly, int lz, int tz = TILE_Z)
 {
     float ox = (float)lx - 0.5f * (TILE_X - 1);
     float oy = (float)ly - 0.5f * (TILE_Y - 1);
-    float oz = (float)lz - 0.5f * (TILE_Z - 1);
+    float oz = (float)lz - 0.5f * (float)(tz - 1);
     VoxelOffset o;
     o.ux = fmaf(ox, g.dx_hi, ox * g.dx_lo);
     o.uy = fmaf(oy, g.dy_hi, oy * g.dy_lo);

@@ -72,7 +72,10 @@ const void* fwd_general_ptr();
 constexpr int CHEB_THREADS = 128;
 constexpr int CHEB_GROUP = 4;                              // lanes per (pair, tile) in the forward
 constexpr int CHEB_GROUPS = CHEB_THREADS / CHEB_GROUP;    // 32
-constexpr int CHEB_ADJ_PCHUNK = 16;                        // pairs staged per adjoint round
+constexpr int CHEB_ADJ_PCHUNK = 16;                        // pairs staged per adjoint round (128-voxel tiles)
+// pairs staged per round of the expansion adjoint over blocks of 8 x 4 x tz voxels (tz = TILE_Z: the tiles;
+// tz = 2 TILE_Z: two tiles along z, 256 threads)
+__host__ __device__ constexpr int adj_cheb_pchunk(int tz) { return tz == TILE_Z ? CHEB_ADJ_PCHUNK : 2 * CHEB_ADJ_PCHUNK; }
 constexpr int CHEB_MIN_L = 10;
 constexpr int CHEB_MAX_L = 32;
 struct ChebDesc {
@@ -93,14 +96,15 @@ __host__ __device__ constexpr int fwd_coef_stride(int LT)
 __host__ __device__ constexpr int fwd_coef_rows(int k_pad) { return k_pad / 2 + 1; }
 // points: the geometry has explicit voxel positions (per-stage voxel offsets are staged too)
 size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, bool points = false);
-size_t adj_cheb_smem_bytes(int LT, int k_pad);
+size_t adj_cheb_smem_bytes(int LT, int k_pad, int tz = TILE_Z);
 const void* fwd_cheb_kernel_ptr(int LT, int group);
-const void* adj_cheb_kernel_ptr(int LT);
+const void* adj_cheb_kernel_ptr(int LT, int tz = TILE_Z);   // nullptr where not built (tz = 8: L <= 24)
 // threads: 64 or 128; group: 4 or 8 lanes per (pair, tile); a.VS = pairs per CTA, a power of two
 // dividing threads / group
 cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
                             int group, size_t smem, cudaStream_t st);
-cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, size_t smem, cudaStream_t st);
+cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, int tz, size_t smem,
+                            cudaStream_t st);
 // tensor-core (tcgen05) expansion stage of the forward (op_cheb_tc_fwd.cu): 256 threads, a.VS = pairs per
 // CTA in {16, 32, 64}, K <= 128
 size_t fwd_cheb_tc_smem_bytes(int LT, int K, int pch);

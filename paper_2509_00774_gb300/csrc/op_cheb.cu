@@ -320,58 +320,64 @@ __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// adjoint: CTA = one voxel tile, thread = voxel; pairs in chunks of CHEB_ADJ_PCHUNK
+// adjoint: CTA = one block of 8 x 4 x TZ voxels, thread = voxel; pairs in chunks of adj_cheb_pchunk(TZ).
+// TZ = 4: the tiles of the geometry (TILE_V voxels); TZ = 8: blocks of two tiles along z, with their own
+// antenna-block table and expansion table (op.g, op.ant and cd describe the blocks), which halves the
+// per-voxel share of the per-(pair, block) work: the residual transform and the coefficient stage.
 // ---------------------------------------------------------------------------
-template <int LT>
+template <int LT, int TZ>
 __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd, const AdjArgs a, int tile,
                                               unsigned char* smem)
 {
     constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
+    constexpr int TV = TILE_X * TILE_Y * TZ; // voxels of a block = threads of the CTA
+    constexpr int PCH = adj_cheb_pchunk(TZ); // pairs staged per round
     const int K = op.K;
     const int KP = cd.k_pad;
     float* coef = reinterpret_cast<float*>(smem);                          // [KP][LS]
     const int RS = KP + 2;                   // r' row stride (float2), staggers the banks
     float2* rp = reinterpret_cast<float2*>(coef + KP * LS);               // [PCH][RS]
-    float2* Cs = rp + CHEB_ADJ_PCHUNK * RS;                                 // [PCH][LS]
-    PairTile* pt = reinterpret_cast<PairTile*>(Cs + CHEB_ADJ_PCHUNK * LS);  // [PCH]
-    float2* w16 = reinterpret_cast<float2*>(pt + CHEB_ADJ_PCHUNK);          // [PCH] e^{+j 2 pi 16 df D_c/c}
+    float2* Cs = rp + PCH * RS;                                             // [PCH][LS]
+    PairTile* pt = reinterpret_cast<PairTile*>(Cs + PCH * LS);              // [PCH]
+    float2* w16 = reinterpret_cast<float2*>(pt + PCH);                      // [PCH] e^{+j 2 pi 16 df D_c/c}
 
     const int tid = threadIdx.x;
     int tx, ty, tz;
     tile_coords(op.g, tile, tx, ty, tz);
     const int lx = tid % TILE_X, ly = (tid / TILE_X) % TILE_Y, lz = tid / (TILE_X * TILE_Y);
     VoxelOffset o;
-    if (op.g.pts) {                          // explicit positions: voxel n = tile * 128 + thread
+    if (TZ == TILE_Z && op.g.pts) {          // explicit positions: voxel n = tile * 128 + thread
         const float4 u = op.g.pts[(size_t)tile * TILE_V + tid];
         o.ux = u.x;
         o.uy = u.y;
         o.uz = u.z;
         o.uu = u.w;
     } else {
-        o = voxel_offset(op.g, lx, ly, lz);
+        o = voxel_offset(op.g, lx, ly, lz, TZ);
     }
-    for (int i = tid; i < KP * LS / 4; i += CHEB_THREADS)
+    for (int i = tid; i < KP * LS / 4; i += TV)
         reinterpret_cast<float4*>(coef)[i] = reinterpret_cast<const float4*>(cd.coef)[i];
     constexpr int LQ = LS / 4;
     float gr = 0.f, gi = 0.f;
     // the pair list and the geometry tables are never written by this library's kernels, so the
     // first chunk's pair tiles are read before the wait on the previous kernel
-    if (tid < min(CHEB_ADJ_PCHUNK, a.n_pairs)) {
+    if (tid < min(PCH, a.n_pairs)) {
         pt[tid] = load_pair_tile(op, a.pairs[tid], tile);
         w16[tid] = tile_step_cis_exact(pt[tid], 16);
     }
     pdl_wait();                              // r comes from the previous kernel
     // the voxel's iterate for the fused update, loaded now so that its latency overlaps the r copies
-    const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TILE_Z + lz;
+    const int ix = tx * TILE_X + lx, iy = ty * TILE_Y + ly, iz = tz * TZ + lz;
     const size_t np = (size_t)tile * TILE_V + tid;
-    const bool in_grid = op.g.pts ? np < (size_t)op.g.nx : (ix < op.g.nx && iy < op.g.ny && iz < op.g.nz);
-    const size_t n = !in_grid ? 0 : op.g.pts ? np : ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
+    const bool pts = TZ == TILE_Z && op.g.pts;
+    const bool in_grid = pts ? np < (size_t)op.g.nx : (ix < op.g.nx && iy < op.g.ny && iz < op.g.nz);
+    const size_t n = !in_grid ? 0 : pts ? np : ((size_t)iz * op.g.ny + iy) * op.g.nx + ix;
     const float2 s_old = (a.s && in_grid) ? a.s[NFM_IDX(n, op.n_vox, op.err)] : make_float2(0.f, 0.f);
 
     // rows of r start on 16-byte boundaries in shared memory (RS even) and, for even K, in r
     const bool r_vec = !(K & 1) && !(reinterpret_cast<uintptr_t>(a.r) & 15);
-    for (int c0 = 0; c0 < a.n_pairs; c0 += CHEB_ADJ_PCHUNK) {
-        const int nc = min(CHEB_ADJ_PCHUNK, a.n_pairs - c0);
+    for (int c0 = 0; c0 < a.n_pairs; c0 += PCH) {
+        const int nc = min(PCH, a.n_pairs - c0);
         if (c0 > 0) {
             __syncthreads();
             if (tid < nc) {
@@ -383,11 +389,11 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
         // it waits, so the loads overlap (one L2 round trip).
         const int k0 = tid % 16;
         if (r_vec) {                         // 16-byte copies of (r_k, r_k+1), k even (K even, r 16-byte aligned)
-            for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16)
+            for (int j = tid / 16; j < nc; j += TV / 16)
                 for (int k = 2 * k0; k < K; k += 32)
                     cp_async_16_ca(rp + j * RS + k, a.r + NFM_IDX((long long)(c0 + j) * K + k, a.r_elems, op.err));
         } else {
-            for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16)
+            for (int j = tid / 16; j < nc; j += TV / 16)
                 for (int k = k0; k < K; k += 16)
                     cp_async_8(rp + j * RS + k, a.r + NFM_IDX((long long)(c0 + j) * K + k, a.r_elems, op.err), true);
         }
@@ -402,7 +408,7 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
         // Phasors: an SFU start each for k0 and K-1-k0, then the pair's exact 16-step phasor up and its
         // conjugate down (at most 4 steps).
         const int KH = K / 2;
-        for (int j = tid / 16; j < nc; j += CHEB_THREADS / 16) {
+        for (int j = tid / 16; j < nc; j += TV / 16) {
             const PairTile& P = pt[j];
             const float2 W = w16[j];
             const float2 Wc = make_float2(W.x, -W.y);
@@ -434,7 +440,7 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
         // rows and table rows of the two parities sit in different banks); the centre row goes to parity 0
         {
             const int n_task = 2 * nc * LQ;  // even, so lane pairs never straddle a round or the end
-            for (int e0 = 0; e0 < n_task; e0 += CHEB_THREADS) {
+            for (int e0 = 0; e0 < n_task; e0 += TV) {
                 const int e = e0 + tid;
                 const bool active = e < n_task;
                 if (!__any_sync(0xffffffffu, active)) continue;   // whole warp past the end
@@ -541,11 +547,13 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
     }
 }
 
-template <int LT>
-__global__ void __launch_bounds__(CHEB_THREADS, 8) adj_cheb_kernel(OpDesc op, ChebDesc cd, AdjArgs a)
+// at most 64 registers either way: 8 CTAs of 128 threads or 4 of 256 per SM
+template <int LT, int TZ>
+__global__ void __launch_bounds__(TILE_X * TILE_Y * TZ, TZ == TILE_Z ? 8 : 4) adj_cheb_kernel(OpDesc op, ChebDesc cd,
+                                                                                         AdjArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    adj_cheb_body<LT>(op, cd, a, blockIdx.x, smem);
+    adj_cheb_body<LT, TZ>(op, cd, a, blockIdx.x, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -585,7 +593,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, 7) adj_cheb_multi_kernel(const M
     const OpDesc op = items[i].op;
     const ChebDesc cd = items[i].cd;
     const AdjArgs a = items[i].a;
-    adj_cheb_body<LT>(op, cd, a, (int)blockIdx.x - items[i].cta0, smem);
+    adj_cheb_body<LT, TILE_Z>(op, cd, a, (int)blockIdx.x - items[i].cta0, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -653,12 +661,12 @@ size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, b
            (points ? (size_t)2 * TS * TILE_V * sizeof(VoxelOffset) : 0);
 }
 
-size_t adj_cheb_smem_bytes(int LT, int k_pad)
+size_t adj_cheb_smem_bytes(int LT, int k_pad, int tz)
 {
     const int LS = (LT + 3) & ~3;
-    return (size_t)k_pad * LS * sizeof(float) + (size_t)CHEB_ADJ_PCHUNK * (k_pad + 2) * sizeof(float2) +
-           (size_t)CHEB_ADJ_PCHUNK * LS * sizeof(float2) + (size_t)CHEB_ADJ_PCHUNK * sizeof(PairTile) +
-           (size_t)CHEB_ADJ_PCHUNK * sizeof(float2);
+    const int pch = adj_cheb_pchunk(tz);
+    return (size_t)k_pad * LS * sizeof(float) + (size_t)pch * (k_pad + 2) * sizeof(float2) +
+           (size_t)pch * LS * sizeof(float2) + (size_t)pch * sizeof(PairTile) + (size_t)pch * sizeof(float2);
 }
 
 template <int G>
@@ -688,23 +696,33 @@ const void* fwd_cheb_kernel_ptr(int LT, int group)
     return nullptr;
 }
 
-const void* adj_cheb_kernel_ptr(int LT)
+template <int TZ>
+static const void* adj_cheb_ptr_tz(int LT)
 {
     switch (LT) {
-    case 10: return (const void*)adj_cheb_kernel<10>;
-    case 12: return (const void*)adj_cheb_kernel<12>;
-    case 14: return (const void*)adj_cheb_kernel<14>;
-    case 16: return (const void*)adj_cheb_kernel<16>;
-    case 18: return (const void*)adj_cheb_kernel<18>;
-    case 20: return (const void*)adj_cheb_kernel<20>;
-    case 22: return (const void*)adj_cheb_kernel<22>;
-    case 24: return (const void*)adj_cheb_kernel<24>;
-    case 26: return (const void*)adj_cheb_kernel<26>;
-    case 28: return (const void*)adj_cheb_kernel<28>;
-    case 30: return (const void*)adj_cheb_kernel<30>;
-    case 32: return (const void*)adj_cheb_kernel<32>;
+    case 10: return (const void*)adj_cheb_kernel<10, TZ>;
+    case 12: return (const void*)adj_cheb_kernel<12, TZ>;
+    case 14: return (const void*)adj_cheb_kernel<14, TZ>;
+    case 16: return (const void*)adj_cheb_kernel<16, TZ>;
+    case 18: return (const void*)adj_cheb_kernel<18, TZ>;
+    case 20: return (const void*)adj_cheb_kernel<20, TZ>;
+    case 22: return (const void*)adj_cheb_kernel<22, TZ>;
+    case 24: return (const void*)adj_cheb_kernel<24, TZ>;
+    default: break;
+    }
+    if (TZ != TILE_Z) return nullptr;        // the two-tile blocks are built for L <= 24
+    switch (LT) {
+    case 26: return (const void*)adj_cheb_kernel<26, TILE_Z>;
+    case 28: return (const void*)adj_cheb_kernel<28, TILE_Z>;
+    case 30: return (const void*)adj_cheb_kernel<30, TILE_Z>;
+    case 32: return (const void*)adj_cheb_kernel<32, TILE_Z>;
     default: return nullptr;
     }
+}
+
+const void* adj_cheb_kernel_ptr(int LT, int tz)
+{
+    return tz == TILE_Z ? adj_cheb_ptr_tz<TILE_Z>(LT) : tz == 2 * TILE_Z ? adj_cheb_ptr_tz<2 * TILE_Z>(LT) : nullptr;
 }
 
 cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
@@ -717,12 +735,13 @@ cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs&
     return launch_pdl(fn, grid, dim3(threads), smem, st, args);
 }
 
-cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, size_t smem, cudaStream_t st)
+cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, int tz, size_t smem,
+                            cudaStream_t st)
 {
-    const void* fn = adj_cheb_kernel_ptr(cd.L);
+    const void* fn = adj_cheb_kernel_ptr(cd.L, tz);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {(void*)&op, (void*)&cd, (void*)&a};
-    return launch_pdl(fn, dim3(op.g.n_tiles), dim3(CHEB_THREADS), smem, st, args);
+    return launch_pdl(fn, dim3(op.g.n_tiles), dim3(TILE_X * TILE_Y * tz), smem, st, args);
 }
 
 const void* fwd_cheb_multi_ptr(int LT)

@@ -171,7 +171,9 @@ def test_batched48_smallest_scenes_spgm_match_oracle():
 def test_fused_batch_matches_branch_batch_and_oracle():
     """The fused batch (one forward, one reduction and one adjoint launch per step index over every scene)
     against the graph of per-scene branches on uneven scenes (grids 8..16, K 16..37, 4 to 36 pairs, ragged
-    minibatches), and against the oracle's epochs; then three scenes of the 48-scene set."""
+    minibatches), and against the oracle's epochs; then three scenes of the 48-scene set.  The per-scene
+    adjoint runs over blocks of two tiles with its own expansion table while the fused adjoint runs over
+    the tiles, so the two agree to the FP32 operator's tolerance (rel 1e-5), not bit for bit."""
     import torch
     from paper_2509_00774_gb300.nfmimo import Batch
     geoms = [_tiny_scene(4, 4, 16, 12, 0), _tiny_scene(6, 4, 37, 8, 1), _tiny_scene(4, 6, 24, 10, 2),
@@ -202,7 +204,7 @@ def test_fused_batch_matches_branch_batch_and_oracle():
         torch.cuda.synchronize()
         for i in range(len(geoms)):
             a, b = to_host(s_f[i]), to_host(s_b[i])
-            assert np.linalg.norm(a - b) <= 1e-6 * max(np.linalg.norm(b), 1e-30), (e, i)
+            assert np.linalg.norm(a - b) <= 1e-5 * max(np.linalg.norm(b), 1e-30), (e, i)
             assert nmse(a, s_o[i]) <= NMSE_TOL, (e, i)
     fused.close()
     branches.close()
@@ -225,6 +227,6 @@ def test_fused_batch_matches_branch_batch_and_oracle():
     torch.cuda.synchronize()
     for i in range(3):
         a, b = to_host(sf[i]), to_host(sb[i])
-        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b), ws[i].name
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b), ws[i].name
     bf.close()
     bb.close()
