@@ -40,14 +40,14 @@ FP32_LANES_PER_SM = 128
 CHEB_GEOM_OPS = 42             # expansion: FP32/SFU ops of geometry and base phase per (pair, voxel)
 
 
-def cheb_flops_per_pair_voxel(L, K):
+def cheb_flops_per_pair_voxel(L, K, block=128):
     """Algorithmic FP32 work of the expansion operator per (pair, voxel), each FMA-pipe operation counted as
-    2 flops: L Chebyshev recurrence steps with a complex-by-real accumulation (3L FMAs); per (pair, tile),
-    spread over the tile's 128 voxels, the expansion over half the band with its mirror (K L FMAs: the
-    band-centred table has b_l(K-1-k) = (-1)^l b_l(k)), the even/odd fold (2K adds) and the tile phasor
-    (a complex multiply and a recurrence step per frequency, 8K); and the geometry (two distances,
-    amplitude, base phase: CHEB_GEOM_OPS ops)."""
-    return 2.0 * (3 * L + (K * L + 10.0 * K) / 128.0 + CHEB_GEOM_OPS)
+    2 flops: L Chebyshev recurrence steps with a complex-by-real accumulation (3L FMAs); per (pair, block),
+    spread over the block's voxels (128 for a tile, 256 for the adjoint's two-tile blocks), the expansion
+    over half the band with its mirror (K L FMAs: the band-centred table has b_l(K-1-k) = (-1)^l b_l(k)),
+    the even/odd fold (2K adds) and the block phasor (a complex multiply and a recurrence step per
+    frequency, 8K); and the geometry (two distances, amplitude, base phase: CHEB_GEOM_OPS ops)."""
+    return 2.0 * (3 * L + (K * L + 10.0 * K) / float(block) + CHEB_GEOM_OPS)
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -658,14 +658,18 @@ def run_ours(args):
     kernels = {}
     elems = bp * geom.K * geom.N        # (row, voxel) pairs per forward / adjoint launch
     cheb = algo == "chebyshev"
-    flops_per_launch = (cheb_flops_per_pair_voxel(cheb_L, geom.K) * bp * geom.N if cheb
-                        else FLOPS_PER_PAIR * elems)
+    # the FP32 expansion adjoint may run over its own blocks (256 voxels) with its own expansion length
+    adj_L, adj_block = ctx.adjoint_info() if cheb and args.precision == "fp32" else (cheb_L, 128)
+    flops_fwd = cheb_flops_per_pair_voxel(cheb_L, geom.K) if cheb else None
+    flops_adj = cheb_flops_per_pair_voxel(adj_L, geom.K, adj_block) if cheb else None
     for kind, (ms, n) in prof.items():
         if n == 0:
             continue
         avg_ms = ms / n
         entry = {"launches": n, "total_ms": ms, "avg_us": avg_ms * 1e3}
         if kind in ("forward_partial", "adjoint") and (cheb or kind == "forward_partial" or args.precision == "fp32"):
+            flops_per_launch = ((flops_fwd if kind == "forward_partial" else flops_adj) * bp * geom.N if cheb
+                                else FLOPS_PER_PAIR * elems)
             tf = flops_per_launch / (avg_ms * 1e-3) / 1e12
             entry.update({"gpairs_per_s": elems / (avg_ms * 1e-3) / 1e9, "tflops": tf,
                           "direct_equivalent_tflops": FLOPS_PER_PAIR * elems / (avg_ms * 1e-3) / 1e12})
@@ -680,9 +684,10 @@ def run_ours(args):
              "adjoint": ("adj_cheb_kernel" if cheb else "adj_kernel") if args.precision == "fp32"
              else ("adj_cheb_tc_kernel" if cheb else "adj_tc_kernel")}[dom]
     if cheb:
-        work = (f"{cheb_flops_per_pair_voxel(cheb_L, geom.K):.0f} flops per (pair, voxel) = 2 x (3L recurrence/accumulate "
-                f"FMAs + (KL + 10K)/128 mirror-folded expansion and tile-phasor ops + {CHEB_GEOM_OPS} geometry ops), "
-                f"L = {cheb_L}, K = {geom.K}; "
+        wL, wB = (cheb_L, 128) if dom == "forward_partial" else (adj_L, adj_block)
+        work = (f"{cheb_flops_per_pair_voxel(wL, geom.K, wB):.0f} flops per (pair, voxel) = 2 x (3L "
+                f"recurrence/accumulate FMAs + (KL + 10K)/{wB} mirror-folded expansion and block-phasor ops + "
+                f"{CHEB_GEOM_OPS} geometry ops), L = {wL}, K = {geom.K}, {wB}-voxel blocks; "
                 f"{bp * geom.N} (pair, voxel) = {elems} (row, voxel) per launch" +
                 ("" if args.precision == "fp32" else
                  "; the expansion contraction runs on tcgen05, the rest on the FP32 lanes"))
@@ -704,7 +709,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name + ("_jittered_freqs" if args.nonuniform else ""), "T": geom.T, "R": geom.R, "K": geom.K, "N": geom.N, "M": geom.M,
                    "pairs_per_batch": bp, "minibatches_per_step": geom.P // bp, "step": "one SPGM epoch",
-                   "operator": (f"fp32 cuda-core tile-local Chebyshev expansion, L = {cheb_L}" if cheb else
+                   "operator": (f"fp32 cuda-core tile-local Chebyshev expansion, forward L = {cheb_L} over 128-voxel "
+                                f"tiles, adjoint L = {adj_L} over {adj_block}-voxel blocks" if cheb else
                                 "forward: fp32 cuda-core three-term phasor recurrence; adjoint: fp32 cuda-core Horner") +
                                ("" if args.precision == "fp32" else
                                 f"; expansion contractions of the forward{' and the adjoint' if cheb else ''} on "

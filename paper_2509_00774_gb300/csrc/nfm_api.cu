@@ -1376,6 +1376,15 @@ int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_m
     return NFM_OK;
 }
 
+int nfm_adjoint_info(nfm_ctx* ctx, int* n_terms, int* block_voxels)
+{
+    NFM_TRY(require_geom(ctx));
+    const bool blk2 = ctx->cheb_L2 > 0 && !ctx->points;
+    if (n_terms) *n_terms = blk2 ? ctx->cheb_L2 : ctx->cheb_L;
+    if (block_voxels) *block_voxels = blk2 ? TILE_X * TILE_Y * 2 * TILE_Z : TILE_V;
+    return NFM_OK;
+}
+
 int nfm_autotune(nfm_ctx* ctx, int n_pairs, int* algorithm_out, int* threads_out, int* group_out,
                  int* pairs_per_cta_out, int* chunks_out)
 {
