@@ -658,10 +658,10 @@ def run_ours(args):
     kernels = {}
     elems = bp * geom.K * geom.N        # (row, voxel) pairs per forward / adjoint launch
     cheb = algo == "chebyshev"
-    # the FP32 expansion adjoint may run over its own blocks (256 voxels) with its own expansion length
-    adj_L, adj_block = ctx.adjoint_info() if cheb and args.precision == "fp32" else (cheb_L, 128)
-    flops_fwd = cheb_flops_per_pair_voxel(cheb_L, geom.K) if cheb else None
-    flops_adj = cheb_flops_per_pair_voxel(adj_L, geom.K, adj_block) if cheb else None
+    # the FP32 expansion operator may run over blocks of two tiles (256 voxels) with their own expansion
+    blk_L, blk_V = ctx.expansion_info() if cheb and args.precision == "fp32" else (cheb_L, 128)
+    flops_fwd = cheb_flops_per_pair_voxel(blk_L, geom.K, blk_V) if cheb else None
+    flops_adj = flops_fwd
     for kind, (ms, n) in prof.items():
         if n == 0:
             continue
@@ -684,7 +684,7 @@ def run_ours(args):
              "adjoint": ("adj_cheb_kernel" if cheb else "adj_kernel") if args.precision == "fp32"
              else ("adj_cheb_tc_kernel" if cheb else "adj_tc_kernel")}[dom]
     if cheb:
-        wL, wB = (cheb_L, 128) if dom == "forward_partial" else (adj_L, adj_block)
+        wL, wB = blk_L, blk_V
         work = (f"{cheb_flops_per_pair_voxel(wL, geom.K, wB):.0f} flops per (pair, voxel) = 2 x (3L "
                 f"recurrence/accumulate FMAs + (KL + 10K)/{wB} mirror-folded expansion and block-phasor ops + "
                 f"{CHEB_GEOM_OPS} geometry ops), L = {wL}, K = {geom.K}, {wB}-voxel blocks; "
@@ -709,8 +709,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name + ("_jittered_freqs" if args.nonuniform else ""), "T": geom.T, "R": geom.R, "K": geom.K, "N": geom.N, "M": geom.M,
                    "pairs_per_batch": bp, "minibatches_per_step": geom.P // bp, "step": "one SPGM epoch",
-                   "operator": (f"fp32 cuda-core tile-local Chebyshev expansion, forward L = {cheb_L} over 128-voxel "
-                                f"tiles, adjoint L = {adj_L} over {adj_block}-voxel blocks" if cheb else
+                   "operator": (f"fp32 cuda-core block-local Chebyshev expansion, L = {blk_L} over {blk_V}-voxel "
+                                f"blocks" if cheb else
                                 "forward: fp32 cuda-core three-term phasor recurrence; adjoint: fp32 cuda-core Horner") +
                                ("" if args.precision == "fp32" else
                                 f"; expansion contractions of the forward{' and the adjoint' if cheb else ''} on "

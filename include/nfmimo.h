@@ -162,14 +162,16 @@ int nfm_set_algorithm(nfm_ctx* ctx, int algo);
  * may be NULL.  Errors: NFM_ERR_STATE without a geometry. */
 int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_max);
 
-/* The expansion the FP32 adjoint uses on this geometry: on a regular grid it runs
- * over blocks of two tiles along z (8 x 4 x 8 voxels) with its own expansion of
- * n_terms terms; otherwise (explicit voxel positions, or a span that needs more
- * terms than the block kernels are built for) over the 8 x 4 x 4 tiles with the
- * forward's.  Writes the expansion length and the voxels per block (256 or 128);
- * 0 terms if the expansion is not available.  Any pointer may be NULL.  Errors:
- * NFM_ERR_STATE without a geometry. */
-int nfm_adjoint_info(nfm_ctx* ctx, int* n_terms, int* block_voxels);
+/* The expansion the FP32 expansion operator (forward and adjoint) uses on this
+ * geometry.  On a regular grid it runs over blocks of two tiles along z
+ * (8 x 4 x 8 voxels) with their own expansion of n_terms terms.  Otherwise
+ * (explicit voxel positions, or a span that needs more terms than the block
+ * kernels are built for) it runs over the 8 x 4 x 4 tiles, with the length
+ * nfm_algorithm_info reports.  The tensor-core modes and the fused batch
+ * always use the tiles.  Writes the expansion length and the voxels per block
+ * (256 or 128); 0 terms if the expansion is not available.  Any pointer may be
+ * NULL.  Errors: NFM_ERR_STATE without a geometry. */
+int nfm_expansion_info(nfm_ctx* ctx, int* n_terms, int* block_voxels);
 
 /* Autotuner (no counterpart in the paper) for minibatches of n_pairs pairs of
  * the current geometry.  Every candidate launch shape of the expansion

@@ -139,6 +139,7 @@ struct nfm_ctx {
     int cheb_L2 = 0;
     float cheb_tau2 = 0.f;
     bool adj_cheb2_attr[CHEB_MAX_L + 1] = {};
+    bool fwd_cheb2_attr[CHEB_MAX_L + 1][2] = {};
     // launch shapes of the expansion forward chosen by nfm_autotune, per minibatch size
     struct FwdShape { int n_pairs, threads, group, pch, chunks; bool direct; };
     std::vector<FwdShape> fwd_tuned;
@@ -553,6 +554,7 @@ struct ChebShape {
     long long nch;
     size_t smem;
     int occ;                 // resident CTAs per SM (0 when the chunk count was given)
+    int tz = TILE_Z;         // z extent of the voxel blocks: TILE_Z (tiles) or 2 TILE_Z (the adjoint's blocks)
 };
 
 // Default shape (threads = 128, 4 lanes per (pair, tile), pairs per CTA = the power of two >=
@@ -560,9 +562,14 @@ struct ChebShape {
 // chunk), or the one given (`chunks` > 0: any count up to one tile per chunk; a chunk shorter than a
 // stage leaves the stage's remaining slots idle).
 int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int group, int pch, double waves, long long chunks,
-               ChebShape* sh)
+               ChebShape* sh, bool tiles_only = false)
 {
-    const int LT = ctx->cheb_L, KP = ctx->cheb_kpad;
+    // on a regular grid the forward runs over the adjoint's blocks of two tiles along z (same tables)
+    const bool blk = !tiles_only && ctx->cheb_L2 > 0 && !ctx->points &&
+                     fwd_cheb_kernel_ptr(ctx->cheb_L2, group, 2 * TILE_Z) != nullptr;
+    const int LT = blk ? ctx->cheb_L2 : ctx->cheb_L, KP = ctx->cheb_kpad;
+    const int tz = blk ? 2 * TILE_Z : TILE_Z;
+    const long long n_tiles = blk ? ctx->gd2.n_tiles : ctx->gd.n_tiles;
     const int ng = threads / group;
     if (pch <= 0) {
         pch = 4;
@@ -574,15 +581,17 @@ int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int group, int pch, doubl
     sh->threads = threads;
     sh->group = group;
     sh->pch = pch;
-    sh->smem = fwd_cheb_smem_bytes(LT, KP, pch, threads, group, ctx->points);
+    sh->tz = tz;
+    sh->smem = fwd_cheb_smem_bytes(LT, KP, pch, threads, group, ctx->points, tz);
     if (sh->smem > ctx->smem_optin) return fail(ctx, NFM_ERR_ARG, "expansion forward needs %zu B shared memory", sh->smem);
-    const void* fn = fwd_cheb_kernel_ptr(LT, group);
+    const void* fn = fwd_cheb_kernel_ptr(LT, group, tz);
     if (!fn) return fail(ctx, NFM_ERR_ARG, "no expansion forward for L = %d, group %d", LT, group);
-    if (!ctx->fwd_cheb_attr[LT][group == 8]) {
+    bool& attr = blk ? ctx->fwd_cheb2_attr[LT][group == 8] : ctx->fwd_cheb_attr[LT][group == 8];
+    if (!attr) {
         NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctx->smem_optin));
         // all of the unified L1 / shared memory as shared memory: the CTA count per SM is set by shared memory
         NFM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        ctx->fwd_cheb_attr[LT][group == 8] = true;
+        attr = true;
     }
     sh->n_groups = (n_pairs + pch - 1) / pch;
     sh->n_slots = sh->n_groups * pch;
@@ -595,10 +604,10 @@ int cheb_shape(nfm_ctx* ctx, int n_pairs, int threads, int group, int pch, doubl
         sh->occ = occ;
         const long long G = (long long)(waves * ctx->num_sms * occ);
         nch = (G + sh->n_groups - 1) / sh->n_groups;
-        const long long max_ch = (ctx->gd.n_tiles + TS - 1) / TS;
+        const long long max_ch = (n_tiles + TS - 1) / TS;
         if (nch > max_ch) nch = max_ch;
     }
-    if (nch > ctx->gd.n_tiles) nch = ctx->gd.n_tiles;
+    if (nch > n_tiles) nch = n_tiles;
     if (nch > 65535) nch = 65535;
     if (nch < 1) nch = 1;
     sh->nch = nch;
@@ -609,7 +618,14 @@ int launch_cheb_forward_shape(nfm_ctx* ctx, const ChebShape& sh, const int* pair
 {
     const size_t partial_bytes = (size_t)sh.nch * sh.n_slots * ctx->K * sizeof(float2);
     NFM_TRY(ensure(ctx, &ctx->d_partial, &ctx->partial_cap, partial_bytes));
-    ChebDesc cd{ctx->d_cheb, ctx->cheb_tau, ctx->cheb_L, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
+    const bool blk = sh.tz != TILE_Z;        // the adjoint's blocks and their tables
+    ChebDesc cd{blk ? ctx->d_cheb2 : ctx->d_cheb, blk ? ctx->cheb_tau2 : ctx->cheb_tau,
+                blk ? ctx->cheb_L2 : ctx->cheb_L, ctx->cheb_kpad, ctx->cheb_fc_hi, ctx->cheb_fc_lo};
+    OpDesc op = op_desc(ctx);
+    if (blk) {
+        op.g = ctx->gd2;
+        op.ant = ctx->d_ant2;
+    }
     FwdArgs a;
     a.pairs = pairs;
     a.n_pairs = n_pairs;
@@ -618,10 +634,10 @@ int launch_cheb_forward_shape(nfm_ctx* ctx, const ChebShape& sh, const int* pair
     a.partial_elems = (long long)(ctx->partial_cap / sizeof(float2)) / ((ctx->hooks & HOOK_SHRINK_EXTENTS) ? 2 : 1);
     a.n_slots = sh.n_slots;
     a.VS = sh.pch;
-    a.tiles_base = (int)(ctx->gd.n_tiles / sh.nch);
-    a.tiles_rem = (int)(ctx->gd.n_tiles % sh.nch);
-    NFM_CK(launch_fwd_cheb(op_desc(ctx), cd, a, dim3(sh.n_groups, (unsigned)sh.nch), sh.threads, sh.group,
-                           sh.smem, ctx->stream));
+    a.tiles_base = (int)(op.g.n_tiles / sh.nch);
+    a.tiles_rem = (int)(op.g.n_tiles % sh.nch);
+    NFM_CK(launch_fwd_cheb(op, cd, a, dim3(sh.n_groups, (unsigned)sh.nch), sh.threads, sh.group, sh.tz, sh.smem,
+                           ctx->stream));
     return NFM_OK;
 }
 
@@ -1376,7 +1392,7 @@ int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_m
     return NFM_OK;
 }
 
-int nfm_adjoint_info(nfm_ctx* ctx, int* n_terms, int* block_voxels)
+int nfm_expansion_info(nfm_ctx* ctx, int* n_terms, int* block_voxels)
 {
     NFM_TRY(require_geom(ctx));
     const bool blk2 = ctx->cheb_L2 > 0 && !ctx->points;
@@ -2271,10 +2287,10 @@ int batch_fused_enqueue(nfm_batch* b, const float* const* y, float* const* s, co
             bool tuned = false;
             for (const auto& tu : c->fwd_tuned)
                 if (tu.n_pairs == np && tu.threads == CHEB_THREADS && tu.group == CHEB_GROUP) {
-                    NFM_TRY(cheb_shape(c, np, tu.threads, tu.group, tu.pch, 0.0, tu.chunks, &sh));
+                    NFM_TRY(cheb_shape(c, np, tu.threads, tu.group, tu.pch, 0.0, tu.chunks, &sh, true));
                     tuned = true;
                 }
-            if (!tuned) NFM_TRY(cheb_shape(c, np, CHEB_THREADS, CHEB_GROUP, 0, 2.0, 0, &sh));
+            if (!tuned) NFM_TRY(cheb_shape(c, np, CHEB_THREADS, CHEB_GROUP, 0, 2.0, 0, &sh, true));
             const size_t pbytes = (size_t)sh.nch * sh.n_slots * c->K * sizeof(float2);
             NFM_TRY(ensure(c, &c->d_partial, &c->partial_cap, pbytes));
             NFM_TRY(ensure(c, &c->d_resid, &c->resid_cap, (size_t)bp[i] * c->K * sizeof(float2)));

@@ -95,14 +95,15 @@ __host__ __device__ constexpr int fwd_coef_stride(int LT)
 // rows the mirror-folded expansion reads (k < K/2 and, for odd K, the centre row).
 __host__ __device__ constexpr int fwd_coef_rows(int k_pad) { return k_pad / 2 + 1; }
 // points: the geometry has explicit voxel positions (per-stage voxel offsets are staged too)
-size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, bool points = false);
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, bool points = false,
+                           int tz = TILE_Z);
 size_t adj_cheb_smem_bytes(int LT, int k_pad, int tz = TILE_Z);
-const void* fwd_cheb_kernel_ptr(int LT, int group);
+const void* fwd_cheb_kernel_ptr(int LT, int group, int tz = TILE_Z);   // nullptr where not built
 const void* adj_cheb_kernel_ptr(int LT, int tz = TILE_Z);   // nullptr where not built (tz = 8: L <= 24)
 // threads: 64 or 128; group: 4 or 8 lanes per (pair, tile); a.VS = pairs per CTA, a power of two
 // dividing threads / group
 cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
-                            int group, size_t smem, cudaStream_t st);
+                            int group, int tz, size_t smem, cudaStream_t st);
 cudaError_t launch_adj_cheb(const OpDesc& op, const ChebDesc& cd, const AdjArgs& a, int tz, size_t smem,
                             cudaStream_t st);
 // tensor-core (tcgen05) expansion stage of the forward (op_cheb_tc_fwd.cu): 256 threads, a.VS = pairs per

@@ -40,10 +40,11 @@ namespace nfm {
 // per lane and are capped at 72 registers (7 CTAs per SM) so nearly twice the warps stay resident.
 // The CTA body for pair group pg and voxel-tile chunk `chunk` (the single-scene kernel passes blockIdx.x
 // and blockIdx.y; the multi-scene kernel its CTA's position within its scene).
-template <int LT, int G>
+template <int LT, int G, int TZ>
 __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd, const FwdArgs a, int pg,
                                               int chunk, unsigned char* smem)
 {
+    constexpr int TV = TILE_X * TILE_Y * TZ; // voxels of a tile (TZ = TILE_Z) or of a two-tile block (TZ = 8)
     constexpr int LS = (LT + 3) & ~3;        // table row stride (zero entries beyond LT)
     constexpr int LSS = fwd_coef_stride(LT); // its row stride in shared memory
     const int ng = blockDim.x / G;           // groups per CTA
@@ -55,9 +56,9 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     const int CR = fwd_coef_rows(KP);        // table rows held: k <= K/2 (the rest follow by the mirror fold)
     float* coef = reinterpret_cast<float*>(smem);                            // [CR][LSS]
     float2* acc = reinterpret_cast<float2*>(coef + CR * LSS);                // [ng][AS]
-    VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + ng * AS);       // [TILE_V]
-    float2* s_st = reinterpret_cast<float2*>(voff + TILE_V);                 // [2][TS][TILE_V]
-    AntHead* ant_st = reinterpret_cast<AntHead*>(s_st + 2 * TS * TILE_V);    // [2][ng][2]
+    VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + ng * AS);       // [TV]
+    float2* s_st = reinterpret_cast<float2*>(voff + TV);                     // [2][TS][TV]
+    AntHead* ant_st = reinterpret_cast<AntHead*>(s_st + 2 * TS * TV);        // [2][ng][2]
     int* pair_s = reinterpret_cast<int*>(ant_st + 2 * ng * 2);               // [PCH] pair or -1
     // explicit voxel positions: the stage's voxel offsets [2][TS][TILE_V] (16-byte aligned after pair_s)
     VoxelOffset* vox_st = reinterpret_cast<VoxelOffset*>(pair_s + ((PCH + 3) & ~3));
@@ -78,9 +79,10 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     for (int i = tid; i < CR * LS / 4; i += nt)
         reinterpret_cast<float4*>(coef)[(i / (LS / 4)) * (LSS / 4) + i % (LS / 4)] =
             reinterpret_cast<const float4*>(cd.coef)[i];
-    if (!op.g.pts)
-        for (int v = tid; v < TILE_V; v += nt)
-            voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y));
+    const bool pts = TZ == TILE_Z && op.g.pts;   // explicit positions come in 128-voxel tiles only
+    if (!pts)
+        for (int v = tid; v < TV; v += nt)
+            voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y), TZ);
     for (int i = tid; i < ng * AS / 2; i += nt)   // the per-slot spectra start at zero (AS even)
         reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid < PCH) {
@@ -118,7 +120,7 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     };
     auto load_s = [&](int q) {                    // the stage's scene values (zero outside the grid)
         const int buf = q & 1;
-        if (op.g.pts) {                           // explicit positions: voxel n = tile * 128 + slot, and its offset
+        if (pts) {                                // explicit positions: voxel n = tile * 128 + slot, and its offset
             for (int sl = 0; sl < TS; ++sl) {
                 const int tile = t_begin + q * TS + sl;
                 if (tile >= t_end) break;
@@ -132,20 +134,23 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
             return;
         }
         const int v1 = tid + nt;                  // (computed per call: nothing stays live across stages)
-        const int off0 = slot_offset(tid), off1 = v1 < TILE_V ? slot_offset(v1) : 0;
+        const int off0 = slot_offset(tid), off1 = v1 < TV ? slot_offset(v1) : 0;
         int tx, ty, tz;                           // coordinates of the stage's first tile, then stepped
         tile_coords(op.g, t_begin + q * TS, tx, ty, tz);
         for (int sl = 0; sl < TS; ++sl) {
             if (t_begin + q * TS + sl >= t_end) break;   // slots past the chunk stay idle
-            const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TILE_Z;
-            const bool full = x0 + TILE_X <= op.g.nx && y0 + TILE_Y <= op.g.ny && z0 + TILE_Z <= op.g.nz;
-            float2* dst = s_st + (buf * TS + sl) * TILE_V;
+            const int x0 = tx * TILE_X, y0 = ty * TILE_Y, z0 = tz * TZ;
+            const bool full = x0 + TILE_X <= op.g.nx && y0 + TILE_Y <= op.g.ny && z0 + TZ <= op.g.nz;
+            float2* dst = s_st + (buf * TS + sl) * TV;
             const long long obase = ((long long)z0 * op.g.ny + y0) * op.g.nx + x0;   // index of origin in s
-            if (full) {
+            if (full && 2 * nt >= TV) {           // one or two slots per thread, offsets precomputed
                 cp_async_8(dst + tid, a.s + NFM_IDX(obase + off0, op.n_vox, op.err), true);
-                if (v1 < TILE_V) cp_async_8(dst + v1, a.s + NFM_IDX(obase + off1, op.n_vox, op.err), true);
+                if (v1 < TV) cp_async_8(dst + v1, a.s + NFM_IDX(obase + off1, op.n_vox, op.err), true);
+            } else if (full) {
+                for (int v = tid; v < TV; v += nt)
+                    cp_async_8(dst + v, a.s + NFM_IDX(obase + slot_offset(v), op.n_vox, op.err), true);
             } else {
-                for (int v = tid; v < TILE_V; v += nt) {
+                for (int v = tid; v < TV; v += nt) {
                     const int ix = x0 + v % TILE_X, iy = y0 + (v / TILE_X) % TILE_Y, iz = z0 + v / (TILE_X * TILE_Y);
                     const bool in = ix < op.g.nx && iy < op.g.ny && iz < op.g.nz;
                     cp_async_8(dst + v, in ? a.s + NFM_IDX(obase + slot_offset(v), op.n_vox, op.err) : a.s, in);
@@ -180,13 +185,13 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
         if (tile < t_end && pair_s[pl] >= 0) {      // uniform over the group's lanes
             const AntHead* ap = ant_st + (buf * ng + g) * 2;
             const PairTile P = fold_pair_head(ap[0], ap[1]);
-            const float2* sb = s_st + (buf * TS + slot) * TILE_V;
-            const VoxelOffset* vsrc = op.g.pts ? vox_st + (buf * TS + slot) * TILE_V : voff;
+            const float2* sb = s_st + (buf * TS + slot) * TV;
+            const VoxelOffset* vsrc = pts ? vox_st + (buf * TS + slot) * TILE_V : voff;
             float mr[LT], mi[LT];
 #pragma unroll
             for (int l = 0; l < LT; ++l) mr[l] = mi[l] = 0.f;
 #pragma unroll 2
-            for (int i = 0; i < TILE_V / G; ++i) {
+            for (int i = 0; i < TV / G; ++i) {
                 const int v = ln + G * i;
                 const float2 sv = sb[v];
                 const ChebVoxel cv = cheb_voxel(P, vsrc[v], cd.fc_hi, cd.fc_lo);
@@ -312,11 +317,11 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     }
 }
 
-template <int LT, int G>
+template <int LT, int G, int TZ>
 __global__ void __launch_bounds__(CHEB_THREADS, G == 8 ? 7 : 5) fwd_cheb_kernel(OpDesc op, ChebDesc cd, FwdArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    fwd_cheb_body<LT, G>(op, cd, a, blockIdx.x, blockIdx.y, smem);
+    fwd_cheb_body<LT, G, TZ>(op, cd, a, blockIdx.x, blockIdx.y, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -581,7 +586,7 @@ __global__ void __launch_bounds__(CHEB_THREADS, 5) fwd_cheb_multi_kernel(const M
     const ChebDesc cd = items[i].cd;
     const FwdArgs a = items[i].a;
     const int local = (int)blockIdx.x - items[i].cta0, ng = items[i].n_groups;
-    fwd_cheb_body<LT, CHEB_GROUP>(op, cd, a, local % ng, local / ng, smem);
+    fwd_cheb_body<LT, CHEB_GROUP, TILE_Z>(op, cd, a, local % ng, local / ng, smem);
 }
 
 template <int LT>
@@ -650,13 +655,14 @@ __global__ void __launch_bounds__(256) cheb_range_kernel(GridDesc g, AntSetup a,
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, bool points)
+size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, bool points, int tz)
 {
     const int ng = threads / group;
     const int TS = ng / pch;
+    const int TV = TILE_X * TILE_Y * tz;
     return (size_t)fwd_coef_rows(k_pad) * fwd_coef_stride(LT) * sizeof(float) +
-           (size_t)ng * (k_pad + 4) * sizeof(float2) + TILE_V * sizeof(VoxelOffset) +
-           (size_t)2 * TS * TILE_V * sizeof(float2) + (size_t)2 * ng * 2 * sizeof(AntHead) +
+           (size_t)ng * (k_pad + 4) * sizeof(float2) + TV * sizeof(VoxelOffset) +
+           (size_t)2 * TS * TV * sizeof(float2) + (size_t)2 * ng * 2 * sizeof(AntHead) +
            (size_t)((pch + 3) & ~3) * sizeof(int) +
            (points ? (size_t)2 * TS * TILE_V * sizeof(VoxelOffset) : 0);
 }
@@ -669,30 +675,35 @@ size_t adj_cheb_smem_bytes(int LT, int k_pad, int tz)
            (size_t)pch * LS * sizeof(float2) + (size_t)pch * sizeof(PairTile) + (size_t)pch * sizeof(float2);
 }
 
-template <int G>
+template <int G, int TZ>
 const void* fwd_cheb_ptr_g(int LT)
 {
     switch (LT) {
-    case 10: return (const void*)fwd_cheb_kernel<10, G>;
-    case 12: return (const void*)fwd_cheb_kernel<12, G>;
-    case 14: return (const void*)fwd_cheb_kernel<14, G>;
-    case 16: return (const void*)fwd_cheb_kernel<16, G>;
-    case 18: return (const void*)fwd_cheb_kernel<18, G>;
-    case 20: return (const void*)fwd_cheb_kernel<20, G>;
-    case 22: return (const void*)fwd_cheb_kernel<22, G>;
-    case 24: return (const void*)fwd_cheb_kernel<24, G>;
-    case 26: return (const void*)fwd_cheb_kernel<26, G>;
-    case 28: return (const void*)fwd_cheb_kernel<28, G>;
-    case 30: return (const void*)fwd_cheb_kernel<30, G>;
-    case 32: return (const void*)fwd_cheb_kernel<32, G>;
+    case 10: return (const void*)fwd_cheb_kernel<10, G, TZ>;
+    case 12: return (const void*)fwd_cheb_kernel<12, G, TZ>;
+    case 14: return (const void*)fwd_cheb_kernel<14, G, TZ>;
+    case 16: return (const void*)fwd_cheb_kernel<16, G, TZ>;
+    case 18: return (const void*)fwd_cheb_kernel<18, G, TZ>;
+    case 20: return (const void*)fwd_cheb_kernel<20, G, TZ>;
+    case 22: return (const void*)fwd_cheb_kernel<22, G, TZ>;
+    case 24: return (const void*)fwd_cheb_kernel<24, G, TZ>;
+    default: break;
+    }
+    if (TZ != TILE_Z) return nullptr;        // the two-tile blocks are built for L <= 24
+    switch (LT) {
+    case 26: return (const void*)fwd_cheb_kernel<26, G, TILE_Z>;
+    case 28: return (const void*)fwd_cheb_kernel<28, G, TILE_Z>;
+    case 30: return (const void*)fwd_cheb_kernel<30, G, TILE_Z>;
+    case 32: return (const void*)fwd_cheb_kernel<32, G, TILE_Z>;
     default: return nullptr;
     }
 }
 
-const void* fwd_cheb_kernel_ptr(int LT, int group)
+const void* fwd_cheb_kernel_ptr(int LT, int group, int tz)
 {
-    if (group == 4) return fwd_cheb_ptr_g<4>(LT);
-    if (group == 8) return fwd_cheb_ptr_g<8>(LT);
+    if (tz == TILE_Z) return group == 4 ? fwd_cheb_ptr_g<4, TILE_Z>(LT) : group == 8 ? fwd_cheb_ptr_g<8, TILE_Z>(LT) : nullptr;
+    if (tz == 2 * TILE_Z)
+        return group == 4 ? fwd_cheb_ptr_g<4, 2 * TILE_Z>(LT) : group == 8 ? fwd_cheb_ptr_g<8, 2 * TILE_Z>(LT) : nullptr;
     return nullptr;
 }
 
@@ -726,9 +737,9 @@ const void* adj_cheb_kernel_ptr(int LT, int tz)
 }
 
 cudaError_t launch_fwd_cheb(const OpDesc& op, const ChebDesc& cd, const FwdArgs& a, dim3 grid, int threads,
-                            int group, size_t smem, cudaStream_t st)
+                            int group, int tz, size_t smem, cudaStream_t st)
 {
-    const void* fn = fwd_cheb_kernel_ptr(cd.L, group);
+    const void* fn = fwd_cheb_kernel_ptr(cd.L, group, tz);
     if (!fn || (threads != 64 && threads != 128)) return cudaErrorInvalidValue;
     if (a.VS < 1 || (threads / group) % a.VS != 0) return cudaErrorInvalidValue;
     void* args[] = {(void*)&op, (void*)&cd, (void*)&a};

@@ -58,7 +58,7 @@ def load_library(path: str | None = None):
         "nfm_set_precision": (i, [vp, i]),
         "nfm_set_algorithm": (i, [vp, i]),
         "nfm_algorithm_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]),
-        "nfm_adjoint_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "nfm_expansion_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "nfm_cheb_coefficients": (i, [d, d, i, i, vp]),
         "nfm_set_forward_shape": (i, [vp, i, i, i, i, i, i]),
         "nfm_set_group_weight": (i, [vp, d]),
@@ -231,11 +231,11 @@ class Context:
         self._check(self._lib.nfm_algorithm_info(self._h, ctypes.byref(a), ctypes.byref(n), ctypes.byref(z)))
         return {1: "direct", 2: "chebyshev"}[a.value], n.value, z.value
 
-    def adjoint_info(self):
-        """(expansion length, voxels per block) of the FP32 expansion adjoint: blocks of two tiles (256
-        voxels) on a regular grid, the 128-voxel tiles otherwise."""
+    def expansion_info(self):
+        """(expansion length, voxels per block) of the FP32 expansion operator (forward and adjoint): blocks
+        of two tiles (256 voxels) on a regular grid, the 128-voxel tiles otherwise."""
         n, v = ctypes.c_int(), ctypes.c_int()
-        self._check(self._lib.nfm_adjoint_info(self._h, ctypes.byref(n), ctypes.byref(v)))
+        self._check(self._lib.nfm_expansion_info(self._h, ctypes.byref(n), ctypes.byref(v)))
         return n.value, v.value
 
     cheb_coefficients = staticmethod(cheb_coefficients)
