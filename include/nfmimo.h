@@ -163,10 +163,11 @@ int nfm_set_algorithm(nfm_ctx* ctx, int algo);
 int nfm_algorithm_info(nfm_ctx* ctx, int* algo_in_use, int* n_terms, double* z_max);
 
 /* The expansion the FP32 expansion operator (forward and adjoint) uses on this
- * geometry.  On a regular grid it runs over blocks of two tiles along z
- * (8 x 4 x 8 voxels) with their own expansion of n_terms terms.  Otherwise
- * (explicit voxel positions, or a span that needs more terms than the block
- * kernels are built for) it runs over the 8 x 4 x 4 tiles, with the length
+ * geometry.  On a regular grid with at least as many blocks as the GPU has SMs
+ * it runs over blocks of two tiles along z (8 x 4 x 8 voxels) with their own
+ * expansion of n_terms terms.  Otherwise (smaller grids, explicit voxel
+ * positions, or a span that needs more terms than the block kernels are built
+ * for) it runs over the 8 x 4 x 4 tiles, with the length
  * nfm_algorithm_info reports.  The tensor-core modes and the fused batch
  * always use the tiles.  Writes the expansion length and the voxels per block
  * (256 or 128); 0 terms if the expansion is not available.  Any pointer may be

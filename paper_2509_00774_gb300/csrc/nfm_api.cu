@@ -374,8 +374,9 @@ int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, doub
 // The FP32 expansion adjoint's blocks of two tiles along z (8 x 4 x 8 voxels, regular grids): a grid
 // descriptor over the blocks, the FP64 antenna-block rows (centres given explicitly to ant_setup_kernel)
 // and an expansion table for the larger span.  |d - d_c| <= |u| (triangle inequality), so the block's
-// corner offset bounds delta.  Leaves cheb_L2 = 0 (the adjoint stays on the tiles) where the span needs
-// more terms than the block kernels are built for.
+// corner offset bounds delta.  Leaves cheb_L2 = 0 (the operator stays on the tiles) where the span needs
+// more terms than the block kernels are built for, or where the grid has fewer blocks than the GPU has
+// SMs (small grids keep twice the CTAs of the tiles).
 int setup_blocks2(nfm_ctx* ctx, const nfm_grid& g, const GridDesc& gd, const AntSetup& as, int K, double df, double c)
 {
     constexpr int TZ2 = 2 * TILE_Z;
@@ -384,6 +385,7 @@ int setup_blocks2(nfm_ctx* ctx, const nfm_grid& g, const GridDesc& gd, const Ant
     g2.n_tiles = g2.tiles_x * g2.tiles_y * g2.tiles_z;
     g2.mx = tile_div_magic(g2.n_tiles, g2.tiles_x);
     g2.my = tile_div_magic(g2.n_tiles, g2.tiles_y);
+    if (g2.n_tiles < ctx->num_sms) return NFM_OK;
     const double hx = 0.5 * (TILE_X - 1) * g.dx, hy = 0.5 * (TILE_Y - 1) * g.dy, hz = 0.5 * (TZ2 - 1) * g.dz;
     const double span = 2.0 * std::sqrt(hx * hx + hy * hy + hz * hz);
     const double margin = 0.95;
