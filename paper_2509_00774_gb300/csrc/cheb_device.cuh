@@ -14,11 +14,12 @@ struct ChebVoxel {
     float amp, th0, delta;
 };
 
-__device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelOffset& o, float fc_hi, float fc_lo)
+// ... from the voxel's q = d^2 - d_c^2 to the TX (qT) and the RX (qR) antenna
+__device__ __forceinline__ ChebVoxel cheb_voxel_q(const PairTile& pt, float qT, float qR, float fc_hi, float fc_lo)
 {
     float rsT, rsR;
-    const float dT = antenna_delta(pt.vTx, pt.vTy, pt.vTz, pt.dcT, pt.dcT2, o, rsT);
-    const float dR = antenna_delta(pt.vRx, pt.vRy, pt.vRz, pt.dcR, pt.dcR2, o, rsR);
+    const float dT = antenna_delta_q(qT, pt.dcT, pt.dcT2, rsT);
+    const float dR = antenna_delta_q(qR, pt.dcR, pt.dcR2, rsR);
     ChebVoxel c;
     c.delta = dT + dR;
     c.amp = INV_4PI * rsT * rsR;
@@ -28,6 +29,14 @@ __device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelO
     const float th = (pt.B + (p - rintf(p))) + fmaf(fc_lo, c.delta, pe);
     c.th0 = frac_turns(th);
     return c;
+}
+
+// ... from the voxel's offset u to the tile centre: q = |u|^2 - 2 v.u, v = r_a - r_c
+__device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelOffset& o, float fc_hi, float fc_lo)
+{
+    const float qT = fmaf(-2.0f, fmaf(pt.vTx, o.ux, fmaf(pt.vTy, o.uy, pt.vTz * o.uz)), o.uu);
+    const float qR = fmaf(-2.0f, fmaf(pt.vRx, o.ux, fmaf(pt.vRy, o.uy, pt.vRz * o.uz)), o.uu);
+    return cheb_voxel_q(pt, qT, qR, fc_hi, fc_lo);
 }
 
 // (cos, sin)(2 pi k df D_c / c) from the reduced step phase S = S_hi + S_lo of the

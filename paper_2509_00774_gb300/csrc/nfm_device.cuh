@@ -231,15 +231,21 @@ struct PVGeom {
     float dth2;  // K2 df D / c       (turns, reduced)
 };
 
-__device__ __forceinline__ float antenna_delta(float vx, float vy, float vz, float dc, float dc2,
-                                               const VoxelOffset& o, float& rs)
+// d - dc and 1/d from q = d^2 - dc^2 (no cancellation: d - dc = q / (dc + d))
+__device__ __forceinline__ float antenna_delta_q(float q, float dc, float dc2, float& rs)
 {
-    float vu = fmaf(vx, o.ux, fmaf(vy, o.uy, vz * o.uz));
-    float q = fmaf(-2.0f, vu, o.uu);           // d^2 - dc^2
     float d2 = dc2 + q;
     rs = rsqrtf(d2);                           // 1/d
     float d = d2 * rs;
     return __fdividef(q, dc + d);              // d - dc
+}
+
+__device__ __forceinline__ float antenna_delta(float vx, float vy, float vz, float dc, float dc2,
+                                               const VoxelOffset& o, float& rs)
+{
+    float vu = fmaf(vx, o.ux, fmaf(vy, o.uy, vz * o.uz));
+    float q = fmaf(-2.0f, vu, o.uu);           // d^2 - dc^2 = |u|^2 - 2 v.u
+    return antenna_delta_q(q, dc, dc2, rs);
 }
 
 __device__ __forceinline__ PVGeom pair_voxel(const PairTile& pt, const VoxelOffset& o, const PhaseConsts& ph)

@@ -56,10 +56,9 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     const int CR = fwd_coef_rows(KP);        // table rows held: k <= K/2 (the rest follow by the mirror fold)
     float* coef = reinterpret_cast<float*>(smem);                            // [CR][LSS]
     float2* acc = reinterpret_cast<float2*>(coef + CR * LSS);                // [ng][AS]
-    VoxelOffset* voff = reinterpret_cast<VoxelOffset*>(acc + ng * AS);       // [TV]
-    float2* s_st = reinterpret_cast<float2*>(voff + TV);                     // [2][TS][TV]
-    AntHead* ant_st = reinterpret_cast<AntHead*>(s_st + 2 * TS * TV);        // [2][ng][2]
-    int* pair_s = reinterpret_cast<int*>(ant_st + 2 * ng * 2);               // [PCH] pair or -1
+    float2* s_st = reinterpret_cast<float2*>(acc + ng * AS);                 // [2][TS][TV]
+    AntHead* ant_st = reinterpret_cast<AntHead*>(s_st + 2 * TS * TV);        // [ng][2], one stage
+    int* pair_s = reinterpret_cast<int*>(ant_st + ng * 2);                   // [PCH] pair or -1
     // explicit voxel positions: the stage's voxel offsets [2][TS][TILE_V] (16-byte aligned after pair_s)
     VoxelOffset* vox_st = reinterpret_cast<VoxelOffset*>(pair_s + ((PCH + 3) & ~3));
 
@@ -80,9 +79,6 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
         reinterpret_cast<float4*>(coef)[(i / (LS / 4)) * (LSS / 4) + i % (LS / 4)] =
             reinterpret_cast<const float4*>(cd.coef)[i];
     const bool pts = TZ == TILE_Z && op.g.pts;   // explicit positions come in 128-voxel tiles only
-    if (!pts)
-        for (int v = tid; v < TV; v += nt)
-            voff[v] = voxel_offset(op.g, v % TILE_X, (v / TILE_X) % TILE_Y, v / (TILE_X * TILE_Y), TZ);
     for (int i = tid; i < ng * AS / 2; i += nt)   // the per-slot spectra start at zero (AS even)
         reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid < PCH) {
@@ -97,7 +93,6 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
     __syncthreads();
 
     auto load_geom = [&](int q) {                 // the leading 32 B of the two antenna-tile rows of every group
-        const int buf = q & 1;
         for (int i = tid; i < ng * 4; i += nt) {
             const int gi = i / 4, part = i % 4;
             const int tile = t_begin + q * TS + gi / PCH;
@@ -105,7 +100,7 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
             if (tile < t_end && pair >= 0) {
                 const AntTile *at, *ar;
                 pair_rows(op, pair, tile, at, ar);
-                AntHead* dst = ant_st + (buf * ng + gi) * 2 + (part < 2 ? 0 : 1);
+                AntHead* dst = ant_st + gi * 2 + (part < 2 ? 0 : 1);
                 cp_async_16(reinterpret_cast<float4*>(dst) + part % 2,
                             reinterpret_cast<const float4*>(part < 2 ? at : ar) + part % 2);
             }
@@ -175,26 +170,24 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
         __syncthreads();
     }
     for (int q = 0; q < n_stages; ++q) {
+        const int buf = q & 1;
+        const int tile = t_begin + q * TS + slot;
+        const bool live = tile < t_end && pair_s[pl] >= 0;   // uniform over the group's lanes
+        PairTile P;
+        if (live) P = fold_pair_head(ant_st[g * 2], ant_st[g * 2 + 1]);
         if (q + 1 < n_stages) {
+            __syncthreads();                 // every group holds its heads: the buffer takes the next stage's
             load_geom(q + 1);
             load_s(q + 1);
             cp_async_commit();
         }
-        const int buf = q & 1;
-        const int tile = t_begin + q * TS + slot;
-        if (tile < t_end && pair_s[pl] >= 0) {      // uniform over the group's lanes
-            const AntHead* ap = ant_st + (buf * ng + g) * 2;
-            const PairTile P = fold_pair_head(ap[0], ap[1]);
+        if (live) {
             const float2* sb = s_st + (buf * TS + slot) * TV;
-            const VoxelOffset* vsrc = pts ? vox_st + (buf * TS + slot) * TILE_V : voff;
             float mr[LT], mi[LT];
 #pragma unroll
             for (int l = 0; l < LT; ++l) mr[l] = mi[l] = 0.f;
-#pragma unroll 2
-            for (int i = 0; i < TV / G; ++i) {
-                const int v = ln + G * i;
-                const float2 sv = sb[v];
-                const ChebVoxel cv = cheb_voxel(P, vsrc[v], cd.fc_hi, cd.fc_lo);
+            // m_l += u_v T_l(t_v), u_v = amp_v s_v e^{-j 2 pi (f0 D_c + f_c delta_v)/c}, t_v = delta_v / xi
+            auto add_voxel = [&](const float2 sv, const ChebVoxel& cv) {
                 const float2 c0 = cis_turns_sfu(cv.th0);
                 const float2 u = cmul_conj(make_float2(cv.amp * sv.x, cv.amp * sv.y), c0);
                 const float t = cv.delta * cd.tau;
@@ -211,6 +204,43 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
                     mi[l] = fmaf(u.y, Tn, mi[l]);
                     Tp = Tc;
                     Tc = Tn;
+                }
+            };
+            if (pts) {
+                const VoxelOffset* vsrc = vox_st + (buf * TS + slot) * TILE_V;
+#pragma unroll 2
+                for (int i = 0; i < TILE_V / G; ++i) {
+                    const int v = ln + G * i;
+                    add_voxel(sb[v], cheb_voxel(P, vsrc[v], cd.fc_hi, cd.fc_lo));
+                }
+            } else {
+                // On the grid, q = d^2 - d_c^2 = |u|^2 - 2 v.u splits over the axes into the sum of
+                // w (w - 2 v_w), w = u_x, u_y, u_z.  The lane's voxels are the columns lx = ln + G a of every
+                // row (ly, lz), in x-fastest order: the x terms are formed once per (pair, block), the z terms
+                // once per plane and the y terms once per row.
+                constexpr int NA = TILE_X / G;
+                float xT[NA], xR[NA];
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    const float ux = voxel_offset(op.g, ln + G * a, 0, 0, TZ).ux;
+                    xT[a] = ux * fmaf(-2.f, P.vTx, ux);
+                    xR[a] = ux * fmaf(-2.f, P.vRx, ux);
+                }
+#pragma unroll 1
+                for (int lz = 0; lz < TZ; ++lz) {
+                    const float uz = voxel_offset(op.g, 0, 0, lz, TZ).uz;
+                    const float zT = uz * fmaf(-2.f, P.vTz, uz), zR = uz * fmaf(-2.f, P.vRz, uz);
+#pragma unroll
+                    for (int ly = 0; ly < TILE_Y; ++ly) {
+                        const float uy = voxel_offset(op.g, 0, ly, 0, TZ).uy;
+                        const float yzT = fmaf(uy, fmaf(-2.f, P.vTy, uy), zT);
+                        const float yzR = fmaf(uy, fmaf(-2.f, P.vRy, uy), zR);
+#pragma unroll
+                        for (int a = 0; a < NA; ++a) {
+                            const int v = ln + G * a + TILE_X * (ly + TILE_Y * lz);
+                            add_voxel(sb[v], cheb_voxel_q(P, xT[a] + yzT, xR[a] + yzR, cd.fc_hi, cd.fc_lo));
+                        }
+                    }
                 }
             }
             // all-reduce over the group's lanes (the same sum order in every lane)
@@ -661,8 +691,8 @@ size_t fwd_cheb_smem_bytes(int LT, int k_pad, int pch, int threads, int group, b
     const int TS = ng / pch;
     const int TV = TILE_X * TILE_Y * tz;
     return (size_t)fwd_coef_rows(k_pad) * fwd_coef_stride(LT) * sizeof(float) +
-           (size_t)ng * (k_pad + 4) * sizeof(float2) + TV * sizeof(VoxelOffset) +
-           (size_t)2 * TS * TV * sizeof(float2) + (size_t)2 * ng * 2 * sizeof(AntHead) +
+           (size_t)ng * (k_pad + 4) * sizeof(float2) +
+           (size_t)2 * TS * TV * sizeof(float2) + (size_t)ng * 2 * sizeof(AntHead) +
            (size_t)((pch + 3) & ~3) * sizeof(int) +
            (points ? (size_t)2 * TS * TILE_V * sizeof(VoxelOffset) : 0);
 }
