@@ -23,10 +23,10 @@ __device__ __forceinline__ ChebVoxel cheb_voxel_q(const PairTile& pt, float qT, 
     ChebVoxel c;
     c.delta = dT + dR;
     c.amp = INV_4PI * rsT * rsR;
-    // B = f_0 D_c / c (reduced) plus f_c delta / c with an exact product split: one rounding at |x| <= 1
-    const float p = fc_hi * c.delta;
-    const float pe = fmaf(fc_hi, c.delta, -p);
-    const float th = (pt.B + (p - rintf(p))) + fmaf(fc_lo, c.delta, pe);
+    // B = f_0 D_c / c (reduced) plus f_c delta / c: the fused fc_hi delta - n, n the integer nearest the
+    // product, rounds once at |x| <= 1/2 (f_c / c = fc_hi + fc_lo)
+    const float n = rintf(fc_hi * c.delta);
+    const float th = fmaf(fc_lo, c.delta, pt.B + fmaf(fc_hi, c.delta, -n));
     c.th0 = frac_turns(th);
     return c;
 }
@@ -39,16 +39,40 @@ __device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelO
     return cheb_voxel_q(pt, qT, qR, fc_hi, fc_lo);
 }
 
+// The pair tile as the adjoint uses it: antenna vectors scaled by -2 (exact), for cheb_voxel_m2 below, and
+// the base phase advanced by k_c steps, B + k_c S (k_c = (K - 1)/2, the band centre), so that the
+// residual phasors can run from the band centre: conj(P_k) = e^{+j 2 pi k_c S} e^{+j 2 pi (k - k_c) S}.
+__device__ __forceinline__ PairTile pair_tile_adj(PairTile p, int K)
+{
+    p.vTx *= -2.f; p.vTy *= -2.f; p.vTz *= -2.f;
+    p.vRx *= -2.f; p.vRy *= -2.f; p.vRz *= -2.f;
+    const float kc = 0.5f * (float)(K - 1);
+    const float q = kc * p.S_hi;
+    const float e = fmaf(kc, p.S_hi, -q);
+    p.B = frac_turns((p.B + (q - rintf(q))) + fmaf(kc, p.S_lo, e));
+    return p;
+}
+
+// cheb_voxel of a pair tile from pair_tile_adj: q = |u|^2 + (-2 v).u in three FMAs per antenna
+__device__ __forceinline__ ChebVoxel cheb_voxel_m2(const PairTile& pm, const VoxelOffset& o, float fc_hi, float fc_lo)
+{
+    const float qT = fmaf(pm.vTx, o.ux, fmaf(pm.vTy, o.uy, fmaf(pm.vTz, o.uz, o.uu)));
+    const float qR = fmaf(pm.vRx, o.ux, fmaf(pm.vRy, o.uy, fmaf(pm.vRz, o.uz, o.uu)));
+    return cheb_voxel_q(pm, qT, qR, fc_hi, fc_lo);
+}
+
 // (cos, sin)(2 pi k df D_c / c) from the reduced step phase S = S_hi + S_lo of the
 // pair tile: k S_hi split exactly (FMA remainder), so one rounding at |x| <= 1/2.
-__device__ __forceinline__ float2 tile_step_cis(const PairTile& pt, int k)
+// (kf: an integer or half-integer step count)
+__device__ __forceinline__ float2 tile_step_cis_f(const PairTile& pt, float kf)
 {
-    const float kf = (float)k;
     const float p = kf * pt.S_hi;
     const float e = fmaf(kf, pt.S_hi, -p);
     const float ph = (p - rintf(p)) + fmaf(kf, pt.S_lo, e);
     return cis_turns_sfu(ph);
 }
+
+__device__ __forceinline__ float2 tile_step_cis(const PairTile& pt, int k) { return tile_step_cis_f(pt, (float)k); }
 
 // The same phasor from the Taylor-series cis_turns (error ~1e-7), for a step that a recurrence repeats.
 __device__ __forceinline__ float2 tile_step_cis_exact(const PairTile& pt, int k)

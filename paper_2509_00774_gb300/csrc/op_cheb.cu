@@ -373,7 +373,7 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
     const int RS = KP + 2;                   // r' row stride (float2), staggers the banks
     float2* rp = reinterpret_cast<float2*>(coef + KP * LS);               // [PCH][RS]
     float2* Cs = rp + PCH * RS;                                             // [PCH][LS]
-    PairTile* pt = reinterpret_cast<PairTile*>(Cs + PCH * LS);              // [PCH]
+    PairTile* pt = reinterpret_cast<PairTile*>(Cs + PCH * LS);              // [PCH], as pair_tile_adj leaves them
     float2* w16 = reinterpret_cast<float2*>(pt + PCH);                      // [PCH] e^{+j 2 pi 16 df D_c/c}
 
     const int tid = threadIdx.x;
@@ -397,7 +397,7 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
     // the pair list and the geometry tables are never written by this library's kernels, so the
     // first chunk's pair tiles are read before the wait on the previous kernel
     if (tid < min(PCH, a.n_pairs)) {
-        pt[tid] = load_pair_tile(op, a.pairs[tid], tile);
+        pt[tid] = pair_tile_adj(load_pair_tile(op, a.pairs[tid], tile), K);
         w16[tid] = tile_step_cis_exact(pt[tid], 16);
     }
     pdl_wait();                              // r comes from the previous kernel
@@ -416,7 +416,7 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
         if (c0 > 0) {
             __syncthreads();
             if (tid < nc) {
-                pt[tid] = load_pair_tile(op, a.pairs[c0 + tid], tile);
+                pt[tid] = pair_tile_adj(load_pair_tile(op, a.pairs[c0 + tid], tile), K);
                 w16[tid] = tile_step_cis_exact(pt[tid], 16);
             }
         }
@@ -435,20 +435,23 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();                     // pt and w16 of this chunk
-        // r'_k = conj(p_k) r_k e^{+j 2 pi k df D_c/c} for k and its mirror K-1-k, folded in place into
+        // r'_k = conj(p_k) r_k e^{+j 2 pi (k - k_c) S}, S = df D_c/c, for k and its mirror K-1-k, folded in place into
         // u_k = r'_k + r'_{K-1-k} (stored at k) and v_k = r'_k - r'_{K-1-k} (stored at K-1-k), k < K/2; for odd K
         // the centre row k_c = K/2 keeps r'.  The band-centred table is mirror-symmetric,
         // b_l(K-1-k) = (-1)^l b_l(k), so C_l needs only b_l(k) u_k (even l) and b_l(k) v_k (odd l) over half the
         // band.  A thread owns both slots of its k, so no barrier separates the transform from the fold.
-        // Phasors: an SFU start each for k0 and K-1-k0, then the pair's exact 16-step phasor up and its
-        // conjugate down (at most 4 steps).
+        // Phasors run from the band centre (the pair tile's base phase carries e^{+j 2 pi k_c S}): k takes
+        // c = e^{+j 2 pi (k - k_c) S} and its mirror K-1-k the conjugate, so with A = x + y, B = x - y
+        //   u = x c + y conj(c) = (c_r A_r - c_i B_i, c_r A_i + c_i B_r),
+        //   v = x c - y conj(c) = (c_r B_r - c_i A_i, c_r B_i + c_i A_r).
+        // c starts from an SFU phasor at k0 and steps by the pair's exact 16-step phasor (at most 4 steps);
+        // the centre row of odd K takes c = 1.
         const int KH = K / 2;
+        const float kc = 0.5f * (float)(K - 1);
         for (int j = tid / 16; j < nc; j += TV / 16) {
-            const PairTile& P = pt[j];
             const float2 W = w16[j];
-            const float2 Wc = make_float2(W.x, -W.y);
             float2* row = rp + j * RS;
-            float2 cu = tile_step_cis(P, k0), cd = tile_step_cis(P, K - 1 - k0);
+            float2 c = tile_step_cis_f(pt[j], (float)k0 - kc);
             for (int k = k0; k < KH; k += 16) {
                 const int km = K - 1 - k;
                 float2 x = row[k], y = row[km];
@@ -456,18 +459,12 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
                     x = cmul_conj(x, op.pulse[k]);
                     y = cmul_conj(y, op.pulse[km]);
                 }
-                x = cmul(x, cu);
-                y = cmul(y, cd);
-                row[k] = make_float2(x.x + y.x, x.y + y.y);
-                row[km] = make_float2(x.x - y.x, x.y - y.y);
-                cu = cmul(cu, W);
-                cd = cmul(cd, Wc);
+                const float Ar = x.x + y.x, Ai = x.y + y.y, Br = x.x - y.x, Bi = x.y - y.y;
+                row[k] = make_float2(fmaf(c.x, Ar, -c.y * Bi), fmaf(c.x, Ai, c.y * Br));
+                row[km] = make_float2(fmaf(c.x, Br, -c.y * Ai), fmaf(c.x, Bi, c.y * Ar));
+                c = cmul(c, W);
             }
-            if ((K & 1) && k0 == KH % 16) {  // centre row (its own mirror)
-                float2 x = row[KH];
-                if (op.pulse) x = cmul_conj(x, op.pulse[KH]);
-                row[KH] = cmul(x, tile_step_cis(P, KH));
-            }
+            if ((K & 1) && op.pulse && k0 == KH % 16) row[KH] = cmul_conj(row[KH], op.pulse[KH]);   // centre row
         }
         __syncthreads();
         // C_l = j^l sum_k b_l(k) r'_k = j^l [sum_{k < K/2} b_l(k) (u_k or v_k) + b_l(k_c) r'_{k_c}], four l per task,
@@ -528,7 +525,7 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
         // per voxel: sum over the chunk's pairs of conj(u') sum_l T_l(t) C_l; the geometry of pair
         // j+1 is computed next to the recurrence of pair j (independent instructions)
         auto stage_pair = [&](int j, float2& w, float& t) {
-            const ChebVoxel cv = cheb_voxel(pt[j], o, cd.fc_hi, cd.fc_lo);
+            const ChebVoxel cv = cheb_voxel_m2(pt[j], o, cd.fc_hi, cd.fc_lo);
             const float2 c0v = cis_turns_sfu(cv.th0);
             w = make_float2(cv.amp * c0v.x, cv.amp * c0v.y);
             t = cv.delta * cd.tau;
@@ -562,6 +559,7 @@ __device__ __forceinline__ void adj_cheb_body(const OpDesc op, const ChebDesc cd
             gi = fmaf(wj.x, ai, fmaf(wj.y, ar, gi));
         };
         stage_pair(0, w, t);
+#pragma unroll 2
         for (int j = 0; j + 1 < nc; ++j) {   // the last pair is peeled: nothing left to stage
             float2 wn;
             float tn;
