@@ -145,7 +145,7 @@ int nfm_set_precision(nfm_ctx* ctx, int mode);
  *                         exp(-j z_k t) = sum_{l<L} (-j)^l b_l(z_k) T_l(t),
  *                       b_0 = J_0, b_l = 2 J_l (Jacobi-Anger), L even in
  *                       [10, 32] chosen at nfm_set_geometry so the dropped tail
- *                       is below 1e-7 at the band edges; per (pair, voxel) the work is
+ *                       is below 2e-6 at the band edges; per (pair, voxel) the work is
  *                       L recurrence steps instead of K terms (relative error ~2e-6,
  *                       as DIRECT);
  *   NFM_ALGO_AUTO       CHEBYSHEV where the geometry allows it (L <= 32), else

@@ -275,6 +275,12 @@ unsigned tile_div_magic(long long n_max, int d)
     return (unsigned)((1ull << 32) / (unsigned long long)d + 1ull);
 }
 
+// Truncation budget of the expansion: the dropped terms' coefficients at the band edge, sum_{l >= L}
+// |b_l(z_max)|, bound the relative error of every element (|T_l(t)| <= 1); 2e-6 keeps it a fifth of the
+// FP32 operator's 1e-5 relative bound and of the order of the FP32 rounding error, and well below it in
+// the mean over the band (the tail falls fast as |z| drops from the edge).
+constexpr double CHEB_TAIL = 2e-6;
+
 void cheb_coefficients(double z_step, double k_center, int K, int L, double* out)
 {
     const double pi = 3.14159265358979323846;
@@ -313,7 +319,7 @@ void cheb_coefficients(double z_step, double k_center, int K, int L, double* out
 // delta = D - D_c over every (pair, tile), the scale tau with |t| <= 0.95, the
 // band centre k_c = (K - 1)/2 (the expansion covers e^{-j z_k t} with
 // z_k = (k - k_c) z_step, |z_k| <= z_step (K - 1)/2), the number of terms L
-// (even, tail below 1e-7 at the band edges) and the table.
+// (even, tail below CHEB_TAIL at the band edges) and the table.
 int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, double f0, double df, double c)
 {
     unsigned long long* d_mx = nullptr;
@@ -341,7 +347,7 @@ int setup_cheb(nfm_ctx* ctx, const GridDesc& gd, const AntSetup& as, int K, doub
     for (int cand = CHEB_MIN_L; cand <= CHEB_MAX_L; cand += 2) {
         double tail = 0.0;
         for (int l = cand; l < LP; ++l) tail += std::fabs(probe[LP + l]);
-        if (tail < 1e-7) {
+        if (tail < CHEB_TAIL) {
             L = cand;
             break;
         }
@@ -398,7 +404,7 @@ int setup_blocks2(nfm_ctx* ctx, const nfm_grid& g, const GridDesc& gd, const Ant
     for (int cand = CHEB_MIN_L; cand <= CHEB_MAX_L; cand += 2) {
         double tail = 0.0;
         for (int l = cand; l < LP; ++l) tail += std::fabs(probe[LP + l]);
-        if (tail < 1e-7) {
+        if (tail < CHEB_TAIL) {
             L = cand;
             break;
         }

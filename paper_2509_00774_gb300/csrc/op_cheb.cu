@@ -15,7 +15,7 @@
 //
 //   e^{-j z t} = sum_l (-j)^l b_l(z) T_l(t),   b_0 = J_0(z),  b_l = 2 J_l(z),
 //
-// truncated after L terms (L even, tail below 1e-7 at the band edges |z| = z_max;
+// truncated after L terms (L even, tail below 2e-6 at the band edges |z| = z_max;
 // centring halves z_max and with it the number of terms).  So per (pair, tile)
 //
 //   forward:  y_k += P_k sum_l (-j)^l b_l(k) m_l,  m_l = sum_v u_v T_l(t_v),
