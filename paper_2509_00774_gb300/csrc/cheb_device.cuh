@@ -14,12 +14,10 @@ struct ChebVoxel {
     float amp, th0, delta;
 };
 
-// ... from the voxel's q = d^2 - d_c^2 to the TX (qT) and the RX (qR) antenna
-__device__ __forceinline__ ChebVoxel cheb_voxel_q(const PairTile& pt, float qT, float qR, float fc_hi, float fc_lo)
+// ... from d - d_c (dT, dR) and 1/d (rsT, rsR) of the TX and the RX antenna
+__device__ __forceinline__ ChebVoxel cheb_voxel_d(const PairTile& pt, float dT, float rsT, float dR, float rsR,
+                                                  float fc_hi, float fc_lo)
 {
-    float rsT, rsR;
-    const float dT = antenna_delta_q(qT, pt.dcT, pt.dcT2, rsT);
-    const float dR = antenna_delta_q(qR, pt.dcR, pt.dcR2, rsR);
     ChebVoxel c;
     c.delta = dT + dR;
     c.amp = INV_4PI * rsT * rsR;
@@ -31,12 +29,23 @@ __device__ __forceinline__ ChebVoxel cheb_voxel_q(const PairTile& pt, float qT, 
     return c;
 }
 
-// ... from the voxel's offset u to the tile centre: q = |u|^2 - 2 v.u, v = r_a - r_c
+// ... from the voxel's q = d^2 - d_c^2 to the TX (qT) and the RX (qR) antenna
+__device__ __forceinline__ ChebVoxel cheb_voxel_q(const PairTile& pt, float qT, float qR, float fc_hi, float fc_lo)
+{
+    float rsT, rsR;
+    const float dT = antenna_delta_q(qT, pt.dcT, pt.dcT2, rsT);
+    const float dR = antenna_delta_q(qR, pt.dcR, pt.dcR2, rsR);
+    return cheb_voxel_d(pt, dT, rsT, dR, rsR, fc_hi, fc_lo);
+}
+
+// ... from the voxel's offset u to the tile centre: q = |u|^2 - 2 v.u, v = r_a - r_c (one antenna after
+// the other: the tensor-core forward measured 10% slower with both q formed first)
 __device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelOffset& o, float fc_hi, float fc_lo)
 {
-    const float qT = fmaf(-2.0f, fmaf(pt.vTx, o.ux, fmaf(pt.vTy, o.uy, pt.vTz * o.uz)), o.uu);
-    const float qR = fmaf(-2.0f, fmaf(pt.vRx, o.ux, fmaf(pt.vRy, o.uy, pt.vRz * o.uz)), o.uu);
-    return cheb_voxel_q(pt, qT, qR, fc_hi, fc_lo);
+    float rsT, rsR;
+    const float dT = antenna_delta(pt.vTx, pt.vTy, pt.vTz, pt.dcT, pt.dcT2, o, rsT);
+    const float dR = antenna_delta(pt.vRx, pt.vRy, pt.vRz, pt.dcR, pt.dcR2, o, rsR);
+    return cheb_voxel_d(pt, dT, rsT, dR, rsR, fc_hi, fc_lo);
 }
 
 // The pair tile as the adjoint uses it: antenna vectors scaled by -2 (exact), for cheb_voxel_m2 below, and
