@@ -150,6 +150,50 @@ def test_random_geometries_match_oracle(seed):
         assert_close_operator(g[cols], want_g, "adjoint", scale_g)
 
 
+def test_block_expansion_on_a_ragged_anisotropic_grid():
+    """The 256-voxel block kernels (two tiles along z) on a grid whose blocks do not tile it (62 x 41 x 21
+    voxels: partial blocks in x, y and z) with three different spacings, so that the per-axis terms of the
+    forward's distance split and the blocks' edge handling are exercised: forward rows, adjoint voxels
+    (edge voxels included) and one fused SPGM step against the oracle."""
+    from tests.gpu_helpers import assert_close_operator
+    rng = np.random.default_rng(77)
+    T, R, K = 6, 5, 24
+    tx = np.concatenate([rng.uniform(-0.15, 0.15, (T, 2)), np.zeros((T, 1))], 1)
+    rx = np.concatenate([rng.uniform(-0.15, 0.15, (R, 2)), np.zeros((R, 1))], 1)
+    nx, ny, nz, dx, dy, dz = 62, 41, 21, 0.0030, 0.0034, 0.0026
+    grid = I.Grid(-nx * dx / 2, -ny * dy / 2, 0.30, dx, dy, dz, nx, ny, nz)
+    geom = I.Geometry(tx, rx, I.uniform_freqs(60e9, 68e9, K), grid)
+    o = Oracle(geom)
+    ctx = make_ctx(geom, algorithm="chebyshev")
+    n_terms, block = ctx.expansion_info()
+    print(f"[cheb] ragged anisotropic grid: L = {n_terms}, {block}-voxel blocks")
+    assert block == 256
+    pairs = rng.permutation(geom.P)[:24]
+    s = (I.complex_gaussian(geom.N, 78)).astype(np.complex64).astype(np.complex128)
+    r = (I.complex_gaussian(pairs.size * K, 79)).astype(np.complex64).astype(np.complex128)
+    rows = o.rows_of_pairs(pairs)
+    ridx = np.sort(rng.choice(rows.size, 64, replace=False))
+    ix, iy, iz = np.meshgrid([0, nx - 1], [0, ny - 1], [0, nz - 1], indexing="ij")
+    edge = ((iz * ny + iy) * nx + ix).reshape(-1)
+    cols = np.unique(np.concatenate([edge, rng.choice(geom.N, 248, replace=False)]))
+    y = to_host(ctx.forward(to_dev(pairs, "int32"), to_dev(s)))
+    g = to_host(ctx.adjoint(to_dev(pairs, "int32"), to_dev(r)))
+    scale_y = np.sqrt((np.abs(o.dense(rows[ridx], np.arange(geom.N))) ** 2) @ (np.abs(s) ** 2))
+    scale_g = np.sqrt((np.abs(o.dense(rows, cols).T) ** 2) @ (np.abs(r) ** 2))
+    assert_close_operator(y[ridx], o.forward(s, rows=rows[ridx]), "forward", scale_y)
+    assert_close_operator(g[cols], o.adjoint(r, rows=rows, cols=cols), "adjoint", scale_g)
+    y_obs = (I.complex_gaussian(geom.P * K, 80) * 1e-3).astype(np.complex64).astype(np.complex128)
+    s0 = (I.complex_gaussian(geom.N, 81) * 0.05).astype(np.complex64).astype(np.complex128)
+    eta, lam = 0.05, 0.4                      # the prox zeroes about 15% of the voxels
+    s_d = to_dev(s0)
+    ctx.spgm_step(to_dev(y_obs), s_d, to_dev(pairs, "int32"), eta, lam)
+    want = o.spgm_step(y_obs, s0, pairs, eta, lam)
+    assert 0.05 < np.mean(want == 0) < 0.5
+    err = nmse(to_host(s_d), want)
+    print(f"[parity] SPGM step, ragged anisotropic grid: NMSE {err:.2e}")
+    assert err <= NMSE_TOL
+
+
 @pytest.mark.parametrize("name", ["mid", "small"])
 def test_spgm_step_matches_composed_calls(name):
     """The fused SPGM step (forward with the residual in its reduction, adjoint with the gradient
