@@ -154,10 +154,11 @@ def test_block_expansion_on_a_ragged_anisotropic_grid():
     """The 256-voxel block kernels (two tiles along z) on a grid whose blocks do not tile it (62 x 41 x 21
     voxels: partial blocks in x, y and z) with three different spacings, so that the per-axis terms of the
     forward's distance split and the blocks' edge handling are exercised: forward rows, adjoint voxels
-    (edge voxels included) and one fused SPGM step against the oracle."""
+    (edge voxels included) and one fused SPGM step against the oracle.  41 pairs: the adjoint runs a
+    full chunk of 32 and an odd remainder of 9."""
     from tests.gpu_helpers import assert_close_operator
     rng = np.random.default_rng(77)
-    T, R, K = 6, 5, 24
+    T, R, K = 8, 7, 24
     tx = np.concatenate([rng.uniform(-0.15, 0.15, (T, 2)), np.zeros((T, 1))], 1)
     rx = np.concatenate([rng.uniform(-0.15, 0.15, (R, 2)), np.zeros((R, 1))], 1)
     nx, ny, nz, dx, dy, dz = 62, 41, 21, 0.0030, 0.0034, 0.0026
@@ -168,7 +169,7 @@ def test_block_expansion_on_a_ragged_anisotropic_grid():
     n_terms, block = ctx.expansion_info()
     print(f"[cheb] ragged anisotropic grid: L = {n_terms}, {block}-voxel blocks")
     assert block == 256
-    pairs = rng.permutation(geom.P)[:24]
+    pairs = rng.permutation(geom.P)[:41]
     s = (I.complex_gaussian(geom.N, 78)).astype(np.complex64).astype(np.complex128)
     r = (I.complex_gaussian(pairs.size * K, 79)).astype(np.complex64).astype(np.complex128)
     rows = o.rows_of_pairs(pairs)
