@@ -181,8 +181,14 @@ def test_block_expansion_on_a_ragged_anisotropic_grid():
     g = to_host(ctx.adjoint(to_dev(pairs, "int32"), to_dev(r)))
     scale_y = np.sqrt((np.abs(o.dense(rows[ridx], np.arange(geom.N))) ** 2) @ (np.abs(s) ** 2))
     scale_g = np.sqrt((np.abs(o.dense(rows, cols).T) ** 2) @ (np.abs(r) ** 2))
-    assert_close_operator(y[ridx], o.forward(s, rows=rows[ridx]), "forward", scale_y)
+    want_y = o.forward(s, rows=rows[ridx])
+    assert_close_operator(y[ridx], want_y, "forward", scale_y)
     assert_close_operator(g[cols], o.adjoint(r, rows=rows, cols=cols), "adjoint", scale_g)
+    for shape in ({"threads": 128, "lanes_per_group": 8, "pairs_per_cta": 4, "chunks": 64},   # one column per lane
+                  {"threads": 64, "lanes_per_group": 4, "pairs_per_cta": 4, "chunks": 200}):  # 4 blocks per stage
+        ctx.set_forward_shape(pairs.size, dict(shape, algorithm="chebyshev"))
+        y = to_host(ctx.forward(to_dev(pairs, "int32"), to_dev(s)))
+        assert_close_operator(y[ridx], want_y, f"forward {shape}", scale_y)
     y_obs = (I.complex_gaussian(geom.P * K, 80) * 1e-3).astype(np.complex64).astype(np.complex128)
     s0 = (I.complex_gaussian(geom.N, 81) * 0.05).astype(np.complex64).astype(np.complex128)
     eta, lam = 0.05, 0.4                      # the prox zeroes about 15% of the voxels
