@@ -48,17 +48,24 @@ __device__ __forceinline__ ChebVoxel cheb_voxel(const PairTile& pt, const VoxelO
     return cheb_voxel_d(pt, dT, rsT, dR, rsR, fc_hi, fc_lo);
 }
 
+// The base phase advanced by k_c steps, B + k_c S (k_c = (K - 1)/2, the band centre), so that the tile
+// phasors can run from the band centre: P_k = e^{-j 2 pi k_c S} e^{-j 2 pi (k - k_c) S}, the first factor
+// carried by every voxel's base phase, the second conjugate between k and its mirror K-1-k.
+__device__ __forceinline__ void centre_base_phase(PairTile& p, int K)
+{
+    const float kc = 0.5f * (float)(K - 1);
+    const float q = __fmul_rn(kc, p.S_hi);      // rounded product: its error e is added back below
+    const float e = fmaf(kc, p.S_hi, -q);
+    p.B = frac_turns((p.B + (q - rintf(q))) + fmaf(kc, p.S_lo, e));
+}
+
 // The pair tile as the adjoint uses it: antenna vectors scaled by -2 (exact), for cheb_voxel_m2 below, and
-// the base phase advanced by k_c steps, B + k_c S (k_c = (K - 1)/2, the band centre), so that the
-// residual phasors can run from the band centre: conj(P_k) = e^{+j 2 pi k_c S} e^{+j 2 pi (k - k_c) S}.
+// the base phase centred on the band.
 __device__ __forceinline__ PairTile pair_tile_adj(PairTile p, int K)
 {
     p.vTx *= -2.f; p.vTy *= -2.f; p.vTz *= -2.f;
     p.vRx *= -2.f; p.vRy *= -2.f; p.vRz *= -2.f;
-    const float kc = 0.5f * (float)(K - 1);
-    const float q = kc * p.S_hi;
-    const float e = fmaf(kc, p.S_hi, -q);
-    p.B = frac_turns((p.B + (q - rintf(q))) + fmaf(kc, p.S_lo, e));
+    centre_base_phase(p, K);
     return p;
 }
 
@@ -75,7 +82,7 @@ __device__ __forceinline__ ChebVoxel cheb_voxel_m2(const PairTile& pm, const Vox
 // (kf: an integer or half-integer step count)
 __device__ __forceinline__ float2 tile_step_cis_f(const PairTile& pt, float kf)
 {
-    const float p = kf * pt.S_hi;
+    const float p = __fmul_rn(kf, pt.S_hi);     // rounded product: its error e is added back below
     const float e = fmaf(kf, pt.S_hi, -p);
     const float ph = (p - rintf(p)) + fmaf(kf, pt.S_lo, e);
     return cis_turns_sfu(ph);
@@ -87,7 +94,7 @@ __device__ __forceinline__ float2 tile_step_cis(const PairTile& pt, int k) { ret
 __device__ __forceinline__ float2 tile_step_cis_exact(const PairTile& pt, int k)
 {
     const float kf = (float)k;
-    const float p = kf * pt.S_hi;
+    const float p = __fmul_rn(kf, pt.S_hi);     // rounded product: its error e is added back below
     const float e = fmaf(kf, pt.S_hi, -p);
     const float ph = (p - rintf(p)) + fmaf(kf, pt.S_lo, e);
     return cis_turns(ph);

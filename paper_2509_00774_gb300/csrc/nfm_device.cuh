@@ -257,7 +257,7 @@ __device__ __forceinline__ PVGeom pair_voxel(const PairTile& pt, const VoxelOffs
     PVGeom gv;
     gv.amp = INV_4PI * rsT * rsR;
     // f0 (D_c + delta)/c: exact product split so only one rounding at |x| <= 1
-    float p = ph.f0c_hi * delta;
+    float p = __fmul_rn(ph.f0c_hi, delta);      // rounded product: its error pe is added back below
     float pe = fmaf(ph.f0c_hi, delta, -p);
     float th = (pt.B + (p - rintf(p))) + fmaf(ph.f0c_lo, delta, pe);
     gv.th0 = frac_turns(th);

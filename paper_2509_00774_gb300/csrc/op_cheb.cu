@@ -174,7 +174,10 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
         const int tile = t_begin + q * TS + slot;
         const bool live = tile < t_end && pair_s[pl] >= 0;   // uniform over the group's lanes
         PairTile P;
-        if (live) P = fold_pair_head(ant_st[g * 2], ant_st[g * 2 + 1]);
+        if (live) {
+            P = fold_pair_head(ant_st[g * 2], ant_st[g * 2 + 1]);
+            centre_base_phase(P, K);
+        }
         if (q + 1 < n_stages) {
             __syncthreads();                 // every group holds its heads: the buffer takes the next stage's
             load_geom(q + 1);
@@ -255,14 +258,15 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
             // expansion over half the band: the band-centred table is mirror-symmetric,
             // b_l(K-1-k) = (-1)^l b_l(k), so with E = sum over even l and O = sum over odd l of
             // (-j)^l b_l(k) m_l, S_k = E + O and S_{K-1-k} = E - O.  Lane ln owns k = ln + G j < K/2 and the
-            // mirrors; (-j)^l is applied by permuting re/im.  The tile phasors P_k = e^{-j 2 pi k df D_c/c}
-            // of k and K-1-k advance by W = P_G and its conjugate (Taylor phasor, error ~1e-7, at most K/(2G)
-            // steps) from directly evaluated starts; for odd K one lane adds the centre row.
+            // mirrors; (-j)^l is applied by permuting re/im.  The tile phasors run from the band centre (the
+            // base phase carries e^{-j 2 pi k_c S}, S = df D_c/c): k takes conj(c), c = e^{+j 2 pi (k - k_c) S},
+            // and its mirror K-1-k takes c, one phasor per k-pair advanced by W = e^{+j 2 pi G S} (Taylor
+            // phasor, error ~1e-7, at most K/(2G) steps) from a directly evaluated start; for odd K one lane
+            // adds the centre row (phasor 1).
             float2* accg = acc + g * AS;
             const int KH = K / 2;
-            float2 cu = tile_step_cis(P, ln), cdn = tile_step_cis(P, K - 1 - ln);
+            float2 cu = tile_step_cis_f(P, (float)ln - 0.5f * (float)(K - 1));
             const float2 W = tile_step_cis_exact(P, G);
-            const float2 Wc = make_float2(W.x, -W.y);
             auto accumulate = [&](int k, float2 c, float sr, float si) {   // y_k += P_k S_k, P_k = (c.x, -c.y)
                 float2 av = accg[k];
                 av.x = fmaf(c.x, sr, fmaf(c.y, si, av.x));
@@ -287,9 +291,8 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
                     }
                 }
                 accumulate(k, cu, er + orr, ei + oi);
-                accumulate(K - 1 - k, cdn, er - orr, ei - oi);
+                accumulate(K - 1 - k, make_float2(cu.x, -cu.y), er - orr, ei - oi);
                 cu = cmul(cu, W);
-                cdn = cmul(cdn, Wc);
             }
             if ((K & 1) && ln == KH % G) {               // centre row k_c = K/2 (its own mirror)
                 const float* b0 = coef + KH * LSS;
@@ -308,7 +311,7 @@ __device__ __forceinline__ void fwd_cheb_body(const OpDesc op, const ChebDesc cd
                         si = fmaf(x.w, mr[l + 3], si);
                     }
                 }
-                accumulate(KH, tile_step_cis(P, KH), sr, si);
+                accumulate(KH, make_float2(1.f, 0.f), sr, si);
             }
         }
         cp_async_wait_all();

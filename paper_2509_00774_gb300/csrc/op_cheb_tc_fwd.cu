@@ -89,7 +89,7 @@ struct FtcSmem {   // byte offsets of the dynamic shared-memory regions
 __device__ __forceinline__ float2 slot_cis(float S_hi, float S_lo, int k)
 {
     const float kf = (float)k;
-    const float p = kf * S_hi;
+    const float p = __fmul_rn(kf, S_hi);        // rounded product: its error e is added back below
     const float e = fmaf(kf, S_hi, -p);
     const float ph = (p - rintf(p)) + fmaf(kf, S_lo, e);
     return cis_turns_sfu(ph);

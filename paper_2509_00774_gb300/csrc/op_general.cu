@@ -49,7 +49,7 @@ cudaError_t launch_antk_setup(const GridDesc& g, const AntSetup& a, const double
 // theta = frac(Bk + fkc * delta) with fkc = f_k/c as hi + lo
 __device__ __forceinline__ float gen_phase(float Bk, float2 fkc, float delta)
 {
-    const float p = fkc.x * delta;
+    const float p = __fmul_rn(fkc.x, delta);    // rounded product: its error pe is added back below
     const float pe = fmaf(fkc.x, delta, -p);
     return frac_turns((Bk + (p - rintf(p))) + fmaf(fkc.y, delta, pe));
 }

@@ -355,7 +355,8 @@ def test_group_regulariser_needs_the_expansion_operator():
 
 def test_bounds_checked_build_matches_and_reports():
     """The bounds-checked build (-DNFM_BOUNDS_CHECK) gives the normal build's results on the default
-    operator path, and when the test hook halves the extents its kernels receive, a checked access past the
+    operator path (to FP32 rounding: the extra checks change where the compiler contracts a multiply and an
+    add into one FMA, so the two builds need not agree bit for bit), and when the test hook halves the extents its kernels receive, a checked access past the
     declared extent (still inside the real buffer) raises the device flag and the next synchronise reports
     NFM_ERR_STATE; the context stays usable."""
     from paper_2509_00774_gb300 import build as nb
@@ -376,7 +377,9 @@ def test_bounds_checked_build_matches_and_reports():
             ctx.spgm_step(y_d, s, pairs, 0.003, 1e-3)
         ctx.synchronize()
         outs.append(to_host(s))
-    assert np.array_equal(outs[0], outs[1])
+    rel = np.linalg.norm(outs[1] - outs[0]) / np.linalg.norm(outs[0])
+    print(f"[check build] 3 SPGM steps vs the normal build: rel_l2 {rel:.2e}")
+    assert rel <= 1e-6
     chk.set_test_hooks(chk.HOOK_SHRINK_EXTENTS)
     s = to_dev(s0)
     chk.spgm_step(y_d, s, pairs, 0.003, 1e-3)
